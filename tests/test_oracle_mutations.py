@@ -1,0 +1,102 @@
+"""Planted mistakes: each plausible slip in the oracle must fail at least one pin.
+
+Every case edits a private copy of the oracle's C source (on the CPU), builds
+it, and runs a compact battery of the independent pins against it.  The
+committed oracle itself passes the same battery.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_13382_gb300 import inputs as I
+
+C = 343.0
+
+MUTATIONS = {
+    "phase_sign": ("cexp(I * k * s + I * k * n2 / (2.0 * E))",
+                   "cexp(-I * k * s + I * k * n2 / (2.0 * E))"),
+    "dropped_1_over_E": ("(8.0 * ORC_PI * ORC_PI)) / E * cexp", "(8.0 * ORC_PI * ORC_PI)) * cexp"),
+    "normalisation": ("(k * b / (8.0 * ORC_PI * ORC_PI))", "(k * b / (4.0 * ORC_PI * ORC_PI))"),
+    "E_sign": ("double complex E = s - I * b;\n    return", "double complex E = s + I * b;\n    return"),
+    "cross_transposed": ("double cx = dy * t[2] - dz * t[1];", "double cx = dy * t[1] - dz * t[2];"),
+    "reflection_factor": ("d[2] = d[2] - 2.0 * dn * nrm[2];", "d[2] = d[2] - dn * nrm[2];"),
+    "gamma_path_sum": ("for (int64_t q = first + 1; q <= j; ++q) g *= gamma[S->bmat[q]];",
+                       "for (int64_t q = first + 1; q <= j; ++q) g += gamma[S->bmat[q]];"),
+    "line_window_local": ("if (!(s >= 0.0)) return 0;", "if (!(s_loc >= 0.0)) return 0;"),
+    "adjoint_b_sign": ("1.0 / b + I / E - k * n2", "1.0 / b - I / E - k * n2"),
+    "fan_offset": ("double z = 1.0 - (2.0 * (double)i + 1.0) / (double)n;",
+                   "double z = 1.0 - (2.0 * (double)i) / (double)n;"),
+    "gaussian_exponent_half": ("I * k * n2 / (2.0 * E)", "I * k * n2 / E"),
+}
+
+
+def _battery():
+    """Independent checks (closed forms, images, FD); True iff all pass."""
+    ok = True
+    # fan: equal-area z bands
+    d = O.fan_fibonacci(1024)
+    ok &= bool(np.allclose(d[:, 2], 1.0 - (2.0 * np.arange(1024) + 1.0) / 1024, atol=1e-15))
+    # free field, point source with the paraxial law p/p_exact - 1 = i r / (k b^2)
+    sc = I.Scene(C, False, 0.0, 0, np.zeros((0, 3, 3)), np.zeros(0, np.int32),
+                 np.zeros(0, np.int32), np.array([1.0], np.float32))
+    tr = O.trace(sc, I.Source(np.zeros(3), 16384, 0, 1e4))
+    recv = np.array([[60.0, 20.0, -30.0], [-80.0, 5.0, 40.0]], np.float32)
+    f, b = 500.0, 100.0
+    k = 2 * math.pi * f / C
+    rr = np.linalg.norm(recv.astype(float), axis=1)
+    p = O.gbs_sum(tr, recv, [f], [b], C, [1.0], window=1)[0]
+    ex = np.exp(1j * k * rr) / (4 * math.pi * rr)
+    ok &= bool(np.all(np.abs(p / ex - 1 - 1j * rr / (k * b * b)) < 1e-4))
+    # ground plane with gamma = 0.6: direct + 0.6 x image
+    sg = I.Scene(C, True, 0.0, 0, np.zeros((0, 3, 3)), np.zeros(0, np.int32),
+                 np.zeros(0, np.int32), np.array([0.6], np.float32))
+    tg = O.trace(sg, I.Source(np.array([0.0, 0.0, 5.0]), 65536, 1, 1e4))
+    recv = np.array([[30.0, 7.0, 10.0], [-60.0, 7.0, 40.0], [15.0, -7.0, 25.0],
+                     [40.0, 7.0, 0.5], [-25.0, 3.0, 1.0]], np.float32)
+    f = 2000.0
+    k = 2 * math.pi * f / C
+    x = recv.astype(float)
+    r1 = np.linalg.norm(x - [0, 0, 5], axis=1); r2 = np.linalg.norm(x - [0, 0, -5], axis=1)
+    exg = (np.exp(1j * k * r1) / (4 * math.pi * r1) * (1 + 1j * r1 / (k * b * b)) +
+           0.6 * np.exp(1j * k * r2) / (4 * math.pi * r2) * (1 + 1j * r2 / (k * b * b)))
+    pg = O.gbs_sum(tg, recv, [f], [b], C, sg.gamma, window=1)[0]
+    ok &= bool(np.all(np.abs(pg - exg) < 5e-4 * np.abs(exg).max()))
+    # off-axis single beam against Eq. 1 in matrix form
+    from tests.test_oracle_pins import _eq1_matrix_form, _one_segment_trace
+    t = np.array([0.3, -0.5, 0.81]); t /= np.linalg.norm(t)
+    o = np.array([1.0, 2.0, 3.0])
+    tr1 = _one_segment_trace(o, t, L=1e6, s0=12.0)
+    xs = (o + 80 * t + np.array([3.0, 1.0, 0.5]) - (np.array([3.0, 1.0, 0.5]) @ t) * t)
+    xs = xs.astype(np.float32)
+    p1 = O.gbs_sum(tr1, xs[None], [700.0], [30.0], C, [1.0], weight=[0.5], window=1,
+                   cutoff=1e9)[0, 0]
+    ref = _eq1_matrix_form(xs.astype(float), o, t, 12.0, 2 * math.pi * 700 / C, 30.0, 0.5, 1.0)
+    ok &= bool(abs(p1 - ref) < 1e-9 * abs(ref))
+    # adjoint in b against central differences (mask frozen)
+    recv = np.array([[30.0, 7.0, 10.0], [-20.0, 3.0, 12.0]], np.float32)
+    g = np.array([[1.0 + 0.5j, -0.3 + 1j]])
+    bb = np.array([40.0])
+    _, _, db = O.gbs_adjoint(tg, recv, [800.0], bb, C, [0.6], g, window=1)
+    h = 1e-4
+    lp = np.real(np.conj(g) * O.gbs_sum(tg, recv, [800.0], bb + h, C, [0.6], window=1,
+                                        b_mask=bb)).sum()
+    lm = np.real(np.conj(g) * O.gbs_sum(tg, recv, [800.0], bb - h, C, [0.6], window=1,
+                                        b_mask=bb)).sum()
+    ok &= bool(math.isclose(db[0], (lp - lm) / (2 * h), rel_tol=1e-5))
+    return ok
+
+
+def test_unmutated_oracle_passes_battery():
+    assert _battery()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = O.source_text()
+    assert src.count(old) >= 1, f"mutation anchor not found: {name}"
+    lib = O.compile_source(src.replace(old, new), str(tmp_path / f"liboracle_{name}.so"))
+    with O.use_library(lib):
+        assert not _battery(), f"planted mistake {name} went undetected"
