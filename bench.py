@@ -1,0 +1,339 @@
+"""Benchmark: Gaussian beam summation throughput on one GB300 (or N, as replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the large open-plane case (point source 2 m above a ground plane
+with reflection coefficient 0.9, 65,536 Fibonacci rays, <= 3 reflections,
+1 km paths; 256 x 256 receivers at 1.5 m over [-500, 500]^2 m; six octave
+bands 125-4000 Hz), synthetic and seeded.  One step is the whole path: fan +
+FP64 trace + scan + compaction + segment prepass + beam summation + merge,
+through the library's gbt_solve.  Metric: (receiver, segment, frequency)
+evaluations per second.  L2 is flushed (256 MiB write) between timed steps
+and excluded from the per-step CUDA-event times.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own
+replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GBS segment x receiver evals/s at <=1e-4 rel L2; batched & fwd+bwd vs plain"
+UNIT = "evals/s"
+# Algorithmic lane-operations (FP32 / integer / MUFU issue slots) the method needs:
+# per (receiver, segment) pair: x - o (3), s_loc (3), s (1), n^2 = |x-o|^2 - s_loc^2 (4),
+# cutoff test (3), window test (1) = 15; per kept (pair, frequency): 1/E (3),
+# Gaussian amplitude (2 + EX2), phase k s + k n^2 s / 2D with range reduction (6 + SIN + COS),
+# complex product and scale (6), accumulation (2) = 22 + 3 MUFU -> 24 counted.
+OPS_PER_PAIR = 15
+OPS_PER_KEPT = 24
+LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
+KERNEL_TAG = "gbs_fwd_kernel<8,LINE> r1"
+# DRAM bytes per launch of the dominant kernel from an ncu capture of this exact kernel
+# version (None until captured for it).
+KERNEL_TRAFFIC = {}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload():
+    from paper_2501_13382_gb300 import inputs as I
+    return I.open_plane_large()
+
+
+def _oracle_sample(w, budget_s: float, seed: int = 17):
+    """Time the FP64 oracle (trace + sum) on a seeded receiver sample sized to ~budget_s."""
+    from oracle import oracle as O
+    from paper_2501_13382_gb300 import inputs as I
+    src = w.sources[0]
+    t0 = time.perf_counter()
+    tr = O.trace(w.scene, src)
+    t_trace = time.perf_counter() - t0
+    n = 16
+    while True:
+        idx = I.receiver_subset(w.receivers, n, seed)
+        t0 = time.perf_counter()
+        p = O.gbs_sum(tr, w.receivers[idx], w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma,
+                      window=w.window, cutoff=w.cutoff)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s * 0.3 or n >= w.receivers.shape[0]:
+            break
+        n = min(w.receivers.shape[0], int(n * max(2.0, budget_s * 0.5 / max(dt, 1e-3))))
+    evals = float(len(idx)) * tr.n_seg * len(w.freqs)
+    return {"idx": idx, "p": p, "evals": evals, "t_sum": dt, "t_trace": t_trace,
+            "n_seg": tr.n_seg}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the same workload and metric."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2501_13382_gb300 import inputs as I
+    w = _workload()
+    n_sample = 48
+    idx = I.receiver_subset(w.receivers, n_sample, 23)
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        tr = O.trace(w.scene, w.sources[0])
+        O.gbs_sum(tr, w.receivers[idx], w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma,
+                  window=w.window, cutoff=w.cutoff)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    evals = float(n_sample) * tr.n_seg * len(w.freqs)
+    sec = float(np.sum(times))
+    value = evals * len(times) / sec
+    cores = O.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "rays": w.sources[0].n_rays, "segments": tr.n_seg,
+                       "receivers_per_step": n_sample, "freqs": len(w.freqs),
+                       "parallelism": "cpu-openmp"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_sample} seeded receivers of {w.receivers.shape[0]} "
+                                       f"per step, full fan trace each step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle work for the CPU baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2501_13382_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2501_13382_gb300 import gbt as G
+
+    w = _workload()
+    src = w.sources[0]
+    stream = torch.cuda.current_stream()
+    sc = G.Scene(w.scene)
+    recv = torch.as_tensor(w.receivers, device="cuda")
+    gam = torch.as_tensor(w.scene.gamma, device="cuda")
+    freqs = list(w.freqs)
+    bb = list(w.beam_b[0])
+    order = G.recv_order(recv)
+    out = torch.empty((len(freqs), recv.shape[0]), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # work statistics (outside the timed region)
+    tr = G.Trace(sc, src)
+    st = G.sum_stats(tr, recv, freqs, bb, gam, order=order, window=w.window, cutoff=w.cutoff)
+    n_seg = st["n_segments"]
+    tr.close()
+    evals = float(recv.shape[0]) * n_seg * len(freqs)
+
+    def step():
+        G.gbs_solve(sc, src, recv, freqs, bb, gam, order=order, window=w.window,
+                    cutoff=w.cutoff, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    G.gbt_timing_enable(True)
+    G.gbt_timing_read(reset=True)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    G.gbt_timing_enable(False)
+    n_k, k_ms = G.gbt_timing_read(reset=True)
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    # e2e: host receivers in, host field out, through the public API each step
+    host_recv = torch.as_tensor(w.receivers).pin_memory()
+    host_out = torch.empty(out.shape, dtype=torch.complex64).pin_memory()
+    recv_e = torch.empty_like(recv)
+
+    def step_e2e():
+        recv_e.copy_(host_recv, non_blocking=True)
+        o = G.recv_order(recv_e)
+        G.gbs_solve(sc, src, recv_e, freqs, bb, gam, order=o, window=w.window,
+                    cutoff=w.cutoff, out=out)
+        host_out.copy_(out, non_blocking=True)
+
+    e2e_ms = float("nan")
+    if not args.no_e2e:
+        for _ in range(2):
+            step_e2e()
+        torch.cuda.synchronize()
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            step_e2e()
+            e2e_ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = float(sum(a.elapsed_time(b) for a, b in e2e_ev))
+    clk.stop()
+    G.gbt_sync()
+
+    if dist:
+        t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    ms_per_step = ms / args.steps
+    value = world * evals / (ms_per_step * 1e-3)
+    e2e_value = world * evals / (e2e_ms / args.steps * 1e-3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    clocks = clk.summary()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    kern_ms = k_ms / max(n_k, 1)
+    ops = OPS_PER_PAIR * float(st["pairs"]) + OPS_PER_KEPT * float(st["triples_kept"])
+    achieved = ops / (kern_ms * 1e-3) / 1e12
+    mhz = clocks["sm_mhz"] or 1492.0
+    peak = n_sm * LANES_PER_SM_CLK * mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
+                "frac": achieved / peak, "traffic": KERNEL_TRAFFIC.get(KERNEL_TAG),
+                "kernel": KERNEL_TAG, "kernel_ms": kern_ms, "kernel_launches": n_k,
+                "ops_per_launch": ops,
+                "peak_basis": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x median SM clock "
+                              f"{mhz:.0f} MHz under load"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "rays": src.n_rays, "segments": n_seg,
+                       "receivers": int(recv.shape[0]), "freqs": len(freqs),
+                       "pairs": st["pairs"], "pairs_prefiltered": st["pairs_prefiltered"],
+                       "triples_kept": st["triples_kept"], "l2": "flushed between steps (256 MiB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(recv.numel() * 4),
+                    "d2h_bytes_per_step": int(out.numel() * 8)},
+            "gpu_launches": 8 * args.steps,
+            "clocks": clocks}
+
+    if world == 1 and not args.no_cpu:
+        # CPU baseline + accuracy check of this run's field on the oracle's sample
+        samp = _oracle_sample(w, args.cpu_budget)
+        from oracle import oracle as O
+        pg = out.cpu().numpy().astype(np.complex128)[:, samp["idx"]]
+        err = float(np.linalg.norm(pg - samp["p"]) / np.linalg.norm(samp["p"]))
+        cpu_value = samp["evals"] / (samp["t_sum"] + samp["t_trace"])
+        line["cpu_baseline"] = {"value": cpu_value, "unit": UNIT, "cores": O.num_threads(),
+                                "kind": "oracle",
+                                "sample": f"{len(samp['idx'])} seeded receivers x {samp['n_seg']} "
+                                          f"segments x {len(freqs)} freqs, FP64 trace + sum"}
+        line["accuracy"] = {"rel_l2_vs_oracle": err, "receivers_checked": len(samp["idx"])}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,273 @@
+/*
+ * gbt.h -- C ABI of libgbt, GB300-native Gaussian beam summation.
+ *
+ * The library computes, on one GPU, the two processes of Gaussian beam
+ * tracing named in Sec. 3.1 of arXiv 2501.13382: ray tracing (RT) of a fan
+ * of rays with specular reflections off planar facets, and Gaussian beam
+ * summation (GBS), the sum of every beam's contribution (Eq. 1, with the
+ * beam parameters of Eq. 2) at every observation point (Eq. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers marked "device" must point to memory of the current CUDA device;
+ *    pointers marked "host" to ordinary host memory.  The caller owns every
+ *    buffer it passes; the library owns only its opaque handles and the
+ *    device memory inside them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call is stream-ordered and returns without waiting for the GPU,
+ *    except where a call says it synchronises.
+ *  - Every call returns a gbt_status.  Invalid arguments are rejected before
+ *    any work is queued (GBT_ERR_INVALID_ARG) and nothing is written.  A
+ *    failed CUDA call returns GBT_ERR_CUDA.  Problems a kernel detects (an
+ *    index out of range, a bounded wait that ran out) set a device status
+ *    word that gbt_sync reports.  gbt_last_error() describes the most recent
+ *    failure on the calling thread.  No C++ exception crosses this ABI.
+ *  - Complex numbers are interleaved float pairs (re, im) ("complex64").
+ *  - Time convention exp(-i omega t): a beam's phase grows as exp(+i k s).
+ */
+#ifndef GBT_H
+#define GBT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBT_VERSION 1
+#define GBT_MAX_FREQ 16          /* frequencies per sum call */
+
+typedef enum gbt_status {
+    GBT_OK = 0,
+    GBT_ERR_INVALID_ARG = 1,     /* rejected before any launch */
+    GBT_ERR_OOM = 2,             /* device allocation failed */
+    GBT_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+    GBT_ERR_TIMEOUT = 4,         /* a bounded device wait ran out (via gbt_sync) */
+    GBT_ERR_DEVICE_STATUS = 5,   /* a kernel flagged an internal error (via gbt_sync) */
+    GBT_ERR_UNSUPPORTED = 6      /* valid request this build does not handle */
+} gbt_status;
+
+enum { GBT_WINDOW_SEGMENT = 0,   /* a beam acts on 0 <= s_loc < L of its segment */
+       GBT_WINDOW_LINE = 1 };    /* a beam acts on its whole unfolded ray, s >= 0 */
+enum { GBT_PRECISION_F32 = 0,    /* FP32 arithmetic, float-float phase, compensated sums */
+       GBT_PRECISION_F64 = 1 };  /* FP64 everywhere (comparison path; slow on GB300) */
+enum { GBT_FAN_FIBONACCI = 0,    /* directions generated on the device */
+       GBT_FAN_EXPLICIT = 1 };   /* directions supplied by the caller */
+
+typedef struct gbt_scene_s gbt_scene_t;   /* opaque handles */
+typedef struct gbt_trace_s gbt_trace_t;
+typedef struct gbt_batch_s gbt_batch_t;
+
+/* ------------------------------------------------------------ allocator --
+ * Optional allocator for the library's own device memory (handles and
+ * scratch).  Without one the library uses cudaMallocAsync / cudaFreeAsync on
+ * the call's stream.  `alloc` returns NULL on failure (-> GBT_ERR_OOM).  The
+ * setting is process-wide and applies to allocations made after the call.
+ * Passing NULL restores the default. */
+typedef struct gbt_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+} gbt_allocator;
+
+gbt_status gbt_set_allocator(const gbt_allocator *allocator);
+
+/* --------------------------------------------------------------- scene --
+ * Reflecting geometry for the RT process (Sec. 3.1: rays interact with
+ * triangular facets; Sec. 4.1: an infinite rigid plate).  The optional ground
+ * is the plane z = ground_z with normal +z (primitive id 0); triangles are
+ * primitives 1..n_tri in the order given.  Triangles that share a facet id are
+ * one planar facet: a ray leaving a facet cannot hit it again.  A reflection
+ * off primitive p multiplies the beam by gamma[material(p)] (supplied at sum
+ * time).  Host arrays are copied; the caller may free them on return.
+ * Synchronises `stream` once (upload). */
+typedef struct gbt_scene_desc {
+    double c;                     /* speed of sound, m/s (> 0) */
+    int32_t ground_enabled;       /* 0 / 1 */
+    int32_t ground_material;      /* material index of the ground */
+    double ground_z;              /* ground height, m */
+    int64_t n_tri;                /* >= 0 */
+    const double *tri_xyz;        /* host, n_tri * 9: v0, v1, v2 (x, y, z each) */
+    const int32_t *tri_material;  /* host, n_tri, each in [0, n_materials) */
+    const int32_t *tri_face;      /* host, n_tri facet ids >= 0, or NULL (own facet each) */
+    int32_t n_materials;          /* >= 1 */
+} gbt_scene_desc;
+
+gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_t **out);
+gbt_status gbt_scene_destroy(gbt_scene_t *scene);
+
+/* --------------------------------------------------------------- trace --
+ * RT process (Sec. 2, Sec. 3.1; Sec. 3.3 for the fan of take-off directions).
+ * Traces rays [ray_begin, ray_begin + ray_count) of a fan of n_rays rays from
+ * `pos` in a homogeneous medium: nearest hit with t > 1e-9 m (ties: lowest
+ * primitive id), specular reflection d' = d - 2 (d.n) n, until the path
+ * length reaches max_path (the last segment is cut there) or the first hit
+ * after max_reflections reflections.  The Fibonacci fan is
+ * z_i = 1 - (2i+1)/N, phi_i = i pi (3 - sqrt 5); every ray carries the
+ * solid-angle weight 4 pi / N unless the sum supplies per-ray weights.
+ * FP64 throughout, without fused multiply-add, in a fixed operation order.
+ *
+ * The result is a CSR list of straight segments in ray order (ray_off over
+ * the traced rays); per segment: origin, unit direction, length L, arclength
+ * s0 at its start, global ray index, depth in its ray, the material of the
+ * reflection that starts it (-1 for the first) and the primitive that ends it
+ * (-1 if none).  Asynchronous: the segment count stays on the device until
+ * gbt_trace_info is called.  `scene` must outlive the trace. */
+typedef struct gbt_source_desc {
+    double pos[3];                /* source position, m */
+    int64_t n_rays;               /* fan size N (>= 1) */
+    int64_t ray_begin;            /* first ray traced (chunking), 0 normally */
+    int64_t ray_count;            /* rays traced; 0 = n_rays - ray_begin */
+    int32_t fan;                  /* GBT_FAN_FIBONACCI or GBT_FAN_EXPLICIT */
+    int32_t max_reflections;      /* >= 0 */
+    const double *dirs;           /* device, ray_count * 3 unit vectors (EXPLICIT only) */
+    double max_path;              /* m (> 0) */
+} gbt_source_desc;
+
+gbt_status gbt_trace(const gbt_scene_t *scene, const gbt_source_desc *src, void *stream,
+                     gbt_trace_t **out);
+
+typedef struct gbt_trace_info {
+    int64_t n_fan;                /* fan size N */
+    int64_t ray_begin, n_rays;    /* traced ray range */
+    int64_t seg_capacity;         /* n_rays * (max_reflections + 1) */
+    int64_t n_segments;           /* exact count (this call synchronises the trace's stream) */
+    /* read-only device views, valid until gbt_trace_destroy */
+    const int32_t *ray_off;       /* n_rays + 1 */
+    const double *seg_o;          /* n_segments * 3 */
+    const double *seg_t;          /* n_segments * 3 */
+    const double *seg_L;          /* n_segments */
+    const double *seg_s0;         /* n_segments */
+    const int32_t *seg_ray;       /* n_segments, global ray index */
+    const int32_t *seg_depth;     /* n_segments */
+    const int32_t *seg_bmat;      /* n_segments */
+    const int32_t *seg_hit;       /* n_segments */
+} gbt_trace_info;
+
+gbt_status gbt_trace_info_get(const gbt_trace_t *trace, gbt_trace_info *info);
+gbt_status gbt_trace_destroy(gbt_trace_t *trace);
+
+/* ----------------------------------------------------------------- sum --
+ * GBS process (Eq. 3): for every receiver x, frequency f and segment j with
+ *   s_loc = (x - o_j).t_j,  s = s0_j + s_loc,  n^2 = |(x - o_j) x t_j|^2,
+ *   E = s - i b_f,  k = 2 pi f / c,
+ * the beam of Eq. 1 (P = I/c and Q(s) = Q0 + c P s from Eq. 2, isotropic,
+ * Q0 = -i b_f I) contributes
+ *   W_ray * Gamma_path_j * (k b_f / (8 pi^2)) * exp(i k s + i k n^2 / (2E)) / E
+ * when k n^2 b_f / (2 (s^2 + b_f^2)) <= cutoff and the pair lies in the
+ * window (SEGMENT: 0 <= s_loc < L_j; LINE: s >= 0).  Gamma_path_j is the
+ * product of gamma over the reflections before segment j.  The constant
+ * k b / (8 pi^2) makes a dense fan sum to the point source exp(ikr)/(4 pi r).
+ *
+ * F32 precision: FP32 arithmetic with float-float arclength and phase
+ * reduction, FP32 MUFU exp/sin/cos, compensated per-receiver accumulation;
+ * relative L2 error against an FP64 evaluation is about 1e-6..1e-5.
+ * `out` (n_freq * n_recv complex64, frequency-major) is overwritten, or added
+ * to when `accumulate` is 1.  Scratch comes from the trace's workspace, so
+ * calls on one trace must not overlap on different streams. */
+typedef struct gbt_sum_args {
+    const float *recv;            /* device, n_recv * 3 (x, y, z), m */
+    int64_t n_recv;               /* >= 0 */
+    const int32_t *recv_order;    /* device permutation of [0, n_recv) or NULL; receivers
+                                     are processed in this order (see gbt_recv_order) */
+    int32_t n_freq;               /* 1 .. GBT_MAX_FREQ */
+    int32_t window;               /* GBT_WINDOW_SEGMENT / GBT_WINDOW_LINE */
+    double freq_hz[GBT_MAX_FREQ]; /* > 0 */
+    double beam_b[GBT_MAX_FREQ];  /* beam parameter b_f, m (> 0) */
+    const float *gamma;           /* device, n_materials reflection coefficients */
+    const float *ray_weight;      /* device, n_fan per-ray weights, or NULL (4 pi / N) */
+    float *out;                   /* device, n_freq * n_recv * 2 floats */
+    double cutoff;                /* C (> 0); 16 drops less than 1.2e-7 of a beam */
+    int32_t precision;            /* GBT_PRECISION_F32 / GBT_PRECISION_F64 */
+    int32_t accumulate;           /* 0 overwrite, 1 add into out */
+    int32_t seg_split;            /* segment ranges per receiver tile; 0 = automatic */
+    int32_t reserved;
+    int64_t max_device_bytes;     /* gbt_solve only: device budget for one chunk; 0 = auto */
+} gbt_sum_args;
+
+gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *stream);
+
+/* Spatially coherent processing order of receivers (Morton order of their
+ * positions quantised to their bounding box), written to order_out (device,
+ * n_recv int32).  Results do not depend on the order; neighbouring receivers
+ * in one warp see similar beams, which keeps the warp's lanes busy. */
+gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out, void *stream);
+
+/* ------------------------------------------------------------ backward --
+ * Adjoint of gbt_sum for a real loss L.  grad_out (device, n_freq * n_recv
+ * complex64) holds g = dL/dRe p + i dL/dIm p.  Writes (overwrites)
+ *   grad_gamma[m]      = dL/dgamma_m        (device, n_materials floats)
+ *   grad_ray_weight[i] = dL/dW_i            (device, n_fan floats; NULL to skip)
+ *   grad_b[f]          = dL/db_f            (device, n_freq doubles; NULL to skip)
+ * using dL/dtheta = sum Re(conj(g) dp/dtheta).  The cull mask and window are
+ * held fixed (the summand is differentiated where it is kept).  Contributions
+ * are recomputed, never stored per (receiver, segment).  F32 only. */
+gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
+                            const float *grad_out, float *grad_gamma, float *grad_ray_weight,
+                            double *grad_b, void *stream);
+
+/* --------------------------------------------------------------- solve --
+ * RT + GBS for one source with the ray range split into chunks so that one
+ * chunk's trace fits args->max_device_bytes (the paper's chunking when rays
+ * exceed device memory, Sec. 4.5.1).  Chunks are traced and summed in ray
+ * order and accumulated into args->out; the result equals one unchunked
+ * trace + sum up to rounding.  src->ray_begin / ray_count must be 0. */
+gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src,
+                     const gbt_sum_args *args, void *stream);
+
+/* --------------------------------------------------------------- batch --
+ * Many GBS instances (sources x frequency sets, uneven segment counts) in one
+ * persistent launch fed by a device work queue of (instance, receiver tile,
+ * segment range) items, captured in a CUDA graph on the first submit and
+ * replayed afterwards.  Each instance is a trace plus sum arguments; the
+ * result of each instance equals gbt_sum on it up to rounding.  All traces
+ * and buffers must stay alive and unchanged in shape while the batch exists;
+ * their contents may change between submits. */
+typedef struct gbt_batch_desc {
+    int32_t n_instances;
+    const gbt_trace_t *const *traces;   /* host array of n_instances handles */
+    const gbt_sum_args *args;         /* host array of n_instances argument sets */
+    int32_t use_graph;                /* 1: capture on first submit, then replay */
+} gbt_batch_desc;
+
+gbt_status gbt_batch_create(const gbt_batch_desc *desc, void *stream, gbt_batch_t **out);
+gbt_status gbt_batch_submit(gbt_batch_t *batch, void *stream);
+gbt_status gbt_batch_destroy(gbt_batch_t *batch);
+
+/* ---------------------------------------------------------- measurement --
+ * Kernel timing: while enabled, each launch of the GBS pair kernel (forward
+ * or backward) is bracketed by CUDA events recorded on its launch stream.
+ * gbt_timing_read waits for the recorded events and returns the number of
+ * launches and their summed device time since the last reset. */
+gbt_status gbt_timing_enable(int32_t enable);
+gbt_status gbt_timing_read(int64_t *launches, double *total_ms, int32_t reset);
+
+/* Work statistics of one gbt_sum call (same arguments): number of
+ * (receiver, segment) pairs, pairs kept by the frequency-union prefilter, and
+ * (receiver, segment, frequency) triples whose beam contributes (window and
+ * cutoff met).  Runs a counting variant of the F32 kernel; synchronises. */
+typedef struct gbt_sum_stats {
+    int64_t n_segments;
+    int64_t pairs;
+    int64_t pairs_prefiltered;
+    int64_t triples_kept;
+} gbt_sum_stats;
+
+gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,
+                             gbt_sum_stats *stats, void *stream);
+
+/* ---------------------------------------------------------------- misc -- */
+
+/* Waits for `stream`, then reads and clears the device status word: returns
+ * GBT_ERR_TIMEOUT or GBT_ERR_DEVICE_STATUS if a kernel flagged a problem. */
+gbt_status gbt_sync(void *stream);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *gbt_last_error(void);
+
+int32_t gbt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBT_H */

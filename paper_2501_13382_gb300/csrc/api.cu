@@ -1,0 +1,600 @@
+// api.cu -- host implementation of the libgbt C ABI (include/gbt.h).
+// Argument validation, handle ownership, device memory, error reporting.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gbt_internal.h"
+
+namespace gbt {
+
+namespace {
+thread_local std::string t_last_error;
+std::mutex g_mu;
+gbt_allocator g_alloc{};
+bool g_has_alloc = false;
+unsigned int *g_status[64] = {};
+int g_sms[64] = {};
+
+int current_device()
+{
+    int d = 0;
+    GBT_CUDA(cudaGetDevice(&d));
+    if (d < 0 || d >= 64) fail(GBT_ERR_UNSUPPORTED, "device index >= 64");
+    return d;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <class F>
+gbt_status guarded(F &&f)
+{
+    try {
+        f();
+        t_last_error.clear();
+        return GBT_OK;
+    } catch (const Error &e) {
+        t_last_error = e.what();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        t_last_error = "host allocation failed";
+        return GBT_ERR_OOM;
+    } catch (const std::exception &e) {
+        t_last_error = e.what();
+        return GBT_ERR_CUDA;
+    } catch (...) {
+        t_last_error = "unknown error";
+        return GBT_ERR_CUDA;
+    }
+}
+}  // namespace
+
+[[noreturn]] void fail(gbt_status code, const std::string &msg) { throw Error(code, msg); }
+
+void check_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return;
+    const gbt_status code = (e == cudaErrorMemoryAllocation) ? GBT_ERR_OOM : GBT_ERR_CUDA;
+    cudaGetLastError();   // clear a non-sticky error
+    throw Error(code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dalloc(size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) bytes = 256;
+    gbt_allocator a;
+    bool has;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        a = g_alloc;
+        has = g_has_alloc;
+    }
+    void *p = nullptr;
+    if (has) {
+        p = a.alloc(bytes, s, a.ctx);
+        if (!p) fail(GBT_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    } else {
+        static bool pool_set[64] = {};
+        const int dev = current_device();
+        if (!pool_set[dev]) {
+            // keep freed blocks in the stream-ordered pool instead of returning them to
+            // the driver at every synchronisation (process-local setting)
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            cudaGetLastError();
+            pool_set[dev] = true;
+        }
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(GBT_ERR_OOM, "cudaMallocAsync(" + std::to_string(bytes) + "): " +
+                                  cudaGetErrorString(e));
+        }
+    }
+    return p;
+}
+
+void dfree(void *p, cudaStream_t s)
+{
+    if (!p) return;
+    gbt_allocator a;
+    bool has;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        a = g_alloc;
+        has = g_has_alloc;
+    }
+    if (has) a.free(p, s, a.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+unsigned int *status_word()
+{
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status[d]) {
+        void *p = nullptr;
+        GBT_CUDA(cudaMalloc(&p, 256));
+        GBT_CUDA(cudaMemset(p, 0, 256));
+        g_status[d] = static_cast<unsigned int *>(p);
+    }
+    return g_status[d];
+}
+
+namespace {
+struct TimingState {
+    bool enabled = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    std::vector<cudaEvent_t> pool;
+};
+TimingState g_timing;
+std::mutex g_timing_mu;
+
+cudaEvent_t timing_event()
+{
+    if (!g_timing.pool.empty()) {
+        cudaEvent_t e = g_timing.pool.back();
+        g_timing.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    GBT_CUDA(cudaEventCreate(&e));
+    return e;
+}
+}  // namespace
+
+void timing_begin(cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (!g_timing.enabled) return;
+    cudaEvent_t a = timing_event(), b = timing_event();
+    GBT_CUDA(cudaEventRecord(a, s));
+    g_timing.events.emplace_back(a, b);
+}
+
+void timing_end(cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (!g_timing.enabled || g_timing.events.empty()) return;
+    GBT_CUDA(cudaEventRecord(g_timing.events.back().second, s));
+}
+
+int num_sms()
+{
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sms[d]) GBT_CUDA(cudaDeviceGetAttribute(&g_sms[d], cudaDevAttrMultiProcessorCount, d));
+    return g_sms[d];
+}
+
+void *DeviceBuffer::ensure(size_t n, cudaStream_t s)
+{
+    if (n <= bytes && ptr) return ptr;
+    release(s);
+    ptr = dalloc(n, s);
+    bytes = n;
+    return ptr;
+}
+
+void DeviceBuffer::release(cudaStream_t s)
+{
+    if (ptr) dfree(ptr, s);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+// ------------------------------------------------------------------ trace --
+
+static void validate_source(const gbt_source_desc &src)
+{
+    GBT_REQUIRE(src.n_rays >= 1, "n_rays must be >= 1");
+    GBT_REQUIRE(src.ray_begin >= 0 && src.ray_begin < src.n_rays, "ray_begin out of range");
+    const int64_t cnt = src.ray_count == 0 ? src.n_rays - src.ray_begin : src.ray_count;
+    GBT_REQUIRE(cnt >= 1 && src.ray_begin + cnt <= src.n_rays, "ray_count out of range");
+    GBT_REQUIRE(src.max_reflections >= 0 && src.max_reflections <= 64,
+                "max_reflections must be in [0, 64]");
+    GBT_REQUIRE(src.max_path > 0 && isfinite(src.max_path), "max_path must be finite and > 0");
+    GBT_REQUIRE(isfinite(src.pos[0]) && isfinite(src.pos[1]) && isfinite(src.pos[2]),
+                "source position must be finite");
+    GBT_REQUIRE(src.fan == GBT_FAN_FIBONACCI || src.fan == GBT_FAN_EXPLICIT, "unknown fan");
+    GBT_REQUIRE(src.fan != GBT_FAN_EXPLICIT || src.dirs, "explicit fan needs dirs");
+    GBT_REQUIRE((double)cnt * (src.max_reflections + 1) < 2147483647.0,
+                "segment capacity exceeds 2^31 - 1: trace fewer rays at a time");
+}
+
+static gbt_trace_t *make_trace(const gbt_scene_t *scene, const gbt_source_desc &src, cudaStream_t s)
+{
+    validate_source(src);
+    const int64_t cnt = src.ray_count == 0 ? src.n_rays - src.ray_begin : src.ray_count;
+    gbt_trace_t *tr = new gbt_trace_s();
+    TraceDev &td = tr->d;
+    td.scene = scene;
+    td.n_fan = src.n_rays;
+    td.ray_begin = src.ray_begin;
+    td.n_rays = cnt;
+    td.max_refl = src.max_reflections;
+    td.max_path = src.max_path;
+    td.capacity = cnt * (int64_t)(src.max_reflections + 1);
+    const size_t cap = (size_t)td.capacity;
+    size_t bytes = align_up((size_t)(cnt + 1) * 4, 256) + 2 * align_up(cap * 24, 256) +
+                   2 * align_up(cap * 8, 256) + 4 * align_up(cap * 4, 256);
+    void *scratch = nullptr;
+    try {
+        td.block = dalloc(bytes, s);
+        char *w = static_cast<char *>(td.block);
+        auto take = [&](size_t b) { char *p = w; w += align_up(b, 256); return p; };
+        td.ray_off = reinterpret_cast<int32_t *>(take((size_t)(cnt + 1) * 4));
+        td.o = reinterpret_cast<double *>(take(cap * 24));
+        td.t = reinterpret_cast<double *>(take(cap * 24));
+        td.L = reinterpret_cast<double *>(take(cap * 8));
+        td.s0 = reinterpret_cast<double *>(take(cap * 8));
+        td.ray = reinterpret_cast<int32_t *>(take(cap * 4));
+        td.depth = reinterpret_cast<int32_t *>(take(cap * 4));
+        td.bmat = reinterpret_cast<int32_t *>(take(cap * 4));
+        td.hit = reinterpret_cast<int32_t *>(take(cap * 4));
+        const size_t sb = trace_scratch_bytes(cnt, src.max_reflections);
+        scratch = dalloc(sb, s);
+        trace_launch(scene->d, td, src, scratch, sb, s);
+        dfree(scratch, s);
+    } catch (...) {
+        if (scratch) dfree(scratch, s);
+        if (td.block) dfree(td.block, s);
+        delete tr;
+        throw;
+    }
+    return tr;
+}
+
+static void validate_sum(const gbt_trace_t *trace, const gbt_sum_args *a, bool need_out = true)
+{
+    GBT_REQUIRE(trace, "trace is NULL");
+    GBT_REQUIRE(a, "args is NULL");
+    GBT_REQUIRE(a->n_recv >= 0, "n_recv must be >= 0");
+    GBT_REQUIRE(a->n_freq >= 1 && a->n_freq <= GBT_MAX_FREQ, "n_freq must be in [1, 16]");
+    GBT_REQUIRE(a->window == GBT_WINDOW_SEGMENT || a->window == GBT_WINDOW_LINE, "unknown window");
+    GBT_REQUIRE(a->precision == GBT_PRECISION_F32 || a->precision == GBT_PRECISION_F64,
+                "unknown precision");
+    GBT_REQUIRE(a->cutoff > 0 && isfinite(a->cutoff), "cutoff must be finite and > 0");
+    GBT_REQUIRE(a->seg_split >= 0 && a->seg_split <= 4096, "seg_split must be in [0, 4096]");
+    for (int f = 0; f < a->n_freq; ++f) {
+        GBT_REQUIRE(a->freq_hz[f] > 0 && isfinite(a->freq_hz[f]), "frequencies must be > 0");
+        GBT_REQUIRE(a->beam_b[f] > 0 && isfinite(a->beam_b[f]), "beam_b must be > 0");
+    }
+    GBT_REQUIRE(a->gamma, "gamma is NULL");
+    if (a->n_recv > 0) {
+        GBT_REQUIRE(a->recv, "recv must be non-NULL");
+        if (need_out) {
+            GBT_REQUIRE(a->out, "out must be non-NULL");
+            GBT_REQUIRE(((uintptr_t)a->out & 7u) == 0, "out must be 8-byte aligned");
+        }
+        GBT_REQUIRE(a->n_recv < 2147483647LL, "n_recv must be < 2^31");
+    }
+}
+
+}  // namespace gbt
+
+using namespace gbt;
+
+extern "C" {
+
+int32_t gbt_version(void) { return GBT_VERSION; }
+
+const char *gbt_last_error(void) { return t_last_error.c_str(); }
+
+gbt_status gbt_set_allocator(const gbt_allocator *allocator)
+{
+    return guarded([&] {
+        if (allocator) GBT_REQUIRE(allocator->alloc && allocator->free, "allocator needs alloc and free");
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (allocator) {
+            g_alloc = *allocator;
+            g_has_alloc = true;
+        } else {
+            g_alloc = gbt_allocator{};
+            g_has_alloc = false;
+        }
+    });
+}
+
+gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_t **out)
+{
+    return guarded([&] {
+        GBT_REQUIRE(desc && out, "desc and out must be non-NULL");
+        *out = nullptr;
+        const gbt_scene_desc &d = *desc;
+        GBT_REQUIRE(d.c > 0 && isfinite(d.c), "speed of sound must be > 0");
+        GBT_REQUIRE(d.n_tri >= 0 && d.n_tri < (1LL << 26), "n_tri out of range");
+        GBT_REQUIRE(d.n_materials >= 1, "n_materials must be >= 1");
+        GBT_REQUIRE(!d.ground_enabled || (d.ground_material >= 0 && d.ground_material < d.n_materials),
+                    "ground_material out of range");
+        GBT_REQUIRE(isfinite(d.ground_z), "ground_z must be finite");
+        if (d.n_tri > 0) {
+            GBT_REQUIRE(d.tri_xyz && d.tri_material, "triangles need tri_xyz and tri_material");
+            for (int64_t k = 0; k < d.n_tri; ++k) {
+                GBT_REQUIRE(d.tri_material[k] >= 0 && d.tri_material[k] < d.n_materials,
+                            "tri_material out of range");
+                if (d.tri_face) GBT_REQUIRE(d.tri_face[k] >= 0, "tri_face must be >= 0");
+                for (int q = 0; q < 9; ++q)
+                    GBT_REQUIRE(isfinite(d.tri_xyz[9 * k + q]), "triangle vertices must be finite");
+            }
+        }
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        gbt_scene_t *sc = new gbt_scene_s();
+        SceneDev &sd = sc->d;
+        sd.c = d.c;
+        sd.ground = d.ground_enabled ? 1 : 0;
+        sd.ground_material = d.ground_material;
+        sd.ground_z = d.ground_z;
+        sd.n_tri = d.n_tri;
+        sd.n_materials = d.n_materials;
+        void *raw = nullptr;
+        try {
+            const size_t nt = (size_t)std::max<int64_t>(d.n_tri, 1);
+            sd.tri = static_cast<double *>(dalloc(nt * 12 * sizeof(double), s));
+            sd.face = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
+            sd.mat = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
+            if (d.n_tri > 0) {
+                std::vector<int32_t> face(d.n_tri);
+                for (int64_t k = 0; k < d.n_tri; ++k) face[k] = d.tri_face ? d.tri_face[k] : (int32_t)k;
+                raw = dalloc((size_t)d.n_tri * 9 * sizeof(double), s);
+                GBT_CUDA(cudaMemcpyAsync(raw, d.tri_xyz, (size_t)d.n_tri * 9 * sizeof(double),
+                                         cudaMemcpyHostToDevice, s));
+                GBT_CUDA(cudaMemcpyAsync(sd.face, face.data(), (size_t)d.n_tri * 4,
+                                         cudaMemcpyHostToDevice, s));
+                GBT_CUDA(cudaMemcpyAsync(sd.mat, d.tri_material, (size_t)d.n_tri * 4,
+                                         cudaMemcpyHostToDevice, s));
+                scene_prepare(sd, static_cast<const double *>(raw), s);
+                dfree(raw, s);
+                raw = nullptr;
+                GBT_CUDA(cudaStreamSynchronize(s));
+            }
+        } catch (...) {
+            if (raw) dfree(raw, s);
+            dfree(sd.tri, s); dfree(sd.face, s); dfree(sd.mat, s);
+            delete sc;
+            throw;
+        }
+        *out = sc;
+    });
+}
+
+gbt_status gbt_scene_destroy(gbt_scene_t *scene)
+{
+    return guarded([&] {
+        if (!scene) return;
+        GBT_CUDA(cudaDeviceSynchronize());
+        dfree(scene->d.tri, nullptr);
+        dfree(scene->d.face, nullptr);
+        dfree(scene->d.mat, nullptr);
+        delete scene;
+    });
+}
+
+gbt_status gbt_trace(const gbt_scene_t *scene, const gbt_source_desc *src, void *stream,
+                     gbt_trace_t **out)
+{
+    return guarded([&] {
+        GBT_REQUIRE(scene && src && out, "scene, src and out must be non-NULL");
+        *out = nullptr;
+        *out = make_trace(scene, *src, static_cast<cudaStream_t>(stream));
+    });
+}
+
+gbt_status gbt_trace_info_get(const gbt_trace_t *trace, gbt_trace_info *info)
+{
+    return guarded([&] {
+        GBT_REQUIRE(trace && info, "trace and info must be non-NULL");
+        gbt_trace_t *tr = const_cast<gbt_trace_t *>(trace);
+        TraceDev &td = tr->d;
+        if (td.n_seg_host < 0) {
+            int32_t n = 0;
+            GBT_CUDA(cudaDeviceSynchronize());
+            GBT_CUDA(cudaMemcpy(&n, td.ray_off + td.n_rays, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            td.n_seg_host = n;
+        }
+        memset(info, 0, sizeof(*info));
+        info->n_fan = td.n_fan;
+        info->ray_begin = td.ray_begin;
+        info->n_rays = td.n_rays;
+        info->seg_capacity = td.capacity;
+        info->n_segments = td.n_seg_host;
+        info->ray_off = td.ray_off;
+        info->seg_o = td.o; info->seg_t = td.t; info->seg_L = td.L; info->seg_s0 = td.s0;
+        info->seg_ray = td.ray; info->seg_depth = td.depth; info->seg_bmat = td.bmat;
+        info->seg_hit = td.hit;
+    });
+}
+
+gbt_status gbt_trace_destroy(gbt_trace_t *trace)
+{
+    return guarded([&] {
+        if (!trace) return;
+        GBT_CUDA(cudaDeviceSynchronize());
+        trace->d.work.release(nullptr);
+        dfree(trace->d.block, nullptr);
+        delete trace;
+    });
+}
+
+gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *stream)
+{
+    return guarded([&] {
+        validate_sum(trace, args);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        gbt_trace_t *tr = const_cast<gbt_trace_t *>(trace);
+        const SceneDev &sd = tr->d.scene->d;
+        const int splits = choose_splits(tr->d, *args);
+        void *w = tr->d.work.ensure(sum_workspace_bytes(tr->d, *args, splits), s);
+        sum_launch(tr->d, sd, *args, splits, w, s);
+    });
+}
+
+gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out, void *stream)
+{
+    return guarded([&] {
+        GBT_REQUIRE(n_recv >= 0 && n_recv < 2147483647LL, "n_recv out of range");
+        if (n_recv == 0) return;
+        GBT_REQUIRE(recv && order_out, "recv and order_out must be non-NULL");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t b = recv_order_scratch_bytes(n_recv);
+        void *scr = dalloc(b, s);
+        try {
+            recv_order_launch(recv, n_recv, order_out, scr, s);
+        } catch (...) {
+            dfree(scr, s);
+            throw;
+        }
+        dfree(scr, s);
+    });
+}
+
+gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
+                            const float *grad_out, float *grad_gamma, float *grad_ray_weight,
+                            double *grad_b, void *stream)
+{
+    return guarded([&] {
+        validate_sum(trace, args, false);
+        GBT_REQUIRE(args->precision == GBT_PRECISION_F32, "backward supports F32 precision only");
+        GBT_REQUIRE(grad_gamma, "grad_gamma is NULL");
+        GBT_REQUIRE(args->n_recv == 0 || grad_out, "grad_out is NULL");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        gbt_trace_t *tr = const_cast<gbt_trace_t *>(trace);
+        const SceneDev &sd = tr->d.scene->d;
+        void *w = tr->d.work.ensure(bwd_workspace_bytes(tr->d, *args), s);
+        bwd_launch(tr->d, sd, *args, grad_out, grad_gamma, grad_ray_weight, grad_b, w, s);
+    });
+}
+
+gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const gbt_sum_args *args,
+                     void *stream)
+{
+    return guarded([&] {
+        GBT_REQUIRE(scene && src && args, "scene, src and args must be non-NULL");
+        GBT_REQUIRE(src->ray_begin == 0 && src->ray_count == 0,
+                    "gbt_solve traces the whole fan: ray_begin and ray_count must be 0");
+        GBT_REQUIRE(src->fan == GBT_FAN_FIBONACCI, "gbt_solve supports the Fibonacci fan");
+        GBT_REQUIRE(args->max_device_bytes >= 0, "max_device_bytes must be >= 0");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int64_t N = src->n_rays;
+        const int64_t per_ray = (int64_t)(src->max_reflections + 1) *
+                                (80 /*compact*/ + 80 /*padded*/ + 4 * F_COUNT + 8 + 8);
+        int64_t chunk = N;
+        if (args->max_device_bytes > 0) {
+            chunk = std::max<int64_t>(1, args->max_device_bytes / std::max<int64_t>(per_ray, 1));
+        }
+        chunk = std::min<int64_t>(chunk, (int64_t)(2147483646LL / (src->max_reflections + 1)));
+        gbt_sum_args a = *args;
+        for (int64_t b = 0; b < N; b += chunk) {
+            gbt_source_desc cs = *src;
+            cs.ray_begin = b;
+            cs.ray_count = std::min<int64_t>(chunk, N - b);
+            gbt_trace_t *tr = make_trace(scene, cs, s);
+            a.accumulate = (b == 0) ? args->accumulate : 1;
+            try {
+                validate_sum(tr, &a);
+                const int splits = choose_splits(tr->d, a);
+                void *w = tr->d.work.ensure(sum_workspace_bytes(tr->d, a, splits), s);
+                sum_launch(tr->d, scene->d, a, splits, w, s);
+            } catch (...) {
+                tr->d.work.release(s);
+                dfree(tr->d.block, s);
+                delete tr;
+                throw;
+            }
+            tr->d.work.release(s);
+            dfree(tr->d.block, s);
+            delete tr;
+        }
+    });
+}
+
+gbt_status gbt_timing_enable(int32_t enable)
+{
+    return guarded([&] {
+        std::lock_guard<std::mutex> lk(g_timing_mu);
+        g_timing.enabled = enable != 0;
+    });
+}
+
+gbt_status gbt_timing_read(int64_t *launches, double *total_ms, int32_t reset)
+{
+    return guarded([&] {
+        GBT_REQUIRE(launches && total_ms, "launches and total_ms must be non-NULL");
+        std::lock_guard<std::mutex> lk(g_timing_mu);
+        double ms = 0.0;
+        for (auto &pr : g_timing.events) {
+            GBT_CUDA(cudaEventSynchronize(pr.second));
+            float t = 0.f;
+            GBT_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+            ms += t;
+        }
+        *launches = (int64_t)g_timing.events.size();
+        *total_ms = ms;
+        if (reset) {
+            for (auto &pr : g_timing.events) {
+                g_timing.pool.push_back(pr.first);
+                g_timing.pool.push_back(pr.second);
+            }
+            g_timing.events.clear();
+        }
+    });
+}
+
+gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,
+                             gbt_sum_stats *stats, void *stream)
+{
+    return guarded([&] {
+        validate_sum(trace, args, false);
+        GBT_REQUIRE(stats, "stats is NULL");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        gbt_trace_t *tr = const_cast<gbt_trace_t *>(trace);
+        gbt_sum_args a = *args;
+        a.precision = GBT_PRECISION_F32;
+        const int splits = choose_splits(tr->d, a);
+        void *w = tr->d.work.ensure(sum_workspace_bytes(tr->d, a, splits), s);
+        unsigned long long *cnt = static_cast<unsigned long long *>(dalloc(64, s));
+        GBT_CUDA(cudaMemsetAsync(cnt, 0, 64, s));
+        try {
+            sum_launch(tr->d, tr->d.scene->d, a, splits, w, s, cnt);
+        } catch (...) {
+            dfree(cnt, s);
+            throw;
+        }
+        unsigned long long h[4] = {0, 0, 0, 0};
+        int32_t nseg = 0;
+        GBT_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GBT_CUDA(cudaMemcpyAsync(&nseg, tr->d.ray_off + tr->d.n_rays, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+        GBT_CUDA(cudaStreamSynchronize(s));
+        dfree(cnt, s);
+        stats->n_segments = nseg;
+        stats->pairs = (int64_t)nseg * a.n_recv;
+        stats->pairs_prefiltered = (int64_t)h[1];
+        stats->triples_kept = (int64_t)h[2];
+    });
+}
+
+gbt_status gbt_sync(void *stream)
+{
+    return guarded([&] {
+        GBT_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+        unsigned int *sw = status_word();
+        unsigned int v = 0;
+        GBT_CUDA(cudaMemcpy(&v, sw, sizeof(v), cudaMemcpyDeviceToHost));
+        if (v) {
+            GBT_CUDA(cudaMemset(sw, 0, sizeof(unsigned int)));
+            if (v & STATUS_TIMEOUT) fail(GBT_ERR_TIMEOUT, "a bounded device wait ran out");
+            fail(GBT_ERR_DEVICE_STATUS, "device status flags 0x" + std::to_string(v));
+        }
+    });
+}
+
+}  // extern "C"

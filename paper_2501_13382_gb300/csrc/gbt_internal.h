@@ -1,0 +1,121 @@
+// gbt_internal.h -- private declarations shared by libgbt's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "gbt.h"
+
+namespace gbt {
+
+// Error carried through the host code; converted to gbt_status at the ABI.
+struct Error : public std::runtime_error {
+    gbt_status code;
+    Error(gbt_status c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+void check_cuda(cudaError_t e, const char *what);
+[[noreturn]] void fail(gbt_status code, const std::string &msg);
+#define GBT_CUDA(call) ::gbt::check_cuda((call), #call)
+#define GBT_REQUIRE(cond, msg) \
+    do { if (!(cond)) ::gbt::fail(GBT_ERR_INVALID_ARG, (msg)); } while (0)
+
+// Device memory through the installed allocator (default: stream-ordered pool).
+void *dalloc(size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+
+// Per-device status word (bit flags set by kernels, read by gbt_sync).
+unsigned int *status_word();
+enum : unsigned int { STATUS_BOUNDS = 1u, STATUS_TIMEOUT = 2u, STATUS_BAD_INPUT = 4u };
+
+int num_sms();
+
+// Optional CUDA-event timing of the main pair kernels (gbt_timing_*).
+void timing_begin(cudaStream_t s);
+void timing_end(cudaStream_t s);
+
+// Growable device buffer owned by a handle.
+struct DeviceBuffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    void *ensure(size_t n, cudaStream_t s);
+    void release(cudaStream_t s);
+};
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTMin = 1e-9;   // smallest accepted hit distance, m
+
+// Scene on the device.  Per triangle 12 doubles: v0, e1 = v1 - v0, e2 = v2 - v0,
+// unit normal (e1 x e2 normalised).
+struct SceneDev {
+    double c = 0;
+    int ground = 0;
+    int ground_material = 0;
+    double ground_z = 0;
+    int64_t n_tri = 0;
+    int n_materials = 0;
+    double *tri = nullptr;       // n_tri * 12
+    int32_t *face = nullptr;     // n_tri
+    int32_t *mat = nullptr;      // n_tri
+    int32_t *mat_host_max = nullptr;
+};
+
+// Segment kernel records (FP32 hi/lo split of the FP64 canonical segments),
+// structure of arrays with `stride` elements per field.
+enum SegField {
+    F_OX = 0, F_OY, F_OZ,            // origin, hi part
+    F_OXL, F_OYL, F_OZL,             // origin, lo part
+    F_TX, F_TY, F_TZ,                // unit direction, hi
+    F_TXL, F_TYL, F_TZL,             // unit direction, lo
+    F_S0, F_S0L,                     // start arclength hi, lo
+    F_L, F_LL,                       // length hi, lo
+    F_AMP,                           // W_ray * Gamma_path
+    F_COUNT
+};
+
+struct TraceDev {
+    const gbt_scene_t *scene = nullptr;
+    int64_t n_fan = 0, ray_begin = 0, n_rays = 0, capacity = 0;
+    int max_refl = 0;
+    double max_path = 0;
+    int32_t *ray_off = nullptr;  // n_rays + 1 (device); ray_off[n_rays] = segment count
+    double *o = nullptr, *t = nullptr, *L = nullptr, *s0 = nullptr;
+    int32_t *ray = nullptr, *depth = nullptr, *bmat = nullptr, *hit = nullptr;
+    void *block = nullptr;       // single allocation holding everything above
+    DeviceBuffer work;           // scratch for sums (records, partials)
+    int64_t n_seg_host = -1;     // cached once read back
+};
+
+// ---- kernels' host-side launchers (trace.cu) ----
+void scene_prepare(SceneDev &sd, const double *tri_raw_dev, cudaStream_t s);
+void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src,
+                  void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t trace_scratch_bytes(int64_t n_rays, int max_refl);
+
+// ---- GBS launchers (gbs.cu) ----
+size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits);
+int choose_splits(const TraceDev &td, const gbt_sum_args &a);
+void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, int splits,
+                void *work, cudaStream_t s, unsigned long long *stats = nullptr);
+void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scratch,
+                       cudaStream_t s);
+size_t recv_order_scratch_bytes(int64_t n);
+
+// ---- backward (gbs_bwd.cu) ----
+size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a);
+void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
+                const float *grad_out, float *grad_gamma, float *grad_w, double *grad_b,
+                void *work, cudaStream_t s);
+
+}  // namespace gbt
+
+struct gbt_scene_s {
+    gbt::SceneDev d;
+};
+
+struct gbt_trace_s {
+    gbt::TraceDev d;
+};

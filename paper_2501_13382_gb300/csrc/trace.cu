@@ -1,0 +1,421 @@
+// trace.cu -- FP64 ray-fan tracer: the RT process of Sec. 3.1 (rays and their
+// specular interactions with triangular facets, Sec. 2), with the fan of
+// take-off directions of Sec. 3.3.
+//
+// This translation unit is compiled with --fmad=false: every FP64 product and
+// sum is rounded on its own, in the order written, so hit sequences are
+// reproducible bit for bit by any IEEE-754 implementation of the same steps.
+//
+// Layout on the GB300: one thread per ray, triangles staged into shared memory
+// in chunks (the whole synthetic city, 768 triangles, fits in one chunk), the
+// per-ray segments written to padded slots ray * (R+1) + depth, then an
+// exclusive scan of the per-ray counts gives the CSR offsets and a compaction
+// kernel writes the flat segment list.  No host synchronisation is needed:
+// the segment count stays on the device (ray_off[n_rays]).
+#include <math.h>
+
+#include "gbt_internal.h"
+
+namespace gbt {
+namespace {
+
+constexpr int kTraceBlock = 128;
+constexpr int kTriChunk = 512;          // triangles per shared-memory chunk
+constexpr int kScanBlock = 1024;        // threads per scan block
+constexpr int kScanItems = 4;           // items per scan thread
+
+__global__ void scene_prep_kernel(const double *__restrict__ raw, int64_t n,
+                                  double *__restrict__ tri)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double *v = raw + 9 * k;
+    double *o = tri + 12 * k;
+    double e1x = v[3] - v[0], e1y = v[4] - v[1], e1z = v[5] - v[2];
+    double e2x = v[6] - v[0], e2y = v[7] - v[1], e2z = v[8] - v[2];
+    double nx = e1y * e2z - e1z * e2y;
+    double ny = e1z * e2x - e1x * e2z;
+    double nz = e1x * e2y - e1y * e2x;
+    double len = sqrt(nx * nx + ny * ny + nz * nz);
+    o[0] = v[0]; o[1] = v[1]; o[2] = v[2];
+    o[3] = e1x; o[4] = e1y; o[5] = e1z;
+    o[6] = e2x; o[7] = e2y; o[8] = e2z;
+    o[9] = nx / len; o[10] = ny / len; o[11] = nz / len;
+}
+
+struct TraceParams {
+    double src[3];
+    int64_t n_fan, ray_begin, n_rays;
+    const double *dirs;        // explicit directions (n_rays * 3) or nullptr
+    int max_refl;
+    double max_path;
+    int ground;
+    double ground_z;
+    int ground_mat;
+    const double *tri;         // n_tri * 12
+    const int32_t *face;
+    const int32_t *mat;
+    int64_t n_tri;
+    int64_t stride;            // max_refl + 1
+    double *po, *pt, *pL, *ps0;
+    int32_t *pbmat, *phit, *cnt;
+};
+
+// Moller-Trumbore test against a triangle given as v0, e1, e2 (12-double record);
+// returns t or -1.  Same operation order as a plain C evaluation of
+//   p = d x e2; det = e1.p; u = (o - v0).p / det; q = (o - v0) x e1;
+//   v = d.q / det; t = e2.q / det  with inclusive barycentric bounds.
+__device__ __forceinline__ double ray_triangle(const double o[3], const double d[3],
+                                               const double *__restrict__ r)
+{
+    const double e1x = r[3], e1y = r[4], e1z = r[5];
+    const double e2x = r[6], e2y = r[7], e2z = r[8];
+    double px = d[1] * e2z - d[2] * e2y;
+    double py = d[2] * e2x - d[0] * e2z;
+    double pz = d[0] * e2y - d[1] * e2x;
+    double det = e1x * px + e1y * py + e1z * pz;
+    if (det == 0.0) return -1.0;
+    double inv = 1.0 / det;
+    double tx = o[0] - r[0], ty = o[1] - r[1], tz = o[2] - r[2];
+    double u = (tx * px + ty * py + tz * pz) * inv;
+    if (u < 0.0 || u > 1.0) return -1.0;
+    double qx = ty * e1z - tz * e1y;
+    double qy = tz * e1x - tx * e1z;
+    double qz = tx * e1y - ty * e1x;
+    double v = (d[0] * qx + d[1] * qy + d[2] * qz) * inv;
+    if (v < 0.0 || u + v > 1.0) return -1.0;
+    return (e2x * qx + e2y * qy + e2z * qz) * inv;
+}
+
+__device__ __forceinline__ void load_tri_chunk(double *st, int32_t *sface, const TraceParams &p,
+                                               int64_t base, int count)
+{
+    for (int idx = threadIdx.x; idx < count * 12; idx += blockDim.x)
+        st[idx] = p.tri[base * 12 + idx];
+    for (int idx = threadIdx.x; idx < count; idx += blockDim.x)
+        sface[idx] = p.face ? p.face[base + idx] : (int32_t)(base + idx);
+}
+
+__global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
+{
+    extern __shared__ double smem[];
+    double *st = smem;                                   // kTriChunk * 12
+    int32_t *sface = reinterpret_cast<int32_t *>(smem + kTriChunk * 12);
+
+    const int64_t i = blockIdx.x * (int64_t)kTraceBlock + threadIdx.x;
+    const bool active = i < p.n_rays;
+    double o[3] = {p.src[0], p.src[1], p.src[2]};
+    double d[3] = {0.0, 0.0, 1.0};
+    if (active) {
+        if (p.dirs) {
+            d[0] = p.dirs[3 * i]; d[1] = p.dirs[3 * i + 1]; d[2] = p.dirs[3 * i + 2];
+        } else {
+            // Fibonacci sphere, ray index g in the whole fan
+            const int64_t g = p.ray_begin + i;
+            const double golden = kPi * (3.0 - sqrt(5.0));
+            double z = 1.0 - (2.0 * (double)g + 1.0) / (double)p.n_fan;
+            double r = sqrt(1.0 - z * z);
+            double phi = (double)g * golden;
+            d[0] = r * cos(phi);
+            d[1] = r * sin(phi);
+            d[2] = z;
+        }
+    }
+    double s0 = 0.0;
+    int last_face = -1;
+    int bmat = -1;
+    int nref = 0, nseg = 0;
+    bool alive = active;
+
+    const int64_t nchunk = (p.n_tri + kTriChunk - 1) / kTriChunk;
+    const bool resident = nchunk <= 1;
+    if (resident && p.n_tri > 0) {
+        load_tri_chunk(st, sface, p, 0, (int)p.n_tri);
+    }
+    __syncthreads();
+
+    for (int bounce = 0; bounce <= p.max_refl; ++bounce) {
+        double tbest = INFINITY;
+        int best = -1;
+        if (alive && p.ground && last_face != -2 && d[2] != 0.0) {
+            double t = (p.ground_z - o[2]) / d[2];
+            if (t > kTMin && t < tbest) { tbest = t; best = 0; }
+        }
+        for (int64_t c = 0; c < nchunk; ++c) {
+            const int64_t base = c * kTriChunk;
+            const int count = (int)min((int64_t)kTriChunk, p.n_tri - base);
+            if (!resident) {
+                __syncthreads();
+                load_tri_chunk(st, sface, p, base, count);
+                __syncthreads();
+            }
+            if (alive) {
+                for (int k = 0; k < count; ++k) {
+                    if (sface[k] == last_face) continue;
+                    double t = ray_triangle(o, d, st + 12 * k);
+                    if (t > kTMin && t < tbest) { tbest = t; best = (int)(base + k + 1); }
+                }
+            }
+        }
+        if (alive) {
+            const double remaining = p.max_path - s0;
+            const int64_t row = i * p.stride + nseg;
+            p.po[3 * row + 0] = o[0]; p.po[3 * row + 1] = o[1]; p.po[3 * row + 2] = o[2];
+            p.pt[3 * row + 0] = d[0]; p.pt[3 * row + 1] = d[1]; p.pt[3 * row + 2] = d[2];
+            p.ps0[row] = s0;
+            p.pbmat[row] = bmat;
+            ++nseg;
+            if (best < 0 || tbest >= remaining) {
+                p.pL[row] = remaining;
+                p.phit[row] = -1;
+                alive = false;
+            } else {
+                p.pL[row] = tbest;
+                p.phit[row] = best;
+                if (nref == p.max_refl) {
+                    alive = false;
+                } else {
+                    double n0, n1, n2;
+                    int face, mat;
+                    if (best == 0) {
+                        n0 = 0.0; n1 = 0.0; n2 = 1.0;
+                        face = -2; mat = p.ground_mat;
+                    } else {
+                        const int64_t k = best - 1;
+                        n0 = p.tri[12 * k + 9]; n1 = p.tri[12 * k + 10]; n2 = p.tri[12 * k + 11];
+                        face = p.face ? p.face[k] : (int)k;
+                        mat = p.mat[k];
+                    }
+                    o[0] = o[0] + tbest * d[0];
+                    o[1] = o[1] + tbest * d[1];
+                    o[2] = o[2] + tbest * d[2];
+                    double dn = d[0] * n0 + d[1] * n1 + d[2] * n2;
+                    d[0] = d[0] - 2.0 * dn * n0;
+                    d[1] = d[1] - 2.0 * dn * n1;
+                    d[2] = d[2] - 2.0 * dn * n2;
+                    s0 = s0 + tbest;
+                    last_face = face;
+                    bmat = mat;
+                    ++nref;
+                }
+            }
+        }
+        if (!__syncthreads_or(alive)) break;
+    }
+    if (active) p.cnt[i] = nseg;
+}
+
+// ---- exclusive scan of per-ray counts (3 phases, deterministic) ----
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        int w = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int excl = x - v + (warp > 0 ? warp_sums[warp - 1] : 0);
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    return excl;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_block_sums(const int32_t *__restrict__ cnt,
+                                                              int64_t n, int32_t *__restrict__ bsum)
+{
+    __shared__ int ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems;
+    int local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int64_t idx = base + (int64_t)threadIdx.x * kScanItems + q;
+        if (idx < n) local += cnt[idx];
+    }
+    int tot;
+    block_exclusive_scan(local, ws, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_of_block_sums(int32_t *bsum, int64_t nb)
+{
+    __shared__ int ws[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += kScanBlock) {
+        int64_t idx = base + threadIdx.x;
+        int v = idx < nb ? bsum[idx] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, ws, &tot);
+        int c = carry;
+        if (idx < nb) bsum[idx] = ex + c;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_final(const int32_t *__restrict__ cnt, int64_t n,
+                                                         const int32_t *__restrict__ bsum,
+                                                         int32_t *__restrict__ off)
+{
+    __shared__ int ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock * kScanItems;
+    int vals[kScanItems];
+    int local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int64_t idx = base + (int64_t)threadIdx.x * kScanItems + q;
+        vals[q] = idx < n ? cnt[idx] : 0;
+        local += vals[q];
+    }
+    int tot;
+    int ex = block_exclusive_scan(local, ws, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int64_t idx = base + (int64_t)threadIdx.x * kScanItems + q;
+        if (idx < n) off[idx] = ex;
+        ex += vals[q];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) off[n] = ex;
+}
+
+struct CompactParams {
+    int64_t n_rays, stride, ray_begin;
+    const int32_t *cnt, *off;
+    const double *po, *pt, *pL, *ps0;
+    const int32_t *pbmat, *phit;
+    double *o, *t, *L, *s0;
+    int32_t *ray, *depth, *bmat, *hit;
+};
+
+__global__ void compact_kernel(CompactParams p)
+{
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (slot >= p.n_rays * p.stride) return;
+    const int64_t i = slot / p.stride;
+    const int dep = (int)(slot - i * p.stride);
+    if (dep >= p.cnt[i]) return;
+    const int64_t j = (int64_t)p.off[i] + dep;
+    p.o[3 * j + 0] = p.po[3 * slot + 0];
+    p.o[3 * j + 1] = p.po[3 * slot + 1];
+    p.o[3 * j + 2] = p.po[3 * slot + 2];
+    p.t[3 * j + 0] = p.pt[3 * slot + 0];
+    p.t[3 * j + 1] = p.pt[3 * slot + 1];
+    p.t[3 * j + 2] = p.pt[3 * slot + 2];
+    p.L[j] = p.pL[slot];
+    p.s0[j] = p.ps0[slot];
+    p.ray[j] = (int32_t)(p.ray_begin + i);
+    p.depth[j] = dep;
+    p.bmat[j] = p.pbmat[slot];
+    p.hit[j] = p.phit[slot];
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+void scene_prepare(SceneDev &sd, const double *tri_raw_dev, cudaStream_t s)
+{
+    if (sd.n_tri == 0) return;
+    const int bs = 128;
+    scene_prep_kernel<<<(unsigned)((sd.n_tri + bs - 1) / bs), bs, 0, s>>>(tri_raw_dev, sd.n_tri,
+                                                                          sd.tri);
+    GBT_CUDA(cudaGetLastError());
+}
+
+size_t trace_scratch_bytes(int64_t n_rays, int max_refl)
+{
+    const size_t cap = (size_t)n_rays * (max_refl + 1);
+    const size_t nb = (size_t)((n_rays + kScanBlock * kScanItems - 1) / (kScanBlock * kScanItems));
+    size_t b = 0;
+    b += align_up(cap * 3 * sizeof(double), 256) * 2;   // po, pt
+    b += align_up(cap * sizeof(double), 256) * 2;       // pL, ps0
+    b += align_up(cap * sizeof(int32_t), 256) * 2;      // pbmat, phit
+    b += align_up((size_t)n_rays * sizeof(int32_t), 256);   // cnt
+    b += align_up((nb + 1) * sizeof(int32_t), 256);     // block sums
+    return b;
+}
+
+void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, void *scratch,
+                  size_t scratch_bytes, cudaStream_t s)
+{
+    const int64_t n = td.n_rays;
+    const int64_t stride = td.max_refl + 1;
+    const size_t cap = (size_t)n * stride;
+    char *w = static_cast<char *>(scratch);
+    auto take = [&](size_t bytes) {
+        char *p = w;
+        w += align_up(bytes, 256);
+        return p;
+    };
+    TraceParams p{};
+    p.src[0] = src.pos[0]; p.src[1] = src.pos[1]; p.src[2] = src.pos[2];
+    p.n_fan = td.n_fan;
+    p.ray_begin = td.ray_begin;
+    p.n_rays = n;
+    p.dirs = src.fan == GBT_FAN_EXPLICIT ? src.dirs : nullptr;
+    p.max_refl = td.max_refl;
+    p.max_path = td.max_path;
+    p.ground = sd.ground;
+    p.ground_z = sd.ground_z;
+    p.ground_mat = sd.ground_material;
+    p.tri = sd.tri;
+    p.face = sd.face;
+    p.mat = sd.mat;
+    p.n_tri = sd.n_tri;
+    p.stride = stride;
+    p.po = reinterpret_cast<double *>(take(cap * 3 * sizeof(double)));
+    p.pt = reinterpret_cast<double *>(take(cap * 3 * sizeof(double)));
+    p.pL = reinterpret_cast<double *>(take(cap * sizeof(double)));
+    p.ps0 = reinterpret_cast<double *>(take(cap * sizeof(double)));
+    p.pbmat = reinterpret_cast<int32_t *>(take(cap * sizeof(int32_t)));
+    p.phit = reinterpret_cast<int32_t *>(take(cap * sizeof(int32_t)));
+    p.cnt = reinterpret_cast<int32_t *>(take((size_t)n * sizeof(int32_t)));
+    const int64_t per = (int64_t)kScanBlock * kScanItems;
+    const int64_t nb = (n + per - 1) / per;
+    int32_t *bsum = reinterpret_cast<int32_t *>(take((size_t)(nb + 1) * sizeof(int32_t)));
+    if ((size_t)(w - static_cast<char *>(scratch)) > scratch_bytes)
+        fail(GBT_ERR_INVALID_ARG, "trace scratch too small");
+
+    const size_t smem = kTriChunk * 12 * sizeof(double) + kTriChunk * sizeof(int32_t);
+    static bool attr_set = false;
+    if (!attr_set) {
+        GBT_CUDA(cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        attr_set = true;
+    }
+    trace_kernel<<<(unsigned)((n + kTraceBlock - 1) / kTraceBlock), kTraceBlock, smem, s>>>(p);
+    GBT_CUDA(cudaGetLastError());
+
+    scan_block_sums<<<(unsigned)nb, kScanBlock, 0, s>>>(p.cnt, n, bsum);
+    scan_of_block_sums<<<1, kScanBlock, 0, s>>>(bsum, nb);
+    scan_final<<<(unsigned)nb, kScanBlock, 0, s>>>(p.cnt, n, bsum, td.ray_off);
+    GBT_CUDA(cudaGetLastError());
+
+    CompactParams c{};
+    c.n_rays = n; c.stride = stride; c.ray_begin = td.ray_begin;
+    c.cnt = p.cnt; c.off = td.ray_off;
+    c.po = p.po; c.pt = p.pt; c.pL = p.pL; c.ps0 = p.ps0; c.pbmat = p.pbmat; c.phit = p.phit;
+    c.o = td.o; c.t = td.t; c.L = td.L; c.s0 = td.s0;
+    c.ray = td.ray; c.depth = td.depth; c.bmat = td.bmat; c.hit = td.hit;
+    const int64_t slots = n * stride;
+    compact_kernel<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(c);
+    GBT_CUDA(cudaGetLastError());
+}
+
+}  // namespace gbt

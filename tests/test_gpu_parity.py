@@ -1,0 +1,234 @@
+"""GPU path vs the FP64 oracle, element by element, on seeded inputs.
+
+Bars: index work (hit primitives, counts, offsets, materials) bit-exact;
+FP64 geometry to FP64 rounding; complex fields within relative L2 1e-4 of the
+oracle (and per element within 1e-4 of the field's maximum)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_13382_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_L2 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_2501_13382_gb300 import build, gbt
+    build.build()
+    gbt.load()
+    torch.cuda.init()
+    return gbt
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(x, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda", dtype=dtype)
+
+
+def _gpu_sum(G, w, src_i=0, recv=None, order=True, precision=0, seg_split=0, n_rays=None,
+             gamma=None, weight=None):
+    import torch
+    src = w.sources[src_i]
+    if n_rays is not None:
+        src = I.Source(src.pos, n_rays, src.max_reflections, src.max_path)
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, src)
+    r = _dev(w.receivers if recv is None else recv, torch.float32)
+    gam = _dev(w.scene.gamma if gamma is None else gamma, torch.float32)
+    wt = None if weight is None else _dev(weight, torch.float32)
+    ordr = G.recv_order(r) if order else None
+    p = G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[src_i]), gam, ray_weight=wt, order=ordr,
+                  window=w.window, cutoff=w.cutoff, precision=precision, seg_split=seg_split)
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    return p.cpu().numpy().astype(np.complex128), tr, sc
+
+
+def _compare_trace(gt, ot, exact_float=False):
+    assert gt["n_segments"] == ot.n_seg
+    assert np.array_equal(gt["ray_off"].cpu().numpy(), ot.ray_off.astype(np.int32))
+    for k in ("hit", "bmat", "depth", "ray"):
+        assert np.array_equal(gt[k].cpu().numpy(), getattr(ot, k)), k
+    for k in ("o", "t", "L", "s0"):
+        g = gt[k].cpu().numpy()
+        o = getattr(ot, k)
+        if exact_float:
+            assert np.array_equal(g, o), k
+        else:
+            assert np.allclose(g, o, rtol=1e-13, atol=1e-11), (k, np.abs(g - o).max())
+
+
+def test_trace_open_plane_matches_oracle(G):
+    w = I.open_plane_small()
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, w.sources[0])
+    _compare_trace(tr.segments(), O.trace(w.scene, w.sources[0]))
+
+
+def test_trace_explicit_directions_bit_exact(G):
+    import torch
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 4096, 8, 1000.0)
+    dirs = O.fan_fibonacci(4096)
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src, dirs=_dev(dirs, torch.float64))
+    _compare_trace(tr.segments(), O.trace(sc0, src, dirs=dirs), exact_float=True)
+
+
+def test_trace_city_fibonacci_matches_oracle(G):
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 16384, 8, 1000.0)
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src)
+    gt = tr.segments()
+    ot = O.trace(sc0, src)
+    _compare_trace(gt, ot)
+    cnt = np.diff(ot.ray_off)
+    assert cnt.max() >= 5 and cnt.min() >= 1       # irregular loops really are irregular
+
+
+def test_trace_ray_range_is_a_slice(G):
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 8192, 8, 1000.0)
+    sc = G.Scene(sc0)
+    full = G.Trace(sc, src).segments()
+    part = G.Trace(sc, src, ray_begin=3001, ray_count=2500).segments()
+    off = full["ray_off"].cpu().numpy()
+    a, b = off[3001], off[5501]
+    assert part["n_segments"] == b - a
+    for k in ("o", "t", "L", "s0", "ray", "hit", "bmat", "depth"):
+        assert np.array_equal(part[k].cpu().numpy(), full[k].cpu().numpy()[a:b]), k
+
+
+def test_sum_open_plane_small_full(G):
+    w = I.open_plane_small()
+    p, tr, sc = _gpu_sum(G, w)
+    _, po = O.solve(w)
+    e = rel_l2(p, po)
+    assert e <= TOL_L2, e
+    assert np.abs(p - po).max() <= TOL_L2 * np.abs(po).max()
+
+
+def test_sum_f64_path_matches_oracle_to_fp64(G):
+    w = I.open_plane_small()
+    p, _, _ = _gpu_sum(G, w, precision=1)
+    _, po = O.solve(w)
+    assert rel_l2(p, po) < 1e-7     # output is complex64: FP32 rounding of the result
+
+
+def test_sum_open_plane_large_sampled(G):
+    """Full-size open-plane workload (65,536 rays, 256^2 receivers, 6 bands), the
+    configuration the benchmark times; the oracle evaluates a seeded sample."""
+    w = I.open_plane_large()
+    p, _, _ = _gpu_sum(G, w)
+    idx = I.receiver_subset(w.receivers, 160, seed=5)
+    tr = O.trace(w.scene, w.sources[0])
+    po = O.gbs_sum(tr, w.receivers[idx], w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma,
+                   window=w.window, cutoff=w.cutoff)
+    for f in range(len(w.freqs)):
+        e = rel_l2(p[f, idx], po[f])
+        assert e <= TOL_L2, (f, e)
+
+
+def test_sum_city_segment_window(G):
+    w = I.city(n_rays=16384, n_recv_side=48)
+    p, _, _ = _gpu_sum(G, w)
+    _, po = O.solve(w)
+    assert rel_l2(p, po) <= TOL_L2
+
+
+def test_split_and_order_do_not_change_results(G):
+    w = I.city(n_rays=8192, n_recv_side=40)
+    base, _, _ = _gpu_sum(G, w, seg_split=1, order=False)
+    ordered, _, _ = _gpu_sum(G, w, seg_split=1, order=True)
+    assert np.array_equal(base, ordered)          # every receiver's sum is independent
+    for s in (3, 17, 64):
+        q, _, _ = _gpu_sum(G, w, seg_split=s)
+        assert rel_l2(q, base) < 1e-6
+
+
+@pytest.mark.parametrize("n", [1, 2, 511, 513, 1000])
+def test_ragged_receiver_counts(G, n):
+    w = I.city(n_rays=4096, n_recv_side=40)
+    rng = np.random.default_rng(n)
+    recv = I.random_receivers(rng, n, [-250, -250, 0.5], [250, 250, 40])
+    p, _, _ = _gpu_sum(G, w, recv=recv)
+    tr = O.trace(w.scene, w.sources[0])
+    po = O.gbs_sum(tr, recv, w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma, window=w.window)
+    assert rel_l2(p, po) <= TOL_L2
+
+
+def test_empty_receiver_set(G):
+    import torch
+    w = I.open_plane_small()
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, w.sources[0])
+    r = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    out = G.gbs_sum(tr, r, [500.0], [18.4], _dev(w.scene.gamma, torch.float32))
+    torch.cuda.synchronize()
+    assert out.shape == (1, 0)
+
+
+def test_weights_gamma_and_accumulate(G):
+    import torch
+    w = I.city(n_rays=4096, n_recv_side=24)
+    rng = np.random.default_rng(11)
+    wt = (4 * np.pi / 4096) * rng.uniform(0.5, 1.5, 4096)
+    gam = rng.uniform(0.3, 1.0, w.scene.n_materials).astype(np.float32)
+    p, tr, sc = _gpu_sum(G, w, weight=wt.astype(np.float32), gamma=gam)
+    otr = O.trace(w.scene, w.sources[0])
+    po = O.gbs_sum(otr, w.receivers, w.freqs, w.beam_b[0], w.scene.c, gam,
+                   weight=wt.astype(np.float32).astype(np.float64), window=w.window)
+    assert rel_l2(p, po) <= TOL_L2
+    # accumulate adds into out
+    r = _dev(w.receivers, torch.float32)
+    out = _dev(p.astype(np.complex64))
+    G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[0]), _dev(gam), ray_weight=_dev(
+        wt.astype(np.float32)), window=w.window, out=out, accumulate=True)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), 2 * po) <= TOL_L2
+
+
+def test_chunked_solve_equals_single_pass(G):
+    import torch
+    w = I.city(n_rays=12000, n_recv_side=32)
+    sc = G.Scene(w.scene)
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    args = (sc, w.sources[0], r, list(w.freqs), list(w.beam_b[0]), gam)
+    one = G.gbs_solve(*args, window=w.window).cpu().numpy()
+    per_ray = (w.sources[0].max_reflections + 1) * (80 + 80 + 4 * 17 + 16)
+    many = G.gbs_solve(*args, window=w.window, max_device_bytes=per_ray * 1700).cpu().numpy()
+    assert rel_l2(many, one) < 1e-6
+    _, po = O.solve(w)
+    assert rel_l2(one.astype(np.complex128), po) <= TOL_L2
+
+
+def test_invalid_arguments_are_rejected_before_launch(G):
+    import torch
+    w = I.open_plane_small()
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, w.sources[0])
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    with pytest.raises(G.GBTError) as e:
+        G.gbs_sum(tr, r, [500.0], [-1.0], gam)
+    assert e.value.status == 1
+    with pytest.raises(G.GBTError):
+        G.gbs_sum(tr, r, [], [], gam)
+    with pytest.raises(G.GBTError):
+        G.gbs_sum(tr, r, [500.0], [10.0], gam, cutoff=0.0)
+    bad = I.Source(np.array([0.0, 0.0, 2.0]), 0, 2, 200.0)
+    with pytest.raises(G.GBTError):
+        G.Trace(sc, bad)
+    G.gbt_sync()
