@@ -56,6 +56,8 @@ struct FwdParams {
     float cutoff;
     float pre_alpha, pre_beta; // prefilter: keep iff alpha n^2 <= s^2 + beta
     int splits;
+    int n_items;               // receiver tiles x splits
+    int *work_counter;         // zeroed before launch; CTAs take items from it
     float4 *partial;           // [splits][nf][n_recv]: re_hi, im_hi, re_lo, im_lo
     unsigned long long *stats; // counting mode when non-null: [1] prefiltered, [2] kept
     FreqConst fc[GBT_MAX_FREQ];
@@ -207,146 +209,160 @@ __global__ void __launch_bounds__(kThreads, 2) gbs_fwd_kernel(const FwdParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FwdSmem<NF> &sm = *reinterpret_cast<FwdSmem<NF> *>(smem_raw);
+    __shared__ int s_item;
 
     const int tid = threadIdx.x;
-    const int64_t tile_base = (int64_t)blockIdx.x * kTileRecv;
-    const int split = blockIdx.y;
     const int64_t n_seg = *p.n_seg_ptr;
-    const int64_t seg_begin = split * n_seg / p.splits;
-    const int64_t seg_end = (split + 1) * n_seg / p.splits;
-
-    // tile centre: the tile's first receiver
-    const int64_t c_idx = p.order ? p.order[tile_base] : tile_base;
-    const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
-
-    float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
-    int64_t ridx[kR];
-    uint32_t valid = 0;
-#pragma unroll
-    for (int k = 0; k < kR; ++k) {
-        const int64_t r = tile_base + (int64_t)tid * kR + k;
-        ridx[k] = -1;
-        xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
-        if (r < p.n_recv) {
-            const int64_t o = p.order ? p.order[r] : r;
-            ridx[k] = o;
-            xa[k] = p.recv[3 * o]; ya[k] = p.recv[3 * o + 1]; za[k] = p.recv[3 * o + 2];
-            xp[k] = xa[k] - cx; yp[k] = ya[k] - cy; zp[k] = za[k] - cz;
-            xx[k] = fmaf(xp[k], xp[k], fmaf(yp[k], yp[k], zp[k] * zp[k]));
-            valid |= 1u << k;
-        }
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int k = 0; k < kR; ++k) sm.acc[f][k][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-    float2 tmp[kR][NF];
-#pragma unroll
-    for (int k = 0; k < kR; ++k)
-#pragma unroll
-        for (int f = 0; f < NF; ++f) tmp[k][f] = make_float2(0.f, 0.f);
-
+    const int64_t n_seg_tiles = (n_seg + kTS - 1) / kTS;
     const float alpha = p.pre_alpha, beta = p.pre_beta;
     uint32_t n_pre = 0, n_kept = 0;
 
-    for (int64_t t0 = seg_begin; t0 < seg_end; t0 += kTS) {
+    // Persistent CTAs: each item is (receiver tile, split); split s covers the
+    // segment tiles s, s + splits, s + 2 splits, ... so every item sees a mix of
+    // ray directions and the work per item is even.
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(p.work_counter, 1);
         __syncthreads();
-        if (tid < kTS) {
-            const int64_t j = t0 + tid;
-            if (j < seg_end) {
-                const float *R = p.rec;
-                const int64_t st = p.stride;
-                float oxh = R[F_OX * st + j], oyh = R[F_OY * st + j], ozh = R[F_OZ * st + j];
-                float oxl = R[F_OXL * st + j], oyl = R[F_OYL * st + j], ozl = R[F_OZL * st + j];
-                float tx = R[F_TX * st + j], ty = R[F_TY * st + j], tz = R[F_TZ * st + j];
-                float ox = (oxh - cx) + oxl, oy = (oyh - cy) + oyl, oz = (ozh - cz) + ozl;
-                float ot = fmaf(ox, tx, fmaf(oy, ty, oz * tz));
-                sm.A[tid] = make_float4(tx, ty, tz, -ot);
-                sm.B[tid] = make_float4(-2.f * ox, -2.f * oy, -2.f * oz,
-                                        fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
-                float s0h = R[F_S0 * st + j], Lh = R[F_L * st + j];
-                sm.Cw[tid] = make_float2(s0h + kWinMargin, Lh + kWinMargin);
-                sm.cold.f[C_OXH][tid] = oxh; sm.cold.f[C_OYH][tid] = oyh;
-                sm.cold.f[C_OZH][tid] = ozh;
-                sm.cold.f[C_OXL][tid] = oxl; sm.cold.f[C_OYL][tid] = oyl;
-                sm.cold.f[C_OZL][tid] = ozl;
-                sm.cold.f[C_TXL][tid] = R[F_TXL * st + j];
-                sm.cold.f[C_TYL][tid] = R[F_TYL * st + j];
-                sm.cold.f[C_TZL][tid] = R[F_TZL * st + j];
-                sm.cold.f[C_S0H][tid] = s0h;
-                sm.cold.f[C_S0L][tid] = R[F_S0L * st + j];
-                sm.cold.f[C_LH][tid] = Lh;
-                sm.cold.f[C_LL][tid] = R[F_LL * st + j];
-                sm.cold.f[C_AMP][tid] = R[F_AMP * st + j];
-            } else {
-                // a record no receiver can keep: far behind its own start
-                sm.A[tid] = make_float4(0.f, 0.f, 0.f, -1e15f);
-                sm.B[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                sm.Cw[tid] = make_float2(0.f, 0.f);
+        const int item = s_item;
+        if (item >= p.n_items) break;
+        const int64_t tile_base = (int64_t)(item / p.splits) * kTileRecv;
+        const int split = item % p.splits;
+
+        // tile centre: the tile's first receiver
+        const int64_t c_idx = p.order ? p.order[tile_base] : tile_base;
+        const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
+
+        float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
+        int64_t ridx[kR];
+        uint32_t valid = 0;
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            const int64_t r = tile_base + (int64_t)tid * kR + k;
+            ridx[k] = -1;
+            xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
+            if (r < p.n_recv) {
+                const int64_t o = p.order ? p.order[r] : r;
+                ridx[k] = o;
+                xa[k] = p.recv[3 * o]; ya[k] = p.recv[3 * o + 1]; za[k] = p.recv[3 * o + 2];
+                xp[k] = xa[k] - cx; yp[k] = ya[k] - cy; zp[k] = za[k] - cz;
+                xx[k] = fmaf(xp[k], xp[k], fmaf(yp[k], yp[k], zp[k] * zp[k]));
+                valid |= 1u << k;
             }
         }
-        __syncthreads();
-        const int nt = (int)min((int64_t)kTS, seg_end - t0);
-        for (int b0 = 0; b0 < nt; b0 += 32) {
-            uint32_t m[kR];
 #pragma unroll
-            for (int k = 0; k < kR; ++k) m[k] = 0u;
-#pragma unroll 8
-            for (int jj = 0; jj < 32; ++jj) {
-                const float4 A = sm.A[b0 + jj];
-                const float4 B = sm.B[b0 + jj];
-                const float2 Cw = sm.Cw[b0 + jj];
+        for (int f = 0; f < NF; ++f)
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
-                    const float sl = fmaf(xp[k], A.x, fmaf(yp[k], A.y, fmaf(zp[k], A.z, A.w)));
-                    const float sm_ = sl + Cw.x;                       // s + margin
-                    const float d2 = fmaf(xp[k], B.x, fmaf(yp[k], B.y, fmaf(zp[k], B.z, xx[k] + B.w)));
-                    const float n2 = fmaf(-sl, sl, d2);
-                    const float q = fmaf(sm_, sm_, beta);
-                    const float e = fmaf(alpha, n2, -q);
-                    uint32_t kb;
-                    if (WINDOW == GBT_WINDOW_LINE) {
-                        kb = __float_as_uint(e) & ~__float_as_uint(sm_);
-                    } else {
-                        const float a = sl + kWinMargin;
-                        const float bb = sl - Cw.y;
-                        kb = __float_as_uint(e) & ~__float_as_uint(a) & __float_as_uint(bb);
-                    }
-                    m[k] = __funnelshift_l(kb, m[k], 1);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kR; ++k) {
-                uint32_t mm = (valid >> k) & 1u ? m[k] : 0u;
-                if (p.stats) n_pre += __popc(mm);
-                while (mm) {
-                    const int jj = __clz(mm);
-                    mm ^= 0x80000000u >> jj;
-                    const int j = b0 + jj;
-                    if (j >= nt) break;           // bits past the tile's end
-                    survivor<NF, WINDOW>(p, xa[k], ya[k], za[k], sm.cold, sm.A[j], j, tmp[k], n_kept);
-                }
-            }
-        }
+            for (int k = 0; k < kR; ++k) sm.acc[f][k][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+        float2 tmp[kR][NF];
 #pragma unroll
         for (int k = 0; k < kR; ++k)
 #pragma unroll
-            for (int f = 0; f < NF; ++f) fold<NF>(sm.acc[f][k][tid], tmp[k][f]);
+            for (int f = 0; f < NF; ++f) tmp[k][f] = make_float2(0.f, 0.f);
+
+        for (int64_t stile = split; stile < n_seg_tiles; stile += p.splits) {
+            const int64_t t0 = stile * kTS;
+            const int64_t seg_end = min(n_seg, t0 + kTS);
+            __syncthreads();
+            if (tid < kTS) {
+                const int64_t j = t0 + tid;
+                if (j < seg_end) {
+                    const float *R = p.rec;
+                    const int64_t st = p.stride;
+                    float oxh = R[F_OX * st + j], oyh = R[F_OY * st + j], ozh = R[F_OZ * st + j];
+                    float oxl = R[F_OXL * st + j], oyl = R[F_OYL * st + j], ozl = R[F_OZL * st + j];
+                    float tx = R[F_TX * st + j], ty = R[F_TY * st + j], tz = R[F_TZ * st + j];
+                    float ox = (oxh - cx) + oxl, oy = (oyh - cy) + oyl, oz = (ozh - cz) + ozl;
+                    float ot = fmaf(ox, tx, fmaf(oy, ty, oz * tz));
+                    sm.A[tid] = make_float4(tx, ty, tz, -ot);
+                    sm.B[tid] = make_float4(-2.f * ox, -2.f * oy, -2.f * oz,
+                                            fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
+                    float s0h = R[F_S0 * st + j], Lh = R[F_L * st + j];
+                    sm.Cw[tid] = make_float2(s0h + kWinMargin, Lh + kWinMargin);
+                    sm.cold.f[C_OXH][tid] = oxh; sm.cold.f[C_OYH][tid] = oyh;
+                    sm.cold.f[C_OZH][tid] = ozh;
+                    sm.cold.f[C_OXL][tid] = oxl; sm.cold.f[C_OYL][tid] = oyl;
+                    sm.cold.f[C_OZL][tid] = ozl;
+                    sm.cold.f[C_TXL][tid] = R[F_TXL * st + j];
+                    sm.cold.f[C_TYL][tid] = R[F_TYL * st + j];
+                    sm.cold.f[C_TZL][tid] = R[F_TZL * st + j];
+                    sm.cold.f[C_S0H][tid] = s0h;
+                    sm.cold.f[C_S0L][tid] = R[F_S0L * st + j];
+                    sm.cold.f[C_LH][tid] = Lh;
+                    sm.cold.f[C_LL][tid] = R[F_LL * st + j];
+                    sm.cold.f[C_AMP][tid] = R[F_AMP * st + j];
+                } else {
+                    // a record no receiver can keep: far behind its own start
+                    sm.A[tid] = make_float4(0.f, 0.f, 0.f, -1e15f);
+                    sm.B[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    sm.Cw[tid] = make_float2(0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            const int nt = (int)(seg_end - t0);
+            for (int b0 = 0; b0 < nt; b0 += 32) {
+                uint32_t m[kR];
+#pragma unroll
+                for (int k = 0; k < kR; ++k) m[k] = 0u;
+#pragma unroll 8
+                for (int jj = 0; jj < 32; ++jj) {
+                    const float4 A = sm.A[b0 + jj];
+                    const float4 B = sm.B[b0 + jj];
+                    const float2 Cw = sm.Cw[b0 + jj];
+#pragma unroll
+                    for (int k = 0; k < kR; ++k) {
+                        const float sl = fmaf(xp[k], A.x, fmaf(yp[k], A.y, fmaf(zp[k], A.z, A.w)));
+                        const float sm_ = sl + Cw.x;                       // s + margin
+                        const float d2 = fmaf(xp[k], B.x, fmaf(yp[k], B.y, fmaf(zp[k], B.z, xx[k] + B.w)));
+                        const float n2 = fmaf(-sl, sl, d2);
+                        const float q = fmaf(sm_, sm_, beta);
+                        const float e = fmaf(alpha, n2, -q);
+                        uint32_t kb;
+                        if (WINDOW == GBT_WINDOW_LINE) {
+                            kb = __float_as_uint(e) & ~__float_as_uint(sm_);
+                        } else {
+                            const float a = sl + kWinMargin;
+                            const float bb = sl - Cw.y;
+                            kb = __float_as_uint(e) & ~__float_as_uint(a) & __float_as_uint(bb);
+                        }
+                        m[k] = __funnelshift_l(kb, m[k], 1);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kR; ++k) {
+                    uint32_t mm = (valid >> k) & 1u ? m[k] : 0u;
+                    if (p.stats) n_pre += __popc(mm);
+                    while (mm) {
+                        const int jj = __clz(mm);
+                        mm ^= 0x80000000u >> jj;
+                        const int j = b0 + jj;
+                        if (j >= nt) break;           // bits past the tile's end
+                        survivor<NF, WINDOW>(p, xa[k], ya[k], za[k], sm.cold, sm.A[j], j, tmp[k],
+                                             n_kept);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kR; ++k)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) fold<NF>(sm.acc[f][k][tid], tmp[k][f]);
+        }
+        if (!p.stats) {
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                if (ridx[k] < 0) continue;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (f >= p.nf) break;
+                    p.partial[((int64_t)split * p.nf + f) * p.n_recv + ridx[k]] = sm.acc[f][k][tid];
+                }
+            }
+        }
+        __syncthreads();
     }
     if (p.stats) {
         atomicAdd(&p.stats[1], (unsigned long long)n_pre);
         atomicAdd(&p.stats[2], (unsigned long long)n_kept);
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < kR; ++k) {
-        if (ridx[k] < 0) continue;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            if (f >= p.nf) break;
-            p.partial[((int64_t)split * p.nf + f) * p.n_recv + ridx[k]] = sm.acc[f][k][tid];
-        }
     }
 }
 
@@ -607,11 +623,16 @@ __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 template <int NF, int WINDOW>
-void launch_fwd(const FwdParams &p, dim3 grid, cudaStream_t s)
+void launch_fwd(const FwdParams &p, cudaStream_t s)
 {
     const size_t smem = sizeof(FwdSmem<NF>);
     GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gbs_fwd_kernel<NF, WINDOW>,
+                                                           kThreads, smem));
+    const int grid = std::max(1, std::min(p.n_items, std::max(per_sm, 1) * num_sms()));
+    GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
     if (!p.stats) timing_begin(s);
     gbs_fwd_kernel<NF, WINDOW><<<grid, kThreads, smem, s>>>(p);
     GBT_CUDA(cudaGetLastError());
@@ -619,12 +640,12 @@ void launch_fwd(const FwdParams &p, dim3 grid, cudaStream_t s)
 }
 
 template <int WINDOW>
-void launch_fwd_nf(const FwdParams &p, dim3 grid, cudaStream_t s)
+void launch_fwd_nf(const FwdParams &p, cudaStream_t s)
 {
-    if (p.nf <= 1) launch_fwd<1, WINDOW>(p, grid, s);
-    else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, grid, s);
-    else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, grid, s);
-    else launch_fwd<8, WINDOW>(p, grid, s);
+    if (p.nf <= 1) launch_fwd<1, WINDOW>(p, s);
+    else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, s);
+    else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, s);
+    else launch_fwd<8, WINDOW>(p, s);
 }
 
 }  // namespace
@@ -640,8 +661,12 @@ int choose_splits(const TraceDev &td, const gbt_sum_args &a)
         return (int)std::min<int64_t>(s, 4096);
     }
     const int64_t tiles = (a.n_recv + kTileRecv - 1) / kTileRecv;
-    int64_t s = (4 * (int64_t)num_sms() + tiles - 1) / (tiles > 0 ? tiles : 1);
+    const int64_t slots = 2 * (int64_t)num_sms();        // resident CTAs
+    int64_t s = (8 * slots + tiles - 1) / (tiles > 0 ? tiles : 1);
     s = std::max<int64_t>(1, std::min<int64_t>(s, (nseg_est + kTS - 1) / kTS));
+    // partial sums stay under ~1 GiB
+    const int64_t per_split = (int64_t)a.n_freq * std::max<int64_t>(a.n_recv, 1) * 16;
+    s = std::min<int64_t>(s, std::max<int64_t>(1, (1LL << 30) / per_split));
     return (int)std::min<int64_t>(s, 4096);
 }
 
@@ -654,6 +679,7 @@ size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits
 {
     size_t b = records_bytes(td);
     b += align_up((size_t)td.capacity * sizeof(double), 256);               // amp64
+    b += 256;                                                               // work counter
     const size_t part = (size_t)splits * a.n_freq * (size_t)a.n_recv;
     b += align_up(part * (a.precision == GBT_PRECISION_F64 ? sizeof(double2) : sizeof(float4)),
                   256);
@@ -669,6 +695,8 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
     w += records_bytes(td);
     double *amp64 = reinterpret_cast<double *>(w);
     w += align_up((size_t)td.capacity * sizeof(double), 256);
+    int *counter = reinterpret_cast<int *>(w);
+    w += 256;
     void *partial = w;
     const int32_t *n_seg_ptr = td.ray_off + td.n_rays;
 
@@ -740,9 +768,11 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
             q.splits = splits;
             q.partial = reinterpret_cast<float4 *>(partial);
             q.stats = stats;
-            dim3 grid((unsigned)((a.n_recv + kTileRecv - 1) / kTileRecv), (unsigned)splits);
-            if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, grid, s);
-            else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, grid, s);
+            const int64_t tiles = (a.n_recv + kTileRecv - 1) / kTileRecv;
+            q.n_items = (int)(tiles * splits);
+            q.work_counter = counter;
+            if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
+            else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
             if (stats) return;
         }
         ReduceParams rp{};

@@ -293,7 +293,7 @@ def source_desc(source, ray_begin: int = 0, ray_count: int = 0, dirs=None) -> gb
 class _CudaView:
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 2, "strides": None}
+                                         "data": (int(ptr), False), "version": 2, "strides": None}
 
 
 class Trace:
