@@ -485,7 +485,7 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const int64_t N = src->n_rays;
         const int64_t per_ray = (int64_t)(src->max_reflections + 1) *
-                                (80 /*compact*/ + 80 /*padded*/ + 4 * F_COUNT + 8 + 8);
+                                (80 /*compact*/ + 80 /*padded*/ + 4 * kRecFloats + 8 + 8);
         int64_t chunk = N;
         if (args->max_device_bytes > 0) {
             chunk = std::max<int64_t>(1, args->max_device_bytes / std::max<int64_t>(per_ray, 1));

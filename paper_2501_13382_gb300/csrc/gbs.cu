@@ -24,17 +24,23 @@
 //    merged in FP64 in a fixed order by a second kernel (deterministic).
 #include <math.h>
 
+#include <algorithm>
+
 #include "gbt_internal.h"
 
 namespace gbt {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kR = 2;                       // receivers per thread
-constexpr int kTileRecv = kThreads * kR;    // receivers per CTA
-constexpr int kTS = 128;                    // segments per shared-memory tile
+constexpr int kConsumerWarps = 15;          // compute warps per CTA (one CTA per SM)
+constexpr int kThreads = 32 * (kConsumerWarps + 1);   // + one producer warp
+constexpr int kStages = 8;                  // shared-memory ring of staged batches
+constexpr int kR = 2;                       // receivers per lane
+constexpr int kWarpRecv = 32 * kR;          // receivers per warp
+constexpr int kCtaRecv = kConsumerWarps * kWarpRecv;
+constexpr int kBatch = 32;                  // segments per staged batch
+constexpr long long kSpinLimit = 1LL << 22; // bounded mbarrier waits
+constexpr int kFoldEvery = 4;               // batches between float-float folds
 constexpr float kWinMargin = 0.01f;         // prefilter window slack (m)
-constexpr int kMaxNF = 8;
 
 struct FreqConst {
     float K_hi, K_lo;     // f / c in turns per metre, float-float
@@ -50,16 +56,17 @@ struct FwdParams {
     const int32_t *order;
     int64_t n_recv;
     const int32_t *n_seg_ptr;
-    const float *rec;          // SoA records, field f at rec + f * stride
-    int64_t stride;
+    const float *rec;          // AoS records, kRecFloats per segment
     int nf;
+    int uniform_b;             // all b equal: frequencies sorted by k, loop stops at first cull
     float cutoff;
     float pre_alpha, pre_beta; // prefilter: keep iff alpha n^2 <= s^2 + beta
     int splits;
-    int n_items;               // receiver tiles x splits
-    int *work_counter;         // zeroed before launch; CTAs take items from it
+    int64_t n_items;           // warp tiles x splits
+    int *work_counter;         // zeroed before launch; warps take items from it
     float4 *partial;           // [splits][nf][n_recv]: re_hi, im_hi, re_lo, im_lo
     unsigned long long *stats; // counting mode when non-null: [1] prefiltered, [2] kept
+    unsigned int *status;      // device status word (timeouts)
     FreqConst fc[GBT_MAX_FREQ];
 };
 
@@ -93,39 +100,130 @@ __device__ __forceinline__ float dop(float a, float b, float c, float d)
     return f + e;
 }
 
-struct ColdSmem {
-    float f[14][kTS];   // oxh oyh ozh oxl oyl ozl txl tyl tzl s0h s0l Lh Ll amp
-};
-enum { C_OXH = 0, C_OYH, C_OZH, C_OXL, C_OYL, C_OZL, C_TXL, C_TYL, C_TZL, C_S0H, C_S0L,
-       C_LH, C_LL, C_AMP };
+typedef unsigned long long f2x;   // two packed floats (lo = receiver 0, hi = receiver 1)
+__device__ __forceinline__ f2x pk(float a, float b)
+{
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2x v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c)
+{
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b)
+{
+    f2x r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b)
+{
+    f2x r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b)
+{
+    f2x r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 
-template <int NF>
-struct FwdSmem {
-    float4 A[kTS];            // tx, ty, tz, -o'.t
-    float4 B[kTS];            // -2o'x, -2o'y, -2o'z, |o'|^2
-    float2 Cw[kTS];           // s0 + margin, L + margin
-    ColdSmem cold;
-    float4 acc[NF][kR][kThreads];   // float-float accumulators per (f, receiver)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n"); }
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                 ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bulk copy (TMA) of `bytes` contiguous bytes into shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Bounded wait: true when the phase of `parity` completed; false on abort or
+// when the iteration limit ran out (then the device status word is flagged).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned int *status)
+{
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    atomicOr(status, STATUS_TIMEOUT);
+    *abort_flag = 1;
+    return false;
+}
+
+// Per-warp shared memory: a double-buffered raw batch and the batch's prefilter
+// (hot) and exact-path (cold) views relative to the warp's first receiver.
+enum { C_OXH = 0, C_OYH, C_OZH, C_OXL, C_OYL, C_OZL, C_TXL, C_TYL, C_TZL, C_S0H, C_S0L,
+       C_LH, C_LL, C_AMP, C_COUNT };
+struct WarpSmem {
+    float4 A[kBatch];               // tx, ty, tz, -o'.t   (exact path reads t_hi here)
+    // prefilter constants, each duplicated into both halves of a float pair:
+    // P[0..3] = t_x, t_y, t_z, -o'.t;  P[4..7] = 2a o'_x, 2a o'_y, 2a o'_z, beta - a |o'|^2;
+    // P[8] = s0 + margin, P[9] = L + margin
+    float4 P[kBatch][5];
+    float cold[C_COUNT][kBatch];
 };
 
 // Exact geometry of one (receiver, segment) pair in float-float; returns false
 // when the pair falls outside the window.
 template <int WINDOW>
-__device__ __forceinline__ bool exact_geometry(float x, float y, float z, const ColdSmem &c,
-                                               const float4 &A, int j, float &sh, float &sl,
-                                               float &n2)
+__device__ __forceinline__ bool exact_geometry(float x, float y, float z, const WarpSmem &w,
+                                               int j, float &sh, float &sl, float &n2)
 {
-    const float oxh = c.f[C_OXH][j], oyh = c.f[C_OYH][j], ozh = c.f[C_OZH][j];
+    const float oxh = w.cold[C_OXH][j], oyh = w.cold[C_OYH][j], ozh = w.cold[C_OZH][j];
+    const float4 A = w.A[j];
     const float thx = A.x, thy = A.y, thz = A.z;
-    const float tlx = c.f[C_TXL][j], tly = c.f[C_TYL][j], tlz = c.f[C_TZL][j];
+    const float tlx = w.cold[C_TXL][j], tly = w.cold[C_TYL][j], tlz = w.cold[C_TZL][j];
     // delta = x - o as (a + e)
     float ax, ex, ay, ey, az, ez;
     two_sum(x, -oxh, ax, ex);
     two_sum(y, -oyh, ay, ey);
     two_sum(z, -ozh, az, ez);
-    ex -= c.f[C_OXL][j];
-    ey -= c.f[C_OYL][j];
-    ez -= c.f[C_OZL][j];
+    ex -= w.cold[C_OXL][j];
+    ey -= w.cold[C_OYL][j];
+    ez -= w.cold[C_OZL][j];
     // s_loc = delta . t
     float p0 = ax * thx, p1 = ay * thy, p2 = az * thz;
     float r0 = fmaf(ax, tlx, fmaf(ex, thx, fmaf(ax, thx, -p0)));
@@ -137,11 +235,11 @@ __device__ __forceinline__ bool exact_geometry(float x, float y, float z, const 
     const float lo = (E1 + E2) + (r0 + r1 + r2);
     if (WINDOW == GBT_WINDOW_SEGMENT) {
         if (!(S + lo >= 0.0f)) return false;
-        if (!((S - c.f[C_LH][j]) + (lo - c.f[C_LL][j]) < 0.0f)) return false;
+        if (!((S - w.cold[C_LH][j]) + (lo - w.cold[C_LL][j]) < 0.0f)) return false;
     }
     float e3;
-    two_sum(c.f[C_S0H][j], S, sh, e3);
-    sl = e3 + (lo + c.f[C_S0L][j]);
+    two_sum(w.cold[C_S0H][j], S, sh, e3);
+    sl = e3 + (lo + w.cold[C_S0L][j]);
     if (WINDOW == GBT_WINDOW_LINE) {
         if (!(sh + sl >= 0.0f)) return false;
     }
@@ -153,214 +251,314 @@ __device__ __forceinline__ bool exact_geometry(float x, float y, float z, const 
     return true;
 }
 
-template <int NF, int WINDOW>
+// One beam's contribution at frequency f given D = s^2 + b^2 and 1/D.
+__device__ __forceinline__ void beam_term(const FreqConst &q, float sh, float sl, float n2,
+                                          float invD, float amp, float2 &acc)
+{
+    const float n2invD = n2 * invD;
+    const float ga = ex2_approx(-q.kb2l2e * n2invD);  // exp(-k b n^2 / (2 D))
+    // phase in turns: frac(K s) in float-float, plus K n^2 s / (2 D)
+    const float ph = q.K_hi * sh;
+    const float pe = fmaf(q.K_hi, sh, -ph);
+    const float corr = fmaf(q.K_hi, sl, fmaf(q.K_lo, sh, pe));
+    float tau = (ph - rintf(ph)) + corr;
+    tau = fmaf(q.halfK * n2invD, sh, tau);
+    tau = tau - rintf(tau);
+    float sn, cs;
+    __sincosf(6.283185307179586f * tau, &sn, &cs);
+    const float g = q.scale * amp * ga * invD;      // (s + i b) / D = 1 / E
+    acc.x = fmaf(g, fmaf(sh, cs, -q.b * sn), acc.x);
+    acc.y = fmaf(g, fmaf(sh, sn, q.b * cs), acc.y);
+}
+
+// All frequencies of one surviving (receiver, segment) pair, added to tmp.
+template <int NF, int WINDOW, bool STATS>
 __device__ __forceinline__ void survivor(const FwdParams &p, float x, float y, float z,
-                                         const ColdSmem &c, const float4 &A, int j,
-                                         float2 (&tmp)[NF], uint32_t &kept)
+                                         const WarpSmem &w, int j, float2 (&tmp)[NF],
+                                         uint32_t &kept)
 {
     float sh, sl, n2;
-    if (!exact_geometry<WINDOW>(x, y, z, c, A, j, sh, sl, n2)) return;
-    const float amp = c.f[C_AMP][j];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        if (f >= p.nf) break;
-        const FreqConst &q = p.fc[f];
-        const float D = fmaf(sh, sh, q.b2);
-        if (q.kb2 * n2 > p.cutoff * D) continue;          // Gaussian cutoff
-        if (p.stats) {
-            ++kept;
-            continue;
-        }
+    if (!exact_geometry<WINDOW>(x, y, z, w, j, sh, sl, n2)) return;
+    const float amp = w.cold[C_AMP][j];
+    if (p.uniform_b) {
+        // one b for all frequencies, sorted by k: the kept set is a prefix
+        const float D = fmaf(sh, sh, p.fc[0].b2);
         const float invD = rcp_approx(D);
-        const float n2invD = n2 * invD;
-        const float ga = ex2_approx(-q.kb2l2e * n2invD);  // exp(-k b n^2 / (2 D))
-        // phase in turns: frac(K s) in float-float, plus K n^2 s / (2 D)
-        const float ph = q.K_hi * sh;
-        const float pe = fmaf(q.K_hi, sh, -ph);
-        const float corr = fmaf(q.K_hi, sl, fmaf(q.K_lo, sh, pe));
-        float tau = (ph - rintf(ph)) + corr;
-        tau = fmaf(q.halfK * n2invD, sh, tau);
-        tau = tau - rintf(tau);
-        float sn, cs;
-        __sincosf(6.283185307179586f * tau, &sn, &cs);
-        const float g = q.scale * amp * ga * invD;      // (s + i b) / D = 1 / E
-        tmp[f].x = fmaf(g, fmaf(sh, cs, -q.b * sn), tmp[f].x);
-        tmp[f].y = fmaf(g, fmaf(sh, sn, q.b * cs), tmp[f].y);
+        const float r = n2 * invD;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f >= p.nf) break;
+            const FreqConst &q = p.fc[f];
+            if (q.kb2 * r > p.cutoff) break;
+            if (STATS) { ++kept; continue; }
+            beam_term(q, sh, sl, n2, invD, amp, tmp[f]);
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f >= p.nf) break;
+            const FreqConst &q = p.fc[f];
+            const float D = fmaf(sh, sh, q.b2);
+            if (q.kb2 * n2 > p.cutoff * D) continue;
+            if (STATS) { ++kept; continue; }
+            beam_term(q, sh, sl, n2, rcp_approx(D), amp, tmp[f]);
+        }
     }
 }
 
-template <int NF>
-__device__ __forceinline__ void fold(float4 &acc, float2 &t)
+// Adds an FP32 partial sum into a float-float accumulator (hi, hi, lo, lo).
+__device__ __forceinline__ void fold(float4 *acc, float2 &t)
 {
     if (t.x != 0.0f || t.y != 0.0f) {
+        float4 a = *acc;
         float s, e;
-        two_sum(acc.x, t.x, s, e);
-        acc.x = s;
-        acc.z += e;
-        two_sum(acc.y, t.y, s, e);
-        acc.y = s;
-        acc.w += e;
+        two_sum(a.x, t.x, s, e);
+        a.x = s;
+        a.z += e;
+        two_sum(a.y, t.y, s, e);
+        a.y = s;
+        a.w += e;
+        *acc = a;
         t = make_float2(0.0f, 0.0f);
     }
 }
 
-template <int NF, int WINDOW>
-__global__ void __launch_bounds__(kThreads, 2) gbs_fwd_kernel(const FwdParams p)
+// Turn lane's raw record into the prefilter view relative to (cx, cy, cz) and
+// the exact-path columns.
+__device__ __forceinline__ void stage_transform(WarpSmem &w, const float4 (&raw)[kRecFloats / 4],
+                                                int lane, bool valid, float cx, float cy, float cz,
+                                                float alpha, float beta)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    FwdSmem<NF> &sm = *reinterpret_cast<FwdSmem<NF> *>(smem_raw);
-    __shared__ int s_item;
+    const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2], r3 = raw[3], r4 = raw[4];
+    float4 *P = w.P[lane];
+    if (valid) {
+        const float ox = (r0.x - cx) + r2.x, oy = (r0.y - cy) + r2.y, oz = (r0.z - cz) + r2.z;
+        const float ot = fmaf(ox, r1.x, fmaf(oy, r1.y, oz * r1.z));
+        const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
+        const float a2 = 2.f * alpha;
+        w.A[lane] = make_float4(r1.x, r1.y, r1.z, -ot);
+        P[0] = make_float4(r1.x, r1.x, r1.y, r1.y);
+        P[1] = make_float4(r1.z, r1.z, -ot, -ot);
+        P[2] = make_float4(a2 * ox, a2 * ox, a2 * oy, a2 * oy);
+        const float c7 = fmaf(-alpha, oo, beta);
+        P[3] = make_float4(a2 * oz, a2 * oz, c7, c7);
+        const float s0m = r0.w + kWinMargin, Lm = r1.w + kWinMargin;
+        P[4] = make_float4(s0m, s0m, Lm, Lm);
+    } else {
+        // a record no receiver can keep: far behind its own start
+        w.A[lane] = make_float4(0.f, 0.f, 0.f, -1e15f);
+        P[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[1] = make_float4(0.f, 0.f, -1e15f, -1e15f);
+        P[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[4] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    w.cold[C_OXH][lane] = r0.x; w.cold[C_OYH][lane] = r0.y; w.cold[C_OZH][lane] = r0.z;
+    w.cold[C_S0H][lane] = r0.w;
+    w.cold[C_LH][lane] = r1.w;
+    w.cold[C_OXL][lane] = r2.x; w.cold[C_OYL][lane] = r2.y; w.cold[C_OZL][lane] = r2.z;
+    w.cold[C_S0L][lane] = r2.w;
+    w.cold[C_TXL][lane] = r3.x; w.cold[C_TYL][lane] = r3.y; w.cold[C_TZL][lane] = r3.z;
+    w.cold[C_LL][lane] = r3.w;
+    w.cold[C_AMP][lane] = r4.x;
+}
 
-    const int tid = threadIdx.x;
-    const int64_t n_seg = *p.n_seg_ptr;
-    const int64_t n_seg_tiles = (n_seg + kTS - 1) / kTS;
-    const float alpha = p.pre_alpha, beta = p.pre_beta;
-    uint32_t n_pre = 0, n_kept = 0;
+template <int NF>
+struct CtaSmem {
+    float4 raw[kStages][kBatch][kRecFloats / 4];   // TMA ring of staged record batches
+    WarpSmem w[kConsumerWarps];                     // per consumer warp
+    float4 acc[kConsumerWarps][NF][kR][32];         // float-float sums (re_hi, im_hi, re_lo, im_lo)
+    unsigned long long full[kStages], empty[kStages];
+    int item, abort_flag;
+};
 
-    // Persistent CTAs: each item is (receiver tile, split); split s covers the
-    // segment tiles s, s + splits, s + 2 splits, ... so every item sees a mix of
-    // ray directions and the work per item is even.
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(p.work_counter, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= p.n_items) break;
-        const int64_t tile_base = (int64_t)(item / p.splits) * kTileRecv;
-        const int split = item % p.splits;
+// One CTA per SM.  A producer warp streams record batches of the current item
+// (receiver tile of 960, segment split) into a ring of shared-memory stages
+// with bulk asynchronous copies; 15 consumer warps each turn a stage into
+// constants relative to their own first receiver, release the stage, and run
+// the prefilter and the exact path for their 64 receivers.  Warps wait for
+// each other only through the ring (8 batches of slack) and once per item.
+template <int NF, int WINDOW, bool STATS>
+__global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    CtaSmem<NF> &S = *reinterpret_cast<CtaSmem<NF> *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool producer = warp == kConsumerWarps;
 
-        // tile centre: the tile's first receiver
-        const int64_t c_idx = p.order ? p.order[tile_base] : tile_base;
-        const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
-
-        float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
-        int64_t ridx[kR];
-        uint32_t valid = 0;
-#pragma unroll
-        for (int k = 0; k < kR; ++k) {
-            const int64_t r = tile_base + (int64_t)tid * kR + k;
-            ridx[k] = -1;
-            xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
-            if (r < p.n_recv) {
-                const int64_t o = p.order ? p.order[r] : r;
-                ridx[k] = o;
-                xa[k] = p.recv[3 * o]; ya[k] = p.recv[3 * o + 1]; za[k] = p.recv[3 * o + 2];
-                xp[k] = xa[k] - cx; yp[k] = ya[k] - cy; zp[k] = za[k] - cz;
-                xx[k] = fmaf(xp[k], xp[k], fmaf(yp[k], yp[k], zp[k] * zp[k]));
-                valid |= 1u << k;
-            }
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(smem_addr(&S.full[st]), 1);
+            mbar_init(smem_addr(&S.empty[st]), kConsumerWarps);
         }
-#pragma unroll
-        for (int f = 0; f < NF; ++f)
-#pragma unroll
-            for (int k = 0; k < kR; ++k) sm.acc[f][k][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
 
-        float2 tmp[kR][NF];
-#pragma unroll
-        for (int k = 0; k < kR; ++k)
-#pragma unroll
-            for (int f = 0; f < NF; ++f) tmp[k][f] = make_float2(0.f, 0.f);
+    const int64_t n_seg = *p.n_seg_ptr;
+    const int64_t n_batches = (n_seg + kBatch - 1) / kBatch;
+    const float alpha = p.pre_alpha, beta = p.pre_beta;
+    volatile int *abort_flag = &S.abort_flag;
+    uint32_t n_pre = 0, n_kept = 0;
+    uint32_t g = 0;   // batches through the ring so far (same count in every role)
 
-        for (int64_t stile = split; stile < n_seg_tiles; stile += p.splits) {
-            const int64_t t0 = stile * kTS;
-            const int64_t seg_end = min(n_seg, t0 + kTS);
-            __syncthreads();
-            if (tid < kTS) {
-                const int64_t j = t0 + tid;
-                if (j < seg_end) {
-                    const float *R = p.rec;
-                    const int64_t st = p.stride;
-                    float oxh = R[F_OX * st + j], oyh = R[F_OY * st + j], ozh = R[F_OZ * st + j];
-                    float oxl = R[F_OXL * st + j], oyl = R[F_OYL * st + j], ozl = R[F_OZL * st + j];
-                    float tx = R[F_TX * st + j], ty = R[F_TY * st + j], tz = R[F_TZ * st + j];
-                    float ox = (oxh - cx) + oxl, oy = (oyh - cy) + oyl, oz = (ozh - cz) + ozl;
-                    float ot = fmaf(ox, tx, fmaf(oy, ty, oz * tz));
-                    sm.A[tid] = make_float4(tx, ty, tz, -ot);
-                    sm.B[tid] = make_float4(-2.f * ox, -2.f * oy, -2.f * oz,
-                                            fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
-                    float s0h = R[F_S0 * st + j], Lh = R[F_L * st + j];
-                    sm.Cw[tid] = make_float2(s0h + kWinMargin, Lh + kWinMargin);
-                    sm.cold.f[C_OXH][tid] = oxh; sm.cold.f[C_OYH][tid] = oyh;
-                    sm.cold.f[C_OZH][tid] = ozh;
-                    sm.cold.f[C_OXL][tid] = oxl; sm.cold.f[C_OYL][tid] = oyl;
-                    sm.cold.f[C_OZL][tid] = ozl;
-                    sm.cold.f[C_TXL][tid] = R[F_TXL * st + j];
-                    sm.cold.f[C_TYL][tid] = R[F_TYL * st + j];
-                    sm.cold.f[C_TZL][tid] = R[F_TZL * st + j];
-                    sm.cold.f[C_S0H][tid] = s0h;
-                    sm.cold.f[C_S0L][tid] = R[F_S0L * st + j];
-                    sm.cold.f[C_LH][tid] = Lh;
-                    sm.cold.f[C_LL][tid] = R[F_LL * st + j];
-                    sm.cold.f[C_AMP][tid] = R[F_AMP * st + j];
-                } else {
-                    // a record no receiver can keep: far behind its own start
-                    sm.A[tid] = make_float4(0.f, 0.f, 0.f, -1e15f);
-                    sm.B[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    sm.Cw[tid] = make_float2(0.f, 0.f);
+    for (;;) {
+        if (threadIdx.x == 0) S.item = atomicAdd(p.work_counter, 1);
+        __syncthreads();
+        const int64_t item = S.item;
+        if (item >= p.n_items || *abort_flag) break;
+        const int64_t tile_base = (item / p.splits) * kCtaRecv;
+        const int split = (int)(item % p.splits);
+        const uint32_t nb = split < n_batches ? (uint32_t)((n_batches - 1 - split) / p.splits + 1) : 0u;
+
+        if (producer) {
+            if (lane == 0) {
+                uint32_t issued = 0;
+                for (uint32_t k = 0; k < nb; ++k) {
+                    const uint32_t q = g + k, st = q % kStages, ph = (q / kStages) & 1u;
+                    if (!mbar_wait(smem_addr(&S.empty[st]), ph ^ 1u, abort_flag, p.status)) break;
+                    const int64_t b = split + (int64_t)k * p.splits;
+                    const int64_t nrec = min((int64_t)kBatch, n_seg - b * kBatch);
+                    const uint32_t bytes = (uint32_t)nrec * kRecFloats * 4;
+                    mbar_arrive_expect_tx(smem_addr(&S.full[st]), bytes);
+                    bulk_g2s(smem_addr(&S.raw[st][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
+                             smem_addr(&S.full[st]));
+                    ++issued;
                 }
-            }
-            __syncthreads();
-            const int nt = (int)(seg_end - t0);
-            for (int b0 = 0; b0 < nt; b0 += 32) {
-                uint32_t m[kR];
-#pragma unroll
-                for (int k = 0; k < kR; ++k) m[k] = 0u;
-#pragma unroll 8
-                for (int jj = 0; jj < 32; ++jj) {
-                    const float4 A = sm.A[b0 + jj];
-                    const float4 B = sm.B[b0 + jj];
-                    const float2 Cw = sm.Cw[b0 + jj];
-#pragma unroll
-                    for (int k = 0; k < kR; ++k) {
-                        const float sl = fmaf(xp[k], A.x, fmaf(yp[k], A.y, fmaf(zp[k], A.z, A.w)));
-                        const float sm_ = sl + Cw.x;                       // s + margin
-                        const float d2 = fmaf(xp[k], B.x, fmaf(yp[k], B.y, fmaf(zp[k], B.z, xx[k] + B.w)));
-                        const float n2 = fmaf(-sl, sl, d2);
-                        const float q = fmaf(sm_, sm_, beta);
-                        const float e = fmaf(alpha, n2, -q);
-                        uint32_t kb;
-                        if (WINDOW == GBT_WINDOW_LINE) {
-                            kb = __float_as_uint(e) & ~__float_as_uint(sm_);
-                        } else {
-                            const float a = sl + kWinMargin;
-                            const float bb = sl - Cw.y;
-                            kb = __float_as_uint(e) & ~__float_as_uint(a) & __float_as_uint(bb);
-                        }
-                        m[k] = __funnelshift_l(kb, m[k], 1);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < kR; ++k) {
-                    uint32_t mm = (valid >> k) & 1u ? m[k] : 0u;
-                    if (p.stats) n_pre += __popc(mm);
-                    while (mm) {
-                        const int jj = __clz(mm);
-                        mm ^= 0x80000000u >> jj;
-                        const int j = b0 + jj;
-                        if (j >= nt) break;           // bits past the tile's end
-                        survivor<NF, WINDOW>(p, xa[k], ya[k], za[k], sm.cold, sm.A[j], j, tmp[k],
-                                             n_kept);
+                if (*abort_flag) {
+                    // let every copy still in flight land before leaving
+                    const uint32_t first = issued > (uint32_t)kStages ? issued - kStages : 0u;
+                    for (uint32_t k = first; k < issued; ++k) {
+                        const uint32_t q = g + k;
+                        for (long long it = 0; it < kSpinLimit; ++it)
+                            if (mbar_try_wait(smem_addr(&S.full[q % kStages]), (q / kStages) & 1u)) break;
                     }
                 }
             }
+        } else {
+            WarpSmem &w = S.w[warp];
+            const int64_t wbase = tile_base + (int64_t)warp * kWarpRecv;
+            const bool warp_live = wbase < p.n_recv;
+            // warp centre: the warp's first receiver
+            const int64_t c_idx = warp_live ? (p.order ? p.order[wbase] : wbase) : 0;
+            const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
+
+            float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
+            int32_t ridx[kR];
+            uint32_t valid = 0;
+            float4 *const part_base = p.partial + (int64_t)split * p.nf * p.n_recv;
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                const int64_t r = wbase + (int64_t)lane * kR + k;
+                xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
+                ridx[k] = -1;
+                if (r < p.n_recv) {
+                    const int64_t o = p.order ? p.order[r] : r;
+                    xa[k] = p.recv[3 * o]; ya[k] = p.recv[3 * o + 1]; za[k] = p.recv[3 * o + 2];
+                    xp[k] = xa[k] - cx; yp[k] = ya[k] - cy; zp[k] = za[k] - cz;
+                    xx[k] = fmaf(xp[k], xp[k], fmaf(yp[k], yp[k], zp[k] * zp[k]));
+                    valid |= 1u << k;
+                    ridx[k] = (int32_t)o;
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f) S.acc[warp][f][k][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            static_assert(kR == 2, "the paired prefilter handles two receivers per lane");
+            const f2x X2 = pk(xp[0], xp[1]), Y2 = pk(yp[0], yp[1]), Z2 = pk(zp[0], zp[1]);
+            const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
+            const f2x AL2 = pk(alpha, alpha);
+            const f2x MG2 = pk(kWinMargin, kWinMargin);
+            float2 tmp[kR][NF];
 #pragma unroll
             for (int k = 0; k < kR; ++k)
 #pragma unroll
-                for (int f = 0; f < NF; ++f) fold<NF>(sm.acc[f][k][tid], tmp[k][f]);
-        }
-        if (!p.stats) {
+                for (int f = 0; f < NF; ++f) tmp[k][f] = make_float2(0.f, 0.f);
+
+            for (uint32_t kb_ = 0; kb_ < nb; ++kb_) {
+                const uint32_t q = g + kb_, st = q % kStages, ph = (q / kStages) & 1u;
+                if (!mbar_wait(smem_addr(&S.full[st]), ph, abort_flag, p.status)) break;
+                const int64_t b = split + (int64_t)kb_ * p.splits;
+                stage_transform(w, S.raw[st][lane], lane, b * kBatch + lane < n_seg, cx, cy, cz,
+                                alpha, beta);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&S.empty[st]));
+                if (!warp_live) continue;
+
+                // ---- prefilter: one keep bit per (receiver, segment); segment jj at bit 31 - jj.
+                // Both receivers of the lane go through paired FP32 instructions:
+                //   s_loc = x'.t - o'.t,  sm = s_loc + s0 + margin,
+                //   g = sm^2 + beta - alpha |x' - o'|^2 + alpha s_loc^2  (= q - alpha n^2),
+                // keep iff g >= 0 and the window test holds.
+                uint32_t m[kR];
 #pragma unroll
-            for (int k = 0; k < kR; ++k) {
-                if (ridx[k] < 0) continue;
+                for (int k = 0; k < kR; ++k) m[k] = 0u;
+#pragma unroll 4
+                for (int jj = 0; jj < kBatch; ++jj) {
+                    const float4 *P = w.P[jj];
+                    const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3], p4 = P[4];
+                    const f2x TX = pk(p0.x, p0.y), TY = pk(p0.z, p0.w), TZ = pk(p1.x, p1.y);
+                    const f2x OT = pk(p1.z, p1.w);
+                    const f2x OX = pk(p2.x, p2.y), OY = pk(p2.z, p2.w), OZ = pk(p3.x, p3.y);
+                    const f2x C7 = pk(p3.z, p3.w), S0 = pk(p4.x, p4.y);
+                    const f2x sl = fma2(X2, TX, fma2(Y2, TY, fma2(Z2, TZ, OT)));
+                    const f2x sm2 = add2(sl, S0);
+                    const f2x nd = fma2(X2, OX, fma2(Y2, OY, fma2(Z2, OZ, add2(NAXX, C7))));
+                    const f2x gg = fma2(mul2(sl, AL2), sl, fma2(sm2, sm2, nd));
+                    float g0, g1, s0_, s1_;
+                    upk(gg, g0, g1);
+                    uint32_t kb0, kb1;
+                    if (WINDOW == GBT_WINDOW_LINE) {
+                        upk(sm2, s0_, s1_);
+                        kb0 = ~(__float_as_uint(g0) | __float_as_uint(s0_));
+                        kb1 = ~(__float_as_uint(g1) | __float_as_uint(s1_));
+                    } else {
+                        const f2x a = add2(sl, MG2);
+                        const f2x bb = sub2(sl, pk(p4.z, p4.w));
+                        float a0, a1, b0_, b1_;
+                        upk(a, a0, a1);
+                        upk(bb, b0_, b1_);
+                        kb0 = ~(__float_as_uint(g0) | __float_as_uint(a0)) & __float_as_uint(b0_);
+                        kb1 = ~(__float_as_uint(g1) | __float_as_uint(a1)) & __float_as_uint(b1_);
+                    }
+                    m[0] = __funnelshift_l(kb0, m[0], 1);
+                    m[1] = __funnelshift_l(kb1, m[1], 1);
+                }
+                // ---- survivors, in segment order per receiver
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if (f >= p.nf) break;
-                    p.partial[((int64_t)split * p.nf + f) * p.n_recv + ridx[k]] = sm.acc[f][k][tid];
+                for (int k = 0; k < kR; ++k) {
+                    uint32_t mm = ((valid >> k) & 1u) ? m[k] : 0u;
+                    if (STATS) n_pre += __popc(mm);
+                    while (mm) {
+                        const int jj = __clz(mm);
+                        mm ^= 0x80000000u >> jj;
+                        survivor<NF, WINDOW, STATS>(p, xa[k], ya[k], za[k], w, jj, tmp[k], n_kept);
+                    }
+                }
+                if (!STATS && (kb_ % kFoldEvery) == kFoldEvery - 1) {
+#pragma unroll
+                    for (int k = 0; k < kR; ++k)
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) fold(&S.acc[warp][f][k][lane], tmp[k][f]);
+                }
+                __syncwarp();
+            }
+            if (!STATS) {
+#pragma unroll
+                for (int k = 0; k < kR; ++k) {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        fold(&S.acc[warp][f][k][lane], tmp[k][f]);
+                        if (f < p.nf && ridx[k] >= 0)
+                            part_base[(int64_t)f * p.n_recv + ridx[k]] = S.acc[warp][f][k][lane];
+                    }
                 }
             }
         }
+        g += nb;
         __syncthreads();
     }
-    if (p.stats) {
+    if (STATS && !producer) {
         atomicAdd(&p.stats[1], (unsigned long long)n_pre);
         atomicAdd(&p.stats[2], (unsigned long long)n_kept);
     }
@@ -377,7 +575,6 @@ struct PrepParams {
     double w_default;
     int n_materials;
     float *rec;
-    int64_t stride;
     // F64 path records (nullptr when not needed)
     double *amp64;
     unsigned int *status;
@@ -407,18 +604,19 @@ __global__ void prepass_kernel(PrepParams p)
     }
     const double w = p.weight ? (double)p.weight[p.ray[j]] : p.w_default;
     const double amp = w * g;
-    float *R = p.rec;
-    const int64_t st = p.stride;
-    float h, l;
-    split_ff(p.o[3 * j + 0], h, l); R[F_OX * st + j] = h; R[F_OXL * st + j] = l;
-    split_ff(p.o[3 * j + 1], h, l); R[F_OY * st + j] = h; R[F_OYL * st + j] = l;
-    split_ff(p.o[3 * j + 2], h, l); R[F_OZ * st + j] = h; R[F_OZL * st + j] = l;
-    split_ff(p.t[3 * j + 0], h, l); R[F_TX * st + j] = h; R[F_TXL * st + j] = l;
-    split_ff(p.t[3 * j + 1], h, l); R[F_TY * st + j] = h; R[F_TYL * st + j] = l;
-    split_ff(p.t[3 * j + 2], h, l); R[F_TZ * st + j] = h; R[F_TZL * st + j] = l;
-    split_ff(p.s0[j], h, l); R[F_S0 * st + j] = h; R[F_S0L * st + j] = l;
-    split_ff(p.L[j], h, l); R[F_L * st + j] = h; R[F_LL * st + j] = l;
-    R[F_AMP * st + j] = (float)amp;
+    float4 *R = reinterpret_cast<float4 *>(p.rec + j * kRecFloats);
+    float oh[3], ol[3], th[3], tl[3], s0h, s0l, Lh, Ll;
+    for (int a = 0; a < 3; ++a) {
+        split_ff(p.o[3 * j + a], oh[a], ol[a]);
+        split_ff(p.t[3 * j + a], th[a], tl[a]);
+    }
+    split_ff(p.s0[j], s0h, s0l);
+    split_ff(p.L[j], Lh, Ll);
+    R[0] = make_float4(oh[0], oh[1], oh[2], s0h);     // R_OXH .. R_S0H
+    R[1] = make_float4(th[0], th[1], th[2], Lh);      // R_TXH .. R_LH
+    R[2] = make_float4(ol[0], ol[1], ol[2], s0l);     // R_OXL .. R_S0L
+    R[3] = make_float4(tl[0], tl[1], tl[2], Ll);      // R_TXL .. R_LL
+    R[4] = make_float4((float)amp, 0.f, 0.f, 0.f);    // R_AMP
     if (p.amp64) p.amp64[j] = amp;
 }
 
@@ -512,6 +710,8 @@ __global__ void __launch_bounds__(kThreads64) gbs_fwd_f64_kernel(const F64Params
 
 struct ReduceParams {
     int64_t n;                 // nf * n_recv
+    int64_t n_recv;
+    int perm[GBT_MAX_FREQ];    // partial frequency slot -> output frequency
     int splits;
     const float4 *p32;
     const double2 *p64;
@@ -535,12 +735,14 @@ __global__ void reduce_kernel(ReduceParams p)
             im += v.y;
         }
     }
+    const int64_t f = i / p.n_recv, r = i - f * p.n_recv;
+    const int64_t oi = (int64_t)p.perm[f] * p.n_recv + r;
     if (p.accumulate) {
-        const float2 o = p.out[i];
+        const float2 o = p.out[oi];
         re += (double)o.x;
         im += (double)o.y;
     }
-    p.out[i] = make_float2((float)re, (float)im);
+    p.out[oi] = make_float2((float)re, (float)im);
 }
 
 // ------------------------------------------------------ receiver order --
@@ -622,21 +824,30 @@ __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+template <int NF, int WINDOW, bool STATS>
+void launch_fwd_t(const FwdParams &p, cudaStream_t s)
+{
+    const size_t smem = sizeof(CtaSmem<NF>);
+    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, STATS>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, gbs_fwd_kernel<NF, WINDOW, STATS>, kThreads, smem));
+    if (per_sm < 1) fail(GBT_ERR_UNSUPPORTED, "GBS kernel does not fit on one SM");
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(p.n_items, (int64_t)std::max(per_sm, 1) * num_sms()));
+    GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
+    if (!STATS) timing_begin(s);
+    gbs_fwd_kernel<NF, WINDOW, STATS><<<grid, kThreads, smem, s>>>(p);
+    GBT_CUDA(cudaGetLastError());
+    if (!STATS) timing_end(s);
+}
+
 template <int NF, int WINDOW>
 void launch_fwd(const FwdParams &p, cudaStream_t s)
 {
-    const size_t smem = sizeof(FwdSmem<NF>);
-    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gbs_fwd_kernel<NF, WINDOW>,
-                                                           kThreads, smem));
-    const int grid = std::max(1, std::min(p.n_items, std::max(per_sm, 1) * num_sms()));
-    GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
-    if (!p.stats) timing_begin(s);
-    gbs_fwd_kernel<NF, WINDOW><<<grid, kThreads, smem, s>>>(p);
-    GBT_CUDA(cudaGetLastError());
-    if (!p.stats) timing_end(s);
+    if (p.stats) launch_fwd_t<NF, WINDOW, true>(p, s);
+    else launch_fwd_t<NF, WINDOW, false>(p, s);
 }
 
 template <int WINDOW>
@@ -660,10 +871,10 @@ int choose_splits(const TraceDev &td, const gbt_sum_args &a)
         s = std::max<int64_t>(1, std::min<int64_t>(s, (nseg_est + kTS64 - 1) / kTS64));
         return (int)std::min<int64_t>(s, 4096);
     }
-    const int64_t tiles = (a.n_recv + kTileRecv - 1) / kTileRecv;
-    const int64_t slots = 2 * (int64_t)num_sms();        // resident CTAs
+    const int64_t tiles = (a.n_recv + kCtaRecv - 1) / kCtaRecv;         // CTA tiles
+    const int64_t slots = (int64_t)num_sms();                           // resident CTAs
     int64_t s = (8 * slots + tiles - 1) / (tiles > 0 ? tiles : 1);
-    s = std::max<int64_t>(1, std::min<int64_t>(s, (nseg_est + kTS - 1) / kTS));
+    s = std::max<int64_t>(1, std::min<int64_t>(s, (nseg_est + kBatch - 1) / kBatch));
     // partial sums stay under ~1 GiB
     const int64_t per_split = (int64_t)a.n_freq * std::max<int64_t>(a.n_recv, 1) * 16;
     s = std::min<int64_t>(s, std::max<int64_t>(1, (1LL << 30) / per_split));
@@ -672,7 +883,7 @@ int choose_splits(const TraceDev &td, const gbt_sum_args &a)
 
 static size_t records_bytes(const TraceDev &td)
 {
-    return align_up((size_t)F_COUNT * align_up((size_t)td.capacity, 64) * sizeof(float), 256);
+    return align_up((size_t)kRecFloats * (size_t)td.capacity * sizeof(float), 256);
 }
 
 size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits)
@@ -691,7 +902,6 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
 {
     char *w = static_cast<char *>(work);
     float *rec = reinterpret_cast<float *>(w);
-    const int64_t stride = (int64_t)align_up((size_t)td.capacity, 64);
     w += records_bytes(td);
     double *amp64 = reinterpret_cast<double *>(w);
     w += align_up((size_t)td.capacity * sizeof(double), 256);
@@ -710,7 +920,6 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         pp.w_default = 4.0 * kPi / (double)td.n_fan;
         pp.n_materials = sd.n_materials;
         pp.rec = rec;
-        pp.stride = stride;
         pp.amp64 = amp64;
         pp.status = status_word();
         prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
@@ -718,6 +927,8 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
     }
 
     const int64_t nout = (int64_t)a.n_freq * a.n_recv;
+    int fperm[GBT_MAX_FREQ];
+    for (int f = 0; f < GBT_MAX_FREQ; ++f) fperm[f] = f;
     if (a.n_recv > 0) {
         if (a.precision == GBT_PRECISION_F64) {
             F64Params q{};
@@ -743,14 +954,24 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
             q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
             q.n_seg_ptr = n_seg_ptr;
             q.rec = rec;
-            q.stride = stride;
             q.nf = a.n_freq;
             q.cutoff = (float)a.cutoff;
+            // frequency order: when every b is equal, sort by k so that the kept
+            // frequencies of a pair form a prefix (wider beams first)
+            int perm[GBT_MAX_FREQ];
+            for (int f = 0; f < a.n_freq; ++f) perm[f] = f;
+            bool uniform = true;
+            for (int f = 1; f < a.n_freq; ++f) uniform = uniform && a.beam_b[f] == a.beam_b[0];
+            if (uniform)
+                std::stable_sort(perm, perm + a.n_freq,
+                                 [&](int x, int y) { return a.freq_hz[x] < a.freq_hz[y]; });
+            q.uniform_b = uniform ? 1 : 0;
             double amin = 1e300, bmax = 0.0;
             for (int f = 0; f < a.n_freq; ++f) {
-                const double K = a.freq_hz[f] / sd.c;       // turns per metre
+                const int g = perm[f];
+                const double K = a.freq_hz[g] / sd.c;       // turns per metre
                 const double k = 2.0 * kPi * K;
-                const double b = a.beam_b[f];
+                const double b = a.beam_b[g];
                 FreqConst &c = q.fc[f];
                 c.K_hi = (float)K;
                 c.K_lo = (float)(K - (double)c.K_hi);
@@ -768,15 +989,19 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
             q.splits = splits;
             q.partial = reinterpret_cast<float4 *>(partial);
             q.stats = stats;
-            const int64_t tiles = (a.n_recv + kTileRecv - 1) / kTileRecv;
-            q.n_items = (int)(tiles * splits);
+            const int64_t tiles = (a.n_recv + kCtaRecv - 1) / kCtaRecv;
+            q.n_items = tiles * splits;
+            q.status = status_word();
             q.work_counter = counter;
             if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
             else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
             if (stats) return;
+            for (int f = 0; f < a.n_freq; ++f) fperm[f] = perm[f];
         }
         ReduceParams rp{};
         rp.n = nout;
+        rp.n_recv = a.n_recv;
+        for (int f = 0; f < GBT_MAX_FREQ; ++f) rp.perm[f] = fperm[f];
         rp.splits = splits;
         rp.p32 = a.precision == GBT_PRECISION_F64 ? nullptr : reinterpret_cast<float4 *>(partial);
         rp.p64 = a.precision == GBT_PRECISION_F64 ? reinterpret_cast<double2 *>(partial) : nullptr;

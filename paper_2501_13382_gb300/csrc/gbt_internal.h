@@ -63,17 +63,16 @@ struct SceneDev {
     int32_t *mat_host_max = nullptr;
 };
 
-// Segment kernel records (FP32 hi/lo split of the FP64 canonical segments),
-// structure of arrays with `stride` elements per field.
-enum SegField {
-    F_OX = 0, F_OY, F_OZ,            // origin, hi part
-    F_OXL, F_OYL, F_OZL,             // origin, lo part
-    F_TX, F_TY, F_TZ,                // unit direction, hi
-    F_TXL, F_TYL, F_TZL,             // unit direction, lo
-    F_S0, F_S0L,                     // start arclength hi, lo
-    F_L, F_LL,                       // length hi, lo
-    F_AMP,                           // W_ray * Gamma_path
-    F_COUNT
+// Segment kernel record: the FP64 canonical segment split into float-float
+// (hi, lo) pairs, 20 floats (80 bytes, 16-byte aligned) per segment, array of
+// structures so one warp stages 32 consecutive records with 16-byte copies.
+enum RecField {
+    R_OXH = 0, R_OYH, R_OZH, R_S0H,      // origin hi, start arclength hi
+    R_TXH, R_TYH, R_TZH, R_LH,           // unit direction hi, length hi
+    R_OXL, R_OYL, R_OZL, R_S0L,          // lo parts
+    R_TXL, R_TYL, R_TZL, R_LL,
+    R_AMP,                               // W_ray * Gamma_path
+    kRecFloats = 20
 };
 
 struct TraceDev {

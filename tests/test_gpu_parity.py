@@ -207,7 +207,7 @@ def test_chunked_solve_equals_single_pass(G):
     gam = _dev(w.scene.gamma, torch.float32)
     args = (sc, w.sources[0], r, list(w.freqs), list(w.beam_b[0]), gam)
     one = G.gbs_solve(*args, window=w.window).cpu().numpy()
-    per_ray = (w.sources[0].max_reflections + 1) * (80 + 80 + 4 * 17 + 16)
+    per_ray = (w.sources[0].max_reflections + 1) * (80 + 80 + 4 * 20 + 16)
     many = G.gbs_solve(*args, window=w.window, max_device_bytes=per_ray * 1700).cpu().numpy()
     assert rel_l2(many, one) < 1e-6
     _, po = O.solve(w)
