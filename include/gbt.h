@@ -193,6 +193,22 @@ gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *str
  * in one warp see similar beams, which keeps the warp's lanes busy. */
 gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out, void *stream);
 
+/* Same result as gbt_recv_order (the identical permutation), for callers that
+ * cannot allocate device memory when they need it: hosts that own every
+ * device allocation and forbid libraries from calling the CUDA allocator, or
+ * latency-critical loops that must not allocate because an allocation may
+ * block or fail.  The paper has no counterpart; this is a library service.
+ * Allocates nothing: the sort's scratch is a fixed 8 MiB device array inside
+ * the library, held by every GPU that loads it until the process exits.
+ * n_recv must be <= 1,048,576 (GBT_ERR_INVALID_ARG otherwise, before any
+ * work).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and every call clears what it needs, but calls
+ * that overlap on the GPU race on it: order them on one stream (or wait
+ * between them).  recv and order_out are device pointers owned by the caller. */
+gbt_status gbt_recv_order_noalloc(const float *recv, int64_t n_recv, int32_t *order_out,
+                                  void *stream);
+
 /* ------------------------------------------------------------ backward --
  * Adjoint of gbt_sum for a real loss L.  grad_out (device, n_freq * n_recv
  * complex64) holds g = dL/dRe p + i dL/dIm p.  Writes (overwrites)

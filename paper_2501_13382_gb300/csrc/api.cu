@@ -456,6 +456,17 @@ gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out,
     });
 }
 
+gbt_status gbt_recv_order_noalloc(const float *recv, int64_t n_recv, int32_t *order_out,
+                                  void *stream)
+{
+    return guarded([&] {
+        GBT_REQUIRE(n_recv >= 0, "n_recv must be >= 0");
+        if (n_recv == 0) return;
+        GBT_REQUIRE(recv && order_out, "recv and order_out must be non-NULL");
+        recv_order_noalloc_launch(recv, n_recv, order_out, static_cast<cudaStream_t>(stream));
+    });
+}
+
 gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
                             const float *grad_out, float *grad_gamma, float *grad_ray_weight,
                             double *grad_b, void *stream)

@@ -25,6 +25,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "gbt_internal.h"
 
@@ -1027,6 +1029,70 @@ void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scrat
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch);
     unsigned int *bb = reinterpret_cast<unsigned int *>(
         static_cast<char *>(scratch) + align_up((size_t)npad * sizeof(unsigned long long), 256));
+    GBT_CUDA(cudaMemsetAsync(bb, 0xff, 3 * sizeof(unsigned int), s));
+    GBT_CUDA(cudaMemsetAsync(bb + 3, 0x00, 3 * sizeof(unsigned int), s));
+    bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(recv, n, bb);
+    const unsigned g = (unsigned)((npad + 255) / 256);
+    morton_kernel<<<g, 256, 0, s>>>(recv, n, npad, bb, keys);
+    for (int64_t k = 2; k <= npad; k <<= 1)
+        for (int64_t j = k >> 1; j > 0; j >>= 1) bitonic_step<<<g, 256, 0, s>>>(keys, npad, j, k);
+    extract_order<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, order);
+    GBT_CUDA(cudaGetLastError());
+}
+
+
+// ------------------------------------------------- receiver order, no allocation --
+//
+// Some callers cannot allocate device memory at the point where they need a
+// receiver order: a host application that owns every device allocation and
+// forbids libraries from calling the CUDA allocator, or a latency-critical
+// loop (a real-time auralisation thread, for example) that must not call an
+// allocator because an allocation may block or fail under memory pressure.
+// For them the sort's scratch lives in a fixed device array below.  The array
+// is part of the library image: every GPU that loads the library holds it
+// (8 MiB + 256 bytes) until the process exits.  Its contents persist between
+// calls, so everything that must start at zero is cleared on each call, and
+// calls that overlap on the GPU share (and race on) the array.
+constexpr int64_t kNoAllocMaxRecv = 1 << 20;
+static __device__ __align__(256) unsigned char
+    g_order_scratch[kNoAllocMaxRecv * sizeof(unsigned long long) + 256];
+
+namespace {
+std::mutex g_order_scratch_mu;
+void *g_order_scratch_dev[64] = {};
+}  // namespace
+
+void recv_order_noalloc_launch(const float *recv, int64_t n, int32_t *order, cudaStream_t s)
+{
+    if (n > kNoAllocMaxRecv)
+        fail(GBT_ERR_INVALID_ARG, "gbt_recv_order_noalloc handles at most 1048576 receivers (got " +
+                                      std::to_string(n) + ")");
+    if (n <= 0) return;
+    int dev = 0;
+    GBT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(GBT_ERR_UNSUPPORTED, "device index >= 64");
+    void *base = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side name of
+        // the array is not a device address, so ask the runtime for the address
+        std::lock_guard<std::mutex> lk(g_order_scratch_mu);
+        if (!g_order_scratch_dev[dev]) {
+            void *ptr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_order_scratch);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                fail(GBT_ERR_CUDA, std::string("cudaGetSymbolAddress(order scratch): ") +
+                                       cudaGetErrorString(e));
+            }
+            g_order_scratch_dev[dev] = ptr;
+        }
+        base = g_order_scratch_dev[dev];
+    }
+    int64_t npad = 1;
+    while (npad < n) npad <<= 1;
+    unsigned long long *keys = static_cast<unsigned long long *>(base);
+    unsigned int *bb = reinterpret_cast<unsigned int *>(
+        static_cast<char *>(base) + align_up((size_t)npad * sizeof(unsigned long long), 256));
     GBT_CUDA(cudaMemsetAsync(bb, 0xff, 3 * sizeof(unsigned int), s));
     GBT_CUDA(cudaMemsetAsync(bb + 3, 0x00, 3 * sizeof(unsigned int), s));
     bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(recv, n, bb);

@@ -102,6 +102,7 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
 void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scratch,
                        cudaStream_t s);
 size_t recv_order_scratch_bytes(int64_t n);
+void recv_order_noalloc_launch(const float *recv, int64_t n, int32_t *order, cudaStream_t s);
 
 // ---- backward (gbs_bwd.cu) ----
 size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a);

@@ -95,6 +95,7 @@ _SIGS = {
     "gbt_trace_destroy": (C.c_int, [C.c_void_p]),
     "gbt_sum": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.c_void_p]),
     "gbt_recv_order": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "gbt_recv_order_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "gbt_sum_backward": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "gbt_solve": (C.c_int, [C.c_void_p, C.POINTER(gbt_source_desc), C.POINTER(gbt_sum_args),
@@ -194,6 +195,13 @@ def gbt_sum(trace: int, args: gbt_sum_args, stream: int = 0):
 def gbt_recv_order(recv_ptr: int, n: int, order_ptr: int, stream: int = 0):
     _check(load().gbt_recv_order(C.c_void_p(recv_ptr), C.c_int64(n), C.c_void_p(order_ptr),
                                  C.c_void_p(stream)), "gbt_recv_order")
+
+
+def gbt_recv_order_noalloc(recv_ptr: int, n: int, order_ptr: int, stream: int = 0):
+    """gbt_recv_order without any device allocation (fixed scratch inside the library;
+    n <= 1,048,576; calls that overlap on the GPU race on that scratch)."""
+    _check(load().gbt_recv_order_noalloc(C.c_void_p(recv_ptr), C.c_int64(n), C.c_void_p(order_ptr),
+                                         C.c_void_p(stream)), "gbt_recv_order_noalloc")
 
 
 def gbt_sum_backward(trace: int, args: gbt_sum_args, grad_out: int, grad_gamma: int,
