@@ -26,7 +26,6 @@ SOURCES = {
     "api.cu": [],
     "trace.cu": ["--fmad=false"],
     "gbs.cu": [],
-    "gbs_bwd.cu": [],
     "batch.cu": [],
 }
 HEADERS = ["gbt_internal.h"]

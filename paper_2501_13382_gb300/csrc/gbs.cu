@@ -41,6 +41,7 @@ constexpr int kWarpRecv = 32 * kR;          // receivers per warp
 constexpr int kCtaRecv = kConsumerWarps * kWarpRecv;
 constexpr int kBatch = 32;                  // segments per staged batch
 constexpr long long kSpinLimit = 1LL << 22; // bounded mbarrier waits
+enum { kFwd = 0, kStats = 1, kBwd = 2 };    // what the pair kernel does with survivors
 constexpr int kFoldEvery = 4;               // batches between float-float folds
 constexpr float kWinMargin = 0.01f;         // prefilter window slack (m)
 
@@ -51,6 +52,7 @@ struct FreqConst {
     float kb2l2e;         // k b / 2 * log2(e)
     float b, b2;          // b, b^2
     float scale;          // k b / (8 pi^2)
+    float kh, invb;       // k / 2, 1 / b  (adjoint)
 };
 
 struct FwdParams {
@@ -69,6 +71,12 @@ struct FwdParams {
     float4 *partial;           // [splits][nf][n_recv]: re_hi, im_hi, re_lo, im_lo
     unsigned long long *stats; // counting mode when non-null: [1] prefiltered, [2] kept
     unsigned int *status;      // device status word (timeouts)
+    // adjoint mode
+    const float2 *grad_out;    // g = dL/dRe p + i dL/dIm p, [user frequency][n_recv]
+    float *seg_G;              // per segment: sum over (r, f) of Re(conj(g) c~)
+    float *seg_H;              // per (sorted frequency, segment): sum over r of Re(conj(g) dc~/db)
+    int64_t seg_stride;        // stride of seg_H rows
+    int fperm[GBT_MAX_FREQ];   // sorted frequency slot -> user frequency index
     FreqConst fc[GBT_MAX_FREQ];
 };
 
@@ -273,6 +281,32 @@ __device__ __forceinline__ void beam_term(const FreqConst &q, float sh, float sl
     acc.y = fmaf(g, fmaf(sh, sn, q.b * cs), acc.y);
 }
 
+// Adjoint terms of one beam: with c~ the contribution without W Gamma_path,
+// G += Re(conj(g) c~) and H += Re(conj(g) dc~/db), where
+// d log c / db = 1/b + i/E - k n^2 / (2 E^2), E = s - i b.
+__device__ __forceinline__ void beam_adjoint(const FreqConst &q, float sh, float sl, float n2,
+                                             float invD, float2 g, float &G, float &H)
+{
+    const float n2invD = n2 * invD;
+    const float ga = ex2_approx(-q.kb2l2e * n2invD);
+    const float ph = q.K_hi * sh;
+    const float pe = fmaf(q.K_hi, sh, -ph);
+    const float corr = fmaf(q.K_hi, sl, fmaf(q.K_lo, sh, pe));
+    float tau = (ph - rintf(ph)) + corr;
+    tau = fmaf(q.halfK * n2invD, sh, tau);
+    tau = tau - rintf(tau);
+    float sn, cs;
+    __sincosf(6.283185307179586f * tau, &sn, &cs);
+    const float gs = q.scale * ga * invD;
+    const float cr = gs * fmaf(sh, cs, -q.b * sn);
+    const float ci = gs * fmaf(sh, sn, q.b * cs);
+    G = fmaf(g.x, cr, fmaf(g.y, ci, G));
+    const float t = q.kh * n2 * invD * invD;                         // k n^2 / (2 D^2)
+    const float dr = q.invb - q.b * invD - t * (sh * sh - q.b2);      // Re d log c / db
+    const float di = sh * invD - t * (2.0f * sh * q.b);               // Im d log c / db
+    H = fmaf(g.x, cr * dr - ci * di, fmaf(g.y, cr * di + ci * dr, H));
+}
+
 // All frequencies of one surviving (receiver, segment) pair, added to tmp.
 template <int NF, int WINDOW, bool STATS>
 __device__ __forceinline__ void survivor(const FwdParams &p, float x, float y, float z,
@@ -306,6 +340,32 @@ __device__ __forceinline__ void survivor(const FwdParams &p, float x, float y, f
             beam_term(q, sh, sl, n2, rcp_approx(D), amp, tmp[f]);
         }
     }
+}
+
+// Adjoint of one surviving pair: per-segment sums in shared memory (gk: this
+// receiver's g per sorted frequency, stride 32 floats2).
+template <int NF, int WINDOW>
+__device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, float y, float z,
+                                                 const WarpSmem &w, int j, const float2 *gk,
+                                                 float *segG, float *segH)
+{
+    float sh, sl, n2;
+    if (!exact_geometry<WINDOW>(x, y, z, w, j, sh, sl, n2)) return;
+    float G = 0.f;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (f >= p.nf) break;
+        const FreqConst &q = p.fc[f];
+        const float D = fmaf(sh, sh, q.b2);
+        if (q.kb2 * n2 > p.cutoff * D) {
+            if (p.uniform_b) break;
+            continue;
+        }
+        float H = 0.f;
+        beam_adjoint(q, sh, sl, n2, rcp_approx(D), gk[f * (kR * 32)], G, H);
+        atomicAdd(&segH[f * 32 + j], H);
+    }
+    if (G != 0.f) atomicAdd(&segG[j], G);
 }
 
 // Adds an FP32 partial sum into a float-float accumulator (hi, hi, lo, lo).
@@ -366,10 +426,19 @@ __device__ __forceinline__ void stage_transform(WarpSmem &w, const float4 (&raw)
 }
 
 template <int NF>
+struct AdjSmem {
+    float2 g[NF][kR][32];      // the warp's receivers' g, per sorted frequency
+    float segG[32];            // per segment of the current batch
+    float segH[NF][32];
+};
+template <int NF>
 struct CtaSmem {
     float4 raw[kStages][kBatch][kRecFloats / 4];   // TMA ring of staged record batches
     WarpSmem w[kConsumerWarps];                     // per consumer warp
-    float4 acc[kConsumerWarps][NF][kR][32];         // float-float sums (re_hi, im_hi, re_lo, im_lo)
+    union {
+        float4 acc[kConsumerWarps][NF][kR][32];     // forward: float-float sums (hi, hi, lo, lo)
+        AdjSmem<NF> adj[kConsumerWarps];            // adjoint
+    };
     unsigned long long full[kStages], empty[kStages];
     int item, abort_flag;
 };
@@ -380,9 +449,10 @@ struct CtaSmem {
 // constants relative to their own first receiver, release the stage, and run
 // the prefilter and the exact path for their 64 receivers.  Warps wait for
 // each other only through the ring (8 batches of slack) and once per item.
-template <int NF, int WINDOW, bool STATS>
+template <int NF, int WINDOW, int MODE>
 __global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
 {
+    constexpr bool STATS = MODE == kStats;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     CtaSmem<NF> &S = *reinterpret_cast<CtaSmem<NF> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -463,9 +533,25 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
                     valid |= 1u << k;
                     ridx[k] = (int32_t)o;
                 }
+                if (MODE == kBwd) {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) S.acc[warp][f][k][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int f = 0; f < NF; ++f)
+                        S.adj[warp].g[f][k][lane] =
+                            (f < p.nf && ridx[k] >= 0)
+                                ? p.grad_out[(int64_t)p.fperm[f] * p.n_recv + ridx[k]]
+                                : make_float2(0.f, 0.f);
+                } else {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        S.acc[warp][f][k][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
+            if (MODE == kBwd) {
+                S.adj[warp].segG[lane] = 0.f;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) S.adj[warp].segH[f][lane] = 0.f;
+            }
+            __syncwarp();
             static_assert(kR == 2, "the paired prefilter handles two receivers per lane");
             const f2x X2 = pk(xp[0], xp[1]), Y2 = pk(yp[0], yp[1]), Z2 = pk(zp[0], zp[1]);
             const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
@@ -534,10 +620,30 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
                     while (mm) {
                         const int jj = __clz(mm);
                         mm ^= 0x80000000u >> jj;
-                        survivor<NF, WINDOW, STATS>(p, xa[k], ya[k], za[k], w, jj, tmp[k], n_kept);
+                        if (MODE == kBwd)
+                            survivor_adjoint<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj,
+                                                         &S.adj[warp].g[0][k][lane],
+                                                         S.adj[warp].segG, &S.adj[warp].segH[0][0]);
+                        else
+                            survivor<NF, WINDOW, STATS>(p, xa[k], ya[k], za[k], w, jj, tmp[k],
+                                                        n_kept);
                     }
                 }
-                if (!STATS && (kb_ % kFoldEvery) == kFoldEvery - 1) {
+                if (MODE == kBwd) {
+                    // per-segment sums of this warp to global, then clear
+                    __syncwarp();
+                    const int64_t jg = b * kBatch + lane;
+                    const float G = S.adj[warp].segG[lane];
+                    if (G != 0.f && jg < n_seg) atomicAdd(&p.seg_G[jg], G);
+                    S.adj[warp].segG[lane] = 0.f;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const float H = S.adj[warp].segH[f][lane];
+                        if (H != 0.f && jg < n_seg) atomicAdd(&p.seg_H[f * p.seg_stride + jg], H);
+                        S.adj[warp].segH[f][lane] = 0.f;
+                    }
+                }
+                if (MODE == kFwd && (kb_ % kFoldEvery) == kFoldEvery - 1) {
 #pragma unroll
                     for (int k = 0; k < kR; ++k)
 #pragma unroll
@@ -545,7 +651,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
                 }
                 __syncwarp();
             }
-            if (!STATS) {
+            if (MODE == kFwd) {
 #pragma unroll
                 for (int k = 0; k < kR; ++k) {
 #pragma unroll
@@ -708,6 +814,91 @@ __global__ void __launch_bounds__(kThreads64) gbs_fwd_f64_kernel(const F64Params
             make_double2(sr[f] + cr[f], si[f] + ci[f]);
 }
 
+// ------------------------------------------------------------ adjoint --
+
+// Per ray: the weight gradient sum_j Gamma_path_j G_j, the material gradient
+// sum over bounces of W (product of the other bounces' gamma) G_j, and the beam
+// parameter gradient sum_j W Gamma_path_j H_jf.  Products of the other
+// bounces are formed directly, so gamma = 0 needs no special case.
+struct RayGradParams {
+    int64_t n_rays, ray_begin;
+    const int32_t *ray_off, *bmat;
+    const float *gamma, *weight;
+    double w_default;
+    const float *seg_G, *seg_H;
+    int64_t seg_stride;
+    int nf, n_materials;
+    float *grad_w;             // n_fan entries (this range written), or nullptr
+    double *acc;               // [n_materials] gamma, then [nf] b (sorted slots)
+    unsigned int *status;
+};
+
+constexpr int kMaxDepth = 65;
+
+__global__ void ray_grad_kernel(RayGradParams p)
+{
+    extern __shared__ double sacc[];
+    const int nacc = p.n_materials + p.nf;
+    for (int k = threadIdx.x; k < nacc; k += blockDim.x) sacc[k] = 0.0;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < p.n_rays) {
+        const int64_t a = p.ray_off[i];
+        const int cnt = (int)(p.ray_off[i + 1] - a);
+        const double W = p.weight ? (double)p.weight[p.ray_begin + i] : p.w_default;
+        double gams[kMaxDepth];
+        int mats[kMaxDepth];
+        double gp = 1.0, gw = 0.0;
+        for (int d = 0; d < cnt && d < kMaxDepth; ++d) {
+            const int64_t j = a + d;
+            if (d >= 1) {
+                int m = p.bmat[j];
+                if (m < 0 || m >= p.n_materials) {
+                    atomicOr(p.status, STATUS_BOUNDS);
+                    m = 0;
+                }
+                mats[d] = m;
+                gams[d] = (double)p.gamma[m];
+                gp *= gams[d];
+            }
+            const double G = (double)p.seg_G[j];
+            gw += gp * G;
+            if (G != 0.0) {
+                for (int q = 1; q <= d; ++q) {
+                    double others = 1.0;
+                    for (int q2 = 1; q2 <= d; ++q2)
+                        if (q2 != q) others *= gams[q2];
+                    atomicAdd(&sacc[mats[q]], W * others * G);
+                }
+            }
+            for (int f = 0; f < p.nf; ++f) {
+                const double H = (double)p.seg_H[f * p.seg_stride + j];
+                if (H != 0.0) atomicAdd(&sacc[p.n_materials + f], W * gp * H);
+            }
+        }
+        if (p.grad_w) p.grad_w[p.ray_begin + i] = (float)gw;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nacc; k += blockDim.x)
+        if (sacc[k] != 0.0) atomicAdd(&p.acc[k], sacc[k]);
+}
+
+struct GradOutParams {
+    const double *acc;
+    int n_materials, nf;
+    int fperm[GBT_MAX_FREQ];
+    float *grad_gamma;
+    double *grad_b;
+};
+
+__global__ void grad_out_kernel(GradOutParams p)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < p.n_materials) p.grad_gamma[k] = (float)p.acc[k];
+    else if (k < p.n_materials + p.nf && p.grad_b)
+        p.grad_b[p.fperm[k - p.n_materials]] = p.acc[k];
+}
+
 // ------------------------------------------------------------- reduce --
 
 struct ReduceParams {
@@ -826,30 +1017,33 @@ __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <int NF, int WINDOW, bool STATS>
+template <int NF, int WINDOW, int MODE>
 void launch_fwd_t(const FwdParams &p, cudaStream_t s)
 {
+    constexpr bool STATS = MODE != kFwd;
     const size_t smem = sizeof(CtaSmem<NF>);
-    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, STATS>,
+    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, MODE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, gbs_fwd_kernel<NF, WINDOW, STATS>, kThreads, smem));
+        &per_sm, gbs_fwd_kernel<NF, WINDOW, MODE>, kThreads, smem));
     if (per_sm < 1) fail(GBT_ERR_UNSUPPORTED, "GBS kernel does not fit on one SM");
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(p.n_items, (int64_t)std::max(per_sm, 1) * num_sms()));
     GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
-    if (!STATS) timing_begin(s);
-    gbs_fwd_kernel<NF, WINDOW, STATS><<<grid, kThreads, smem, s>>>(p);
+    if (MODE != kStats) timing_begin(s);
+    gbs_fwd_kernel<NF, WINDOW, MODE><<<grid, kThreads, smem, s>>>(p);
     GBT_CUDA(cudaGetLastError());
-    if (!STATS) timing_end(s);
+    if (MODE != kStats) timing_end(s);
+    (void)STATS;
 }
 
 template <int NF, int WINDOW>
 void launch_fwd(const FwdParams &p, cudaStream_t s)
 {
-    if (p.stats) launch_fwd_t<NF, WINDOW, true>(p, s);
-    else launch_fwd_t<NF, WINDOW, false>(p, s);
+    if (p.grad_out) launch_fwd_t<NF, WINDOW, kBwd>(p, s);
+    else if (p.stats) launch_fwd_t<NF, WINDOW, kStats>(p, s);
+    else launch_fwd_t<NF, WINDOW, kFwd>(p, s);
 }
 
 template <int WINDOW>
@@ -859,6 +1053,54 @@ void launch_fwd_nf(const FwdParams &p, cudaStream_t s)
     else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, s);
     else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, s);
     else launch_fwd<8, WINDOW>(p, s);
+}
+
+// Kernel parameters shared by the forward, counting and adjoint launches.
+FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
+                                  const float *rec)
+{
+    FwdParams q{};
+    q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
+    q.n_seg_ptr = td.ray_off + td.n_rays;
+    q.rec = rec;
+    q.nf = a.n_freq;
+    q.cutoff = (float)a.cutoff;
+    // frequency order: when every b is equal, sort by k so that the kept
+    // frequencies of a pair form a prefix (wider beams first)
+    int perm[GBT_MAX_FREQ];
+    for (int f = 0; f < a.n_freq; ++f) perm[f] = f;
+    bool uniform = true;
+    for (int f = 1; f < a.n_freq; ++f) uniform = uniform && a.beam_b[f] == a.beam_b[0];
+    if (uniform)
+        std::stable_sort(perm, perm + a.n_freq,
+                         [&](int x, int y) { return a.freq_hz[x] < a.freq_hz[y]; });
+    q.uniform_b = uniform ? 1 : 0;
+    double amin = 1e300, bmax = 0.0;
+    for (int f = 0; f < GBT_MAX_FREQ; ++f) q.fperm[f] = f;
+    for (int f = 0; f < a.n_freq; ++f) {
+        const int g = perm[f];
+        q.fperm[f] = g;
+        const double K = a.freq_hz[g] / sd.c;       // turns per metre
+        const double k = 2.0 * kPi * K;
+        const double b = a.beam_b[g];
+        FreqConst &c = q.fc[f];
+        c.K_hi = (float)K;
+        c.K_lo = (float)(K - (double)c.K_hi);
+        c.halfK = (float)(0.5 * K);
+        c.kb2 = (float)(0.5 * k * b);
+        c.kb2l2e = (float)(0.5 * k * b * 1.4426950408889634);
+        c.b = (float)b;
+        c.b2 = (float)(b * b);
+        c.scale = (float)(k * b / (8.0 * kPi * kPi));
+        c.kh = (float)(0.5 * k);
+        c.invb = (float)(1.0 / b);
+        amin = std::min(amin, 0.5 * k * b);
+        bmax = std::max(bmax, b * b);
+    }
+    q.pre_alpha = (float)(amin / (a.cutoff + 1.0));
+    q.pre_beta = (float)bmax;
+    q.status = status_word();
+    return q;
 }
 
 }  // namespace
@@ -952,53 +1194,17 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
                 gbs_fwd_f64_kernel<GBT_WINDOW_SEGMENT><<<grid, kThreads64, 0, s>>>(q);
             GBT_CUDA(cudaGetLastError());
         } else {
-            FwdParams q{};
-            q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
-            q.n_seg_ptr = n_seg_ptr;
-            q.rec = rec;
-            q.nf = a.n_freq;
-            q.cutoff = (float)a.cutoff;
-            // frequency order: when every b is equal, sort by k so that the kept
-            // frequencies of a pair form a prefix (wider beams first)
-            int perm[GBT_MAX_FREQ];
-            for (int f = 0; f < a.n_freq; ++f) perm[f] = f;
-            bool uniform = true;
-            for (int f = 1; f < a.n_freq; ++f) uniform = uniform && a.beam_b[f] == a.beam_b[0];
-            if (uniform)
-                std::stable_sort(perm, perm + a.n_freq,
-                                 [&](int x, int y) { return a.freq_hz[x] < a.freq_hz[y]; });
-            q.uniform_b = uniform ? 1 : 0;
-            double amin = 1e300, bmax = 0.0;
-            for (int f = 0; f < a.n_freq; ++f) {
-                const int g = perm[f];
-                const double K = a.freq_hz[g] / sd.c;       // turns per metre
-                const double k = 2.0 * kPi * K;
-                const double b = a.beam_b[g];
-                FreqConst &c = q.fc[f];
-                c.K_hi = (float)K;
-                c.K_lo = (float)(K - (double)c.K_hi);
-                c.halfK = (float)(0.5 * K);
-                c.kb2 = (float)(0.5 * k * b);
-                c.kb2l2e = (float)(0.5 * k * b * 1.4426950408889634);
-                c.b = (float)b;
-                c.b2 = (float)(b * b);
-                c.scale = (float)(k * b / (8.0 * kPi * kPi));
-                amin = std::min(amin, 0.5 * k * b);
-                bmax = std::max(bmax, b * b);
-            }
-            q.pre_alpha = (float)(amin / (a.cutoff + 1.0));
-            q.pre_beta = (float)bmax;
+            FwdParams q = make_pair_params(td, sd, a, rec);
             q.splits = splits;
             q.partial = reinterpret_cast<float4 *>(partial);
             q.stats = stats;
             const int64_t tiles = (a.n_recv + kCtaRecv - 1) / kCtaRecv;
             q.n_items = tiles * splits;
-            q.status = status_word();
             q.work_counter = counter;
             if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
             else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
             if (stats) return;
-            for (int f = 0; f < a.n_freq; ++f) fperm[f] = perm[f];
+            for (int f = 0; f < a.n_freq; ++f) fperm[f] = q.fperm[f];
         }
         ReduceParams rp{};
         rp.n = nout;
@@ -1040,6 +1246,107 @@ void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scrat
     GBT_CUDA(cudaGetLastError());
 }
 
+
+// ------------------------------------------------------------ adjoint --
+
+static size_t bwd_layout(const TraceDev &td, const gbt_sum_args &a, const SceneDev *sd,
+                         size_t *off)
+{
+    // records | amp64 | counter | seg_G | seg_H | acc
+    size_t b = 0;
+    off[0] = b; b += records_bytes(td);
+    off[1] = b; b += align_up((size_t)td.capacity * sizeof(double), 256);
+    off[2] = b; b += 256;
+    off[3] = b; b += align_up((size_t)td.capacity * sizeof(float), 256);
+    off[4] = b; b += align_up((size_t)a.n_freq * td.capacity * sizeof(float), 256);
+    off[5] = b; b += align_up((size_t)((sd ? sd->n_materials : 1024) + GBT_MAX_FREQ) * sizeof(double), 256);
+    return b;
+}
+
+size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a)
+{
+    size_t off[6];
+    return bwd_layout(td, a, &td.scene->d, off);
+}
+
+void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
+                const float *grad_out, float *grad_gamma, float *grad_w, double *grad_b,
+                void *work, cudaStream_t s)
+{
+    size_t off[6];
+    bwd_layout(td, a, &sd, off);
+    char *w = static_cast<char *>(work);
+    float *rec = reinterpret_cast<float *>(w + off[0]);
+    double *amp64 = reinterpret_cast<double *>(w + off[1]);
+    int *counter = reinterpret_cast<int *>(w + off[2]);
+    float *seg_G = reinterpret_cast<float *>(w + off[3]);
+    float *seg_H = reinterpret_cast<float *>(w + off[4]);
+    double *acc = reinterpret_cast<double *>(w + off[5]);
+    const int32_t *n_seg_ptr = td.ray_off + td.n_rays;
+
+    GBT_CUDA(cudaMemsetAsync(seg_G, 0, (size_t)td.capacity * sizeof(float), s));
+    GBT_CUDA(cudaMemsetAsync(seg_H, 0, (size_t)a.n_freq * td.capacity * sizeof(float), s));
+    GBT_CUDA(cudaMemsetAsync(acc, 0, (size_t)(sd.n_materials + GBT_MAX_FREQ) * sizeof(double), s));
+    if (grad_w) GBT_CUDA(cudaMemsetAsync(grad_w, 0, (size_t)td.n_fan * sizeof(float), s));
+
+    if (td.capacity > 0) {
+        PrepParams pp{};
+        pp.n_seg_ptr = n_seg_ptr;
+        pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
+        pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
+        pp.gamma = a.gamma;
+        pp.weight = a.ray_weight;
+        pp.w_default = 4.0 * kPi / (double)td.n_fan;
+        pp.n_materials = sd.n_materials;
+        pp.rec = rec;
+        pp.amp64 = amp64;
+        pp.status = status_word();
+        prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
+        GBT_CUDA(cudaGetLastError());
+    }
+    FwdParams q = make_pair_params(td, sd, a, rec);
+    if (a.n_recv > 0) {
+        const int splits = choose_splits(td, a);
+        q.splits = splits;
+        q.n_items = ((a.n_recv + kCtaRecv - 1) / kCtaRecv) * splits;
+        q.work_counter = counter;
+        q.grad_out = reinterpret_cast<const float2 *>(grad_out);
+        q.seg_G = seg_G;
+        q.seg_H = seg_H;
+        q.seg_stride = td.capacity;
+        if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
+        else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
+    }
+    RayGradParams r{};
+    r.n_rays = td.n_rays;
+    r.ray_begin = td.ray_begin;
+    r.ray_off = td.ray_off;
+    r.bmat = td.bmat;
+    r.gamma = a.gamma;
+    r.weight = a.ray_weight;
+    r.w_default = 4.0 * kPi / (double)td.n_fan;
+    r.seg_G = seg_G;
+    r.seg_H = seg_H;
+    r.seg_stride = td.capacity;
+    r.nf = a.n_freq;
+    r.n_materials = sd.n_materials;
+    r.grad_w = grad_w;
+    r.acc = acc;
+    r.status = status_word();
+    const size_t sh = (size_t)(sd.n_materials + a.n_freq) * sizeof(double);
+    ray_grad_kernel<<<(unsigned)((td.n_rays + 127) / 128), 128, sh, s>>>(r);
+    GBT_CUDA(cudaGetLastError());
+    GradOutParams g{};
+    g.acc = acc;
+    g.n_materials = sd.n_materials;
+    g.nf = a.n_freq;
+    for (int f = 0; f < GBT_MAX_FREQ; ++f) g.fperm[f] = q.fperm[f];
+    g.grad_gamma = grad_gamma;
+    g.grad_b = grad_b;
+    const int nk = sd.n_materials + a.n_freq;
+    grad_out_kernel<<<(unsigned)((nk + 127) / 128), 128, 0, s>>>(g);
+    GBT_CUDA(cudaGetLastError());
+}
 
 // ------------------------------------------------- receiver order, no allocation --
 //
