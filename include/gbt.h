@@ -240,12 +240,19 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src,
  * and buffers must stay alive and unchanged in shape while the batch exists;
  * their contents may change between submits. */
 typedef struct gbt_batch_desc {
-    int32_t n_instances;
-    const gbt_trace_t *const *traces;   /* host array of n_instances handles */
-    const gbt_sum_args *args;         /* host array of n_instances argument sets */
+    int32_t n_instances;              /* >= 1 */
+    const gbt_trace_t *const *traces; /* host array of n_instances handles */
+    const gbt_sum_args *args;         /* host array of n_instances argument sets; all F32,
+                                         one window, n_freq <= 8 */
     int32_t use_graph;                /* 1: capture on first submit, then replay */
+    int32_t autotune;                 /* 1: time a few work splittings at create, keep the best */
 } gbt_batch_desc;
 
+/* Create synchronises `stream` once (it reads each trace's segment count to
+ * order the instances longest first and to size their work) and allocates
+ * the batch's device workspace; with autotune it also runs the batch a few
+ * times.  Submit queues the whole batch on `stream` (graph replay after the
+ * first submit when use_graph is set); outputs land in each instance's out. */
 gbt_status gbt_batch_create(const gbt_batch_desc *desc, void *stream, gbt_batch_t **out);
 gbt_status gbt_batch_submit(gbt_batch_t *batch, void *stream);
 gbt_status gbt_batch_destroy(gbt_batch_t *batch);

@@ -26,7 +26,6 @@ SOURCES = {
     "api.cu": [],
     "trace.cu": ["--fmad=false"],
     "gbs.cu": [],
-    "batch.cu": [],
 }
 HEADERS = ["gbt_internal.h"]
 

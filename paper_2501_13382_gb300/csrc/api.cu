@@ -593,6 +593,42 @@ gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,
     });
 }
 
+gbt_status gbt_batch_create(const gbt_batch_desc *desc, void *stream, gbt_batch_t **out)
+{
+    return guarded([&] {
+        GBT_REQUIRE(desc && out, "desc and out must be non-NULL");
+        *out = nullptr;
+        GBT_REQUIRE(desc->n_instances >= 1, "n_instances must be >= 1");
+        GBT_REQUIRE(desc->traces && desc->args, "traces and args must be non-NULL");
+        for (int i = 0; i < desc->n_instances; ++i) validate_sum(desc->traces[i], &desc->args[i]);
+        gbt_batch_t *b = new gbt_batch_s();
+        try {
+            b->impl = batch_create(*desc, static_cast<cudaStream_t>(stream));
+        } catch (...) {
+            delete b;
+            throw;
+        }
+        *out = b;
+    });
+}
+
+gbt_status gbt_batch_submit(gbt_batch_t *batch, void *stream)
+{
+    return guarded([&] {
+        GBT_REQUIRE(batch && batch->impl, "batch is NULL");
+        batch_submit(batch->impl, static_cast<cudaStream_t>(stream));
+    });
+}
+
+gbt_status gbt_batch_destroy(gbt_batch_t *batch)
+{
+    return guarded([&] {
+        if (!batch) return;
+        batch_destroy(batch->impl);
+        delete batch;
+    });
+}
+
 gbt_status gbt_sync(void *stream)
 {
     return guarded([&] {

@@ -26,6 +26,8 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
+#include <cmath>
 #include <string>
 
 #include "gbt_internal.h"
@@ -55,7 +57,7 @@ struct FreqConst {
     float kh, invb;       // k / 2, 1 / b  (adjoint)
 };
 
-struct FwdParams {
+struct alignas(16) FwdParams {
     const float *recv;
     const int32_t *order;
     int64_t n_recv;
@@ -77,8 +79,14 @@ struct FwdParams {
     float *seg_H;              // per (sorted frequency, segment): sum over r of Re(conj(g) dc~/db)
     int64_t seg_stride;        // stride of seg_H rows
     int fperm[GBT_MAX_FREQ];   // sorted frequency slot -> user frequency index
+    // batched launch: per-instance parameters and the first global item of each
+    const struct FwdParams *inst;
+    const int64_t *inst_off;   // n_inst + 1 entries
+    int n_inst;
     FreqConst fc[GBT_MAX_FREQ];
 };
+
+static_assert(sizeof(FwdParams) % 16 == 0, "instance parameters are copied as 16-byte words");
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -440,7 +448,9 @@ struct CtaSmem {
         AdjSmem<NF> adj[kConsumerWarps];            // adjoint
     };
     unsigned long long full[kStages], empty[kStages];
-    int item, abort_flag;
+    FwdParams inst;            // batched launch: the current item's instance
+    int64_t item;
+    int inst_idx, abort_flag;
 };
 
 // One CTA per SM.  A producer warp streams record batches of the current item
@@ -449,8 +459,8 @@ struct CtaSmem {
 // constants relative to their own first receiver, release the stage, and run
 // the prefilter and the exact path for their 64 receivers.  Warps wait for
 // each other only through the ring (8 batches of slack) and once per item.
-template <int NF, int WINDOW, int MODE>
-__global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
+template <int NF, int WINDOW, int MODE, bool BATCHED>
+__global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParams prm)
 {
     constexpr bool STATS = MODE == kStats;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -468,18 +478,44 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
     }
     __syncthreads();
 
-    const int64_t n_seg = *p.n_seg_ptr;
-    const int64_t n_batches = (n_seg + kBatch - 1) / kBatch;
-    const float alpha = p.pre_alpha, beta = p.pre_beta;
     volatile int *abort_flag = &S.abort_flag;
     uint32_t n_pre = 0, n_kept = 0;
     uint32_t g = 0;   // batches through the ring so far (same count in every role)
 
     for (;;) {
-        if (threadIdx.x == 0) S.item = atomicAdd(p.work_counter, 1);
+        if (threadIdx.x == 0) {
+            int64_t it = atomicAdd(prm.work_counter, 1);
+            int inst = 0;
+            if (BATCHED && it < prm.n_items) {
+                int lo = 0, hi = prm.n_inst - 1;      // last instance with inst_off <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (prm.inst_off[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                inst = lo;
+                it -= prm.inst_off[lo];
+            } else if (BATCHED) {
+                it = prm.n_items;
+            }
+            S.item = it;
+            S.inst_idx = inst;
+        }
         __syncthreads();
+        if (BATCHED && S.item < prm.n_items) {
+            // the item's instance parameters into shared memory
+            const int4 *src = reinterpret_cast<const int4 *>(prm.inst + S.inst_idx);
+            int4 *dst = reinterpret_cast<int4 *>(&S.inst);
+            for (int q = threadIdx.x; q < (int)(sizeof(FwdParams) / 16); q += blockDim.x)
+                dst[q] = src[q];
+            __syncthreads();
+        }
+        const FwdParams &p = *(BATCHED ? &S.inst : &prm);
         const int64_t item = S.item;
-        if (item >= p.n_items || *abort_flag) break;
+        if (item >= (BATCHED ? prm.n_items : p.n_items) || *abort_flag) break;
+        const int64_t n_seg = *p.n_seg_ptr;
+        const int64_t n_batches = (n_seg + kBatch - 1) / kBatch;
+        const float alpha = p.pre_alpha, beta = p.pre_beta;
         const int64_t tile_base = (item / p.splits) * kCtaRecv;
         const int split = (int)(item % p.splits);
         const uint32_t nb = split < n_batches ? (uint32_t)((n_batches - 1 - split) / p.splits + 1) : 0u;
@@ -667,8 +703,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const FwdParams p)
         __syncthreads();
     }
     if (STATS && !producer) {
-        atomicAdd(&p.stats[1], (unsigned long long)n_pre);
-        atomicAdd(&p.stats[2], (unsigned long long)n_kept);
+        atomicAdd(&prm.stats[1], (unsigned long long)n_pre);
+        atomicAdd(&prm.stats[2], (unsigned long long)n_kept);
     }
 }
 
@@ -1017,22 +1053,22 @@ __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <int NF, int WINDOW, int MODE>
+template <int NF, int WINDOW, int MODE, bool BATCHED = false>
 void launch_fwd_t(const FwdParams &p, cudaStream_t s)
 {
     constexpr bool STATS = MODE != kFwd;
     const size_t smem = sizeof(CtaSmem<NF>);
-    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, MODE>,
+    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, gbs_fwd_kernel<NF, WINDOW, MODE>, kThreads, smem));
+        &per_sm, gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED>, kThreads, smem));
     if (per_sm < 1) fail(GBT_ERR_UNSUPPORTED, "GBS kernel does not fit on one SM");
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(p.n_items, (int64_t)std::max(per_sm, 1) * num_sms()));
     GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
     if (MODE != kStats) timing_begin(s);
-    gbs_fwd_kernel<NF, WINDOW, MODE><<<grid, kThreads, smem, s>>>(p);
+    gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED><<<grid, kThreads, smem, s>>>(p);
     GBT_CUDA(cudaGetLastError());
     if (MODE != kStats) timing_end(s);
     (void)STATS;
@@ -1346,6 +1382,289 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     const int nk = sd.n_materials + a.n_freq;
     grad_out_kernel<<<(unsigned)((nk + 127) / 128), 128, 0, s>>>(g);
     GBT_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------ batched --
+
+// Many (trace, sum arguments) instances in one persistent launch: one global
+// work counter over the items of all instances (instances ordered by cost,
+// longest first), each CTA loading the item's instance parameters.
+template <int NF, int WINDOW>
+int batched_prepare()
+{
+    const size_t smem = sizeof(CtaSmem<NF>);
+    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, kFwd, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, gbs_fwd_kernel<NF, WINDOW, kFwd, true>, kThreads, smem));
+    if (per_sm < 1) fail(GBT_ERR_UNSUPPORTED, "GBS kernel does not fit on one SM");
+    return per_sm;
+}
+
+template <int NF, int WINDOW>
+void batched_launch(const FwdParams &prm, int grid, cudaStream_t s)
+{
+    GBT_CUDA(cudaMemsetAsync(prm.work_counter, 0, sizeof(int), s));
+    gbs_fwd_kernel<NF, WINDOW, kFwd, true><<<grid, kThreads, sizeof(CtaSmem<NF>), s>>>(prm);
+    GBT_CUDA(cudaGetLastError());
+}
+
+typedef int (*BatchedPrepFn)();
+typedef void (*BatchedLaunchFn)(const FwdParams &, int, cudaStream_t);
+
+struct BatchImpl {
+    std::vector<const gbt_trace_t *> traces;
+    std::vector<gbt_sum_args> args;
+    std::vector<int> order;            // instance processing order (cost, descending)
+    std::vector<int64_t> n_seg, cost;
+    std::vector<int> splits;
+    std::vector<size_t> rec_off, part_off;
+    std::vector<FwdParams> table;      // in processing order
+    std::vector<int64_t> inst_off;
+    void *work = nullptr;
+    size_t work_bytes = 0;
+    int *counter = nullptr;
+    FwdParams *d_table = nullptr;
+    int64_t *d_off = nullptr;
+    int grid = 1;
+    int nf_max = 1, window = 0;
+    BatchedLaunchFn launch = nullptr;
+    bool use_graph = false;
+    cudaStream_t capture_stream = nullptr;   // private stream the graph is recorded on
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_plan(BatchImpl &B, double items_per_slot)
+{
+    // splits per instance: items proportional to the instance's cost
+    const int64_t slots = (int64_t)B.grid;
+    double total = 0.0;
+    for (int64_t c : B.cost) total += (double)std::max<int64_t>(c, 1);
+    const int n = (int)B.args.size();
+    B.splits.assign(n, 1);
+    for (int i = 0; i < n; ++i) {
+        const gbt_sum_args &a = B.args[i];
+        const int64_t tiles = std::max<int64_t>(1, (a.n_recv + kCtaRecv - 1) / kCtaRecv);
+        const double want = items_per_slot * slots * (double)std::max<int64_t>(B.cost[i], 1) / total;
+        int64_t sp = (int64_t)std::ceil(want / (double)tiles);
+        const int64_t nb = std::max<int64_t>(1, (B.n_seg[i] + kBatch - 1) / kBatch);
+        sp = std::max<int64_t>(1, std::min<int64_t>(sp, nb));
+        const int64_t per_split = (int64_t)a.n_freq * std::max<int64_t>(a.n_recv, 1) * 16;
+        sp = std::min<int64_t>(sp, std::max<int64_t>(1, (1LL << 30) / per_split));
+        B.splits[i] = (int)std::min<int64_t>(sp, 4096);
+    }
+}
+
+static void batch_layout(BatchImpl &B, cudaStream_t s)
+{
+    const int n = (int)B.args.size();
+    B.rec_off.assign(n, 0);
+    B.part_off.assign(n, 0);
+    size_t b = 0;
+    for (int i = 0; i < n; ++i) {
+        B.rec_off[i] = b;
+        b += records_bytes(B.traces[i]->d);
+        B.part_off[i] = b;
+        b += align_up((size_t)B.splits[i] * B.args[i].n_freq * (size_t)B.args[i].n_recv *
+                          sizeof(float4), 256);
+    }
+    const size_t tab = align_up((size_t)n * sizeof(FwdParams), 256);
+    const size_t off = align_up((size_t)(n + 1) * sizeof(int64_t), 256);
+    const size_t need = b + 256 + tab + off;
+    if (need > B.work_bytes) {
+        if (B.work) dfree(B.work, s);
+        B.work = dalloc(need, s);
+        B.work_bytes = need;
+    }
+    char *w = static_cast<char *>(B.work);
+    B.counter = reinterpret_cast<int *>(w + b);
+    B.d_table = reinterpret_cast<FwdParams *>(w + b + 256);
+    B.d_off = reinterpret_cast<int64_t *>(w + b + 256 + tab);
+
+    B.table.clear();
+    B.inst_off.assign(1, 0);
+    for (int k = 0; k < n; ++k) {
+        const int i = B.order[k];
+        const TraceDev &td = B.traces[i]->d;
+        const gbt_sum_args &a = B.args[i];
+        float *rec = reinterpret_cast<float *>(w + B.rec_off[i]);
+        FwdParams q = make_pair_params(td, td.scene->d, a, rec);
+        q.splits = B.splits[i];
+        q.n_items = ((a.n_recv + kCtaRecv - 1) / kCtaRecv) * q.splits;
+        q.partial = reinterpret_cast<float4 *>(w + B.part_off[i]);
+        q.work_counter = B.counter;
+        B.table.push_back(q);
+        B.inst_off.push_back(B.inst_off.back() + q.n_items);
+    }
+    GBT_CUDA(cudaMemcpyAsync(B.d_table, B.table.data(), (size_t)n * sizeof(FwdParams),
+                             cudaMemcpyHostToDevice, s));
+    GBT_CUDA(cudaMemcpyAsync(B.d_off, B.inst_off.data(), (size_t)(n + 1) * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s));
+    GBT_CUDA(cudaStreamSynchronize(s));
+}
+
+static void batch_record(BatchImpl &B, cudaStream_t s)
+{
+    const int n = (int)B.args.size();
+    char *w = static_cast<char *>(B.work);
+    for (int i = 0; i < n; ++i) {
+        const TraceDev &td = B.traces[i]->d;
+        const gbt_sum_args &a = B.args[i];
+        if (td.capacity == 0) continue;
+        PrepParams pp{};
+        pp.n_seg_ptr = td.ray_off + td.n_rays;
+        pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
+        pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
+        pp.gamma = a.gamma;
+        pp.weight = a.ray_weight;
+        pp.w_default = 4.0 * kPi / (double)td.n_fan;
+        pp.n_materials = td.scene->d.n_materials;
+        pp.rec = reinterpret_cast<float *>(w + B.rec_off[i]);
+        pp.amp64 = nullptr;
+        pp.status = status_word();
+        prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
+        GBT_CUDA(cudaGetLastError());
+    }
+    FwdParams prm = B.table[0];
+    prm.inst = B.d_table;
+    prm.inst_off = B.d_off;
+    prm.n_inst = n;
+    prm.n_items = B.inst_off.back();
+    prm.work_counter = B.counter;
+    B.launch(prm, B.grid, s);
+    for (int k = 0; k < n; ++k) {
+        const int i = B.order[k];
+        const gbt_sum_args &a = B.args[i];
+        if (a.n_recv == 0) continue;
+        ReduceParams rp{};
+        rp.n = (int64_t)a.n_freq * a.n_recv;
+        rp.n_recv = a.n_recv;
+        for (int f = 0; f < GBT_MAX_FREQ; ++f) rp.perm[f] = B.table[k].fperm[f];
+        rp.splits = B.splits[i];
+        rp.p32 = reinterpret_cast<float4 *>(w + B.part_off[i]);
+        rp.p64 = nullptr;
+        rp.out = reinterpret_cast<float2 *>(a.out);
+        rp.accumulate = a.accumulate;
+        reduce_kernel<<<(unsigned)((rp.n + 255) / 256), 256, 0, s>>>(rp);
+        GBT_CUDA(cudaGetLastError());
+    }
+}
+
+BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
+{
+    BatchImpl *B = new BatchImpl();
+    try {
+        const int n = d.n_instances;
+        B->traces.assign(d.traces, d.traces + n);
+        B->args.assign(d.args, d.args + n);
+        B->use_graph = d.use_graph != 0;
+        B->window = d.args[0].window;
+        for (int i = 0; i < n; ++i) {
+            GBT_REQUIRE(d.args[i].window == B->window, "batch instances must share one window");
+            GBT_REQUIRE(d.args[i].precision == GBT_PRECISION_F32, "batches are F32 only");
+            GBT_REQUIRE(d.args[i].n_freq <= 8, "batches support up to 8 frequencies");
+            B->nf_max = std::max(B->nf_max, (int)d.args[i].n_freq);
+        }
+        status_word();   // allocate before any capture
+        // one synchronisation: segment counts of every trace
+        GBT_CUDA(cudaStreamSynchronize(s));
+        B->n_seg.resize(n);
+        B->cost.resize(n);
+        for (int i = 0; i < n; ++i) {
+            int32_t ns = 0;
+            const TraceDev &td = d.traces[i]->d;
+            GBT_CUDA(cudaMemcpy(&ns, td.ray_off + td.n_rays, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            B->n_seg[i] = ns;
+            B->cost[i] = (int64_t)ns * d.args[i].n_recv * d.args[i].n_freq;
+        }
+        B->order.resize(n);
+        for (int i = 0; i < n; ++i) B->order[i] = i;
+        std::stable_sort(B->order.begin(), B->order.end(),
+                         [&](int x, int y) { return B->cost[x] > B->cost[y]; });
+        int per_sm = 1;
+        BatchedPrepFn prep = nullptr;
+        const int nf = B->nf_max <= 1 ? 1 : B->nf_max <= 2 ? 2 : B->nf_max <= 4 ? 4 : 8;
+#define GBT_PICK(NFV)                                                                     \
+    if (nf == NFV) {                                                                      \
+        prep = B->window == GBT_WINDOW_LINE ? batched_prepare<NFV, GBT_WINDOW_LINE>       \
+                                            : batched_prepare<NFV, GBT_WINDOW_SEGMENT>;   \
+        B->launch = B->window == GBT_WINDOW_LINE ? batched_launch<NFV, GBT_WINDOW_LINE>   \
+                                                 : batched_launch<NFV, GBT_WINDOW_SEGMENT>; \
+    }
+        GBT_PICK(1) GBT_PICK(2) GBT_PICK(4) GBT_PICK(8)
+#undef GBT_PICK
+        per_sm = prep();
+        B->grid = per_sm * num_sms();
+        double best_ips = 8.0;
+        if (d.autotune) {
+            // autotuner: time a few work granularities (items per resident CTA)
+            float best = 1e30f;
+            cudaEvent_t e0, e1;
+            GBT_CUDA(cudaEventCreate(&e0));
+            GBT_CUDA(cudaEventCreate(&e1));
+            for (double ips : {4.0, 8.0, 16.0, 32.0}) {
+                batch_plan(*B, ips);
+                batch_layout(*B, s);
+                batch_record(*B, s);   // warm
+                GBT_CUDA(cudaEventRecord(e0, s));
+                batch_record(*B, s);
+                GBT_CUDA(cudaEventRecord(e1, s));
+                GBT_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                GBT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; best_ips = ips; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        batch_plan(*B, best_ips);
+        batch_layout(*B, s);
+    } catch (...) {
+        if (B->work) dfree(B->work, s);
+        delete B;
+        throw;
+    }
+    return B;
+}
+
+void batch_submit(BatchImpl *B, cudaStream_t s)
+{
+    if (!B->use_graph) {
+        batch_record(*B, s);
+        return;
+    }
+    if (!B->exec) {
+        // record on a private stream (the caller's may be the legacy default stream,
+        // which cannot be captured); the graph is then launched on the caller's stream
+        if (!B->capture_stream)
+            GBT_CUDA(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = B->capture_stream;
+        GBT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        try {
+            batch_record(*B, cs);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        GBT_CUDA(cudaStreamEndCapture(cs, &B->graph));
+        GBT_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+    }
+    GBT_CUDA(cudaGraphLaunch(B->exec, s));
+}
+
+void batch_destroy(BatchImpl *B)
+{
+    if (!B) return;
+    cudaDeviceSynchronize();
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+    if (B->work) dfree(B->work, nullptr);
+    delete B;
 }
 
 // ------------------------------------------------- receiver order, no allocation --

@@ -104,7 +104,13 @@ void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scrat
 size_t recv_order_scratch_bytes(int64_t n);
 void recv_order_noalloc_launch(const float *recv, int64_t n, int32_t *order, cudaStream_t s);
 
-// ---- backward (gbs_bwd.cu) ----
+// ---- batched persistent launch (gbs.cu) ----
+struct BatchImpl;
+BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s);
+void batch_submit(BatchImpl *b, cudaStream_t s);
+void batch_destroy(BatchImpl *b);
+
+// ---- backward (gbs.cu) ----
 size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a);
 void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
                 const float *grad_out, float *grad_gamma, float *grad_w, double *grad_b,
@@ -118,4 +124,8 @@ struct gbt_scene_s {
 
 struct gbt_trace_s {
     gbt::TraceDev d;
+};
+
+struct gbt_batch_s {
+    gbt::BatchImpl *impl;
 };

@@ -77,7 +77,7 @@ class gbt_sum_stats(C.Structure):
 
 class gbt_batch_desc(C.Structure):
     _fields_ = [("n_instances", C.c_int32), ("traces", C.c_void_p), ("args", C.c_void_p),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("autotune", C.c_int32)]
 
 
 _lib = None
@@ -428,6 +428,57 @@ def gbs_solve(scene: Scene, source, recv, freqs, beam_b, gamma, ray_weight=None,
                  PRECISION_F32, accumulate, 0, max_device_bytes)
     gbt_solve(scene.handle, source_desc(source), a, _stream_ptr())
     return out
+
+
+class Batch:
+    """Many (trace, receivers, frequencies) instances solved in one persistent launch.
+
+    ``instances`` is a list of dicts with keys trace, recv, freqs, beam_b, gamma and
+    optionally ray_weight, order, out (complex64 [F, Nr]); all share window and cutoff.
+    ``submit()`` queues the whole batch (a CUDA graph replay after the first call when
+    use_graph is set); results land in each instance's ``out``."""
+
+    def __init__(self, instances, window: int = WINDOW_SEGMENT, cutoff: float = 16.0,
+                 use_graph: bool = True, autotune: bool = False):
+        import torch
+        self.instances = []
+        args = []
+        for inst in instances:
+            recv = inst["recv"]
+            _check_tensors(recv, inst["gamma"], inst.get("ray_weight"), inst.get("order"))
+            out = inst.get("out")
+            if out is None:
+                out = torch.empty((len(inst["freqs"]), recv.shape[0]), dtype=torch.complex64,
+                                  device=recv.device)
+            d = dict(inst, out=out)
+            self.instances.append(d)
+            args.append(sum_args(recv, inst["freqs"], inst["beam_b"], inst["gamma"], out,
+                                 inst.get("ray_weight"), inst.get("order"), window, cutoff))
+        n = len(args)
+        self._args = (gbt_sum_args * n)(*args)
+        self._traces = (C.c_void_p * n)(*[d["trace"].handle for d in self.instances])
+        desc = gbt_batch_desc(n, C.cast(self._traces, C.c_void_p).value,
+                              C.cast(self._args, C.c_void_p).value, 1 if use_graph else 0,
+                              1 if autotune else 0)
+        self.handle = gbt_batch_create(desc, _stream_ptr())
+
+    @property
+    def outputs(self):
+        return [d["out"] for d in self.instances]
+
+    def submit(self):
+        gbt_batch_submit(self.handle, _stream_ptr())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gbt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gbs_sum_backward(trace: Trace, recv, freqs, beam_b, gamma, grad_out, ray_weight=None,

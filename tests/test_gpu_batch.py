@@ -1,0 +1,76 @@
+"""Batched persistent launch (gbt_batch_*) vs one gbt_sum per instance, and vs the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_13382_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_2501_13382_gb300 import build, gbt
+    build.build()
+    gbt.load()
+    torch.cuda.init()
+    return gbt
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _batch_setup(G, n_src=6, side=40, seed=44):
+    import torch
+    w = I.batched_city(n_sources=n_src)
+    rng = np.random.default_rng(seed)
+    sc = G.Scene(w.scene)
+    gam = torch.as_tensor(w.scene.gamma, device="cuda")
+    insts, srcs = [], []
+    for i, s in enumerate(w.sources):
+        n = int(rng.integers(1024, 12000))              # uneven ray counts
+        src = I.Source(s.pos, n, s.max_reflections, s.max_path)
+        recv_np = I.receiver_grid(side + 4 * i, 250.0, 1.5)  # uneven receiver counts
+        recv = torch.as_tensor(recv_np, device="cuda")
+        freqs = list(w.freqs[i % 3:i % 3 + 3 + (i % 2)])
+        b = [I.beam_b_rule(n, f) for f in freqs]
+        tr = G.Trace(sc, src)
+        insts.append(dict(trace=tr, recv=recv, freqs=freqs, beam_b=b, gamma=gam,
+                          order=G.recv_order(recv)))
+        srcs.append((src, recv_np, freqs, b))
+    return w, sc, gam, insts, srcs
+
+
+def test_batch_equals_per_instance_sums(G):
+    import torch
+    w, sc, gam, insts, _ = _batch_setup(G)
+    batch = G.Batch(insts, window=w.window, use_graph=True)
+    for rep in range(2):                               # capture, then replay
+        batch.submit()
+        torch.cuda.synchronize()
+        G.gbt_sync()
+        for d, out in zip(batch.instances, batch.outputs):
+            ref = G.gbs_sum(d["trace"], d["recv"], d["freqs"], d["beam_b"], gam, order=d["order"],
+                            window=w.window)
+            torch.cuda.synchronize()
+            e = rel_l2(out.cpu().numpy().astype(np.complex128), ref.cpu().numpy().astype(np.complex128))
+            assert e < 1e-6, (rep, e)
+
+
+def test_batch_graph_replay_sees_new_gamma(G):
+    import torch
+    w, sc, gam, insts, srcs = _batch_setup(G, n_src=3, side=32, seed=3)
+    batch = G.Batch(insts, window=w.window, use_graph=True, autotune=True)
+    batch.submit()
+    torch.cuda.synchronize()
+    new_gamma = np.linspace(0.5, 0.99, w.scene.n_materials).astype(np.float32)
+    gam.copy_(torch.as_tensor(new_gamma, device="cuda"))   # same buffer, new contents
+    batch.submit()
+    torch.cuda.synchronize()
+    src, recv_np, freqs, b = srcs[1]
+    otr = O.trace(w.scene, src)
+    po = O.gbs_sum(otr, recv_np, freqs, b, w.scene.c, new_gamma, window=w.window)
+    got = batch.outputs[1].cpu().numpy().astype(np.complex128)
+    assert rel_l2(got, po) < 1e-4
