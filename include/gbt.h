@@ -181,7 +181,9 @@ typedef struct gbt_sum_args {
     int32_t precision;            /* GBT_PRECISION_F32 / GBT_PRECISION_F64 */
     int32_t accumulate;           /* 0 overwrite, 1 add into out */
     int32_t seg_split;            /* segment ranges per receiver tile; 0 = automatic */
-    int32_t reserved;
+    int32_t tile_cull;            /* 1: skip, per warp of 64 receivers, segments whose beams
+                                     provably reach none of them (same result, less work);
+                                     0: test every pair */
     int64_t max_device_bytes;     /* gbt_solve only: device budget for one chunk; 0 = auto */
 } gbt_sum_args;
 
@@ -274,6 +276,7 @@ typedef struct gbt_sum_stats {
     int64_t pairs;
     int64_t pairs_prefiltered;
     int64_t triples_kept;
+    int64_t pairs_tested;         /* pairs that reached the per-pair test (all, unless tile_cull) */
 } gbt_sum_stats;
 
 gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,

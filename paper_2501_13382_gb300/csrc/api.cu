@@ -590,6 +590,7 @@ gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,
         stats->pairs = (int64_t)nseg * a.n_recv;
         stats->pairs_prefiltered = (int64_t)h[1];
         stats->triples_kept = (int64_t)h[2];
+        stats->pairs_tested = (int64_t)h[3];
     });
 }
 

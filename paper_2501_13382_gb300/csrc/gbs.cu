@@ -65,6 +65,7 @@ struct alignas(16) FwdParams {
     const float *rec;          // AoS records, kRecFloats per segment
     int nf;
     int uniform_b;             // all b equal: frequencies sorted by k, loop stops at first cull
+    int tile_cull;             // skip segments that reach none of a warp's receivers
     float cutoff;
     float pre_alpha, pre_beta; // prefilter: keep iff alpha n^2 <= s^2 + beta
     int splits;
@@ -395,14 +396,35 @@ __device__ __forceinline__ void fold(float4 *acc, float2 &t)
 
 // Turn lane's raw record into the prefilter view relative to (cx, cy, cz) and
 // the exact-path columns.
-__device__ __forceinline__ void stage_transform(WarpSmem &w, const float4 (&raw)[kRecFloats / 4],
+// The warp's receivers lie in the ball (sphere centre, radius) given relative
+// to (cx, cy, cz).  Returns false when the segment's beam provably reaches none
+// of them: the distance to the ray is 1-Lipschitz, so n >= n_c - R and
+// |s| <= |s_c| + R for every receiver in the ball.
+template <int WINDOW>
+__device__ __forceinline__ bool stage_transform(WarpSmem &w, const float4 (&raw)[kRecFloats / 4],
                                                 int lane, bool valid, float cx, float cy, float cz,
-                                                float alpha, float beta)
+                                                float alpha, float beta, float4 sphere)
 {
     const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2], r3 = raw[3], r4 = raw[4];
     float4 *P = w.P[lane];
+    bool pass = false;
     if (valid) {
         const float ox = (r0.x - cx) + r2.x, oy = (r0.y - cy) + r2.y, oz = (r0.z - cz) + r2.z;
+        {
+            const float dx = sphere.x - ox, dy = sphere.y - oy, dz = sphere.z - oz;
+            const float sc = fmaf(dx, r1.x, fmaf(dy, r1.y, dz * r1.z));
+            const float cxr = dy * r1.z - dz * r1.y, cyr = dz * r1.x - dx * r1.z,
+                        czr = dx * r1.y - dy * r1.x;
+            const float nc = sqrtf(fmaf(cxr, cxr, fmaf(cyr, cyr, czr * czr)));
+            // radius plus slack for rounding at these magnitudes
+            const float R = sphere.w * 1.0001f + 0.05f + 1e-5f * (fabsf(ox) + fabsf(oy) + fabsf(oz));
+            bool win;
+            if (WINDOW == GBT_WINDOW_LINE) win = r0.w + sc + R >= -kWinMargin;
+            else win = (sc + R >= -kWinMargin) && (sc - R <= r1.w + kWinMargin);
+            const float sabs = fabsf(r0.w + sc) + R;
+            const float nn = nc - R;
+            pass = win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
+        }
         const float ot = fmaf(ox, r1.x, fmaf(oy, r1.y, oz * r1.z));
         const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
         const float a2 = 2.f * alpha;
@@ -431,6 +453,7 @@ __device__ __forceinline__ void stage_transform(WarpSmem &w, const float4 (&raw)
     w.cold[C_TXL][lane] = r3.x; w.cold[C_TYL][lane] = r3.y; w.cold[C_TZL][lane] = r3.z;
     w.cold[C_LL][lane] = r3.w;
     w.cold[C_AMP][lane] = r4.x;
+    return pass;
 }
 
 template <int NF>
@@ -480,6 +503,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
 
     volatile int *abort_flag = &S.abort_flag;
     uint32_t n_pre = 0, n_kept = 0;
+    unsigned long long n_test = 0;
     uint32_t g = 0;   // batches through the ring so far (same count in every role)
 
     for (;;) {
@@ -588,6 +612,32 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 for (int f = 0; f < NF; ++f) S.adj[warp].segH[f][lane] = 0.f;
             }
             __syncwarp();
+            // bounding ball of the warp's receivers (relative to its first receiver)
+            float4 sphere = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p.tile_cull) {
+                float sx = 0.f, sy = 0.f, sz = 0.f, nv = 0.f;
+#pragma unroll
+                for (int k = 0; k < kR; ++k)
+                    if ((valid >> k) & 1u) { sx += xp[k]; sy += yp[k]; sz += zp[k]; nv += 1.f; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                    sz += __shfl_xor_sync(0xffffffffu, sz, o);
+                    nv += __shfl_xor_sync(0xffffffffu, nv, o);
+                }
+                if (nv > 0.f) { sx /= nv; sy /= nv; sz /= nv; }
+                float r2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < kR; ++k)
+                    if ((valid >> k) & 1u) {
+                        const float ex = xp[k] - sx, ey = yp[k] - sy, ez = zp[k] - sz;
+                        r2 = fmaxf(r2, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                    }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+                sphere = make_float4(sx, sy, sz, sqrtf(r2));
+            }
             static_assert(kR == 2, "the paired prefilter handles two receivers per lane");
             const f2x X2 = pk(xp[0], xp[1]), Y2 = pk(yp[0], yp[1]), Z2 = pk(zp[0], zp[1]);
             const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
@@ -603,8 +653,10 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 const uint32_t q = g + kb_, st = q % kStages, ph = (q / kStages) & 1u;
                 if (!mbar_wait(smem_addr(&S.full[st]), ph, abort_flag, p.status)) break;
                 const int64_t b = split + (int64_t)kb_ * p.splits;
-                stage_transform(w, S.raw[st][lane], lane, b * kBatch + lane < n_seg, cx, cy, cz,
-                                alpha, beta);
+                const bool seg_ok = b * kBatch + lane < n_seg;
+                const bool pass = stage_transform<WINDOW>(w, S.raw[st][lane], lane, seg_ok, cx, cy,
+                                                          cz, alpha, beta, sphere);
+                const uint32_t tmask = __ballot_sync(0xffffffffu, pass);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_addr(&S.empty[st]));
                 if (!warp_live) continue;
@@ -617,8 +669,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 uint32_t m[kR];
 #pragma unroll
                 for (int k = 0; k < kR; ++k) m[k] = 0u;
-#pragma unroll 4
-                for (int jj = 0; jj < kBatch; ++jj) {
+                // keep bits of segment jj for both receivers (sign bit = keep)
+                auto pair_bits = [&](int jj, uint32_t &kb0, uint32_t &kb1) {
                     const float4 *P = w.P[jj];
                     const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3], p4 = P[4];
                     const f2x TX = pk(p0.x, p0.y), TY = pk(p0.z, p0.w), TZ = pk(p1.x, p1.y);
@@ -631,7 +683,6 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     const f2x gg = fma2(mul2(sl, AL2), sl, fma2(sm2, sm2, nd));
                     float g0, g1, s0_, s1_;
                     upk(gg, g0, g1);
-                    uint32_t kb0, kb1;
                     if (WINDOW == GBT_WINDOW_LINE) {
                         upk(sm2, s0_, s1_);
                         kb0 = ~(__float_as_uint(g0) | __float_as_uint(s0_));
@@ -645,8 +696,28 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                         kb0 = ~(__float_as_uint(g0) | __float_as_uint(a0)) & __float_as_uint(b0_);
                         kb1 = ~(__float_as_uint(g1) | __float_as_uint(a1)) & __float_as_uint(b1_);
                     }
-                    m[0] = __funnelshift_l(kb0, m[0], 1);
-                    m[1] = __funnelshift_l(kb1, m[1], 1);
+                };
+                if (p.tile_cull) {
+                    // only the segments that can reach this warp's receivers
+                    uint32_t T = tmask;
+                    if (STATS) n_test += __popc(T) * __popc(valid);
+                    while (T) {
+                        const int jj = __ffs(T) - 1;
+                        T &= T - 1;
+                        uint32_t kb0, kb1;
+                        pair_bits(jj, kb0, kb1);
+                        m[0] |= (kb0 >> 31) << (31 - jj);
+                        m[1] |= (kb1 >> 31) << (31 - jj);
+                    }
+                } else {
+                    if (STATS) n_test += (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * __popc(valid);
+#pragma unroll 4
+                    for (int jj = 0; jj < kBatch; ++jj) {
+                        uint32_t kb0, kb1;
+                        pair_bits(jj, kb0, kb1);
+                        m[0] = __funnelshift_l(kb0, m[0], 1);
+                        m[1] = __funnelshift_l(kb1, m[1], 1);
+                    }
                 }
                 // ---- survivors, in segment order per receiver
 #pragma unroll
@@ -705,6 +776,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
     if (STATS && !producer) {
         atomicAdd(&prm.stats[1], (unsigned long long)n_pre);
         atomicAdd(&prm.stats[2], (unsigned long long)n_kept);
+        atomicAdd(&prm.stats[3], n_test);
     }
 }
 
@@ -1101,6 +1173,7 @@ FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum
     q.rec = rec;
     q.nf = a.n_freq;
     q.cutoff = (float)a.cutoff;
+    q.tile_cull = a.tile_cull ? 1 : 0;
     // frequency order: when every b is equal, sort by k so that the kept
     // frequencies of a pair form a prefix (wider beams first)
     int perm[GBT_MAX_FREQ];

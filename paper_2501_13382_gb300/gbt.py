@@ -66,13 +66,13 @@ class gbt_sum_args(C.Structure):
                 ("freq_hz", C.c_double * MAX_FREQ), ("beam_b", C.c_double * MAX_FREQ),
                 ("gamma", C.c_void_p), ("ray_weight", C.c_void_p), ("out", C.c_void_p),
                 ("cutoff", C.c_double), ("precision", C.c_int32), ("accumulate", C.c_int32),
-                ("seg_split", C.c_int32), ("reserved", C.c_int32),
+                ("seg_split", C.c_int32), ("tile_cull", C.c_int32),
                 ("max_device_bytes", C.c_int64)]
 
 
 class gbt_sum_stats(C.Structure):
     _fields_ = [("n_segments", C.c_int64), ("pairs", C.c_int64), ("pairs_prefiltered", C.c_int64),
-                ("triples_kept", C.c_int64)]
+                ("triples_kept", C.c_int64), ("pairs_tested", C.c_int64)]
 
 
 class gbt_batch_desc(C.Structure):
@@ -360,7 +360,7 @@ def recv_order(recv) -> "torch.Tensor":
 def sum_args(recv, freqs: Sequence[float], beam_b: Sequence[float], gamma, out,
              ray_weight=None, order=None, window: int = WINDOW_LINE, cutoff: float = 16.0,
              precision: int = PRECISION_F32, accumulate: bool = False, seg_split: int = 0,
-             max_device_bytes: int = 0) -> gbt_sum_args:
+             max_device_bytes: int = 0, tile_cull: bool = False) -> gbt_sum_args:
     a = gbt_sum_args()
     a.recv = _ptr(recv)
     a.n_recv = int(recv.shape[0]) if recv is not None else 0
@@ -377,6 +377,7 @@ def sum_args(recv, freqs: Sequence[float], beam_b: Sequence[float], gamma, out,
     a.precision = int(precision)
     a.accumulate = 1 if accumulate else 0
     a.seg_split = int(seg_split)
+    a.tile_cull = 1 if tile_cull else 0
     a.max_device_bytes = int(max_device_bytes)
     return a
 
@@ -393,7 +394,7 @@ def _check_tensors(recv, gamma, ray_weight, order):
 
 def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
             window: int = WINDOW_LINE, cutoff: float = 16.0, precision: int = PRECISION_F32,
-            out=None, accumulate: bool = False, seg_split: int = 0):
+            out=None, accumulate: bool = False, seg_split: int = 0, tile_cull: bool = False):
     """Complex pressure p[f, r] (torch complex64 on the device)."""
     import torch
     _check_tensors(recv, gamma, ray_weight, order)
@@ -401,23 +402,25 @@ def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=Non
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
     a = sum_args(recv, freqs, beam_b, gamma, out, ray_weight, order, window, cutoff, precision,
-                 accumulate, seg_split)
+                 accumulate, seg_split, tile_cull=tile_cull)
     gbt_sum(trace.handle, a, _stream_ptr())
     return out
 
 
 def sum_stats(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
-              window: int = WINDOW_LINE, cutoff: float = 16.0) -> dict:
+              window: int = WINDOW_LINE, cutoff: float = 16.0, tile_cull: bool = False) -> dict:
     _check_tensors(recv, gamma, ray_weight, order)
-    a = sum_args(recv, freqs, beam_b, gamma, None, ray_weight, order, window, cutoff)
+    a = sum_args(recv, freqs, beam_b, gamma, None, ray_weight, order, window, cutoff,
+                 tile_cull=tile_cull)
     st = gbt_sum_stats_get(trace.handle, a, _stream_ptr())
     return {"n_segments": st.n_segments, "pairs": st.pairs,
-            "pairs_prefiltered": st.pairs_prefiltered, "triples_kept": st.triples_kept}
+            "pairs_prefiltered": st.pairs_prefiltered, "triples_kept": st.triples_kept,
+            "pairs_tested": st.pairs_tested}
 
 
 def gbs_solve(scene: Scene, source, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
               window: int = WINDOW_LINE, cutoff: float = 16.0, max_device_bytes: int = 0,
-              out=None, accumulate: bool = False):
+              out=None, accumulate: bool = False, tile_cull: bool = False):
     """Trace + sum of one source, chunked over rays under a device-byte budget."""
     import torch
     _check_tensors(recv, gamma, ray_weight, order)
@@ -425,7 +428,7 @@ def gbs_solve(scene: Scene, source, recv, freqs, beam_b, gamma, ray_weight=None,
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
     a = sum_args(recv, freqs, beam_b, gamma, out, ray_weight, order, window, cutoff,
-                 PRECISION_F32, accumulate, 0, max_device_bytes)
+                 PRECISION_F32, accumulate, 0, max_device_bytes, tile_cull=tile_cull)
     gbt_solve(scene.handle, source_desc(source), a, _stream_ptr())
     return out
 
@@ -439,7 +442,7 @@ class Batch:
     use_graph is set); results land in each instance's ``out``."""
 
     def __init__(self, instances, window: int = WINDOW_SEGMENT, cutoff: float = 16.0,
-                 use_graph: bool = True, autotune: bool = False):
+                 use_graph: bool = True, autotune: bool = False, tile_cull: bool = False):
         import torch
         self.instances = []
         args = []
@@ -453,7 +456,8 @@ class Batch:
             d = dict(inst, out=out)
             self.instances.append(d)
             args.append(sum_args(recv, inst["freqs"], inst["beam_b"], inst["gamma"], out,
-                                 inst.get("ray_weight"), inst.get("order"), window, cutoff))
+                                 inst.get("ray_weight"), inst.get("order"), window, cutoff,
+                                 tile_cull=tile_cull))
         n = len(args)
         self._args = (gbt_sum_args * n)(*args)
         self._traces = (C.c_void_p * n)(*[d["trace"].handle for d in self.instances])
@@ -483,7 +487,7 @@ class Batch:
 
 def gbs_sum_backward(trace: Trace, recv, freqs, beam_b, gamma, grad_out, ray_weight=None,
                      order=None, window: int = WINDOW_LINE, cutoff: float = 16.0,
-                     need_weight: bool = True, need_b: bool = True):
+                     need_weight: bool = True, need_b: bool = True, tile_cull: bool = False):
     """(d gamma, d ray_weight, d b) of a real loss with dL/dp = grad_out (complex64 [F, Nr])."""
     import torch
     _check_tensors(recv, gamma, ray_weight, order)
@@ -492,7 +496,8 @@ def gbs_sum_backward(trace: Trace, recv, freqs, beam_b, gamma, grad_out, ray_wei
     dg = torch.empty_like(gamma)
     dw = torch.empty(trace.n_fan, dtype=torch.float32, device=recv.device) if need_weight else None
     db = torch.empty(len(freqs), dtype=torch.float64, device=recv.device) if need_b else None
-    a = sum_args(recv, freqs, beam_b, gamma, None, ray_weight, order, window, cutoff)
+    a = sum_args(recv, freqs, beam_b, gamma, None, ray_weight, order, window, cutoff,
+                 tile_cull=tile_cull)
     a.out = 0
     gbt_sum_backward(trace.handle, a, _ptr(go), _ptr(dg), _ptr(dw), _ptr(db), _stream_ptr())
     return dg, dw, db

@@ -110,3 +110,21 @@ def test_autograd_loss_gradients(G):
     assert _rel(gam.grad.cpu().numpy(), dg_o) < TOL
     assert _rel(bt.grad.cpu().numpy(), db_o) < TOL
     assert math.isclose(float(loss.detach()), float(np.sum(np.abs(po - target) ** 2)), rel_tol=1e-3)
+
+
+def test_backward_tile_cull_matches_dense(G):
+    import torch
+    sc0, src, recv, freqs, b, gamma, win = _problem(n_rays=8192, side=48, seed=12)
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src)
+    r = torch.as_tensor(recv, device="cuda")
+    rng = np.random.default_rng(4)
+    g = torch.as_tensor((rng.normal(size=(len(freqs), recv.shape[0])) +
+                         1j * rng.normal(size=(len(freqs), recv.shape[0]))).astype(np.complex64),
+                        device="cuda")
+    gam = torch.as_tensor(gamma, device="cuda")
+    d = G.gbs_sum_backward(tr, r, list(freqs), list(b), gam, g, window=win)
+    c = G.gbs_sum_backward(tr, r, list(freqs), list(b), gam, g, window=win, tile_cull=True)
+    torch.cuda.synchronize()
+    for x, y in zip(d, c):
+        assert _rel(y.cpu().numpy(), x.cpu().numpy()) < 1e-5
