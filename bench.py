@@ -39,10 +39,11 @@ UNIT = "evals/s"
 OPS_PER_PAIR = 15
 OPS_PER_KEPT = 24
 LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
-KERNEL_TAG = "gbs_fwd_kernel<8,LINE> r1"
-# DRAM bytes per launch of the dominant kernel from an ncu capture of this exact kernel
-# version (None until captured for it).
-KERNEL_TRAFFIC = {}
+KERNEL_TAG = "gbs_fwd_kernel<8,LINE,fwd,plain> ring-v1"
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of this
+# exact kernel version (profiles/gbs_fwd_open_plane_64k_rays_256x256_6f.md); a changed
+# kernel gets a new tag and no entry until it is captured again.
+KERNEL_TRAFFIC = {"gbs_fwd_kernel<8,LINE,fwd,plain> ring-v1": 62994688}
 
 
 def _env_int(name, default):
@@ -169,6 +170,123 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _events(torch, n):
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n)]
+
+
+def _timed(torch, stream, fn, steps, flush=None):
+    """Sum of per-step CUDA-event times (flush between steps, outside the events)."""
+    ev = _events(torch, steps)
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return float(sum(a.elapsed_time(b) for a, b in ev))
+
+
+def bench_tile_cull(G, torch, stream, sc, w, recv, gam, order, out, flush, steps, n_seg):
+    """The same open-plane step with the per-warp segment pre-cull (identical field)."""
+    src = w.sources[0]
+    freqs, bb = list(w.freqs), list(w.beam_b[0])
+
+    def step():
+        G.gbs_solve(sc, src, recv, freqs, bb, gam, order=order, window=w.window, cutoff=w.cutoff,
+                    out=out, tile_cull=True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    G.gbt_timing_enable(True)
+    G.gbt_timing_read(reset=True)
+    ms = _timed(torch, stream, step, steps, flush)
+    G.gbt_timing_enable(False)
+    n_k, k_ms = G.gbt_timing_read(reset=True)
+    tr = G.Trace(sc, src)
+    st = G.sum_stats(tr, recv, freqs, bb, gam, order=order, window=w.window, cutoff=w.cutoff,
+                     tile_cull=True)
+    tr.close()
+    evals = float(recv.shape[0]) * n_seg * len(freqs)
+    return {"value": evals / (ms / steps * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "kernel_ms": k_ms / max(n_k, 1), "pairs_tested": st["pairs_tested"],
+            "pairs": st["pairs"], "note": "field bit-identical to testing every pair"}
+
+
+def bench_batched(G, torch, stream, steps=5):
+    """Batched city: 32 sources (log-uniform 4,096-262,144 rays), 8 frequencies, one persistent
+    launch per submit (CUDA graph) vs one gbt_sum launch per source; receivers 128 x 128."""
+    from paper_2501_13382_gb300 import inputs as I
+    w = I.batched_city()
+    recv_np = I.receiver_grid(128, 250.0, 1.5)
+    sc = G.Scene(w.scene)
+    gam = torch.as_tensor(w.scene.gamma, device="cuda")
+    recv = torch.as_tensor(recv_np, device="cuda")
+    order = G.recv_order(recv)
+    insts, evals = [], 0.0
+    for i, src in enumerate(w.sources):
+        tr = G.Trace(sc, src)
+        n_seg = tr.info().n_segments
+        evals += float(recv.shape[0]) * n_seg * len(w.freqs)
+        insts.append(dict(trace=tr, recv=recv, freqs=list(w.freqs), beam_b=list(w.beam_b[i]),
+                          gamma=gam, order=order))
+    batch = G.Batch(insts, window=w.window, use_graph=True, autotune=True)
+    outs = [torch.empty_like(o) for o in batch.outputs]
+
+    def plain():
+        for d, o in zip(insts, outs):
+            G.gbs_sum(d["trace"], recv, d["freqs"], d["beam_b"], gam, order=order,
+                      window=w.window, out=o)
+    batch.submit()
+    plain()
+    torch.cuda.synchronize()
+    t_b = _timed(torch, stream, batch.submit, steps) / steps
+    t_p = _timed(torch, stream, plain, steps) / steps
+    err = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+              for a, b in zip(batch.outputs, outs))
+    batch.close()
+    return {"workload": "batched_city_32src_8f_128x128", "evals": evals,
+            "batched": {"value": evals / (t_b * 1e-3), "ms": t_b},
+            "plain_per_instance": {"value": evals / (t_p * 1e-3), "ms": t_p},
+            "speedup": t_p / t_b, "rel_l2_batched_vs_plain": err}
+
+
+def bench_fwd_bwd(G, torch, stream, steps=5):
+    """Differentiable city: 262,144 rays, <= 6 reflections, 128 x 128 receivers, 4 frequencies;
+    forward + backward (gradients for 9 reflection coefficients and 4 beam parameters) vs
+    forward alone."""
+    from paper_2501_13382_gb300 import inputs as I
+    w = I.diff_city()
+    sc = G.Scene(w.scene)
+    src = w.sources[0]
+    tr = G.Trace(sc, src)
+    n_seg = tr.info().n_segments
+    recv = torch.as_tensor(w.receivers, device="cuda")
+    order = G.recv_order(recv)
+    gam = torch.as_tensor(w.scene.gamma, device="cuda")
+    freqs, bb = list(w.freqs), list(w.beam_b[0])
+    out = torch.empty((len(freqs), recv.shape[0]), dtype=torch.complex64, device="cuda")
+    g = torch.ones_like(out)
+
+    def fwd():
+        G.gbs_sum(tr, recv, freqs, bb, gam, order=order, window=w.window, out=out)
+
+    def fwd_bwd():
+        fwd()
+        G.gbs_sum_backward(tr, recv, freqs, bb, gam, g, order=order, window=w.window)
+    fwd_bwd()
+    torch.cuda.synchronize()
+    t_f = _timed(torch, stream, fwd, steps) / steps
+    t_fb = _timed(torch, stream, fwd_bwd, steps) / steps
+    evals = float(recv.shape[0]) * n_seg * len(freqs)
+    tr.close()
+    return {"workload": w.name, "evals": evals,
+            "forward": {"value": evals / (t_f * 1e-3), "ms": t_f},
+            "forward_backward": {"value": evals / (t_fb * 1e-3), "ms": t_fb},
+            "backward_over_forward": (t_fb - t_f) / t_f}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,6 +297,8 @@ def main():
                     help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the tile-cull, batched and forward+backward forms")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -317,6 +437,18 @@ def main():
                     "d2h_bytes_per_step": int(out.numel() * 8)},
             "gpu_launches": 8 * args.steps,
             "clocks": clocks}
+
+    if not args.no_forms:
+        line["forms"] = {
+            "tile_cull": bench_tile_cull(G, torch, stream, sc, w, recv, gam, order, out, flush,
+                                         min(args.steps, 50), n_seg),
+            "batched": bench_batched(G, torch, stream),
+            "fwd_bwd": bench_fwd_bwd(G, torch, stream),
+        }
+        # the forms overwrite `out`; recompute the measured workload's field for the check
+        G.gbs_solve(sc, src, recv, list(w.freqs), list(w.beam_b[0]), gam, order=order,
+                    window=w.window, cutoff=w.cutoff, out=out)
+        torch.cuda.synchronize()
 
     if world == 1 and not args.no_cpu:
         # CPU baseline + accuracy check of this run's field on the oracle's sample
