@@ -288,6 +288,14 @@ gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,
  * GBT_ERR_TIMEOUT or GBT_ERR_DEVICE_STATUS if a kernel flagged a problem. */
 gbt_status gbt_sync(void *stream);
 
+/* Self test of the failure path for device waits (no counterpart in the paper):
+ * launches one thread that waits on a shared-memory barrier phase that nothing
+ * completes, with the same bounded try-wait loop the pair kernel uses, for at
+ * most `spins` tries (1 .. 2^24).  The wait runs out, the kernel flags a
+ * timeout and returns; the following gbt_sync returns GBT_ERR_TIMEOUT and
+ * clears the flag, and the context stays usable. */
+gbt_status gbt_selftest_timeout(int64_t spins, void *stream);
+
 /* Description of the last failure on the calling thread ("" if none). */
 const char *gbt_last_error(void);
 

@@ -630,6 +630,14 @@ gbt_status gbt_batch_destroy(gbt_batch_t *batch)
     });
 }
 
+gbt_status gbt_selftest_timeout(int64_t spins, void *stream)
+{
+    return guarded([&] {
+        GBT_REQUIRE(spins >= 1 && spins <= (1LL << 24), "spins must be in [1, 2^24]");
+        selftest_timeout_launch((long long)spins, static_cast<cudaStream_t>(stream));
+    });
+}
+
 gbt_status gbt_sync(void *stream)
 {
     return guarded([&] {

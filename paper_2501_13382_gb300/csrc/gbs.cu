@@ -1740,6 +1740,28 @@ void batch_destroy(BatchImpl *B)
     delete B;
 }
 
+// ---------------------------------------------------- bounded-wait self test --
+
+// Waits on an mbarrier phase that nothing completes, with the same bounded
+// try-wait loop the pair kernel uses; when the limit runs out it flags
+// STATUS_TIMEOUT and returns, leaving the context usable.
+__global__ void selftest_wait_kernel(long long spins, unsigned int *status)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_addr(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (long long it = 0; it < spins; ++it)
+        if (mbar_try_wait(smem_addr(&bar), 0u)) return;
+    atomicOr(status, STATUS_TIMEOUT);
+}
+
+void selftest_timeout_launch(long long spins, cudaStream_t s)
+{
+    selftest_wait_kernel<<<1, 32, 0, s>>>(spins, status_word());
+    GBT_CUDA(cudaGetLastError());
+}
+
 // ------------------------------------------------- receiver order, no allocation --
 //
 // Some callers cannot allocate device memory at the point where they need a

@@ -102,6 +102,7 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
 void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scratch,
                        cudaStream_t s);
 size_t recv_order_scratch_bytes(int64_t n);
+void selftest_timeout_launch(long long spins, cudaStream_t s);
 void recv_order_noalloc_launch(const float *recv, int64_t n, int32_t *order, cudaStream_t s);
 
 // ---- batched persistent launch (gbs.cu) ----

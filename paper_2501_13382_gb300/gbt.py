@@ -105,6 +105,7 @@ _SIGS = {
     "gbt_batch_submit": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gbt_batch_destroy": (C.c_int, [C.c_void_p]),
     "gbt_sync": (C.c_int, [C.c_void_p]),
+    "gbt_selftest_timeout": (C.c_int, [C.c_int64, C.c_void_p]),
     "gbt_timing_enable": (C.c_int, [C.c_int32]),
     "gbt_timing_read": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int32]),
     "gbt_sum_stats_get": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.POINTER(gbt_sum_stats),
@@ -233,6 +234,41 @@ def gbt_batch_destroy(batch: int):
 
 def gbt_sync(stream: int = 0):
     _check(load().gbt_sync(C.c_void_p(stream)), "gbt_sync")
+
+
+def gbt_selftest_timeout(spins: int, stream: int = 0):
+    _check(load().gbt_selftest_timeout(C.c_int64(spins), C.c_void_p(stream)), "gbt_selftest_timeout")
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+_allocator_keepalive = []
+
+
+def gbt_set_allocator(alloc=None, free=None):
+    """Install Python callables alloc(bytes, stream) -> int and free(ptr, stream) as the
+    library's device allocator (None restores the default stream-ordered pool)."""
+    if alloc is None:
+        _check(load().gbt_set_allocator(None), "gbt_set_allocator")
+        _allocator_keepalive.clear()
+        return
+    a = ALLOC_FN(lambda n, stream, ctx: alloc(int(n), stream or 0) or None)
+    f = FREE_FN(lambda ptr, stream, ctx: free(int(ptr or 0), stream or 0))
+    desc = gbt_allocator(C.cast(a, C.c_void_p).value, C.cast(f, C.c_void_p).value, None)
+    _allocator_keepalive[:] = [a, f, desc]
+    _check(load().gbt_set_allocator(C.byref(desc)), "gbt_set_allocator")
+
+
+def use_torch_allocator():
+    """Route the library's device memory through torch's caching allocator."""
+    import torch
+
+    def alloc(n, stream):
+        return torch.cuda.caching_allocator_alloc(n, torch.cuda.current_device(), stream or None)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+    gbt_set_allocator(alloc, free)
 
 
 def gbt_timing_enable(enable: bool):
