@@ -44,7 +44,7 @@ constexpr int kCtaRecv = kConsumerWarps * kWarpRecv;
 constexpr int kBatch = 32;                  // segments per staged batch
 constexpr long long kSpinLimit = 1LL << 22; // bounded mbarrier waits
 enum { kFwd = 0, kStats = 1, kBwd = 2 };    // what the pair kernel does with survivors
-constexpr int kFoldEvery = 4;               // batches between float-float folds
+constexpr int kFoldEvery = 16;              // batches between float-float folds
 constexpr float kWinMargin = 0.01f;         // prefilter window slack (m)
 
 struct FreqConst {
@@ -582,7 +582,9 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             float4 *const part_base = p.partial + (int64_t)split * p.nf * p.n_recv;
 #pragma unroll
             for (int k = 0; k < kR; ++k) {
-                const int64_t r = wbase + (int64_t)lane * kR + k;
+                // lane holds receivers lane and lane + 32 of the warp: the two halves of
+                // the warp's Morton patch, so a beam edge splits work evenly over lanes
+                const int64_t r = wbase + (int64_t)k * 32 + lane;
                 xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
                 ridx[k] = -1;
                 if (r < p.n_recv) {
@@ -649,6 +651,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
 #pragma unroll
                 for (int f = 0; f < NF; ++f) tmp[k][f] = make_float2(0.f, 0.f);
 
+            bool dirty = false;   // survivors since the last fold (this lane)
             for (uint32_t kb_ = 0; kb_ < nb; ++kb_) {
                 const uint32_t q = g + kb_, st = q % kStages, ph = (q / kStages) & 1u;
                 if (!mbar_wait(smem_addr(&S.full[st]), ph, abort_flag, p.status)) break;
@@ -750,7 +753,9 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                         S.adj[warp].segH[f][lane] = 0.f;
                     }
                 }
-                if (MODE == kFwd && (kb_ % kFoldEvery) == kFoldEvery - 1) {
+                if (MODE == kFwd) dirty |= (m[0] | m[1]) != 0u;
+                if (MODE == kFwd && (kb_ % kFoldEvery) == kFoldEvery - 1 && dirty) {
+                    dirty = false;
 #pragma unroll
                     for (int k = 0; k < kR; ++k)
 #pragma unroll
@@ -1160,6 +1165,7 @@ void launch_fwd_nf(const FwdParams &p, cudaStream_t s)
     if (p.nf <= 1) launch_fwd<1, WINDOW>(p, s);
     else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, s);
     else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, s);
+    else if (p.nf <= 6) launch_fwd<6, WINDOW>(p, s);
     else launch_fwd<8, WINDOW>(p, s);
 }
 
