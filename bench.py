@@ -104,9 +104,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _workload():
+WORKLOADS = ("open_plane_large", "open_plane_small", "city", "diff_city")
+
+
+def _workload(name: str = "open_plane_large"):
+    """The metric is quoted on open_plane_large (default); the others can be measured on
+    request with --workload (the batched city is measured as a form)."""
     from paper_2501_13382_gb300 import inputs as I
-    return I.open_plane_large()
+    return {"open_plane_large": I.open_plane_large, "open_plane_small": I.open_plane_small,
+            "city": I.city, "diff_city": I.diff_city}[name]()
 
 
 def _oracle_sample(w, budget_s: float, seed: int = 17):
@@ -139,7 +145,7 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from paper_2501_13382_gb300 import inputs as I
-    w = _workload()
+    w = _workload(args.workload)
     n_sample = 48
     idx = I.receiver_subset(w.receivers, n_sample, 23)
     times = []
@@ -297,6 +303,9 @@ def main():
                     help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--workload", default="open_plane_large", choices=WORKLOADS)
+    ap.add_argument("--tile-cull", action="store_true",
+                    help="time the tile-cull variant as the main step")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the tile-cull, batched and forward+backward forms")
     args = ap.parse_args()
@@ -322,7 +331,7 @@ def main():
         dist.barrier()
     from paper_2501_13382_gb300 import gbt as G
 
-    w = _workload()
+    w = _workload(args.workload)
     src = w.sources[0]
     stream = torch.cuda.current_stream()
     sc = G.Scene(w.scene)
@@ -336,14 +345,15 @@ def main():
 
     # work statistics (outside the timed region)
     tr = G.Trace(sc, src)
-    st = G.sum_stats(tr, recv, freqs, bb, gam, order=order, window=w.window, cutoff=w.cutoff)
+    st = G.sum_stats(tr, recv, freqs, bb, gam, order=order, window=w.window, cutoff=w.cutoff,
+                     tile_cull=args.tile_cull)
     n_seg = st["n_segments"]
     tr.close()
     evals = float(recv.shape[0]) * n_seg * len(freqs)
 
     def step():
         G.gbs_solve(sc, src, recv, freqs, bb, gam, order=order, window=w.window,
-                    cutoff=w.cutoff, out=out)
+                    cutoff=w.cutoff, out=out, tile_cull=args.tile_cull)
 
     for _ in range(args.warmup):
         step()
@@ -376,7 +386,7 @@ def main():
         recv_e.copy_(host_recv, non_blocking=True)
         o = G.recv_order(recv_e)
         G.gbs_solve(sc, src, recv_e, freqs, bb, gam, order=o, window=w.window,
-                    cutoff=w.cutoff, out=out)
+                    cutoff=w.cutoff, out=out, tile_cull=args.tile_cull)
         host_out.copy_(out, non_blocking=True)
 
     e2e_ms = float("nan")
@@ -412,12 +422,13 @@ def main():
     clocks = clk.summary()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     kern_ms = k_ms / max(n_k, 1)
-    ops = OPS_PER_PAIR * float(st["pairs"]) + OPS_PER_KEPT * float(st["triples_kept"])
+    ops = OPS_PER_PAIR * float(st["pairs_tested"]) + OPS_PER_KEPT * float(st["triples_kept"])
     achieved = ops / (kern_ms * 1e-3) / 1e12
     mhz = clocks["sm_mhz"] or 1492.0
     peak = n_sm * LANES_PER_SM_CLK * mhz * 1e6 / 1e12
+    tag = KERNEL_TAG if (args.workload == "open_plane_large" and not args.tile_cull) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
-                "frac": achieved / peak, "traffic": KERNEL_TRAFFIC.get(KERNEL_TAG),
+                "frac": achieved / peak, "traffic": KERNEL_TRAFFIC.get(tag),
                 "kernel": KERNEL_TAG, "kernel_ms": kern_ms, "kernel_launches": n_k,
                 "ops_per_launch": ops,
                 "peak_basis": f"{n_sm} SMs x {LANES_PER_SM_CLK} lanes x median SM clock "
@@ -429,7 +440,8 @@ def main():
             "config": {"workload": w.name, "rays": src.n_rays, "segments": n_seg,
                        "receivers": int(recv.shape[0]), "freqs": len(freqs),
                        "pairs": st["pairs"], "pairs_prefiltered": st["pairs_prefiltered"],
-                       "triples_kept": st["triples_kept"], "l2": "flushed between steps (256 MiB)",
+                       "triples_kept": st["triples_kept"], "pairs_tested": st["pairs_tested"],
+                       "tile_cull": bool(args.tile_cull), "l2": "flushed between steps (256 MiB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT,
@@ -438,7 +450,7 @@ def main():
             "gpu_launches": 8 * args.steps,
             "clocks": clocks}
 
-    if not args.no_forms:
+    if not args.no_forms and args.workload == "open_plane_large" and not args.tile_cull:
         line["forms"] = {
             "tile_cull": bench_tile_cull(G, torch, stream, sc, w, recv, gam, order, out, flush,
                                          min(args.steps, 50), n_seg),

@@ -8,7 +8,8 @@
  *
  * It is deliberately slow and direct: loops in the order the method states,
  * double precision throughout, no blocking or fusion.  OpenMP only splits the
- * receiver loop (each receiver's sum is independent and keeps its own order).
+ * receiver loop of the sum and the ray loop of the tracer (each receiver's sum
+ * and each ray's path are independent and keep their own order).
  *
  * What it computes (paper: "Accelerating Gaussian beam tracing method with
  * dynamic parallelism on GPUs", arXiv 2501.13382):
@@ -134,6 +135,8 @@ void orc_trace(const orc_scene *sc, const double *src, const double *dirs,
                double *seg_s0, int32_t *seg_bmat, int32_t *seg_hit)
 {
     const int64_t stride = max_refl + 1;
+    /* rays are independent: each writes only its own padded rows */
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n_rays; ++i) {
         double o[3] = {src[0], src[1], src[2]};
         double d[3] = {dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2]};

@@ -341,6 +341,9 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
             sd.tri = static_cast<double *>(dalloc(nt * 12 * sizeof(double), s));
             sd.face = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
             sd.mat = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
+            sd.n_clusters = (d.n_tri + kTriCluster - 1) / kTriCluster;
+            sd.cbox = static_cast<double *>(
+                dalloc((size_t)std::max<int64_t>(sd.n_clusters, 1) * 6 * sizeof(double), s));
             if (d.n_tri > 0) {
                 std::vector<int32_t> face(d.n_tri);
                 for (int64_t k = 0; k < d.n_tri; ++k) face[k] = d.tri_face ? d.tri_face[k] : (int32_t)k;
@@ -351,6 +354,28 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
                                          cudaMemcpyHostToDevice, s));
                 GBT_CUDA(cudaMemcpyAsync(sd.mat, d.tri_material, (size_t)d.n_tri * 4,
                                          cudaMemcpyHostToDevice, s));
+                // cluster boxes on the host: exact min/max, then a relative expansion far
+                // above FP64 rounding so the slab test is conservative
+                std::vector<double> box((size_t)sd.n_clusters * 6);
+                for (int64_t c = 0; c < sd.n_clusters; ++c) {
+                    double lo[3] = {INFINITY, INFINITY, INFINITY};
+                    double hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                    const int64_t k1 = std::min<int64_t>(d.n_tri, (c + 1) * kTriCluster);
+                    for (int64_t k = c * kTriCluster; k < k1; ++k)
+                        for (int v = 0; v < 3; ++v)
+                            for (int a = 0; a < 3; ++a) {
+                                const double x = d.tri_xyz[9 * k + 3 * v + a];
+                                lo[a] = std::min(lo[a], x);
+                                hi[a] = std::max(hi[a], x);
+                            }
+                    for (int a = 0; a < 3; ++a) {
+                        const double pad = 1e-7 * (1.0 + std::max(fabs(lo[a]), fabs(hi[a])));
+                        box[6 * c + a] = lo[a] - pad;
+                        box[6 * c + 3 + a] = hi[a] + pad;
+                    }
+                }
+                GBT_CUDA(cudaMemcpyAsync(sd.cbox, box.data(), box.size() * sizeof(double),
+                                         cudaMemcpyHostToDevice, s));
                 scene_prepare(sd, static_cast<const double *>(raw), s);
                 dfree(raw, s);
                 raw = nullptr;
@@ -358,7 +383,7 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
             }
         } catch (...) {
             if (raw) dfree(raw, s);
-            dfree(sd.tri, s); dfree(sd.face, s); dfree(sd.mat, s);
+            dfree(sd.tri, s); dfree(sd.face, s); dfree(sd.mat, s); dfree(sd.cbox, s);
             delete sc;
             throw;
         }
@@ -374,6 +399,7 @@ gbt_status gbt_scene_destroy(gbt_scene_t *scene)
         dfree(scene->d.tri, nullptr);
         dfree(scene->d.face, nullptr);
         dfree(scene->d.mat, nullptr);
+        dfree(scene->d.cbox, nullptr);
         delete scene;
     });
 }

@@ -60,8 +60,12 @@ struct SceneDev {
     double *tri = nullptr;       // n_tri * 12
     int32_t *face = nullptr;     // n_tri
     int32_t *mat = nullptr;      // n_tri
-    int32_t *mat_host_max = nullptr;
+    // bounding boxes of consecutive triangle clusters (kTriCluster each), expanded so
+    // a box test never rejects a hit: per cluster xmin, ymin, zmin, xmax, ymax, zmax
+    double *cbox = nullptr;
+    int64_t n_clusters = 0;
 };
+constexpr int kTriCluster = 8;
 
 // Segment kernel record: the FP64 canonical segment split into float-float
 // (hi, lo) pairs, 20 floats (80 bytes, 16-byte aligned) per segment, array of

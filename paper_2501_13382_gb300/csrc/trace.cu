@@ -21,6 +21,7 @@ namespace {
 
 constexpr int kTraceBlock = 128;
 constexpr int kTriChunk = 512;          // triangles per shared-memory chunk
+static_assert(kTriChunk % kTriCluster == 0, "chunks hold whole clusters");
 constexpr int kScanBlock = 1024;        // threads per scan block
 constexpr int kScanItems = 4;           // items per scan thread
 
@@ -56,6 +57,8 @@ struct TraceParams {
     const int32_t *face;
     const int32_t *mat;
     int64_t n_tri;
+    const double *cbox;        // n_clusters * 6
+    int64_t n_clusters;
     int64_t stride;            // max_refl + 1
     double *po, *pt, *pL, *ps0;
     int32_t *pbmat, *phit, *cnt;
@@ -87,11 +90,27 @@ __device__ __forceinline__ double ray_triangle(const double o[3], const double d
     return (e2x * qx + e2y * qy + e2z * qz) * inv;
 }
 
-__device__ __forceinline__ void load_tri_chunk(double *st, int32_t *sface, const TraceParams &p,
-                                               int64_t base, int count)
+// One axis of a ray/box slab test: narrows [tn, tf]; false when the ray is parallel to
+// the slab and outside it.
+__device__ __forceinline__ bool slab(double o, double d, double inv, double lo, double hi,
+                                     double &tn, double &tf)
+{
+    if (d == 0.0) return !(o < lo || o > hi);
+    double t1 = (lo - o) * inv, t2 = (hi - o) * inv;
+    if (t1 > t2) { const double tt = t1; t1 = t2; t2 = tt; }
+    tn = fmax(tn, t1);
+    tf = fmin(tf, t2);
+    return true;
+}
+
+__device__ __forceinline__ void load_tri_chunk(double *st, double *sbox, int32_t *sface,
+                                               const TraceParams &p, int64_t base, int count)
 {
     for (int idx = threadIdx.x; idx < count * 12; idx += blockDim.x)
         st[idx] = p.tri[base * 12 + idx];
+    const int c0 = (int)(base / kTriCluster), nc = (count + kTriCluster - 1) / kTriCluster;
+    for (int idx = threadIdx.x; idx < nc * 6; idx += blockDim.x)
+        sbox[idx] = p.cbox[(int64_t)c0 * 6 + idx];
     for (int idx = threadIdx.x; idx < count; idx += blockDim.x)
         sface[idx] = p.face ? p.face[base + idx] : (int32_t)(base + idx);
 }
@@ -100,7 +119,8 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
 {
     extern __shared__ double smem[];
     double *st = smem;                                   // kTriChunk * 12
-    int32_t *sface = reinterpret_cast<int32_t *>(smem + kTriChunk * 12);
+    double *sbox = smem + kTriChunk * 12;                // (kTriChunk / kTriCluster) * 6
+    int32_t *sface = reinterpret_cast<int32_t *>(sbox + (kTriChunk / kTriCluster) * 6);
 
     const int64_t i = blockIdx.x * (int64_t)kTraceBlock + threadIdx.x;
     const bool active = i < p.n_rays;
@@ -130,7 +150,7 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
     const int64_t nchunk = (p.n_tri + kTriChunk - 1) / kTriChunk;
     const bool resident = nchunk <= 1;
     if (resident && p.n_tri > 0) {
-        load_tri_chunk(st, sface, p, 0, (int)p.n_tri);
+        load_tri_chunk(st, sbox, sface, p, 0, (int)p.n_tri);
     }
     __syncthreads();
 
@@ -146,14 +166,27 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
             const int count = (int)min((int64_t)kTriChunk, p.n_tri - base);
             if (!resident) {
                 __syncthreads();
-                load_tri_chunk(st, sface, p, base, count);
+                load_tri_chunk(st, sbox, sface, p, base, count);
                 __syncthreads();
             }
             if (alive) {
-                for (int k = 0; k < count; ++k) {
-                    if (sface[k] == last_face) continue;
-                    double t = ray_triangle(o, d, st + 12 * k);
-                    if (t > kTMin && t < tbest) { tbest = t; best = (int)(base + k + 1); }
+                // clusters in index order; a cluster whose (expanded) box the ray misses,
+                // or enters only beyond the best hit so far, holds no hit that could win
+                const double id0 = 1.0 / d[0], id1 = 1.0 / d[1], id2 = 1.0 / d[2];
+                const int nc = (count + kTriCluster - 1) / kTriCluster;
+                for (int c = 0; c < nc; ++c) {
+                    const double *bx = sbox + 6 * c;
+                    double tn = 0.0, tf = tbest;
+                    bool hit_box = slab(o[0], d[0], id0, bx[0], bx[3], tn, tf);
+                    hit_box = hit_box && slab(o[1], d[1], id1, bx[1], bx[4], tn, tf);
+                    hit_box = hit_box && slab(o[2], d[2], id2, bx[2], bx[5], tn, tf);
+                    if (!hit_box || tn > tf) continue;
+                    const int k1 = min(count, (c + 1) * kTriCluster);
+                    for (int k = c * kTriCluster; k < k1; ++k) {
+                        if (sface[k] == last_face) continue;
+                        double t = ray_triangle(o, d, st + 12 * k);
+                        if (t > kTMin && t < tbest) { tbest = t; best = (int)(base + k + 1); }
+                    }
                 }
             }
         }
@@ -378,6 +411,8 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     p.face = sd.face;
     p.mat = sd.mat;
     p.n_tri = sd.n_tri;
+    p.cbox = sd.cbox;
+    p.n_clusters = sd.n_clusters;
     p.stride = stride;
     p.po = reinterpret_cast<double *>(take(cap * 3 * sizeof(double)));
     p.pt = reinterpret_cast<double *>(take(cap * 3 * sizeof(double)));
@@ -392,7 +427,8 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     if ((size_t)(w - static_cast<char *>(scratch)) > scratch_bytes)
         fail(GBT_ERR_INVALID_ARG, "trace scratch too small");
 
-    const size_t smem = kTriChunk * 12 * sizeof(double) + kTriChunk * sizeof(int32_t);
+    const size_t smem = kTriChunk * 12 * sizeof(double) +
+                        (kTriChunk / kTriCluster) * 6 * sizeof(double) + kTriChunk * sizeof(int32_t);
     static bool attr_set = false;
     if (!attr_set) {
         GBT_CUDA(cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -255,3 +255,34 @@ def test_tile_cull_is_exact(G, which):
     assert st_c["pairs_prefiltered"] == st_d["pairs_prefiltered"]
     assert st_c["triples_kept"] == st_d["triples_kept"]
     assert st_c["pairs_tested"] < 0.5 * st_d["pairs"]
+
+
+def test_city_full_size_sampled(G):
+    """The full synthetic city: 1,048,576 rays, <= 8 reflections, 512^2 receivers, 1 kHz,
+    in the launch configuration of the benchmark (receiver order, whole-fan solve); the
+    oracle evaluates a seeded sample of receivers."""
+    import torch
+    w = I.city()
+    sc = G.Scene(w.scene)
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    p = G.gbs_solve(sc, w.sources[0], r, list(w.freqs), list(w.beam_b[0]), gam,
+                    order=G.recv_order(r), window=w.window, tile_cull=True).cpu().numpy()
+    idx = I.receiver_subset(w.receivers, 96, seed=21)
+    otr = O.trace(w.scene, w.sources[0])
+    po = O.gbs_sum(otr, w.receivers[idx], w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma,
+                   window=w.window)
+    assert rel_l2(p[:, idx].astype(np.complex128), po) <= TOL_L2
+
+
+def test_diff_city_full_size_sampled(G):
+    """Differentiable city (262,144 rays, <= 6 reflections, 128^2 receivers, 4 bands)."""
+    import torch
+    w = I.diff_city()
+    p, _, _ = _gpu_sum(G, w)
+    idx = I.receiver_subset(w.receivers, 128, seed=22)
+    otr = O.trace(w.scene, w.sources[0])
+    po = O.gbs_sum(otr, w.receivers[idx], w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma,
+                   window=w.window)
+    for f in range(len(w.freqs)):
+        assert rel_l2(p[f, idx], po[f]) <= TOL_L2
