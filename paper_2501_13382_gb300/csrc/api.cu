@@ -342,8 +342,8 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
             sd.face = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
             sd.mat = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
             sd.n_clusters = (d.n_tri + kTriCluster - 1) / kTriCluster;
-            sd.cbox = static_cast<double *>(
-                dalloc((size_t)std::max<int64_t>(sd.n_clusters, 1) * 6 * sizeof(double), s));
+            sd.cbox = static_cast<float *>(
+                dalloc((size_t)std::max<int64_t>(sd.n_clusters, 1) * 6 * sizeof(float), s));
             if (d.n_tri > 0) {
                 std::vector<int32_t> face(d.n_tri);
                 for (int64_t k = 0; k < d.n_tri; ++k) face[k] = d.tri_face ? d.tri_face[k] : (int32_t)k;
@@ -354,9 +354,9 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
                                          cudaMemcpyHostToDevice, s));
                 GBT_CUDA(cudaMemcpyAsync(sd.mat, d.tri_material, (size_t)d.n_tri * 4,
                                          cudaMemcpyHostToDevice, s));
-                // cluster boxes on the host: exact min/max, then a relative expansion far
-                // above FP64 rounding so the slab test is conservative
-                std::vector<double> box((size_t)sd.n_clusters * 6);
+                // cluster boxes on the host: exact min/max, then an expansion (1 mm plus
+                // 2e-6 relative) far above the rounding of the FP32 slab test, rounded outward
+                std::vector<float> box((size_t)sd.n_clusters * 6);
                 for (int64_t c = 0; c < sd.n_clusters; ++c) {
                     double lo[3] = {INFINITY, INFINITY, INFINITY};
                     double hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -369,12 +369,12 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
                                 hi[a] = std::max(hi[a], x);
                             }
                     for (int a = 0; a < 3; ++a) {
-                        const double pad = 1e-7 * (1.0 + std::max(fabs(lo[a]), fabs(hi[a])));
-                        box[6 * c + a] = lo[a] - pad;
-                        box[6 * c + 3 + a] = hi[a] + pad;
+                        const double pad = 1e-3 + 2e-6 * std::max(fabs(lo[a]), fabs(hi[a]));
+                        box[6 * c + a] = nextafterf((float)(lo[a] - pad), -INFINITY);
+                        box[6 * c + 3 + a] = nextafterf((float)(hi[a] + pad), INFINITY);
                     }
                 }
-                GBT_CUDA(cudaMemcpyAsync(sd.cbox, box.data(), box.size() * sizeof(double),
+                GBT_CUDA(cudaMemcpyAsync(sd.cbox, box.data(), box.size() * sizeof(float),
                                          cudaMemcpyHostToDevice, s));
                 scene_prepare(sd, static_cast<const double *>(raw), s);
                 dfree(raw, s);

@@ -60,9 +60,10 @@ struct SceneDev {
     double *tri = nullptr;       // n_tri * 12
     int32_t *face = nullptr;     // n_tri
     int32_t *mat = nullptr;      // n_tri
-    // bounding boxes of consecutive triangle clusters (kTriCluster each), expanded so
-    // a box test never rejects a hit: per cluster xmin, ymin, zmin, xmax, ymax, zmax
-    double *cbox = nullptr;
+    // bounding boxes of consecutive triangle clusters (kTriCluster each), in FP32,
+    // expanded far beyond FP32 rounding so a box test never rejects a hit:
+    // per cluster xmin, ymin, zmin, xmax, ymax, zmax
+    float *cbox = nullptr;
     int64_t n_clusters = 0;
 };
 constexpr int kTriCluster = 8;

@@ -57,7 +57,7 @@ struct TraceParams {
     const int32_t *face;
     const int32_t *mat;
     int64_t n_tri;
-    const double *cbox;        // n_clusters * 6
+    const float *cbox;         // n_clusters * 6
     int64_t n_clusters;
     int64_t stride;            // max_refl + 1
     double *po, *pt, *pL, *ps0;
@@ -92,18 +92,20 @@ __device__ __forceinline__ double ray_triangle(const double o[3], const double d
 
 // One axis of a ray/box slab test: narrows [tn, tf]; false when the ray is parallel to
 // the slab and outside it.
-__device__ __forceinline__ bool slab(double o, double d, double inv, double lo, double hi,
-                                     double &tn, double &tf)
+// In FP32: the boxes are padded by 1 mm + 2e-6 relative, far more than the rounding
+// of these few operations at scene scale, so a box the exact ray meets is never missed.
+__device__ __forceinline__ bool slab(float o, float d, float inv, float lo, float hi, float &tn,
+                                     float &tf)
 {
-    if (d == 0.0) return !(o < lo || o > hi);
-    double t1 = (lo - o) * inv, t2 = (hi - o) * inv;
-    if (t1 > t2) { const double tt = t1; t1 = t2; t2 = tt; }
-    tn = fmax(tn, t1);
-    tf = fmin(tf, t2);
+    if (d == 0.0f) return !(o < lo || o > hi);
+    float t1 = (lo - o) * inv, t2 = (hi - o) * inv;
+    if (t1 > t2) { const float tt = t1; t1 = t2; t2 = tt; }
+    tn = fmaxf(tn, t1);
+    tf = fminf(tf, t2);
     return true;
 }
 
-__device__ __forceinline__ void load_tri_chunk(double *st, double *sbox, int32_t *sface,
+__device__ __forceinline__ void load_tri_chunk(double *st, float *sbox, int32_t *sface,
                                                const TraceParams &p, int64_t base, int count)
 {
     for (int idx = threadIdx.x; idx < count * 12; idx += blockDim.x)
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
 {
     extern __shared__ double smem[];
     double *st = smem;                                   // kTriChunk * 12
-    double *sbox = smem + kTriChunk * 12;                // (kTriChunk / kTriCluster) * 6
+    float *sbox = reinterpret_cast<float *>(smem + kTriChunk * 12);   // clusters * 6
     int32_t *sface = reinterpret_cast<int32_t *>(sbox + (kTriChunk / kTriCluster) * 6);
 
     const int64_t i = blockIdx.x * (int64_t)kTraceBlock + threadIdx.x;
@@ -172,14 +174,17 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
             if (alive) {
                 // clusters in index order; a cluster whose (expanded) box the ray misses,
                 // or enters only beyond the best hit so far, holds no hit that could win
-                const double id0 = 1.0 / d[0], id1 = 1.0 / d[1], id2 = 1.0 / d[2];
+                const float of0 = (float)o[0], of1 = (float)o[1], of2 = (float)o[2];
+                const float df0 = (float)d[0], df1 = (float)d[1], df2 = (float)d[2];
+                const float id0 = 1.0f / df0, id1 = 1.0f / df1, id2 = 1.0f / df2;
                 const int nc = (count + kTriCluster - 1) / kTriCluster;
                 for (int c = 0; c < nc; ++c) {
-                    const double *bx = sbox + 6 * c;
-                    double tn = 0.0, tf = tbest;
-                    bool hit_box = slab(o[0], d[0], id0, bx[0], bx[3], tn, tf);
-                    hit_box = hit_box && slab(o[1], d[1], id1, bx[1], bx[4], tn, tf);
-                    hit_box = hit_box && slab(o[2], d[2], id2, bx[2], bx[5], tn, tf);
+                    const float *bx = sbox + 6 * c;
+                    // upper bound: the best hit so far, widened like the boxes
+                    float tn = 0.0f, tf = (float)tbest * 1.000001f + 1e-3f;
+                    bool hit_box = slab(of0, df0, id0, bx[0], bx[3], tn, tf);
+                    hit_box = hit_box && slab(of1, df1, id1, bx[1], bx[4], tn, tf);
+                    hit_box = hit_box && slab(of2, df2, id2, bx[2], bx[5], tn, tf);
                     if (!hit_box || tn > tf) continue;
                     const int k1 = min(count, (c + 1) * kTriCluster);
                     for (int k = c * kTriCluster; k < k1; ++k) {
@@ -428,7 +433,7 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
         fail(GBT_ERR_INVALID_ARG, "trace scratch too small");
 
     const size_t smem = kTriChunk * 12 * sizeof(double) +
-                        (kTriChunk / kTriCluster) * 6 * sizeof(double) + kTriChunk * sizeof(int32_t);
+                        (kTriChunk / kTriCluster) * 6 * sizeof(float) + kTriChunk * sizeof(int32_t);
     static bool attr_set = false;
     if (!attr_set) {
         GBT_CUDA(cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
