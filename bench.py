@@ -39,11 +39,11 @@ UNIT = "evals/s"
 OPS_PER_PAIR = 15
 OPS_PER_KEPT = 24
 LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
-KERNEL_TAG = "gbs_fwd_kernel<6,LINE,fwd,plain> ring-v2"
+KERNEL_TAG = "gbs_fwd_kernel<6,LINE,fwd,plain> ring-v2, heaviest tiles first"
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of this
 # exact kernel version (profiles/gbs_fwd_open_plane_64k_rays_256x256_6f.md); a changed
 # kernel gets a new tag and no entry until it is captured again.
-KERNEL_TRAFFIC = {"gbs_fwd_kernel<8,LINE,fwd,plain> ring-v1": 62994688}
+KERNEL_TRAFFIC = {"gbs_fwd_kernel<6,LINE,fwd,plain> ring-v2, heaviest tiles first": 63850496}
 
 
 def _env_int(name, default):
@@ -368,12 +368,14 @@ def main():
     time.sleep(0.3)
     G.gbt_timing_enable(True)
     G.gbt_timing_read(reset=True)
+    G.gbt_launches_read(reset=True)
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    launches = G.gbt_launches_read(reset=True)
     G.gbt_timing_enable(False)
     n_k, k_ms = G.gbt_timing_read(reset=True)
     ms = float(sum(a.elapsed_time(b) for a, b in ev))
@@ -447,7 +449,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(recv.numel() * 4),
                     "d2h_bytes_per_step": int(out.numel() * 8)},
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": launches,
             "clocks": clocks}
 
     if not args.no_forms and args.workload == "open_plane_large" and not args.tile_cull:

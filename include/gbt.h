@@ -267,6 +267,13 @@ gbt_status gbt_batch_destroy(gbt_batch_t *batch);
 gbt_status gbt_timing_enable(int32_t enable);
 gbt_status gbt_timing_read(int64_t *launches, double *total_ms, int32_t reset);
 
+/* Kernel launch count: every kernel the library puts on a stream (tracer,
+ * scan, compaction, prepass, tile order, pair kernel, merge, receiver order,
+ * adjoint kernels) adds one, counted on the host at launch time in all threads;
+ * reset != 0 zeroes the count after reading it.  A graph replay of a batch
+ * counts the kernels of the captured graph once per submit.  No GPU work. */
+gbt_status gbt_launches_read(int64_t *launches, int32_t reset);
+
 /* Work statistics of one gbt_sum call (same arguments): number of
  * (receiver, segment) pairs, pairs kept by the frequency-union prefilter, and
  * (receiver, segment, frequency) triples whose beam contributes (window and

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -150,6 +151,12 @@ cudaEvent_t timing_event()
     return e;
 }
 }  // namespace
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void timing_begin(cudaStream_t s)
 {
@@ -582,6 +589,14 @@ gbt_status gbt_timing_read(int64_t *launches, double *total_ms, int32_t reset)
             }
             g_timing.events.clear();
         }
+    });
+}
+
+gbt_status gbt_launches_read(int64_t *launches, int32_t reset)
+{
+    return guarded([&] {
+        GBT_REQUIRE(launches, "launches must be non-NULL");
+        *launches = reset ? g_launches.exchange(0) : g_launches.load();
     });
 }
 

@@ -1,27 +1,34 @@
 // gbs.cu -- Gaussian beam summation (Eq. 3 with the beam of Eq. 1 / Eq. 2)
-// for every (receiver, segment, frequency) triple.
+// for every (receiver, segment, frequency) triple, its adjoint, and the
+// receiver order they use.
 //
-// GB300 design (FP32 path):
-//  * Receivers are processed in a spatially coherent order (Morton order of
-//    their positions), 512 per CTA (256 threads x 2), held in registers both
-//    absolute (for the exact path) and relative to the CTA's first receiver
-//    (for the prefilter, which keeps every quantity small and the expansion
-//    |x - o|^2 = |x'|^2 - 2 x'.o' + |o'|^2 well conditioned).
-//  * Segments stream through shared memory in tiles of 128; each CTA covers
-//    one receiver tile and one of `splits` contiguous segment ranges, so the
-//    grid fills all SMs whatever the receiver count.
-//  * Prefilter (every pair, frequency independent): s_loc, s, n^2 and the
-//    union of the per-frequency Gaussian cutoffs, conservative by one unit of
-//    the exponent and 1 cm of window, 13-15 FP32/ALU instructions per pair.
-//    The keep bit goes into a 32-bit mask per receiver (one funnel shift),
-//    so no divergent branch sits in the pair loop.
-//  * Survivors (typically 0.1-5 % of pairs) are then visited in segment order
-//    by scanning the mask, and evaluated exactly: float-float differences and
-//    dot products give s to ~1e-12 relative; the phase k s is reduced modulo
-//    one turn in float-float before the FP32 MUFU sin/cos; n^2 comes from a
-//    compensated cross product.  Per-tile FP32 partial sums are folded into
-//    float-float accumulators in shared memory, and the segment ranges are
-//    merged in FP64 in a fixed order by a second kernel (deterministic).
+// GB300 design of the FP32 pair kernel:
+//  * A prepass turns every traced segment into an 80-byte record (origin and
+//    start distance as float-float, direction, length, amplitude).
+//  * Receivers are visited in Morton order.  A CTA tile is 960 receivers: 15
+//    consumer warps x 64, each lane holding receivers lane and lane + 32 of its
+//    warp's patch, in registers, absolute (exact path) and relative to the
+//    warp's first receiver (prefilter).
+//  * One persistent CTA per SM takes (tile, split) items from an atomic
+//    counter; split s of a tile owns record batches s, s + splits, ...  Tiles
+//    are dispatched heaviest first (sampled estimate of the beams that reach
+//    them), so the queue drains on light items.
+//  * A producer warp streams 32-record batches into an 8-stage shared-memory
+//    ring with bulk asynchronous copies completed on mbarriers; every consumer
+//    warp re-expresses the batch relative to its own patch.  All waits are
+//    bounded and raise a status flag instead of hanging.
+//  * Prefilter (every pair, frequency independent): a paired FP32 (f32x2)
+//    evaluation of the union of the per-frequency Gaussian cutoffs and the
+//    window, conservative by a margin, gives one keep bit per pair.  With the
+//    tile pre-cull, a batch's segments that cannot reach a warp's bounding ball
+//    are skipped first.
+//  * Survivors (typically a few percent of pairs) are evaluated exactly per
+//    lane: float-float s and phase (reduced in turns before the MUFU sin/cos),
+//    compensated cross product for n^2.  FP32 sums per lane are folded into
+//    float-float accumulators in shared memory every 16 batches, and the
+//    per-split partials are merged in FP64 in a fixed order by a second kernel,
+//    so results do not depend on scheduling.
+
 #include <math.h>
 
 #include <algorithm>
@@ -69,8 +76,9 @@ struct alignas(16) FwdParams {
     float cutoff;
     float pre_alpha, pre_beta; // prefilter: keep iff alpha n^2 <= s^2 + beta
     int splits;
-    int64_t n_items;           // warp tiles x splits
-    int *work_counter;         // zeroed before launch; warps take items from it
+    int64_t n_items;           // CTA tiles x splits
+    int *work_counter;         // zeroed before launch; CTAs take items from it
+    const int32_t *tile_perm;  // dispatch rank -> CTA tile (heaviest first), or null
     float4 *partial;           // [splits][nf][n_recv]: re_hi, im_hi, re_lo, im_lo
     unsigned long long *stats; // counting mode when non-null: [1] prefiltered, [2] kept
     unsigned int *status;      // device status word (timeouts)
@@ -394,6 +402,29 @@ __device__ __forceinline__ void fold(float4 *acc, float2 &t)
     }
 }
 
+// Conservative test: can the segment (origin (ox, oy, oz) relative to the frame
+// of `sphere`, record words r0 / r1) keep any receiver inside the ball `sphere`
+// (centre xyz, radius w)?  The distance from the segment line to a point is
+// 1-Lipschitz, so shrinking the ball's centre distance by the radius bounds n
+// from below and |s| from above over the whole ball; the radius carries slack
+// for FP32 rounding at these magnitudes.
+template <int WINDOW>
+__device__ __forceinline__ bool ball_may_keep(const float4 &r0, const float4 &r1, float ox, float oy,
+                                              float oz, const float4 &sphere, float alpha, float beta)
+{
+    const float dx = sphere.x - ox, dy = sphere.y - oy, dz = sphere.z - oz;
+    const float sc = fmaf(dx, r1.x, fmaf(dy, r1.y, dz * r1.z));
+    const float cxr = dy * r1.z - dz * r1.y, cyr = dz * r1.x - dx * r1.z, czr = dx * r1.y - dy * r1.x;
+    const float nc = sqrtf(fmaf(cxr, cxr, fmaf(cyr, cyr, czr * czr)));
+    const float R = sphere.w * 1.0001f + 0.05f + 1e-5f * (fabsf(ox) + fabsf(oy) + fabsf(oz));
+    bool win;
+    if (WINDOW == GBT_WINDOW_LINE) win = r0.w + sc + R >= -kWinMargin;
+    else win = (sc + R >= -kWinMargin) && (sc - R <= r1.w + kWinMargin);
+    const float sabs = fabsf(r0.w + sc) + R;
+    const float nn = nc - R;
+    return win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
+}
+
 // Turn lane's raw record into the prefilter view relative to (cx, cy, cz) and
 // the exact-path columns.
 // The warp's receivers lie in the ball (sphere centre, radius) given relative
@@ -410,21 +441,7 @@ __device__ __forceinline__ bool stage_transform(WarpSmem &w, const float4 (&raw)
     bool pass = false;
     if (valid) {
         const float ox = (r0.x - cx) + r2.x, oy = (r0.y - cy) + r2.y, oz = (r0.z - cz) + r2.z;
-        {
-            const float dx = sphere.x - ox, dy = sphere.y - oy, dz = sphere.z - oz;
-            const float sc = fmaf(dx, r1.x, fmaf(dy, r1.y, dz * r1.z));
-            const float cxr = dy * r1.z - dz * r1.y, cyr = dz * r1.x - dx * r1.z,
-                        czr = dx * r1.y - dy * r1.x;
-            const float nc = sqrtf(fmaf(cxr, cxr, fmaf(cyr, cyr, czr * czr)));
-            // radius plus slack for rounding at these magnitudes
-            const float R = sphere.w * 1.0001f + 0.05f + 1e-5f * (fabsf(ox) + fabsf(oy) + fabsf(oz));
-            bool win;
-            if (WINDOW == GBT_WINDOW_LINE) win = r0.w + sc + R >= -kWinMargin;
-            else win = (sc + R >= -kWinMargin) && (sc - R <= r1.w + kWinMargin);
-            const float sabs = fabsf(r0.w + sc) + R;
-            const float nn = nc - R;
-            pass = win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
-        }
+        pass = ball_may_keep<WINDOW>(r0, r1, ox, oy, oz, sphere, alpha, beta);
         const float ot = fmaf(ox, r1.x, fmaf(oy, r1.y, oz * r1.z));
         const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
         const float a2 = 2.f * alpha;
@@ -540,7 +557,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
         const int64_t n_seg = *p.n_seg_ptr;
         const int64_t n_batches = (n_seg + kBatch - 1) / kBatch;
         const float alpha = p.pre_alpha, beta = p.pre_beta;
-        const int64_t tile_base = (item / p.splits) * kCtaRecv;
+        const int64_t tile_rank = item / p.splits;
+        const int64_t tile_base = (p.tile_perm ? (int64_t)p.tile_perm[tile_rank] : tile_rank) * kCtaRecv;
         const int split = (int)(item % p.splits);
         const uint32_t nb = split < n_batches ? (uint32_t)((n_batches - 1 - split) / p.splits + 1) : 0u;
 
@@ -1014,6 +1032,94 @@ __global__ void grad_out_kernel(GradOutParams p)
 
 // ------------------------------------------------------------- reduce --
 
+// ---- dispatch order of the CTA tiles: heaviest first
+// Items of one tile cost about the same (their batches interleave over the whole
+// segment list), but tiles differ by the number of beams that reach them.  A
+// sampled count of segments whose Gaussian can reach each tile's bounding ball
+// ranks the tiles so the persistent CTAs take the heavy ones first and the queue
+// drains with light items (longest processing time first).  The order only
+// changes which CTA computes an item, never the arithmetic of any sum.
+constexpr int kWeightSamples = 1 << 15;        // sampled segments per estimate
+constexpr int64_t kMaxOrderedTiles = 1 << 14;  // beyond this the rank pass is skipped
+
+__global__ void tile_ball_kernel(const float *recv, const int32_t *order, int64_t n_recv,
+                                 float4 *ball, unsigned int *weight)
+{
+    __shared__ float red[4][8];
+    const int64_t base = (int64_t)blockIdx.x * kCtaRecv;
+    const int n = (int)(n_recv - base < (int64_t)kCtaRecv ? n_recv - base : (int64_t)kCtaRecv);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t o = order ? order[base + j] : base + j;
+        sx += recv[3 * o]; sy += recv[3 * o + 1]; sz += recv[3 * o + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (lane == 0) { red[0][wid] = sx; red[1][wid] = sy; red[2][wid] = sz; }
+    __syncthreads();
+    sx = sy = sz = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { sx += red[0][k]; sy += red[1][k]; sz += red[2][k]; }
+    const float cx = sx / (float)n, cy = sy / (float)n, cz = sz / (float)n;
+    float r2 = 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t o = order ? order[base + j] : base + j;
+        const float dx = recv[3 * o] - cx, dy = recv[3 * o + 1] - cy, dz = recv[3 * o + 2] - cz;
+        r2 = fmaxf(r2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    __syncthreads();
+    if (lane == 0) red[3][wid] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r2 = fmaxf(r2, red[3][k]);
+        ball[blockIdx.x] = make_float4(cx, cy, cz, sqrtf(r2));
+        weight[blockIdx.x] = 0u;
+    }
+}
+
+template <int WINDOW>
+__global__ void tile_weight_kernel(const float *rec, const int32_t *n_seg_ptr, const float4 *ball,
+                                   int64_t n_tiles, float alpha, float beta, unsigned int *weight)
+{
+    const int64_t ns = *n_seg_ptr;
+    const int64_t stride = ns > kWeightSamples ? (ns + kWeightSamples - 1) / kWeightSamples : 1;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * stride;
+    const bool ok = j < ns;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    if (ok) {
+        const float4 *R = reinterpret_cast<const float4 *>(rec + j * kRecFloats);
+        r0 = R[0]; r1 = R[1]; r2 = R[2];
+    }
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const float4 b = ball[t];
+        bool pass = false;
+        if (ok)
+            pass = ball_may_keep<WINDOW>(r0, r1, (r0.x - b.x) + r2.x, (r0.y - b.y) + r2.y,
+                                         (r0.z - b.z) + r2.z, make_float4(0.f, 0.f, 0.f, b.w),
+                                         alpha, beta);
+        const unsigned int m = __ballot_sync(0xffffffffu, pass);
+        if ((threadIdx.x & 31) == 0 && m) atomicAdd(&weight[t], (unsigned int)__popc(m));
+    }
+}
+
+// perm[rank] = tile, ranks by weight descending, ties by tile index (a permutation)
+__global__ void tile_rank_kernel(const unsigned int *weight, int64_t n_tiles, int32_t *perm)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const unsigned int wt = weight[t];
+    int64_t rank = 0;
+    for (int64_t u = 0; u < n_tiles; ++u) {
+        const unsigned int wu = weight[u];
+        rank += (wu > wt) || (wu == wt && u < t);
+    }
+    perm[rank] = (int32_t)t;
+}
+
 struct ReduceParams {
     int64_t n;                 // nf * n_recv
     int64_t n_recv;
@@ -1146,6 +1252,7 @@ void launch_fwd_t(const FwdParams &p, cudaStream_t s)
     GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
     if (MODE != kStats) timing_begin(s);
     gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED><<<grid, kThreads, smem, s>>>(p);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
     if (MODE != kStats) timing_end(s);
     (void)STATS;
@@ -1240,6 +1347,50 @@ int choose_splits(const TraceDev &td, const gbt_sum_args &a)
     return (int)std::min<int64_t>(s, 4096);
 }
 
+static int64_t cta_tiles(int64_t n_recv) { return (n_recv + kCtaRecv - 1) / kCtaRecv; }
+
+// Workspace of the tile order: balls, weights and the permutation.
+static size_t tile_order_bytes(int64_t n_recv)
+{
+    const int64_t t = cta_tiles(n_recv);
+    if (t < 2 || t > kMaxOrderedTiles) return 0;
+    return align_up((size_t)t * sizeof(float4), 256) + 2 * align_up((size_t)t * sizeof(int32_t), 256);
+}
+
+// Where the permutation sits inside a tile-order workspace (null: no ordering).
+static int32_t *tile_order_perm(void *ws, int64_t n_recv)
+{
+    const int64_t t = cta_tiles(n_recv);
+    if (t < 2 || t > kMaxOrderedTiles) return nullptr;
+    return reinterpret_cast<int32_t *>(static_cast<char *>(ws) +
+                                       align_up((size_t)t * sizeof(float4), 256) +
+                                       align_up((size_t)t * sizeof(int32_t), 256));
+}
+
+// Launches the tile order for q's receivers and records (the records must be
+// written earlier on s); returns the permutation inside ws, or null when the
+// tiles are too few or too many to rank.
+static const int32_t *tile_order_launch(const FwdParams &q, int window, void *ws, cudaStream_t s)
+{
+    int32_t *perm = tile_order_perm(ws, q.n_recv);
+    if (!perm) return nullptr;
+    const int64_t t = cta_tiles(q.n_recv);
+    float4 *ball = static_cast<float4 *>(ws);
+    unsigned int *weight = reinterpret_cast<unsigned int *>(static_cast<char *>(ws) +
+                                                            align_up((size_t)t * sizeof(float4), 256));
+    tile_ball_kernel<<<(unsigned)t, 256, 0, s>>>(q.recv, q.order, q.n_recv, ball, weight);
+    if (window == GBT_WINDOW_LINE)
+        tile_weight_kernel<GBT_WINDOW_LINE><<<kWeightSamples / 256, 256, 0, s>>>(
+            q.rec, q.n_seg_ptr, ball, t, q.pre_alpha, q.pre_beta, weight);
+    else
+        tile_weight_kernel<GBT_WINDOW_SEGMENT><<<kWeightSamples / 256, 256, 0, s>>>(
+            q.rec, q.n_seg_ptr, ball, t, q.pre_alpha, q.pre_beta, weight);
+    tile_rank_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(weight, t, perm);
+    GBT_CUDA(cudaGetLastError());
+    note_launches(3);
+    return perm;
+}
+
 static size_t records_bytes(const TraceDev &td)
 {
     return align_up((size_t)kRecFloats * (size_t)td.capacity * sizeof(float), 256);
@@ -1253,6 +1404,7 @@ size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits
     const size_t part = (size_t)splits * a.n_freq * (size_t)a.n_recv;
     b += align_up(part * (a.precision == GBT_PRECISION_F64 ? sizeof(double2) : sizeof(float4)),
                   256);
+    if (a.precision != GBT_PRECISION_F64) b += tile_order_bytes(a.n_recv);
     return b;
 }
 
@@ -1267,6 +1419,10 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
     int *counter = reinterpret_cast<int *>(w);
     w += 256;
     void *partial = w;
+    w += align_up((size_t)splits * a.n_freq * (size_t)a.n_recv *
+                      (a.precision == GBT_PRECISION_F64 ? sizeof(double2) : sizeof(float4)),
+                  256);
+    void *order_ws = w;
     const int32_t *n_seg_ptr = td.ray_off + td.n_rays;
 
     if (td.capacity > 0) {
@@ -1282,6 +1438,7 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         pp.amp64 = amp64;
         pp.status = status_word();
         prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
+        note_launches(1);
         GBT_CUDA(cudaGetLastError());
     }
 
@@ -1307,15 +1464,16 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
                 gbs_fwd_f64_kernel<GBT_WINDOW_LINE><<<grid, kThreads64, 0, s>>>(q);
             else
                 gbs_fwd_f64_kernel<GBT_WINDOW_SEGMENT><<<grid, kThreads64, 0, s>>>(q);
+            note_launches(1);
             GBT_CUDA(cudaGetLastError());
         } else {
             FwdParams q = make_pair_params(td, sd, a, rec);
             q.splits = splits;
             q.partial = reinterpret_cast<float4 *>(partial);
             q.stats = stats;
-            const int64_t tiles = (a.n_recv + kCtaRecv - 1) / kCtaRecv;
-            q.n_items = tiles * splits;
+            q.n_items = cta_tiles(a.n_recv) * splits;
             q.work_counter = counter;
+            q.tile_perm = tile_order_launch(q, a.window, order_ws, s);
             if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
             else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
             if (stats) return;
@@ -1331,6 +1489,7 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         rp.out = reinterpret_cast<float2 *>(a.out);
         rp.accumulate = a.accumulate;
         reduce_kernel<<<(unsigned)((nout + 255) / 256), 256, 0, s>>>(rp);
+        note_launches(1);
         GBT_CUDA(cudaGetLastError());
     }
 }
@@ -1353,11 +1512,17 @@ void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scrat
     GBT_CUDA(cudaMemsetAsync(bb, 0xff, 3 * sizeof(unsigned int), s));
     GBT_CUDA(cudaMemsetAsync(bb + 3, 0x00, 3 * sizeof(unsigned int), s));
     bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(recv, n, bb);
+    note_launches(1);
     const unsigned g = (unsigned)((npad + 255) / 256);
     morton_kernel<<<g, 256, 0, s>>>(recv, n, npad, bb, keys);
+    note_launches(1);
     for (int64_t k = 2; k <= npad; k <<= 1)
-        for (int64_t j = k >> 1; j > 0; j >>= 1) bitonic_step<<<g, 256, 0, s>>>(keys, npad, j, k);
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            bitonic_step<<<g, 256, 0, s>>>(keys, npad, j, k);
+            note_launches(1);
+        }
     extract_order<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, order);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
 
@@ -1367,7 +1532,7 @@ void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scrat
 static size_t bwd_layout(const TraceDev &td, const gbt_sum_args &a, const SceneDev *sd,
                          size_t *off)
 {
-    // records | amp64 | counter | seg_G | seg_H | acc
+    // records | amp64 | counter | seg_G | seg_H | acc | tile order
     size_t b = 0;
     off[0] = b; b += records_bytes(td);
     off[1] = b; b += align_up((size_t)td.capacity * sizeof(double), 256);
@@ -1375,12 +1540,13 @@ static size_t bwd_layout(const TraceDev &td, const gbt_sum_args &a, const SceneD
     off[3] = b; b += align_up((size_t)td.capacity * sizeof(float), 256);
     off[4] = b; b += align_up((size_t)a.n_freq * td.capacity * sizeof(float), 256);
     off[5] = b; b += align_up((size_t)((sd ? sd->n_materials : 1024) + GBT_MAX_FREQ) * sizeof(double), 256);
+    off[6] = b; b += tile_order_bytes(a.n_recv);
     return b;
 }
 
 size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a)
 {
-    size_t off[6];
+    size_t off[7];
     return bwd_layout(td, a, &td.scene->d, off);
 }
 
@@ -1388,7 +1554,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
                 const float *grad_out, float *grad_gamma, float *grad_w, double *grad_b,
                 void *work, cudaStream_t s)
 {
-    size_t off[6];
+    size_t off[7];
     bwd_layout(td, a, &sd, off);
     char *w = static_cast<char *>(work);
     float *rec = reinterpret_cast<float *>(w + off[0]);
@@ -1417,6 +1583,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
         pp.amp64 = amp64;
         pp.status = status_word();
         prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
+        note_launches(1);
         GBT_CUDA(cudaGetLastError());
     }
     FwdParams q = make_pair_params(td, sd, a, rec);
@@ -1429,6 +1596,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
         q.seg_G = seg_G;
         q.seg_H = seg_H;
         q.seg_stride = td.capacity;
+        q.tile_perm = tile_order_launch(q, a.window, w + off[6], s);
         if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
         else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
     }
@@ -1450,6 +1618,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     r.status = status_word();
     const size_t sh = (size_t)(sd.n_materials + a.n_freq) * sizeof(double);
     ray_grad_kernel<<<(unsigned)((td.n_rays + 127) / 128), 128, sh, s>>>(r);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
     GradOutParams g{};
     g.acc = acc;
@@ -1460,6 +1629,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     g.grad_b = grad_b;
     const int nk = sd.n_materials + a.n_freq;
     grad_out_kernel<<<(unsigned)((nk + 127) / 128), 128, 0, s>>>(g);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
 
@@ -1486,6 +1656,7 @@ void batched_launch(const FwdParams &prm, int grid, cudaStream_t s)
 {
     GBT_CUDA(cudaMemsetAsync(prm.work_counter, 0, sizeof(int), s));
     gbs_fwd_kernel<NF, WINDOW, kFwd, true><<<grid, kThreads, sizeof(CtaSmem<NF>), s>>>(prm);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
 
@@ -1498,7 +1669,7 @@ struct BatchImpl {
     std::vector<int> order;            // instance processing order (cost, descending)
     std::vector<int64_t> n_seg, cost;
     std::vector<int> splits;
-    std::vector<size_t> rec_off, part_off;
+    std::vector<size_t> rec_off, part_off, ord_off;
     std::vector<FwdParams> table;      // in processing order
     std::vector<int64_t> inst_off;
     void *work = nullptr;
@@ -1513,6 +1684,7 @@ struct BatchImpl {
     cudaStream_t capture_stream = nullptr;   // private stream the graph is recorded on
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int64_t graph_kernels = 0;               // kernel nodes of the recorded graph
 };
 
 static void batch_plan(BatchImpl &B, double items_per_slot)
@@ -1541,6 +1713,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
     const int n = (int)B.args.size();
     B.rec_off.assign(n, 0);
     B.part_off.assign(n, 0);
+    B.ord_off.assign(n, 0);
     size_t b = 0;
     for (int i = 0; i < n; ++i) {
         B.rec_off[i] = b;
@@ -1548,6 +1721,8 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         B.part_off[i] = b;
         b += align_up((size_t)B.splits[i] * B.args[i].n_freq * (size_t)B.args[i].n_recv *
                           sizeof(float4), 256);
+        B.ord_off[i] = b;
+        b += tile_order_bytes(B.args[i].n_recv);
     }
     const size_t tab = align_up((size_t)n * sizeof(FwdParams), 256);
     const size_t off = align_up((size_t)(n + 1) * sizeof(int64_t), 256);
@@ -1574,6 +1749,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         q.n_items = ((a.n_recv + kCtaRecv - 1) / kCtaRecv) * q.splits;
         q.partial = reinterpret_cast<float4 *>(w + B.part_off[i]);
         q.work_counter = B.counter;
+        q.tile_perm = tile_order_perm(w + B.ord_off[i], a.n_recv);
         B.table.push_back(q);
         B.inst_off.push_back(B.inst_off.back() + q.n_items);
     }
@@ -1604,7 +1780,12 @@ static void batch_record(BatchImpl &B, cudaStream_t s)
         pp.amp64 = nullptr;
         pp.status = status_word();
         prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
+        note_launches(1);
         GBT_CUDA(cudaGetLastError());
+    }
+    for (int k = 0; k < n; ++k) {
+        const int i = B.order[k];
+        if (B.table[k].tile_perm) tile_order_launch(B.table[k], B.window, w + B.ord_off[i], s);
     }
     FwdParams prm = B.table[0];
     prm.inst = B.d_table;
@@ -1627,6 +1808,7 @@ static void batch_record(BatchImpl &B, cudaStream_t s)
         rp.out = reinterpret_cast<float2 *>(a.out);
         rp.accumulate = a.accumulate;
         reduce_kernel<<<(unsigned)((rp.n + 255) / 256), 256, 0, s>>>(rp);
+        note_launches(1);
         GBT_CUDA(cudaGetLastError());
     }
 }
@@ -1731,6 +1913,18 @@ void batch_submit(BatchImpl *B, cudaStream_t s)
         }
         GBT_CUDA(cudaStreamEndCapture(cs, &B->graph));
         GBT_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+        // the launches were counted while recording; later replays add the graph's kernels
+        size_t nn = 0;
+        GBT_CUDA(cudaGraphGetNodes(B->graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) GBT_CUDA(cudaGraphGetNodes(B->graph, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            GBT_CUDA(cudaGraphNodeGetType(nd, &t));
+            if (t == cudaGraphNodeTypeKernel) ++B->graph_kernels;
+        }
+    } else {
+        note_launches(B->graph_kernels);
     }
     GBT_CUDA(cudaGraphLaunch(B->exec, s));
 }
@@ -1765,6 +1959,7 @@ __global__ void selftest_wait_kernel(long long spins, unsigned int *status)
 void selftest_timeout_launch(long long spins, cudaStream_t s)
 {
     selftest_wait_kernel<<<1, 32, 0, s>>>(spins, status_word());
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
 
@@ -1823,11 +2018,17 @@ void recv_order_noalloc_launch(const float *recv, int64_t n, int32_t *order, cud
     GBT_CUDA(cudaMemsetAsync(bb, 0xff, 3 * sizeof(unsigned int), s));
     GBT_CUDA(cudaMemsetAsync(bb + 3, 0x00, 3 * sizeof(unsigned int), s));
     bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(recv, n, bb);
+    note_launches(1);
     const unsigned g = (unsigned)((npad + 255) / 256);
     morton_kernel<<<g, 256, 0, s>>>(recv, n, npad, bb, keys);
+    note_launches(1);
     for (int64_t k = 2; k <= npad; k <<= 1)
-        for (int64_t j = k >> 1; j > 0; j >>= 1) bitonic_step<<<g, 256, 0, s>>>(keys, npad, j, k);
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            bitonic_step<<<g, 256, 0, s>>>(keys, npad, j, k);
+            note_launches(1);
+        }
     extract_order<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, order);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
 

@@ -33,6 +33,9 @@ enum : unsigned int { STATUS_BOUNDS = 1u, STATUS_TIMEOUT = 2u, STATUS_BAD_INPUT 
 
 int num_sms();
 
+// Count of kernels the library has put on a stream (gbt_launches_read).
+void note_launches(int64_t n);
+
 // Optional CUDA-event timing of the main pair kernels (gbt_timing_*).
 void timing_begin(cudaStream_t s);
 void timing_end(cudaStream_t s);

@@ -373,6 +373,7 @@ void scene_prepare(SceneDev &sd, const double *tri_raw_dev, cudaStream_t s)
     const int bs = 128;
     scene_prep_kernel<<<(unsigned)((sd.n_tri + bs - 1) / bs), bs, 0, s>>>(tri_raw_dev, sd.n_tri,
                                                                           sd.tri);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
 
@@ -441,11 +442,15 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
         attr_set = true;
     }
     trace_kernel<<<(unsigned)((n + kTraceBlock - 1) / kTraceBlock), kTraceBlock, smem, s>>>(p);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 
     scan_block_sums<<<(unsigned)nb, kScanBlock, 0, s>>>(p.cnt, n, bsum);
+    note_launches(1);
     scan_of_block_sums<<<1, kScanBlock, 0, s>>>(bsum, nb);
+    note_launches(1);
     scan_final<<<(unsigned)nb, kScanBlock, 0, s>>>(p.cnt, n, bsum, td.ray_off);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 
     CompactParams c{};
@@ -456,6 +461,7 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     c.ray = td.ray; c.depth = td.depth; c.bmat = td.bmat; c.hit = td.hit;
     const int64_t slots = n * stride;
     compact_kernel<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(c);
+    note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
 

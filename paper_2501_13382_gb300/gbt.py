@@ -108,6 +108,7 @@ _SIGS = {
     "gbt_selftest_timeout": (C.c_int, [C.c_int64, C.c_void_p]),
     "gbt_timing_enable": (C.c_int, [C.c_int32]),
     "gbt_timing_read": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int32]),
+    "gbt_launches_read": (C.c_int, [C.POINTER(C.c_int64), C.c_int32]),
     "gbt_sum_stats_get": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.POINTER(gbt_sum_stats),
                                     C.c_void_p]),
 }
@@ -281,6 +282,13 @@ def gbt_timing_read(reset: bool = True):
     _check(load().gbt_timing_read(C.byref(n), C.byref(ms), C.c_int32(1 if reset else 0)),
            "gbt_timing_read")
     return int(n.value), float(ms.value)
+
+
+def gbt_launches_read(reset: bool = True) -> int:
+    """Kernels the library has launched (since the last reset)."""
+    n = C.c_int64(0)
+    _check(load().gbt_launches_read(C.byref(n), C.c_int32(1 if reset else 0)), "gbt_launches_read")
+    return int(n.value)
 
 
 def gbt_sum_stats_get(trace: int, args: gbt_sum_args, stream: int = 0) -> gbt_sum_stats:

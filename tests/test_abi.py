@@ -39,6 +39,11 @@ def test_version_and_error_string_without_gpu(lib):
     assert isinstance(lib.gbt_last_error(), bytes)
 
 
+def test_launch_counter_reads_without_gpu(lib):
+    gbt.gbt_launches_read(reset=True)
+    assert gbt.gbt_launches_read(reset=False) == 0      # nothing launched on a host-only run
+
+
 def test_struct_layouts_match_header_sizes(lib):
     # the C compiler's view of the argument structs, compiled here from the header
     import subprocess, tempfile
