@@ -97,11 +97,15 @@ struct alignas(16) FwdParams {
 
 static_assert(sizeof(FwdParams) % 16 == 0, "instance parameters are copied as 16-byte words");
 
+// Error-free transformations depend on every operation being rounded as written:
+// nvcc contracts a product feeding an add into one FMA by default, which would
+// round differently in each inlined copy.  The __f*_rn intrinsics are never
+// contracted, so these sites use them wherever a rounding is relied upon.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    s = a + b;
-    float bv = s - a;
-    e = (a - (s - bv)) + (b - bv);
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
 }
 
 __device__ __forceinline__ float rcp_approx(float x)
@@ -121,9 +125,9 @@ __device__ __forceinline__ float ex2_approx(float x)
 // Kahan's difference of products a*b - c*d, accurate to about one ulp.
 __device__ __forceinline__ float dop(float a, float b, float c, float d)
 {
-    float w = c * d;
-    float e = fmaf(-c, d, w);
-    float f = fmaf(a, b, -w);
+    const float w = __fmul_rn(c, d);
+    const float e = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
     return f + e;
 }
 
@@ -252,7 +256,7 @@ __device__ __forceinline__ bool exact_geometry(float x, float y, float z, const 
     ey -= w.cold[C_OYL][j];
     ez -= w.cold[C_OZL][j];
     // s_loc = delta . t
-    float p0 = ax * thx, p1 = ay * thy, p2 = az * thz;
+    const float p0 = __fmul_rn(ax, thx), p1 = __fmul_rn(ay, thy), p2 = __fmul_rn(az, thz);
     float r0 = fmaf(ax, tlx, fmaf(ex, thx, fmaf(ax, thx, -p0)));
     float r1 = fmaf(ay, tly, fmaf(ey, thy, fmaf(ay, thy, -p1)));
     float r2 = fmaf(az, tlz, fmaf(ez, thz, fmaf(az, thz, -p2)));
@@ -285,10 +289,10 @@ __device__ __forceinline__ void beam_term(const FreqConst &q, float sh, float sl
     const float n2invD = n2 * invD;
     const float ga = ex2_approx(-q.kb2l2e * n2invD);  // exp(-k b n^2 / (2 D))
     // phase in turns: frac(K s) in float-float, plus K n^2 s / (2 D)
-    const float ph = q.K_hi * sh;
+    const float ph = __fmul_rn(q.K_hi, sh);       // rounded: pe below is its exact error
     const float pe = fmaf(q.K_hi, sh, -ph);
     const float corr = fmaf(q.K_hi, sl, fmaf(q.K_lo, sh, pe));
-    float tau = (ph - rintf(ph)) + corr;
+    float tau = __fsub_rn(ph, rintf(ph)) + corr;
     tau = fmaf(q.halfK * n2invD, sh, tau);
     tau = tau - rintf(tau);
     float sn, cs;
@@ -306,10 +310,10 @@ __device__ __forceinline__ void beam_adjoint(const FreqConst &q, float sh, float
 {
     const float n2invD = n2 * invD;
     const float ga = ex2_approx(-q.kb2l2e * n2invD);
-    const float ph = q.K_hi * sh;
+    const float ph = __fmul_rn(q.K_hi, sh);       // rounded: pe below is its exact error
     const float pe = fmaf(q.K_hi, sh, -ph);
     const float corr = fmaf(q.K_hi, sl, fmaf(q.K_lo, sh, pe));
-    float tau = (ph - rintf(ph)) + corr;
+    float tau = __fsub_rn(ph, rintf(ph)) + corr;
     tau = fmaf(q.halfK * n2invD, sh, tau);
     tau = tau - rintf(tau);
     float sn, cs;
