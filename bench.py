@@ -221,8 +221,9 @@ def bench_tile_cull(G, torch, stream, sc, w, recv, gam, order, out, flush, steps
 
 
 def bench_batched(G, torch, stream, steps=5):
-    """Batched city: 32 sources (log-uniform 4,096-262,144 rays), 8 frequencies, one persistent
-    launch per submit (CUDA graph) vs one gbt_sum launch per source; receivers 128 x 128."""
+    """Batched city: 32 sources (log-uniform 4,096-262,144 rays), 8 frequencies, receivers
+    128 x 128.  One graph-replayed batch submit (form chosen by the autotuner, and each form
+    on its own) vs one gbt_sum launch per source."""
     from paper_2501_13382_gb300 import inputs as I
     w = I.batched_city()
     recv_np = I.receiver_grid(128, 250.0, 1.5)
@@ -237,25 +238,32 @@ def bench_batched(G, torch, stream, steps=5):
         evals += float(recv.shape[0]) * n_seg * len(w.freqs)
         insts.append(dict(trace=tr, recv=recv, freqs=list(w.freqs), beam_b=list(w.beam_b[i]),
                           gamma=gam, order=order))
-    batch = G.Batch(insts, window=w.window, use_graph=True, autotune=True)
-    outs = [torch.empty_like(o) for o in batch.outputs]
+    outs = [torch.empty((len(w.freqs), recv.shape[0]), dtype=torch.complex64, device="cuda")
+            for _ in insts]
 
     def plain():
         for d, o in zip(insts, outs):
             G.gbs_sum(d["trace"], recv, d["freqs"], d["beam_b"], gam, order=order,
                       window=w.window, out=o)
-    batch.submit()
     plain()
     torch.cuda.synchronize()
-    t_b = _timed(torch, stream, batch.submit, steps) / steps
     t_p = _timed(torch, stream, plain, steps) / steps
-    err = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
-              for a, b in zip(batch.outputs, outs))
-    batch.close()
+    forms = {}
+    for name, form in (("auto", G.BATCH_AUTO), ("fused", G.BATCH_FUSED),
+                       ("concurrent", G.BATCH_CONCURRENT)):
+        batch = G.Batch(insts, window=w.window, use_graph=True, autotune=True, form=form)
+        batch.submit()
+        torch.cuda.synchronize()
+        t_b = _timed(torch, stream, batch.submit, steps) / steps
+        err = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+                  for a, b in zip(batch.outputs, outs))
+        batch.close()
+        forms[name] = {"value": evals / (t_b * 1e-3), "ms": t_b, "rel_l2_vs_plain": err}
     return {"workload": "batched_city_32src_8f_128x128", "evals": evals,
-            "batched": {"value": evals / (t_b * 1e-3), "ms": t_b},
+            "batched": forms["auto"], "fused_autotuned": forms["fused"],
+            "concurrent": forms["concurrent"],
             "plain_per_instance": {"value": evals / (t_p * 1e-3), "ms": t_p},
-            "speedup": t_p / t_b, "rel_l2_batched_vs_plain": err}
+            "speedup": t_p / forms["auto"]["ms"]}
 
 
 def bench_fwd_bwd(G, torch, stream, steps=5):

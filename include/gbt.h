@@ -234,27 +234,39 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src,
                      const gbt_sum_args *args, void *stream);
 
 /* --------------------------------------------------------------- batch --
- * Many GBS instances (sources x frequency sets, uneven segment counts) in one
- * persistent launch fed by a device work queue of (instance, receiver tile,
- * segment range) items, captured in a CUDA graph on the first submit and
- * replayed afterwards.  Each instance is a trace plus sum arguments; the
- * result of each instance equals gbt_sum on it up to rounding.  All traces
- * and buffers must stay alive and unchanged in shape while the batch exists;
- * their contents may change between submits. */
+ * Many GBS instances (sources x frequency sets, uneven segment counts) run as
+ * one unit, captured in a CUDA graph on the first submit and replayed
+ * afterwards.  Each instance is a trace plus sum arguments; the result of each
+ * instance equals gbt_sum on it up to rounding.  Two execution forms:
+ *   FUSED       one persistent launch fed by a device work queue of
+ *               (instance, receiver tile, segment range) items, instances
+ *               longest first (the load-imbalance remedy of Sec. 3.4 taken to
+ *               the whole batch);
+ *   CONCURRENT  each instance's single-sum kernels on one of a few branch
+ *               streams forked from the submit stream and joined back, so one
+ *               instance's draining tail overlaps the next instance's start.
+ * AUTO takes the faster of the two measured at create when autotune is set,
+ * else CONCURRENT.  All traces and buffers must stay alive and unchanged in
+ * shape while the batch exists; their contents may change between submits. */
+enum { GBT_BATCH_AUTO = 0, GBT_BATCH_FUSED = 1, GBT_BATCH_CONCURRENT = 2 };
+
 typedef struct gbt_batch_desc {
     int32_t n_instances;              /* >= 1 */
     const gbt_trace_t *const *traces; /* host array of n_instances handles */
     const gbt_sum_args *args;         /* host array of n_instances argument sets; all F32,
                                          one window, n_freq <= 8 */
     int32_t use_graph;                /* 1: capture on first submit, then replay */
-    int32_t autotune;                 /* 1: time a few work splittings at create, keep the best */
+    int32_t autotune;                 /* 1: time the candidate forms / work splittings at
+                                         create (running the batch a few times), keep the best */
+    int32_t form;                     /* GBT_BATCH_AUTO, _FUSED or _CONCURRENT */
 } gbt_batch_desc;
 
 /* Create synchronises `stream` once (it reads each trace's segment count to
  * order the instances longest first and to size their work) and allocates
  * the batch's device workspace; with autotune it also runs the batch a few
  * times.  Submit queues the whole batch on `stream` (graph replay after the
- * first submit when use_graph is set); outputs land in each instance's out. */
+ * first submit when use_graph is set); outputs land in each instance's out.
+ * GBT_ERR_INVALID_ARG for an unknown form. */
 gbt_status gbt_batch_create(const gbt_batch_desc *desc, void *stream, gbt_batch_t **out);
 gbt_status gbt_batch_submit(gbt_batch_t *batch, void *stream);
 gbt_status gbt_batch_destroy(gbt_batch_t *batch);

@@ -642,6 +642,9 @@ gbt_status gbt_batch_create(const gbt_batch_desc *desc, void *stream, gbt_batch_
         *out = nullptr;
         GBT_REQUIRE(desc->n_instances >= 1, "n_instances must be >= 1");
         GBT_REQUIRE(desc->traces && desc->args, "traces and args must be non-NULL");
+        GBT_REQUIRE(desc->form == GBT_BATCH_AUTO || desc->form == GBT_BATCH_FUSED ||
+                        desc->form == GBT_BATCH_CONCURRENT,
+                    "form must be GBT_BATCH_AUTO, GBT_BATCH_FUSED or GBT_BATCH_CONCURRENT");
         for (int i = 0; i < desc->n_instances; ++i) validate_sum(desc->traces[i], &desc->args[i]);
         gbt_batch_t *b = new gbt_batch_s();
         try {

@@ -54,15 +54,21 @@ enum { kFwd = 0, kStats = 1, kBwd = 2 };    // what the pair kernel does with su
 constexpr int kFoldEvery = 16;              // batches between float-float folds
 constexpr float kWinMargin = 0.01f;         // prefilter window slack (m)
 
-struct FreqConst {
+// Per-frequency constants, grouped in 16-byte words in the order the survivor
+// path needs them (cutoff test, then the beam), so a kernel that reads them from
+// shared memory (the batched launch) needs two vector loads per kept frequency.
+struct alignas(16) FreqConst {
+    float kb2;            // k b / 2  (Gaussian exponent factor)
+    float b2;             // b^2
     float K_hi, K_lo;     // f / c in turns per metre, float-float
     float halfK;          // K / 2: second phase term K n^2 s / (2 D) in turns
-    float kb2;            // k b / 2  (Gaussian exponent factor)
     float kb2l2e;         // k b / 2 * log2(e)
-    float b, b2;          // b, b^2
     float scale;          // k b / (8 pi^2)
+    float b;              // b
     float kh, invb;       // k / 2, 1 / b  (adjoint)
+    float pad0, pad1;
 };
+static_assert(sizeof(FreqConst) == 48, "three 16-byte words");
 
 struct alignas(16) FwdParams {
     const float *recv;
@@ -1241,7 +1247,7 @@ __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 template <int NF, int WINDOW, int MODE, bool BATCHED = false>
-void launch_fwd_t(const FwdParams &p, cudaStream_t s)
+void launch_fwd_t(const FwdParams &p, cudaStream_t s, bool timed)
 {
     constexpr bool STATS = MODE != kFwd;
     const size_t smem = sizeof(CtaSmem<NF>);
@@ -1254,30 +1260,30 @@ void launch_fwd_t(const FwdParams &p, cudaStream_t s)
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(p.n_items, (int64_t)std::max(per_sm, 1) * num_sms()));
     GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
-    if (MODE != kStats) timing_begin(s);
+    if (MODE != kStats && timed) timing_begin(s);
     gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED><<<grid, kThreads, smem, s>>>(p);
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
-    if (MODE != kStats) timing_end(s);
+    if (MODE != kStats && timed) timing_end(s);
     (void)STATS;
 }
 
 template <int NF, int WINDOW>
-void launch_fwd(const FwdParams &p, cudaStream_t s)
+void launch_fwd(const FwdParams &p, cudaStream_t s, bool timed)
 {
-    if (p.grad_out) launch_fwd_t<NF, WINDOW, kBwd>(p, s);
-    else if (p.stats) launch_fwd_t<NF, WINDOW, kStats>(p, s);
-    else launch_fwd_t<NF, WINDOW, kFwd>(p, s);
+    if (p.grad_out) launch_fwd_t<NF, WINDOW, kBwd>(p, s, timed);
+    else if (p.stats) launch_fwd_t<NF, WINDOW, kStats>(p, s, timed);
+    else launch_fwd_t<NF, WINDOW, kFwd>(p, s, timed);
 }
 
 template <int WINDOW>
-void launch_fwd_nf(const FwdParams &p, cudaStream_t s)
+void launch_fwd_nf(const FwdParams &p, cudaStream_t s, bool timed = true)
 {
-    if (p.nf <= 1) launch_fwd<1, WINDOW>(p, s);
-    else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, s);
-    else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, s);
-    else if (p.nf <= 6) launch_fwd<6, WINDOW>(p, s);
-    else launch_fwd<8, WINDOW>(p, s);
+    if (p.nf <= 1) launch_fwd<1, WINDOW>(p, s, timed);
+    else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, s, timed);
+    else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, s, timed);
+    else if (p.nf <= 6) launch_fwd<6, WINDOW>(p, s, timed);
+    else launch_fwd<8, WINDOW>(p, s, timed);
 }
 
 // Kernel parameters shared by the forward, counting and adjoint launches.
@@ -1665,6 +1671,8 @@ void batched_launch(const FwdParams &prm, int grid, cudaStream_t s)
 }
 
 typedef int (*BatchedPrepFn)();
+enum { kFused = 0, kConcurrent = 1 };      // how a batch executes
+constexpr int kBranches = 4;               // branch streams of a concurrent batch
 typedef void (*BatchedLaunchFn)(const FwdParams &, int, cudaStream_t);
 
 struct BatchImpl {
@@ -1689,6 +1697,13 @@ struct BatchImpl {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t graph_kernels = 0;               // kernel nodes of the recorded graph
+    // kConcurrent: each instance runs the single-instance pair kernel (parameters
+    // in constant space) on one of a few branch streams forked from the submit
+    // stream, so one instance's draining tail overlaps the next one's start
+    int mode = kFused;
+    std::vector<cudaStream_t> branch;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
 };
 
 static void batch_plan(BatchImpl &B, double items_per_slot)
@@ -1712,6 +1727,14 @@ static void batch_plan(BatchImpl &B, double items_per_slot)
     }
 }
 
+// Concurrent batches split each instance as a single sum would.
+static void batch_plan_concurrent(BatchImpl &B)
+{
+    const int n = (int)B.args.size();
+    B.splits.assign(n, 1);
+    for (int i = 0; i < n; ++i) B.splits[i] = choose_splits(B.traces[i]->d, B.args[i]);
+}
+
 static void batch_layout(BatchImpl &B, cudaStream_t s)
 {
     const int n = (int)B.args.size();
@@ -1728,9 +1751,10 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         B.ord_off[i] = b;
         b += tile_order_bytes(B.args[i].n_recv);
     }
+    const size_t cnt = align_up((size_t)n * sizeof(int), 256);    // one work counter per instance
     const size_t tab = align_up((size_t)n * sizeof(FwdParams), 256);
     const size_t off = align_up((size_t)(n + 1) * sizeof(int64_t), 256);
-    const size_t need = b + 256 + tab + off;
+    const size_t need = b + cnt + tab + off;
     if (need > B.work_bytes) {
         if (B.work) dfree(B.work, s);
         B.work = dalloc(need, s);
@@ -1738,8 +1762,8 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
     }
     char *w = static_cast<char *>(B.work);
     B.counter = reinterpret_cast<int *>(w + b);
-    B.d_table = reinterpret_cast<FwdParams *>(w + b + 256);
-    B.d_off = reinterpret_cast<int64_t *>(w + b + 256 + tab);
+    B.d_table = reinterpret_cast<FwdParams *>(w + b + cnt);
+    B.d_off = reinterpret_cast<int64_t *>(w + b + cnt + tab);
 
     B.table.clear();
     B.inst_off.assign(1, 0);
@@ -1752,7 +1776,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         q.splits = B.splits[i];
         q.n_items = ((a.n_recv + kCtaRecv - 1) / kCtaRecv) * q.splits;
         q.partial = reinterpret_cast<float4 *>(w + B.part_off[i]);
-        q.work_counter = B.counter;
+        q.work_counter = B.mode == kConcurrent ? B.counter + k : B.counter;
         q.tile_perm = tile_order_perm(w + B.ord_off[i], a.n_recv);
         B.table.push_back(q);
         B.inst_off.push_back(B.inst_off.back() + q.n_items);
@@ -1764,29 +1788,92 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
     GBT_CUDA(cudaStreamSynchronize(s));
 }
 
-static void batch_record(BatchImpl &B, cudaStream_t s)
+static void batch_prepass(BatchImpl &B, int i, cudaStream_t s)
+{
+    const TraceDev &td = B.traces[i]->d;
+    const gbt_sum_args &a = B.args[i];
+    if (td.capacity == 0) return;
+    PrepParams pp{};
+    pp.n_seg_ptr = td.ray_off + td.n_rays;
+    pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
+    pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
+    pp.gamma = a.gamma;
+    pp.weight = a.ray_weight;
+    pp.w_default = 4.0 * kPi / (double)td.n_fan;
+    pp.n_materials = td.scene->d.n_materials;
+    pp.rec = reinterpret_cast<float *>(static_cast<char *>(B.work) + B.rec_off[i]);
+    pp.amp64 = nullptr;
+    pp.status = status_word();
+    prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
+    note_launches(1);
+    GBT_CUDA(cudaGetLastError());
+}
+
+// Merge of instance i (processing index k) into its output.
+static void batch_reduce(BatchImpl &B, int k, cudaStream_t s)
+{
+    const int i = B.order[k];
+    const gbt_sum_args &a = B.args[i];
+    if (a.n_recv == 0) return;
+    ReduceParams rp{};
+    rp.n = (int64_t)a.n_freq * a.n_recv;
+    rp.n_recv = a.n_recv;
+    for (int f = 0; f < GBT_MAX_FREQ; ++f) rp.perm[f] = B.table[k].fperm[f];
+    rp.splits = B.splits[i];
+    rp.p32 = reinterpret_cast<float4 *>(static_cast<char *>(B.work) + B.part_off[i]);
+    rp.p64 = nullptr;
+    rp.out = reinterpret_cast<float2 *>(a.out);
+    rp.accumulate = a.accumulate;
+    reduce_kernel<<<(unsigned)((rp.n + 255) / 256), 256, 0, s>>>(rp);
+    note_launches(1);
+    GBT_CUDA(cudaGetLastError());
+}
+
+// Concurrent form: instances (longest first) dealt round-robin to branch streams
+// forked from s and joined back into it; on each branch an instance's prepass,
+// tile order, pair kernel and merge follow one another.
+static void batch_record_concurrent(BatchImpl &B, cudaStream_t s)
 {
     const int n = (int)B.args.size();
-    char *w = static_cast<char *>(B.work);
-    for (int i = 0; i < n; ++i) {
-        const TraceDev &td = B.traces[i]->d;
-        const gbt_sum_args &a = B.args[i];
-        if (td.capacity == 0) continue;
-        PrepParams pp{};
-        pp.n_seg_ptr = td.ray_off + td.n_rays;
-        pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
-        pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
-        pp.gamma = a.gamma;
-        pp.weight = a.ray_weight;
-        pp.w_default = 4.0 * kPi / (double)td.n_fan;
-        pp.n_materials = td.scene->d.n_materials;
-        pp.rec = reinterpret_cast<float *>(w + B.rec_off[i]);
-        pp.amp64 = nullptr;
-        pp.status = status_word();
-        prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
-        note_launches(1);
-        GBT_CUDA(cudaGetLastError());
+    const int nb = std::max(1, std::min(n, kBranches));
+    if (B.branch.empty()) {
+        B.branch.assign(nb, nullptr);
+        B.join.assign(nb, nullptr);
+        for (int j = 0; j < nb; ++j) {
+            GBT_CUDA(cudaStreamCreateWithFlags(&B.branch[j], cudaStreamNonBlocking));
+            GBT_CUDA(cudaEventCreateWithFlags(&B.join[j], cudaEventDisableTiming));
+        }
+        GBT_CUDA(cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming));
     }
+    GBT_CUDA(cudaEventRecord(B.fork, s));
+    for (int j = 0; j < nb; ++j) GBT_CUDA(cudaStreamWaitEvent(B.branch[j], B.fork, 0));
+    char *w = static_cast<char *>(B.work);
+    for (int k = 0; k < n; ++k) {
+        const int i = B.order[k];
+        cudaStream_t bs = B.branch[k % nb];
+        batch_prepass(B, i, bs);
+        if (B.args[i].n_recv == 0) continue;
+        const FwdParams &q = B.table[k];
+        if (q.tile_perm) tile_order_launch(q, B.window, w + B.ord_off[i], bs);
+        if (B.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, bs, false);
+        else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, bs, false);
+        batch_reduce(B, k, bs);
+    }
+    for (int j = 0; j < nb; ++j) {
+        GBT_CUDA(cudaEventRecord(B.join[j], B.branch[j]));
+        GBT_CUDA(cudaStreamWaitEvent(s, B.join[j], 0));
+    }
+}
+
+static void batch_record(BatchImpl &B, cudaStream_t s)
+{
+    if (B.mode == kConcurrent) {
+        batch_record_concurrent(B, s);
+        return;
+    }
+    const int n = (int)B.args.size();
+    char *w = static_cast<char *>(B.work);
+    for (int i = 0; i < n; ++i) batch_prepass(B, i, s);
     for (int k = 0; k < n; ++k) {
         const int i = B.order[k];
         if (B.table[k].tile_perm) tile_order_launch(B.table[k], B.window, w + B.ord_off[i], s);
@@ -1798,23 +1885,7 @@ static void batch_record(BatchImpl &B, cudaStream_t s)
     prm.n_items = B.inst_off.back();
     prm.work_counter = B.counter;
     B.launch(prm, B.grid, s);
-    for (int k = 0; k < n; ++k) {
-        const int i = B.order[k];
-        const gbt_sum_args &a = B.args[i];
-        if (a.n_recv == 0) continue;
-        ReduceParams rp{};
-        rp.n = (int64_t)a.n_freq * a.n_recv;
-        rp.n_recv = a.n_recv;
-        for (int f = 0; f < GBT_MAX_FREQ; ++f) rp.perm[f] = B.table[k].fperm[f];
-        rp.splits = B.splits[i];
-        rp.p32 = reinterpret_cast<float4 *>(w + B.part_off[i]);
-        rp.p64 = nullptr;
-        rp.out = reinterpret_cast<float2 *>(a.out);
-        rp.accumulate = a.accumulate;
-        reduce_kernel<<<(unsigned)((rp.n + 255) / 256), 256, 0, s>>>(rp);
-        note_launches(1);
-        GBT_CUDA(cudaGetLastError());
-    }
+    for (int k = 0; k < n; ++k) batch_reduce(B, k, s);
 }
 
 BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
@@ -1862,33 +1933,47 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
 #undef GBT_PICK
         per_sm = prep();
         B->grid = per_sm * num_sms();
-        double best_ips = 8.0;
-        if (d.autotune) {
-            // autotuner: time a few work granularities (items per resident CTA)
+        // candidates: the concurrent form, then the fused launch at a few work
+        // granularities (items per resident CTA); 0 items marks the concurrent form
+        auto plan = [&](double ips) {
+            B->mode = ips > 0.0 ? kFused : kConcurrent;
+            if (ips > 0.0) batch_plan(*B, ips);
+            else batch_plan_concurrent(*B);
+            batch_layout(*B, s);
+        };
+        // the fused form's default granularity when it is not tuned
+        double best_ips = d.form == GBT_BATCH_FUSED ? 32.0 : 0.0;
+        std::vector<double> cands;
+        if (d.form != GBT_BATCH_FUSED) cands.push_back(0.0);
+        if (d.form != GBT_BATCH_CONCURRENT) for (double v : {4.0, 8.0, 16.0, 32.0}) cands.push_back(v);
+        if (d.autotune && cands.size() > 1) {
             float best = 1e30f;
             cudaEvent_t e0, e1;
             GBT_CUDA(cudaEventCreate(&e0));
             GBT_CUDA(cudaEventCreate(&e1));
-            for (double ips : {4.0, 8.0, 16.0, 32.0}) {
-                batch_plan(*B, ips);
-                batch_layout(*B, s);
-                batch_record(*B, s);   // warm
-                GBT_CUDA(cudaEventRecord(e0, s));
-                batch_record(*B, s);
-                GBT_CUDA(cudaEventRecord(e1, s));
-                GBT_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                GBT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) { best = ms; best_ips = ips; }
+            try {
+                for (double ips : cands) {
+                    plan(ips);
+                    batch_record(*B, s);   // warm
+                    GBT_CUDA(cudaEventRecord(e0, s));
+                    batch_record(*B, s);
+                    GBT_CUDA(cudaEventRecord(e1, s));
+                    GBT_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    GBT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) { best = ms; best_ips = ips; }
+                }
+            } catch (...) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                throw;
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
         }
-        batch_plan(*B, best_ips);
-        batch_layout(*B, s);
+        plan(best_ips);
     } catch (...) {
-        if (B->work) dfree(B->work, s);
-        delete B;
+        batch_destroy(B);
         throw;
     }
     return B;
@@ -1940,6 +2025,9 @@ void batch_destroy(BatchImpl *B)
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+    for (cudaStream_t b : B->branch) if (b) cudaStreamDestroy(b);
+    for (cudaEvent_t e : B->join) if (e) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
     if (B->work) dfree(B->work, nullptr);
     delete B;
 }

@@ -22,6 +22,7 @@ HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "gbt.h")
 
 MAX_FREQ = 16
 WINDOW_SEGMENT, WINDOW_LINE = 0, 1
+BATCH_AUTO, BATCH_FUSED, BATCH_CONCURRENT = 0, 1, 2
 PRECISION_F32, PRECISION_F64 = 0, 1
 FAN_FIBONACCI, FAN_EXPLICIT = 0, 1
 
@@ -77,7 +78,7 @@ class gbt_sum_stats(C.Structure):
 
 class gbt_batch_desc(C.Structure):
     _fields_ = [("n_instances", C.c_int32), ("traces", C.c_void_p), ("args", C.c_void_p),
-                ("use_graph", C.c_int32), ("autotune", C.c_int32)]
+                ("use_graph", C.c_int32), ("autotune", C.c_int32), ("form", C.c_int32)]
 
 
 _lib = None
@@ -486,7 +487,8 @@ class Batch:
     use_graph is set); results land in each instance's ``out``."""
 
     def __init__(self, instances, window: int = WINDOW_SEGMENT, cutoff: float = 16.0,
-                 use_graph: bool = True, autotune: bool = False, tile_cull: bool = False):
+                 use_graph: bool = True, autotune: bool = False, tile_cull: bool = False,
+                 form: int = BATCH_AUTO):
         import torch
         self.instances = []
         args = []
@@ -507,7 +509,7 @@ class Batch:
         self._traces = (C.c_void_p * n)(*[d["trace"].handle for d in self.instances])
         desc = gbt_batch_desc(n, C.cast(self._traces, C.c_void_p).value,
                               C.cast(self._args, C.c_void_p).value, 1 if use_graph else 0,
-                              1 if autotune else 0)
+                              1 if autotune else 0, int(form))
         self.handle = gbt_batch_create(desc, _stream_ptr())
 
     @property

@@ -51,6 +51,16 @@ def test_null_handles_rejected(lib):
     assert lib.gbt_trace_destroy(None) == 0 and lib.gbt_scene_destroy(None) == 0
 
 
+def test_unknown_batch_form_rejected_on_host(lib):
+    traces = (ctypes.c_void_p * 1)(None)
+    args = (G.gbt_sum_args * 1)()
+    d = G.gbt_batch_desc(1, ctypes.cast(traces, ctypes.c_void_p).value,
+                         ctypes.cast(args, ctypes.c_void_p).value, 1, 0, 7)
+    with pytest.raises(G.GBTError) as e:
+        G.gbt_batch_create(d, 0)
+    assert e.value.status == 1 and b"form" in lib.gbt_last_error()
+
+
 @pytest.mark.gpu
 def test_bounded_device_wait_times_out_and_context_survives(lib):
     import torch

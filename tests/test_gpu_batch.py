@@ -1,4 +1,5 @@
-"""Batched persistent launch (gbt_batch_*) vs one gbt_sum per instance, and vs the oracle."""
+"""Batches (gbt_batch_*, fused persistent and concurrent forms) vs one gbt_sum per
+instance, and vs the oracle."""
 import numpy as np
 import pytest
 
@@ -43,10 +44,14 @@ def _batch_setup(G, n_src=6, side=40, seed=44):
     return w, sc, gam, insts, srcs
 
 
-def test_batch_equals_per_instance_sums(G):
+@pytest.mark.parametrize("form,use_graph", [(1, True), (1, False), (2, True), (2, False)])
+def test_batch_equals_per_instance_sums(G, form, use_graph):
+    """FUSED: one persistent launch over all instances' items (other splits than a
+    single sum, so equal up to rounding).  CONCURRENT: the single-sum kernels with
+    the single sum's splits on branch streams, so bit-identical."""
     import torch
     w, sc, gam, insts, _ = _batch_setup(G)
-    batch = G.Batch(insts, window=w.window, use_graph=True)
+    batch = G.Batch(insts, window=w.window, use_graph=use_graph, form=form)
     for rep in range(2):                               # capture, then replay
         batch.submit()
         torch.cuda.synchronize()
@@ -55,14 +60,21 @@ def test_batch_equals_per_instance_sums(G):
             ref = G.gbs_sum(d["trace"], d["recv"], d["freqs"], d["beam_b"], gam, order=d["order"],
                             window=w.window)
             torch.cuda.synchronize()
-            e = rel_l2(out.cpu().numpy().astype(np.complex128), ref.cpu().numpy().astype(np.complex128))
-            assert e < 1e-6, (rep, e)
+            got = out.cpu().numpy().astype(np.complex128)
+            ref = ref.cpu().numpy().astype(np.complex128)
+            if form == G.BATCH_CONCURRENT:
+                assert np.array_equal(got, ref), rep
+            else:
+                e = rel_l2(got, ref)
+                assert e < 1e-6, (rep, e)
+    batch.close()
 
 
-def test_batch_graph_replay_sees_new_gamma(G):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_graph_replay_sees_new_gamma(G, form):
     import torch
     w, sc, gam, insts, srcs = _batch_setup(G, n_src=3, side=32, seed=3)
-    batch = G.Batch(insts, window=w.window, use_graph=True, autotune=True)
+    batch = G.Batch(insts, window=w.window, use_graph=True, autotune=True, form=form)
     batch.submit()
     torch.cuda.synchronize()
     new_gamma = np.linspace(0.5, 0.99, w.scene.n_materials).astype(np.float32)
