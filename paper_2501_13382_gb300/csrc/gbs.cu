@@ -44,7 +44,8 @@ namespace {
 
 constexpr int kConsumerWarps = 15;          // compute warps per CTA (one CTA per SM)
 constexpr int kThreads = 32 * (kConsumerWarps + 1);   // + one producer warp
-constexpr int kStages = 8;                  // shared-memory ring of staged batches
+constexpr int kStages = 4;                  // ring of raw record batches (bulk-copy targets)
+constexpr int kStaged = 8;                  // ring of staged batches shared by the consumer warps
 constexpr int kR = 2;                       // receivers per lane
 constexpr int kWarpRecv = 32 * kR;          // receivers per warp
 constexpr int kCtaRecv = kConsumerWarps * kWarpRecv;
@@ -172,6 +173,29 @@ __device__ __forceinline__ f2x mul2(f2x a, f2x b)
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ f2x neg2(f2x a) { return a ^ 0x8000000080000000ull; }
+__device__ __forceinline__ f2x splat(float a) { return pk(a, a); }
+// two_sum on both halves; the paired operations round each half exactly like the
+// scalar ones, so both paths give identical results
+__device__ __forceinline__ void two_sum2(f2x a, f2x b, f2x &s, f2x &e)
+{
+    s = add2(a, b);
+    const f2x bv = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bv)), sub2(b, bv));
+}
+__device__ __forceinline__ f2x dop2(f2x a, f2x b, f2x c, f2x d)
+{
+    const f2x w = mul2(c, d);
+    const f2x e = fma2(neg2(c), d, w);
+    const f2x f = fma2(a, b, neg2(w));
+    return add2(f, e);
+}
+__device__ __forceinline__ f2x rint2(f2x a)
+{
+    float x, y;
+    upk(a, x, y);
+    return pk(rintf(x), rintf(y));
+}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
 {
@@ -230,12 +254,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return false;
 }
 
-// Per-warp shared memory: a double-buffered raw batch and the batch's prefilter
-// (hot) and exact-path (cold) views relative to the warp's first receiver.
+// One staged batch, shared by every consumer warp of the CTA: the prefilter (hot)
+// view relative to the CTA tile's first receiver and the exact-path (cold) view.
 enum { C_OXH = 0, C_OYH, C_OZH, C_OXL, C_OYL, C_OZL, C_TXL, C_TYL, C_TZL, C_S0H, C_S0L,
        C_LH, C_LL, C_AMP, C_COUNT };
-struct WarpSmem {
+struct StageSmem {
     float4 A[kBatch];               // tx, ty, tz, -o'.t   (exact path reads t_hi here)
+    float4 O[kBatch];               // o' = o - tile centre, s0_hi (per-warp ball test)
     // prefilter constants, each duplicated into both halves of a float pair:
     // P[0..3] = t_x, t_y, t_z, -o'.t;  P[4..7] = 2a o'_x, 2a o'_y, 2a o'_z, beta - a |o'|^2;
     // P[8] = s0 + margin, P[9] = L + margin
@@ -246,7 +271,7 @@ struct WarpSmem {
 // Exact geometry of one (receiver, segment) pair in float-float; returns false
 // when the pair falls outside the window.
 template <int WINDOW>
-__device__ __forceinline__ bool exact_geometry(float x, float y, float z, const WarpSmem &w,
+__device__ __forceinline__ bool exact_geometry(float x, float y, float z, const StageSmem &w,
                                                int j, float &sh, float &sl, float &n2)
 {
     const float oxh = w.cold[C_OXH][j], oyh = w.cold[C_OYH][j], ozh = w.cold[C_OZH][j];
@@ -334,37 +359,150 @@ __device__ __forceinline__ void beam_adjoint(const FreqConst &q, float sh, float
     H = fmaf(g.x, cr * dr - ci * di, fmaf(g.y, cr * di + ci * dr, H));
 }
 
-// All frequencies of one surviving (receiver, segment) pair, added to tmp.
-template <int NF, int WINDOW, bool STATS>
-__device__ __forceinline__ void survivor(const FwdParams &p, float x, float y, float z,
-                                         const WarpSmem &w, int j, float2 (&tmp)[NF],
-                                         uint32_t &kept)
+// Counting pass: the kept (pair, frequency) triples of one surviving pair, with
+// the same geometry and cutoff arithmetic as the forward path.
+template <int NF, int WINDOW>
+__device__ __forceinline__ void survivor_count(const FwdParams &p, float x, float y, float z,
+                                               const StageSmem &w, int j, uint32_t &kept)
 {
     float sh, sl, n2;
     if (!exact_geometry<WINDOW>(x, y, z, w, j, sh, sl, n2)) return;
-    const float amp = w.cold[C_AMP][j];
     if (p.uniform_b) {
-        // one b for all frequencies, sorted by k: the kept set is a prefix
         const float D = fmaf(sh, sh, p.fc[0].b2);
-        const float invD = rcp_approx(D);
-        const float r = n2 * invD;
+        const float r = n2 * rcp_approx(D);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f >= p.nf) break;
+            if (p.fc[f].kb2 * r > p.cutoff) break;
+            ++kept;
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f >= p.nf) break;
+            const float D = fmaf(sh, sh, p.fc[f].b2);
+            if (p.fc[f].kb2 * n2 > p.cutoff * D) continue;
+            ++kept;
+        }
+    }
+}
+
+// Two surviving pairs at once in paired FP32: receiver 0 of the lane with
+// segment j0 and receiver 1 with segment j1 (a side without a survivor repeats
+// the other side's segment and is masked out).  Every operation is the paired
+// twin of the single-pair path's (exact_geometry, beam_term), so each half
+// rounds identically to it; only the MUFU operations run per half.  accx / accy
+// hold the two receivers' real / imaginary sums per sorted frequency.
+template <int NF, int WINDOW>
+__device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, f2x Z,
+                                              const StageSmem &w, int j0, int j1, bool h0, bool h1,
+                                              f2x (&accx)[NF], f2x (&accy)[NF])
+{
+    const float4 A0 = w.A[j0], A1 = w.A[j1];
+    const f2x THX = pk(A0.x, A1.x), THY = pk(A0.y, A1.y), THZ = pk(A0.z, A1.z);
+    const f2x TLX = pk(w.cold[C_TXL][j0], w.cold[C_TXL][j1]);
+    const f2x TLY = pk(w.cold[C_TYL][j0], w.cold[C_TYL][j1]);
+    const f2x TLZ = pk(w.cold[C_TZL][j0], w.cold[C_TZL][j1]);
+    // delta = x - o as (a + e)
+    f2x ax, ex, ay, ey, az, ez;
+    two_sum2(X, neg2(pk(w.cold[C_OXH][j0], w.cold[C_OXH][j1])), ax, ex);
+    two_sum2(Y, neg2(pk(w.cold[C_OYH][j0], w.cold[C_OYH][j1])), ay, ey);
+    two_sum2(Z, neg2(pk(w.cold[C_OZH][j0], w.cold[C_OZH][j1])), az, ez);
+    ex = sub2(ex, pk(w.cold[C_OXL][j0], w.cold[C_OXL][j1]));
+    ey = sub2(ey, pk(w.cold[C_OYL][j0], w.cold[C_OYL][j1]));
+    ez = sub2(ez, pk(w.cold[C_OZL][j0], w.cold[C_OZL][j1]));
+    // s_loc = delta . t
+    const f2x p0 = mul2(ax, THX), p1 = mul2(ay, THY), p2 = mul2(az, THZ);
+    const f2x r0 = fma2(ax, TLX, fma2(ex, THX, fma2(ax, THX, neg2(p0))));
+    const f2x r1 = fma2(ay, TLY, fma2(ey, THY, fma2(ay, THY, neg2(p1))));
+    const f2x r2 = fma2(az, TLZ, fma2(ez, THZ, fma2(az, THZ, neg2(p2))));
+    f2x S1, E1, S, E2;
+    two_sum2(p0, p1, S1, E1);
+    two_sum2(S1, p2, S, E2);
+    const f2x lo = add2(add2(E1, E2), add2(add2(r0, r1), r2));
+    bool k0 = h0, k1 = h1;
+    float u0, u1;
+    if (WINDOW == GBT_WINDOW_SEGMENT) {
+        upk(add2(S, lo), u0, u1);
+        k0 = k0 && u0 >= 0.0f;
+        k1 = k1 && u1 >= 0.0f;
+        upk(add2(sub2(S, pk(w.cold[C_LH][j0], w.cold[C_LH][j1])),
+                 sub2(lo, pk(w.cold[C_LL][j0], w.cold[C_LL][j1]))), u0, u1);
+        k0 = k0 && u0 < 0.0f;
+        k1 = k1 && u1 < 0.0f;
+    }
+    f2x sh, e3;
+    two_sum2(pk(w.cold[C_S0H][j0], w.cold[C_S0H][j1]), S, sh, e3);
+    const f2x sl = add2(e3, add2(lo, pk(w.cold[C_S0L][j0], w.cold[C_S0L][j1])));
+    if (WINDOW == GBT_WINDOW_LINE) {
+        upk(add2(sh, sl), u0, u1);
+        k0 = k0 && u0 >= 0.0f;
+        k1 = k1 && u1 >= 0.0f;
+    }
+    if (!(k0 || k1)) return;
+    // n = delta x t, compensated
+    const f2x nx = add2(dop2(ay, THZ, az, THY),
+                        fma2(ay, TLZ, fma2(neg2(az), TLY, fma2(ey, THZ, neg2(mul2(ez, THY))))));
+    const f2x ny = add2(dop2(az, THX, ax, THZ),
+                        fma2(az, TLX, fma2(neg2(ax), TLZ, fma2(ez, THX, neg2(mul2(ex, THZ))))));
+    const f2x nz = add2(dop2(ax, THY, ay, THX),
+                        fma2(ax, TLY, fma2(neg2(ay), TLX, fma2(ex, THY, neg2(mul2(ey, THX))))));
+    const f2x n2 = fma2(nx, nx, fma2(ny, ny, mul2(nz, nz)));
+    const f2x amp = pk(w.cold[C_AMP][j0], w.cold[C_AMP][j1]);
+    float n20, n21;
+    upk(n2, n20, n21);
+
+    // one beam term on both halves, each half kept where its flag is set
+    auto beam = [&](const FreqConst &q, f2x invD, bool kf0, bool kf1, f2x &bx, f2x &by) {
+        const f2x n2invD = mul2(n2, invD);
+        float e0, e1;
+        upk(mul2(splat(-q.kb2l2e), n2invD), e0, e1);
+        const f2x ga = pk(ex2_approx(e0), ex2_approx(e1));
+        const f2x KH = splat(q.K_hi);
+        const f2x ph = mul2(KH, sh);
+        const f2x pe = fma2(KH, sh, neg2(ph));
+        const f2x corr = fma2(KH, sl, fma2(splat(q.K_lo), sh, pe));
+        f2x tau = add2(sub2(ph, rint2(ph)), corr);
+        tau = fma2(mul2(splat(q.halfK), n2invD), sh, tau);
+        tau = sub2(tau, rint2(tau));
+        float t0, t1, s0, c0, s1, c1;
+        upk(mul2(splat(6.283185307179586f), tau), t0, t1);
+        __sincosf(t0, &s0, &c0);
+        __sincosf(t1, &s1, &c1);
+        const f2x SN = pk(s0, s1), CS = pk(c0, c1);
+        const f2x gg = mul2(mul2(mul2(mul2(splat(q.scale), amp), ga), invD),
+                            pk(kf0 ? 1.0f : 0.0f, kf1 ? 1.0f : 0.0f));
+        const f2x B = splat(q.b);
+        bx = fma2(gg, fma2(sh, CS, neg2(mul2(B, SN))), bx);
+        by = fma2(gg, fma2(sh, SN, mul2(B, CS)), by);
+    };
+    if (p.uniform_b) {
+        // one b for all frequencies, sorted by k: each half keeps a prefix
+        float d0, d1;
+        upk(fma2(sh, sh, splat(p.fc[0].b2)), d0, d1);
+        const f2x invD = pk(rcp_approx(d0), rcp_approx(d1));
+        float r0_, r1_;
+        upk(mul2(n2, invD), r0_, r1_);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             if (f >= p.nf) break;
             const FreqConst &q = p.fc[f];
-            if (q.kb2 * r > p.cutoff) break;
-            if (STATS) { ++kept; continue; }
-            beam_term(q, sh, sl, n2, invD, amp, tmp[f]);
+            k0 = k0 && !(q.kb2 * r0_ > p.cutoff);
+            k1 = k1 && !(q.kb2 * r1_ > p.cutoff);
+            if (!(k0 || k1)) break;
+            beam(q, invD, k0, k1, accx[f], accy[f]);
         }
     } else {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             if (f >= p.nf) break;
             const FreqConst &q = p.fc[f];
-            const float D = fmaf(sh, sh, q.b2);
-            if (q.kb2 * n2 > p.cutoff * D) continue;
-            if (STATS) { ++kept; continue; }
-            beam_term(q, sh, sl, n2, rcp_approx(D), amp, tmp[f]);
+            float d0, d1;
+            upk(fma2(sh, sh, splat(q.b2)), d0, d1);
+            const bool kf0 = k0 && !(q.kb2 * n20 > p.cutoff * d0);
+            const bool kf1 = k1 && !(q.kb2 * n21 > p.cutoff * d1);
+            if (!(kf0 || kf1)) continue;
+            beam(q, pk(rcp_approx(d0), rcp_approx(d1)), kf0, kf1, accx[f], accy[f]);
         }
     }
 }
@@ -373,7 +511,7 @@ __device__ __forceinline__ void survivor(const FwdParams &p, float x, float y, f
 // receiver's g per sorted frequency, stride 32 floats2).
 template <int NF, int WINDOW>
 __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, float y, float z,
-                                                 const WarpSmem &w, int j, const float2 *gk,
+                                                 const StageSmem &w, int j, const float2 *gk,
                                                  float *segG, float *segH)
 {
     float sh, sl, n2;
@@ -395,6 +533,9 @@ __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, fl
     if (G != 0.f) atomicAdd(&segG[j], G);
 }
 
+// Folds the two halves of a paired FP32 sum into two float-float accumulators.
+__device__ __forceinline__ void fold_pair(float4 *acc0, float4 *acc1, f2x &sx, f2x &sy);
+
 // Adds an FP32 partial sum into a float-float accumulator (hi, hi, lo, lo).
 __device__ __forceinline__ void fold(float4 *acc, float2 &t)
 {
@@ -410,6 +551,17 @@ __device__ __forceinline__ void fold(float4 *acc, float2 &t)
         *acc = a;
         t = make_float2(0.0f, 0.0f);
     }
+}
+
+__device__ __forceinline__ void fold_pair(float4 *acc0, float4 *acc1, f2x &sx, f2x &sy)
+{
+    float x0, x1, y0, y1;
+    upk(sx, x0, x1);
+    upk(sy, y0, y1);
+    float2 t0 = make_float2(x0, y0), t1 = make_float2(x1, y1);
+    fold(acc0, t0);
+    fold(acc1, t1);
+    sx = sy = 0ull;
 }
 
 // Conservative test: can the segment (origin (ox, oy, oz) relative to the frame
@@ -435,23 +587,19 @@ __device__ __forceinline__ bool ball_may_keep(const float4 &r0, const float4 &r1
     return win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
 }
 
-// Turn lane's raw record into the prefilter view relative to (cx, cy, cz) and
-// the exact-path columns.
-// The warp's receivers lie in the ball (sphere centre, radius) given relative
-// to (cx, cy, cz).  Returns false when the segment's beam provably reaches none
-// of them: the distance to the ray is 1-Lipschitz, so n >= n_c - R and
-// |s| <= |s_c| + R for every receiver in the ball.
-template <int WINDOW>
-__device__ __forceinline__ bool stage_transform(WarpSmem &w, const float4 (&raw)[kRecFloats / 4],
-                                                int lane, bool valid, float cx, float cy, float cz,
-                                                float alpha, float beta, float4 sphere)
+// Stage lane's raw record for the whole CTA: the prefilter view relative to the
+// tile centre (cx, cy, cz), the origin in that frame for the per-warp ball test,
+// and the exact-path view.  A record past the segment count becomes one no
+// receiver can keep.
+__device__ __forceinline__ void stage_batch(StageSmem &w, const float4 (&raw)[kRecFloats / 4],
+                                            int lane, bool valid, float cx, float cy, float cz,
+                                            float alpha, float beta)
 {
     const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2], r3 = raw[3], r4 = raw[4];
     float4 *P = w.P[lane];
-    bool pass = false;
     if (valid) {
         const float ox = (r0.x - cx) + r2.x, oy = (r0.y - cy) + r2.y, oz = (r0.z - cz) + r2.z;
-        pass = ball_may_keep<WINDOW>(r0, r1, ox, oy, oz, sphere, alpha, beta);
+        w.O[lane] = make_float4(ox, oy, oz, r0.w);
         const float ot = fmaf(ox, r1.x, fmaf(oy, r1.y, oz * r1.z));
         const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
         const float a2 = 2.f * alpha;
@@ -463,24 +611,26 @@ __device__ __forceinline__ bool stage_transform(WarpSmem &w, const float4 (&raw)
         P[3] = make_float4(a2 * oz, a2 * oz, c7, c7);
         const float s0m = r0.w + kWinMargin, Lm = r1.w + kWinMargin;
         P[4] = make_float4(s0m, s0m, Lm, Lm);
+        w.cold[C_OXH][lane] = r0.x; w.cold[C_OYH][lane] = r0.y; w.cold[C_OZH][lane] = r0.z;
+        w.cold[C_S0H][lane] = r0.w;
+        w.cold[C_LH][lane] = r1.w;
+        w.cold[C_OXL][lane] = r2.x; w.cold[C_OYL][lane] = r2.y; w.cold[C_OZL][lane] = r2.z;
+        w.cold[C_S0L][lane] = r2.w;
+        w.cold[C_TXL][lane] = r3.x; w.cold[C_TYL][lane] = r3.y; w.cold[C_TZL][lane] = r3.z;
+        w.cold[C_LL][lane] = r3.w;
+        w.cold[C_AMP][lane] = r4.x;
     } else {
-        // a record no receiver can keep: far behind its own start
+        // far behind its own start, and with finite exact-path values
+        w.O[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
         w.A[lane] = make_float4(0.f, 0.f, 0.f, -1e15f);
         P[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         P[1] = make_float4(0.f, 0.f, -1e15f, -1e15f);
         P[2] = make_float4(0.f, 0.f, 0.f, 0.f);
         P[3] = make_float4(0.f, 0.f, 0.f, 0.f);
         P[4] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < C_COUNT; ++c) w.cold[c][lane] = 0.f;
     }
-    w.cold[C_OXH][lane] = r0.x; w.cold[C_OYH][lane] = r0.y; w.cold[C_OZH][lane] = r0.z;
-    w.cold[C_S0H][lane] = r0.w;
-    w.cold[C_LH][lane] = r1.w;
-    w.cold[C_OXL][lane] = r2.x; w.cold[C_OYL][lane] = r2.y; w.cold[C_OZL][lane] = r2.z;
-    w.cold[C_S0L][lane] = r2.w;
-    w.cold[C_TXL][lane] = r3.x; w.cold[C_TYL][lane] = r3.y; w.cold[C_TZL][lane] = r3.z;
-    w.cold[C_LL][lane] = r3.w;
-    w.cold[C_AMP][lane] = r4.x;
-    return pass;
 }
 
 template <int NF>
@@ -491,24 +641,26 @@ struct AdjSmem {
 };
 template <int NF>
 struct CtaSmem {
-    float4 raw[kStages][kBatch][kRecFloats / 4];   // TMA ring of staged record batches
-    WarpSmem w[kConsumerWarps];                     // per consumer warp
+    float4 raw[kStages][kBatch][kRecFloats / 4];   // bulk-copy ring of raw record batches
+    StageSmem stg[kStaged];                         // staged batches for all consumer warps
     union {
         float4 acc[kConsumerWarps][NF][kR][32];     // forward: float-float sums (hi, hi, lo, lo)
         AdjSmem<NF> adj[kConsumerWarps];            // adjoint
     };
-    unsigned long long full[kStages], empty[kStages];
+    unsigned long long full[kStages];                // raw batch landed
+    unsigned long long ready[kStaged], freed[kStaged];   // staged batch written / consumed
     FwdParams inst;            // batched launch: the current item's instance
     int64_t item;
     int inst_idx, abort_flag;
 };
 
 // One CTA per SM.  A producer warp streams record batches of the current item
-// (receiver tile of 960, segment split) into a ring of shared-memory stages
-// with bulk asynchronous copies; 15 consumer warps each turn a stage into
-// constants relative to their own first receiver, release the stage, and run
-// the prefilter and the exact path for their 64 receivers.  Warps wait for
-// each other only through the ring (8 batches of slack) and once per item.
+// (receiver tile of 960, segment split) into a ring of raw stages with bulk
+// asynchronous copies and stages each batch once for the whole CTA (relative to
+// the tile's first receiver) into a second ring; 15 consumer warps run the
+// prefilter and the exact path of every staged batch for their 64 receivers.
+// Warps wait for each other only through the staged ring (8 batches of slack)
+// and once per item.
 template <int NF, int WINDOW, int MODE, bool BATCHED>
 __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParams prm)
 {
@@ -519,9 +671,10 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
     const bool producer = warp == kConsumerWarps;
 
     if (threadIdx.x == 0) {
-        for (int st = 0; st < kStages; ++st) {
-            mbar_init(smem_addr(&S.full[st]), 1);
-            mbar_init(smem_addr(&S.empty[st]), kConsumerWarps);
+        for (int st = 0; st < kStages; ++st) mbar_init(smem_addr(&S.full[st]), 1);
+        for (int st = 0; st < kStaged; ++st) {
+            mbar_init(smem_addr(&S.ready[st]), 32);
+            mbar_init(smem_addr(&S.freed[st]), kConsumerWarps);
         }
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -571,38 +724,52 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
         const int64_t tile_base = (p.tile_perm ? (int64_t)p.tile_perm[tile_rank] : tile_rank) * kCtaRecv;
         const int split = (int)(item % p.splits);
         const uint32_t nb = split < n_batches ? (uint32_t)((n_batches - 1 - split) / p.splits + 1) : 0u;
+        // frame of the staged batches: the tile's first receiver
+        const int64_t c_idx = p.order ? p.order[tile_base] : tile_base;
+        const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
 
         if (producer) {
-            if (lane == 0) {
-                uint32_t issued = 0;
-                for (uint32_t k = 0; k < nb; ++k) {
-                    const uint32_t q = g + k, st = q % kStages, ph = (q / kStages) & 1u;
-                    if (!mbar_wait(smem_addr(&S.empty[st]), ph ^ 1u, abort_flag, p.status)) break;
-                    const int64_t b = split + (int64_t)k * p.splits;
-                    const int64_t nrec = min((int64_t)kBatch, n_seg - b * kBatch);
-                    const uint32_t bytes = (uint32_t)nrec * kRecFloats * 4;
-                    mbar_arrive_expect_tx(smem_addr(&S.full[st]), bytes);
-                    bulk_g2s(smem_addr(&S.raw[st][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
-                             smem_addr(&S.full[st]));
-                    ++issued;
-                }
-                if (*abort_flag) {
-                    // let every copy still in flight land before leaving
-                    const uint32_t first = issued > (uint32_t)kStages ? issued - kStages : 0u;
-                    for (uint32_t k = first; k < issued; ++k) {
-                        const uint32_t q = g + k;
-                        for (long long it = 0; it < kSpinLimit; ++it)
-                            if (mbar_try_wait(smem_addr(&S.full[q % kStages]), (q / kStages) & 1u)) break;
-                    }
+            // bulk copies run kStages batches ahead; every lane stages one record
+            auto issue = [&](uint32_t k) {
+                const uint32_t q = g + k, rs = q % kStages;
+                const int64_t b = split + (int64_t)k * p.splits;
+                const int64_t nrec = min((int64_t)kBatch, n_seg - b * kBatch);
+                const uint32_t bytes = (uint32_t)nrec * kRecFloats * 4;
+                mbar_arrive_expect_tx(smem_addr(&S.full[rs]), bytes);
+                bulk_g2s(smem_addr(&S.raw[rs][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
+                         smem_addr(&S.full[rs]));
+            };
+            uint32_t issued = 0, landed = 0;
+            if (lane == 0)
+                for (; issued < nb && issued < (uint32_t)kStages; ++issued) issue(issued);
+            for (uint32_t k = 0; k < nb; ++k) {
+                const uint32_t q = g + k, rs = q % kStages, qs = q % kStaged;
+                bool ok = mbar_wait(smem_addr(&S.full[rs]), (q / kStages) & 1u, abort_flag, p.status);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                landed = k + 1;
+                ok = mbar_wait(smem_addr(&S.freed[qs]), ((q / kStaged) & 1u) ^ 1u, abort_flag,
+                               p.status);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                const int64_t b = split + (int64_t)k * p.splits;
+                stage_batch(S.stg[qs], S.raw[rs][lane], lane, b * kBatch + lane < n_seg, cx, cy, cz,
+                            alpha, beta);
+                mbar_arrive(smem_addr(&S.ready[qs]));
+                __syncwarp();
+                if (lane == 0 && issued < nb) issue(issued++);
+            }
+            if (lane == 0 && *abort_flag) {
+                // let every copy still in flight land before leaving
+                for (uint32_t k = landed; k < issued; ++k) {
+                    const uint32_t q = g + k;
+                    for (long long it = 0; it < kSpinLimit; ++it)
+                        if (mbar_try_wait(smem_addr(&S.full[q % kStages]), (q / kStages) & 1u)) break;
                 }
             }
         } else {
-            WarpSmem &w = S.w[warp];
             const int64_t wbase = tile_base + (int64_t)warp * kWarpRecv;
             const bool warp_live = wbase < p.n_recv;
-            // warp centre: the warp's first receiver
-            const int64_t c_idx = warp_live ? (p.order ? p.order[wbase] : wbase) : 0;
-            const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
 
             float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
             int32_t ridx[kR];
@@ -642,7 +809,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 for (int f = 0; f < NF; ++f) S.adj[warp].segH[f][lane] = 0.f;
             }
             __syncwarp();
-            // bounding ball of the warp's receivers (relative to its first receiver)
+            // bounding ball of the warp's receivers (relative to the tile centre)
             float4 sphere = make_float4(0.f, 0.f, 0.f, 0.f);
             if (p.tile_cull) {
                 float sx = 0.f, sy = 0.f, sz = 0.f, nv = 0.f;
@@ -673,24 +840,32 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
             const f2x AL2 = pk(alpha, alpha);
             const f2x MG2 = pk(kWinMargin, kWinMargin);
-            float2 tmp[kR][NF];
+            // per-batch FP32 sums of the lane's two receivers, paired (re, im)
+            f2x accx[NF], accy[NF];
 #pragma unroll
-            for (int k = 0; k < kR; ++k)
-#pragma unroll
-                for (int f = 0; f < NF; ++f) tmp[k][f] = make_float2(0.f, 0.f);
+            for (int f = 0; f < NF; ++f) accx[f] = accy[f] = 0ull;
+            const f2x XA = pk(xa[0], xa[1]), YA = pk(ya[0], ya[1]), ZA = pk(za[0], za[1]);
 
             bool dirty = false;   // survivors since the last fold (this lane)
             for (uint32_t kb_ = 0; kb_ < nb; ++kb_) {
-                const uint32_t q = g + kb_, st = q % kStages, ph = (q / kStages) & 1u;
-                if (!mbar_wait(smem_addr(&S.full[st]), ph, abort_flag, p.status)) break;
+                const uint32_t q = g + kb_, qs = q % kStaged;
+                bool ok = mbar_wait(smem_addr(&S.ready[qs]), (q / kStaged) & 1u, abort_flag, p.status);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                const StageSmem &w = S.stg[qs];
+                if (!warp_live) {
+                    if (lane == 0) mbar_arrive(smem_addr(&S.freed[qs]));
+                    continue;
+                }
                 const int64_t b = split + (int64_t)kb_ * p.splits;
-                const bool seg_ok = b * kBatch + lane < n_seg;
-                const bool pass = stage_transform<WINDOW>(w, S.raw[st][lane], lane, seg_ok, cx, cy,
-                                                          cz, alpha, beta, sphere);
-                const uint32_t tmask = __ballot_sync(0xffffffffu, pass);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_addr(&S.empty[st]));
-                if (!warp_live) continue;
+                uint32_t tmask = 0u;
+                if (p.tile_cull) {
+                    // segment `lane` of the batch against the warp's receiver ball
+                    const float4 O = w.O[lane], A = w.A[lane];
+                    const bool pass = b * kBatch + lane < n_seg &&
+                                      ball_may_keep<WINDOW>(O, make_float4(A.x, A.y, A.z, w.cold[C_LH][lane]),
+                                                            O.x, O.y, O.z, sphere, alpha, beta);
+                    tmask = __ballot_sync(0xffffffffu, pass);
+                }
 
                 // ---- prefilter: one keep bit per (receiver, segment); segment jj at bit 31 - jj.
                 // Both receivers of the lane go through paired FP32 instructions:
@@ -751,20 +926,34 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     }
                 }
                 // ---- survivors, in segment order per receiver
+                if (MODE == kFwd) {
+                    // the two receivers' survivors side by side, each in segment order
+                    uint32_t mm0 = (valid & 1u) ? m[0] : 0u, mm1 = (valid & 2u) ? m[1] : 0u;
+                    while (mm0 | mm1) {
+                        const bool h0 = mm0 != 0u, h1 = mm1 != 0u;
+                        int j0 = __clz(mm0), j1 = __clz(mm1);
+                        if (h0) mm0 ^= 0x80000000u >> j0;
+                        if (h1) mm1 ^= 0x80000000u >> j1;
+                        if (!h0) j0 = j1;
+                        if (!h1) j1 = j0;
+                        survivor_pair<NF, WINDOW>(p, XA, YA, ZA, w, j0, j1, h0, h1, accx, accy);
+                    }
+                } else {
 #pragma unroll
-                for (int k = 0; k < kR; ++k) {
-                    uint32_t mm = ((valid >> k) & 1u) ? m[k] : 0u;
-                    if (STATS) n_pre += __popc(mm);
-                    while (mm) {
-                        const int jj = __clz(mm);
-                        mm ^= 0x80000000u >> jj;
-                        if (MODE == kBwd)
-                            survivor_adjoint<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj,
-                                                         &S.adj[warp].g[0][k][lane],
-                                                         S.adj[warp].segG, &S.adj[warp].segH[0][0]);
-                        else
-                            survivor<NF, WINDOW, STATS>(p, xa[k], ya[k], za[k], w, jj, tmp[k],
-                                                        n_kept);
+                    for (int k = 0; k < kR; ++k) {
+                        uint32_t mm = ((valid >> k) & 1u) ? m[k] : 0u;
+                        if (STATS) n_pre += __popc(mm);
+                        while (mm) {
+                            const int jj = __clz(mm);
+                            mm ^= 0x80000000u >> jj;
+                            if (MODE == kBwd)
+                                survivor_adjoint<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj,
+                                                             &S.adj[warp].g[0][k][lane],
+                                                             S.adj[warp].segG,
+                                                             &S.adj[warp].segH[0][0]);
+                            else
+                                survivor_count<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj, n_kept);
+                        }
                     }
                 }
                 if (MODE == kBwd) {
@@ -785,18 +974,20 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 if (MODE == kFwd && (kb_ % kFoldEvery) == kFoldEvery - 1 && dirty) {
                     dirty = false;
 #pragma unroll
-                    for (int k = 0; k < kR; ++k)
-#pragma unroll
-                        for (int f = 0; f < NF; ++f) fold(&S.acc[warp][f][k][lane], tmp[k][f]);
+                    for (int f = 0; f < NF; ++f)
+                        fold_pair(&S.acc[warp][f][0][lane], &S.acc[warp][f][1][lane], accx[f], accy[f]);
                 }
                 __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&S.freed[qs]));
             }
             if (MODE == kFwd) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    fold_pair(&S.acc[warp][f][0][lane], &S.acc[warp][f][1][lane], accx[f], accy[f]);
 #pragma unroll
                 for (int k = 0; k < kR; ++k) {
 #pragma unroll
                     for (int f = 0; f < NF; ++f) {
-                        fold(&S.acc[warp][f][k][lane], tmp[k][f]);
                         if (f < p.nf && ridx[k] >= 0)
                             part_base[(int64_t)f * p.n_recv + ridx[k]] = S.acc[warp][f][k][lane];
                     }
