@@ -44,7 +44,7 @@ namespace {
 
 constexpr int kConsumerWarps = 15;          // compute warps per CTA (one CTA per SM)
 constexpr int kThreads = 32 * (kConsumerWarps + 1);   // + one producer warp
-constexpr int kStages = 4;                  // ring of raw record batches (bulk-copy targets)
+constexpr int kStages = 8;                  // ring of raw record batches (bulk-copy targets)
 constexpr int kStaged = 8;                  // ring of staged batches shared by the consumer warps
 constexpr int kR = 2;                       // receivers per lane
 constexpr int kWarpRecv = 32 * kR;          // receivers per warp
@@ -86,6 +86,10 @@ struct alignas(16) FwdParams {
     int64_t n_items;           // CTA tiles x splits
     int *work_counter;         // zeroed before launch; CTAs take items from it
     const int32_t *tile_perm;  // dispatch rank -> CTA tile (heaviest first), or null
+    // tile pre-cull: per CTA tile, the segments whose beams can reach its receivers
+    const int32_t *list;       // segment indices, each tile's in segment order, or null
+    const int64_t *list_off;   // per tile: first entry in list
+    const int32_t *list_n;     // per tile: entries, or -1 (no list: stream every segment)
     float4 *partial;           // [splits][nf][n_recv]: re_hi, im_hi, re_lo, im_lo
     unsigned long long *stats; // counting mode when non-null: [1] prefiltered, [2] kept
     unsigned int *status;      // device status word (timeouts)
@@ -206,6 +210,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n"); }
+// waits until at most kStages - 1 of this thread's commit groups are pending
+__device__ __forceinline__ void cp_async_wait_stages()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 1) : "memory");
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -266,6 +275,7 @@ struct StageSmem {
     // P[8] = s0 + margin, P[9] = L + margin
     float4 P[kBatch][5];
     float cold[C_COUNT][kBatch];
+    int32_t seg[kBatch];            // global segment index of each staged record
 };
 
 // Exact geometry of one (receiver, segment) pair in float-float; returns false
@@ -592,11 +602,12 @@ __device__ __forceinline__ bool ball_may_keep(const float4 &r0, const float4 &r1
 // and the exact-path view.  A record past the segment count becomes one no
 // receiver can keep.
 __device__ __forceinline__ void stage_batch(StageSmem &w, const float4 (&raw)[kRecFloats / 4],
-                                            int lane, bool valid, float cx, float cy, float cz,
-                                            float alpha, float beta)
+                                            int lane, bool valid, int32_t seg, float cx, float cy,
+                                            float cz, float alpha, float beta)
 {
     const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2], r3 = raw[3], r4 = raw[4];
     float4 *P = w.P[lane];
+    w.seg[lane] = valid ? seg : -1;
     if (valid) {
         const float ox = (r0.x - cx) + r2.x, oy = (r0.y - cy) + r2.y, oz = (r0.z - cz) + r2.z;
         w.O[lane] = make_float4(ox, oy, oz, r0.w);
@@ -684,7 +695,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
     volatile int *abort_flag = &S.abort_flag;
     uint32_t n_pre = 0, n_kept = 0;
     unsigned long long n_test = 0;
-    uint32_t g = 0;   // batches through the ring so far (same count in every role)
+    uint32_t g = 0;       // batches through the staged ring so far (same count in every role)
+    uint32_t gfull = 0;   // producer: batches through the raw ring by bulk copy
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -717,11 +729,21 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
         const FwdParams &p = *(BATCHED ? &S.inst : &prm);
         const int64_t item = S.item;
         if (item >= (BATCHED ? prm.n_items : p.n_items) || *abort_flag) break;
-        const int64_t n_seg = *p.n_seg_ptr;
-        const int64_t n_batches = (n_seg + kBatch - 1) / kBatch;
         const float alpha = p.pre_alpha, beta = p.pre_beta;
         const int64_t tile_rank = item / p.splits;
-        const int64_t tile_base = (p.tile_perm ? (int64_t)p.tile_perm[tile_rank] : tile_rank) * kCtaRecv;
+        const int64_t tile = p.tile_perm ? (int64_t)p.tile_perm[tile_rank] : tile_rank;
+        const int64_t tile_base = tile * kCtaRecv;
+        // the segments this item streams: the tile's list, or every segment
+        const int32_t *lst = nullptr;
+        int64_t n_seg = *p.n_seg_ptr;
+        if (p.list) {
+            const int32_t ln = p.list_n[tile];
+            if (ln >= 0) {
+                lst = p.list + p.list_off[tile];
+                n_seg = ln;
+            }
+        }
+        const int64_t n_batches = (n_seg + kBatch - 1) / kBatch;
         const int split = (int)(item % p.splits);
         const uint32_t nb = split < n_batches ? (uint32_t)((n_batches - 1 - split) / p.splits + 1) : 0u;
         // frame of the staged batches: the tile's first receiver
@@ -729,40 +751,74 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
         const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
 
         if (producer) {
-            // bulk copies run kStages batches ahead; every lane stages one record
-            auto issue = [&](uint32_t k) {
-                const uint32_t q = g + k, rs = q % kStages;
-                const int64_t b = split + (int64_t)k * p.splits;
-                const int64_t nrec = min((int64_t)kBatch, n_seg - b * kBatch);
-                const uint32_t bytes = (uint32_t)nrec * kRecFloats * 4;
-                mbar_arrive_expect_tx(smem_addr(&S.full[rs]), bytes);
-                bulk_g2s(smem_addr(&S.raw[rs][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
-                         smem_addr(&S.full[rs]));
+            // bulk copies run kStages batches ahead (one copy of consecutive records, or one
+            // 80-byte copy per lane from the tile's list); every lane stages one record
+            // Contiguous segments: one bulk copy per batch, completed on the `full`
+            // mbarrier of its raw stage (uses counted by gfull).  A tile's list: every
+            // lane gathers its own record with 16-byte async copies, one commit group per
+            // batch and always kStages groups in flight (empty ones past the end), and
+            // later stages only that record, so no lane waits on another's copies.
+            auto list_idx = [&](uint32_t k) -> int32_t {   // loaded one issue ahead
+                const int64_t e = (split + (int64_t)k * p.splits) * kBatch + lane;
+                return (k < nb && e < n_seg) ? lst[e] : -1;
             };
+            int32_t next_idx = lst ? list_idx(0) : -1;
+            auto issue = [&](uint32_t k) {   // all lanes, k in increasing order
+                if (lst) {
+                    const int32_t idx = next_idx;
+                    next_idx = list_idx(k + 1);
+                    if (idx >= 0) {
+                        const float4 *src = reinterpret_cast<const float4 *>(
+                            p.rec + (int64_t)idx * kRecFloats);
+                        float4 *dst = S.raw[k % kStages][lane];
+#pragma unroll
+                        for (int c = 0; c < kRecFloats / 4; ++c) cp_async16(dst + c, src + c, 16);
+                    }
+                    cp_async_commit();
+                } else if (lane == 0) {
+                    const uint32_t q = gfull + k, rs = q % kStages;
+                    const int64_t b = split + (int64_t)k * p.splits;
+                    const uint32_t bytes = (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * kRecFloats * 4;
+                    mbar_arrive_expect_tx(smem_addr(&S.full[rs]), bytes);
+                    bulk_g2s(smem_addr(&S.raw[rs][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
+                             smem_addr(&S.full[rs]));
+                }
+            };
+            const uint32_t ahead = lst ? (uint32_t)kStages : min(nb, (uint32_t)kStages);
             uint32_t issued = 0, landed = 0;
-            if (lane == 0)
-                for (; issued < nb && issued < (uint32_t)kStages; ++issued) issue(issued);
+            for (; issued < ahead; ++issued) issue(issued);
             for (uint32_t k = 0; k < nb; ++k) {
-                const uint32_t q = g + k, rs = q % kStages, qs = q % kStaged;
-                bool ok = mbar_wait(smem_addr(&S.full[rs]), (q / kStages) & 1u, abort_flag, p.status);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-                landed = k + 1;
+                const uint32_t q = g + k, qs = q % kStaged;
+                const uint32_t rs = lst ? k % kStages : (gfull + k) % kStages;
+                bool ok = true;
+                if (lst) {
+                    cp_async_wait_stages();                 // this lane's copies of batch k
+                } else {
+                    ok = mbar_wait(smem_addr(&S.full[rs]), ((gfull + k) / kStages) & 1u, abort_flag,
+                                   p.status);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    landed = k + 1;
+                }
                 ok = mbar_wait(smem_addr(&S.freed[qs]), ((q / kStaged) & 1u) ^ 1u, abort_flag,
                                p.status);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 const int64_t b = split + (int64_t)k * p.splits;
-                stage_batch(S.stg[qs], S.raw[rs][lane], lane, b * kBatch + lane < n_seg, cx, cy, cz,
-                            alpha, beta);
+                const int64_t e = b * kBatch + lane;
+                const bool valid = e < n_seg;
+                stage_batch(S.stg[qs], S.raw[rs][lane], lane, valid,
+                            valid ? (lst ? lst[e] : (int32_t)e) : -1, cx, cy, cz, alpha, beta);
                 mbar_arrive(smem_addr(&S.ready[qs]));
                 __syncwarp();
-                if (lane == 0 && issued < nb) issue(issued++);
+                if (lst || issued < nb) issue(issued++);
             }
-            if (lane == 0 && *abort_flag) {
-                // let every copy still in flight land before leaving
+            if (lst) {
+                cp_async_wait0();   // every gather of this item has landed
+            } else if (lane == 0 && *abort_flag) {
+                // let every bulk copy still in flight land before leaving
                 for (uint32_t k = landed; k < issued; ++k) {
-                    const uint32_t q = g + k;
+                    const uint32_t q = gfull + k;
                     for (long long it = 0; it < kSpinLimit; ++it)
                         if (mbar_try_wait(smem_addr(&S.full[q % kStages]), (q / kStages) & 1u)) break;
                 }
@@ -959,14 +1015,14 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 if (MODE == kBwd) {
                     // per-segment sums of this warp to global, then clear
                     __syncwarp();
-                    const int64_t jg = b * kBatch + lane;
+                    const int64_t jg = w.seg[lane];
                     const float G = S.adj[warp].segG[lane];
-                    if (G != 0.f && jg < n_seg) atomicAdd(&p.seg_G[jg], G);
+                    if (G != 0.f && jg >= 0) atomicAdd(&p.seg_G[jg], G);
                     S.adj[warp].segG[lane] = 0.f;
 #pragma unroll
                     for (int f = 0; f < NF; ++f) {
                         const float H = S.adj[warp].segH[f][lane];
-                        if (H != 0.f && jg < n_seg) atomicAdd(&p.seg_H[f * p.seg_stride + jg], H);
+                        if (H != 0.f && jg >= 0) atomicAdd(&p.seg_H[f * p.seg_stride + jg], H);
                         S.adj[warp].segH[f][lane] = 0.f;
                     }
                 }
@@ -995,6 +1051,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             }
         }
         g += nb;
+        if (!lst) gfull += nb;
         __syncthreads();
     }
     if (STATS && !producer) {
@@ -1321,6 +1378,157 @@ __global__ void tile_rank_kernel(const unsigned int *weight, int64_t n_tiles, in
     perm[rank] = (int32_t)t;
 }
 
+// ---- tile pre-cull: per CTA tile, the list of segments that can reach it
+// Two passes over (chunk of 1024 segments) x (tile) with the ball test of the
+// pre-cull: counts, then the indices, each tile's list in segment order (so the
+// sums keep their order and stay deterministic).  Tiles take consecutive ranges
+// of the list buffer lightest first; a tile that does not fit streams every
+// segment, which gives the same field.
+constexpr int kListChunk = 1024;
+
+template <int WINDOW>
+__device__ __forceinline__ bool seg_reaches_ball(const float4 &r0, const float4 &r1, const float4 &r2,
+                                                 const float4 &b, float alpha, float beta)
+{
+    return ball_may_keep<WINDOW>(r0, r1, (r0.x - b.x) + r2.x, (r0.y - b.y) + r2.y,
+                                 (r0.z - b.z) + r2.z, make_float4(0.f, 0.f, 0.f, b.w), alpha, beta);
+}
+
+template <int WINDOW>
+__global__ void __launch_bounds__(kListChunk) list_count_kernel(
+    const float *rec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
+    int64_t n_chunks, float alpha, float beta, int32_t *counts)
+{
+    extern __shared__ int32_t cnt_s[];
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) cnt_s[t] = 0;
+    __syncthreads();
+    const int64_t ns = *n_seg_ptr;
+    const int64_t c = blockIdx.x;
+    if (c * kListChunk < ns) {
+        const int64_t j = c * kListChunk + threadIdx.x;
+        const bool ok = j < ns;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        if (ok) {
+            const float4 *R = reinterpret_cast<const float4 *>(rec + j * kRecFloats);
+            r0 = R[0]; r1 = R[1]; r2 = R[2];
+        }
+        for (int64_t t = 0; t < n_tiles; ++t) {
+            const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, r2, ball[t], alpha, beta);
+            const unsigned int m = __ballot_sync(0xffffffffu, pass);
+            if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt_s[t], (int32_t)__popc(m));
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) counts[t * n_chunks + c] = cnt_s[t];
+}
+
+// Exclusive scan of 1024 values held one per thread; returns the block total.
+__device__ __forceinline__ int64_t block_scan_1024(int64_t v, int64_t &excl, int64_t *ws)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t x = ws[lane];
+        int64_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        ws[lane] = xi - x;
+        if (lane == 31) ws[32] = xi;
+    }
+    __syncthreads();
+    excl = incl - v + ws[wid];
+    const int64_t total = ws[32];
+    __syncthreads();
+    return total;
+}
+
+// One block per tile: chunk counts -> exclusive offsets within the tile; the tile's total.
+__global__ void __launch_bounds__(1024) list_scan_chunks_kernel(int32_t *counts, int64_t n_chunks,
+                                                                unsigned int *total)
+{
+    __shared__ int64_t ws[33];
+    int32_t *row = counts + (int64_t)blockIdx.x * n_chunks;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < n_chunks; base += 1024) {
+        const int64_t c = base + threadIdx.x;
+        const int64_t v = c < n_chunks ? row[c] : 0;
+        int64_t excl;
+        const int64_t tot = block_scan_1024(v, excl, ws);
+        if (c < n_chunks) row[c] = (int32_t)(carry + excl);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) total[blockIdx.x] = (unsigned int)carry;
+}
+
+// One block: list ranges, tiles lightest first (perm lists them heaviest first).
+__global__ void __launch_bounds__(1024) list_layout_kernel(const unsigned int *total,
+                                                           const int32_t *perm, int64_t n_tiles,
+                                                           int64_t cap, int64_t *list_off,
+                                                           int32_t *list_n)
+{
+    __shared__ int64_t ws[33];
+    const int64_t per = (n_tiles + 1023) / 1024;
+    const int64_t i0 = (int64_t)threadIdx.x * per;
+    auto tile_at = [&](int64_t i) {   // i-th lightest tile
+        const int64_t r = n_tiles - 1 - i;
+        return perm ? (int64_t)perm[r] : r;
+    };
+    int64_t sum = 0;
+    for (int64_t i = i0; i < i0 + per && i < n_tiles; ++i) sum += total[tile_at(i)];
+    int64_t off;
+    block_scan_1024(sum, off, ws);
+    for (int64_t i = i0; i < i0 + per && i < n_tiles; ++i) {
+        const int64_t t = tile_at(i);
+        const int64_t n = total[t];
+        list_off[t] = off;
+        list_n[t] = off + n <= cap ? (int32_t)n : -1;
+        off += n;
+    }
+}
+
+template <int WINDOW>
+__global__ void __launch_bounds__(kListChunk) list_write_kernel(
+    const float *rec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
+    int64_t n_chunks, float alpha, float beta, const int32_t *chunk_off, const int64_t *list_off,
+    const int32_t *list_n, int32_t *list)
+{
+    __shared__ int32_t wsum[32];
+    const int64_t ns = *n_seg_ptr;
+    const int64_t c = blockIdx.x;
+    if (c * kListChunk >= ns) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t j = c * kListChunk + threadIdx.x;
+    const bool ok = j < ns;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    if (ok) {
+        const float4 *R = reinterpret_cast<const float4 *>(rec + j * kRecFloats);
+        r0 = R[0]; r1 = R[1]; r2 = R[2];
+    }
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        if (list_n[t] < 0) continue;
+        const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, r2, ball[t], alpha, beta);
+        const unsigned int m = __ballot_sync(0xffffffffu, pass);
+        if (lane == 0) wsum[wid] = __popc(m);
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < wid; ++w) before += wsum[w];
+        if (pass)
+            list[list_off[t] + chunk_off[t * n_chunks + c] + before +
+                 __popc(m & ((1u << lane) - 1u))] = (int32_t)j;
+        __syncthreads();
+    }
+}
+
 struct ReduceParams {
     int64_t n;                 // nf * n_recv
     int64_t n_recv;
@@ -1550,46 +1758,115 @@ int choose_splits(const TraceDev &td, const gbt_sum_args &a)
 
 static int64_t cta_tiles(int64_t n_recv) { return (n_recv + kCtaRecv - 1) / kCtaRecv; }
 
-// Workspace of the tile order: balls, weights and the permutation.
-static size_t tile_order_bytes(int64_t n_recv)
+// Tile workspace: balls, weights and the dispatch permutation (heaviest tiles
+// first), plus, with the tile pre-cull, the per-tile segment lists.
+struct TileWs {
+    float4 *ball = nullptr;
+    unsigned int *weight = nullptr;
+    int32_t *perm = nullptr;
+    int32_t *counts = nullptr;     // [tiles][chunks]: counts, then offsets within the tile
+    int64_t *list_off = nullptr;
+    int32_t *list_n = nullptr;
+    int32_t *list = nullptr;
+    int64_t tiles = 0, chunks = 0, cap = 0;
+    bool order = false, lists = false;
+    size_t bytes = 0;              // workspace the layout needs
+};
+
+static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, bool tile_cull)
 {
-    const int64_t t = cta_tiles(n_recv);
-    if (t < 2 || t > kMaxOrderedTiles) return 0;
-    return align_up((size_t)t * sizeof(float4), 256) + 2 * align_up((size_t)t * sizeof(int32_t), 256);
+    TileWs t;
+    t.tiles = cta_tiles(n_recv);
+    t.order = t.tiles >= 2 && t.tiles <= kMaxOrderedTiles;
+    t.lists = tile_cull && t.tiles >= 1 && t.tiles <= kMaxOrderedTiles && seg_capacity > 0;
+    if (!t.order && !t.lists) return t;
+    t.chunks = t.lists ? (seg_capacity + kListChunk - 1) / kListChunk : 0;
+    // room for a quarter of all (tile, segment) pairs, at least 16M entries
+    const int64_t all = t.tiles * seg_capacity;
+    t.cap = t.lists ? std::min<int64_t>(all, std::max<int64_t>(int64_t(1) << 24, all / 4)) : 0;
+    char *w = static_cast<char *>(ws);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *r = w ? w + off : nullptr;
+        off += align_up(bytes, 256);
+        return r;
+    };
+    t.ball = reinterpret_cast<float4 *>(take((size_t)t.tiles * sizeof(float4)));
+    t.weight = reinterpret_cast<unsigned int *>(take((size_t)t.tiles * sizeof(unsigned int)));
+    t.perm = reinterpret_cast<int32_t *>(take((size_t)t.tiles * sizeof(int32_t)));
+    if (t.lists) {
+        t.counts = reinterpret_cast<int32_t *>(take((size_t)(t.tiles * t.chunks) * sizeof(int32_t)));
+        t.list_off = reinterpret_cast<int64_t *>(take((size_t)t.tiles * sizeof(int64_t)));
+        t.list_n = reinterpret_cast<int32_t *>(take((size_t)t.tiles * sizeof(int32_t)));
+        t.list = reinterpret_cast<int32_t *>(take((size_t)t.cap * sizeof(int32_t)));
+    }
+    t.bytes = off;
+    return t;
 }
 
-// Where the permutation sits inside a tile-order workspace (null: no ordering).
-static int32_t *tile_order_perm(void *ws, int64_t n_recv)
+static size_t tile_ws_bytes(int64_t n_recv, int64_t seg_capacity, bool tile_cull)
 {
-    const int64_t t = cta_tiles(n_recv);
-    if (t < 2 || t > kMaxOrderedTiles) return nullptr;
-    return reinterpret_cast<int32_t *>(static_cast<char *>(ws) +
-                                       align_up((size_t)t * sizeof(float4), 256) +
-                                       align_up((size_t)t * sizeof(int32_t), 256));
+    return tile_ws_layout(nullptr, n_recv, seg_capacity, tile_cull).bytes;
 }
 
-// Launches the tile order for q's receivers and records (the records must be
-// written earlier on s); returns the permutation inside ws, or null when the
-// tiles are too few or too many to rank.
-static const int32_t *tile_order_launch(const FwdParams &q, int window, void *ws, cudaStream_t s)
+// Launches the tile preparation for q's receivers and records (the records must
+// be written earlier on s) and points q at its results: the dispatch order and,
+// with the pre-cull, the segment lists.  Weights are the exact list sizes when
+// the lists are built, else a sampled count.
+static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStream_t s)
 {
-    int32_t *perm = tile_order_perm(ws, q.n_recv);
-    if (!perm) return nullptr;
-    const int64_t t = cta_tiles(q.n_recv);
-    float4 *ball = static_cast<float4 *>(ws);
-    unsigned int *weight = reinterpret_cast<unsigned int *>(static_cast<char *>(ws) +
-                                                            align_up((size_t)t * sizeof(float4), 256));
-    tile_ball_kernel<<<(unsigned)t, 256, 0, s>>>(q.recv, q.order, q.n_recv, ball, weight);
-    if (window == GBT_WINDOW_LINE)
-        tile_weight_kernel<GBT_WINDOW_LINE><<<kWeightSamples / 256, 256, 0, s>>>(
-            q.rec, q.n_seg_ptr, ball, t, q.pre_alpha, q.pre_beta, weight);
-    else
-        tile_weight_kernel<GBT_WINDOW_SEGMENT><<<kWeightSamples / 256, 256, 0, s>>>(
-            q.rec, q.n_seg_ptr, ball, t, q.pre_alpha, q.pre_beta, weight);
-    tile_rank_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(weight, t, perm);
+    if (!t.order && !t.lists) return;
+    const int64_t T = t.tiles;
+    int64_t n = 0;
+    tile_ball_kernel<<<(unsigned)T, 256, 0, s>>>(q.recv, q.order, q.n_recv, t.ball, t.weight);
+    ++n;
+    if (t.lists) {
+        const size_t sm = (size_t)T * sizeof(int32_t);
+        if (window == GBT_WINDOW_LINE) {
+            GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_LINE>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            list_count_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, sm, s>>>(
+                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts);
+        } else {
+            GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_SEGMENT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            list_count_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, sm, s>>>(
+                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts);
+        }
+        list_scan_chunks_kernel<<<(unsigned)T, 1024, 0, s>>>(t.counts, t.chunks, t.weight);
+        n += 2;
+    } else {
+        if (window == GBT_WINDOW_LINE)
+            tile_weight_kernel<GBT_WINDOW_LINE><<<kWeightSamples / 256, 256, 0, s>>>(
+                q.rec, q.n_seg_ptr, t.ball, T, q.pre_alpha, q.pre_beta, t.weight);
+        else
+            tile_weight_kernel<GBT_WINDOW_SEGMENT><<<kWeightSamples / 256, 256, 0, s>>>(
+                q.rec, q.n_seg_ptr, t.ball, T, q.pre_alpha, q.pre_beta, t.weight);
+        ++n;
+    }
+    if (t.order) {
+        tile_rank_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(t.weight, T, t.perm);
+        ++n;
+        q.tile_perm = t.perm;
+    }
+    if (t.lists) {
+        list_layout_kernel<<<1, 1024, 0, s>>>(t.weight, t.order ? t.perm : nullptr, T, t.cap,
+                                              t.list_off, t.list_n);
+        if (window == GBT_WINDOW_LINE)
+            list_write_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                t.list_off, t.list_n, t.list);
+        else
+            list_write_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                t.list_off, t.list_n, t.list);
+        n += 2;
+        q.list = t.list;
+        q.list_off = t.list_off;
+        q.list_n = t.list_n;
+    }
     GBT_CUDA(cudaGetLastError());
-    note_launches(3);
-    return perm;
+    note_launches(n);
 }
 
 static size_t records_bytes(const TraceDev &td)
@@ -1605,7 +1882,7 @@ size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits
     const size_t part = (size_t)splits * a.n_freq * (size_t)a.n_recv;
     b += align_up(part * (a.precision == GBT_PRECISION_F64 ? sizeof(double2) : sizeof(float4)),
                   256);
-    if (a.precision != GBT_PRECISION_F64) b += tile_order_bytes(a.n_recv);
+    if (a.precision != GBT_PRECISION_F64) b += tile_ws_bytes(a.n_recv, td.capacity, a.tile_cull != 0);
     return b;
 }
 
@@ -1674,7 +1951,7 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
             q.stats = stats;
             q.n_items = cta_tiles(a.n_recv) * splits;
             q.work_counter = counter;
-            q.tile_perm = tile_order_launch(q, a.window, order_ws, s);
+            tile_prep_launch(q, a.window, tile_ws_layout(order_ws, a.n_recv, td.capacity, a.tile_cull != 0), s);
             if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
             else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
             if (stats) return;
@@ -1741,7 +2018,7 @@ static size_t bwd_layout(const TraceDev &td, const gbt_sum_args &a, const SceneD
     off[3] = b; b += align_up((size_t)td.capacity * sizeof(float), 256);
     off[4] = b; b += align_up((size_t)a.n_freq * td.capacity * sizeof(float), 256);
     off[5] = b; b += align_up((size_t)((sd ? sd->n_materials : 1024) + GBT_MAX_FREQ) * sizeof(double), 256);
-    off[6] = b; b += tile_order_bytes(a.n_recv);
+    off[6] = b; b += tile_ws_bytes(a.n_recv, td.capacity, a.tile_cull != 0);
     return b;
 }
 
@@ -1797,7 +2074,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
         q.seg_G = seg_G;
         q.seg_H = seg_H;
         q.seg_stride = td.capacity;
-        q.tile_perm = tile_order_launch(q, a.window, w + off[6], s);
+        tile_prep_launch(q, a.window, tile_ws_layout(w + off[6], a.n_recv, td.capacity, a.tile_cull != 0), s);
         if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
         else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
     }
@@ -1940,7 +2217,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         b += align_up((size_t)B.splits[i] * B.args[i].n_freq * (size_t)B.args[i].n_recv *
                           sizeof(float4), 256);
         B.ord_off[i] = b;
-        b += tile_order_bytes(B.args[i].n_recv);
+        b += tile_ws_bytes(B.args[i].n_recv, B.traces[i]->d.capacity, B.args[i].tile_cull != 0);
     }
     const size_t cnt = align_up((size_t)n * sizeof(int), 256);    // one work counter per instance
     const size_t tab = align_up((size_t)n * sizeof(FwdParams), 256);
@@ -1968,7 +2245,13 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         q.n_items = ((a.n_recv + kCtaRecv - 1) / kCtaRecv) * q.splits;
         q.partial = reinterpret_cast<float4 *>(w + B.part_off[i]);
         q.work_counter = B.mode == kConcurrent ? B.counter + k : B.counter;
-        q.tile_perm = tile_order_perm(w + B.ord_off[i], a.n_recv);
+        {
+            const TileWs t = tile_ws_layout(w + B.ord_off[i], a.n_recv, td.capacity, a.tile_cull != 0);
+            q.tile_perm = t.order ? t.perm : nullptr;
+            q.list = t.lists ? t.list : nullptr;
+            q.list_off = t.lists ? t.list_off : nullptr;
+            q.list_n = t.lists ? t.list_n : nullptr;
+        }
         B.table.push_back(q);
         B.inst_off.push_back(B.inst_off.back() + q.n_items);
     }
@@ -2045,7 +2328,12 @@ static void batch_record_concurrent(BatchImpl &B, cudaStream_t s)
         batch_prepass(B, i, bs);
         if (B.args[i].n_recv == 0) continue;
         const FwdParams &q = B.table[k];
-        if (q.tile_perm) tile_order_launch(q, B.window, w + B.ord_off[i], bs);
+        {
+            FwdParams qq = q;
+            tile_prep_launch(qq, B.window,
+                             tile_ws_layout(w + B.ord_off[i], B.args[i].n_recv,
+                                            B.traces[i]->d.capacity, B.args[i].tile_cull != 0), bs);
+        }
         if (B.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, bs, false);
         else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, bs, false);
         batch_reduce(B, k, bs);
@@ -2067,7 +2355,10 @@ static void batch_record(BatchImpl &B, cudaStream_t s)
     for (int i = 0; i < n; ++i) batch_prepass(B, i, s);
     for (int k = 0; k < n; ++k) {
         const int i = B.order[k];
-        if (B.table[k].tile_perm) tile_order_launch(B.table[k], B.window, w + B.ord_off[i], s);
+        FwdParams qq = B.table[k];
+        tile_prep_launch(qq, B.window,
+                         tile_ws_layout(w + B.ord_off[i], B.args[i].n_recv, B.traces[i]->d.capacity,
+                                        B.args[i].tile_cull != 0), s);
     }
     FwdParams prm = B.table[0];
     prm.inst = B.d_table;

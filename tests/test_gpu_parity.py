@@ -181,8 +181,14 @@ def test_many_tiles_every_receiver_against_oracle(G):
                   order=order, window=w.window, cutoff=w.cutoff)
     # prepass, tile order (ball, weight, rank), pair kernel, merge
     assert G.gbt_launches_read(reset=True) == 6
+    pc = G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[0]), _dev(w.scene.gamma, torch.float32),
+                   order=order, window=w.window, cutoff=w.cutoff, tile_cull=True)
+    # prepass, ball, list counts, count scan, rank, list layout, list write, pair kernel, merge
+    assert G.gbt_launches_read(reset=True) == 9
     torch.cuda.synchronize()
     G.gbt_sync()
+    # per-tile lists: the same terms, regrouped into other batches and splits
+    assert rel_l2(pc.cpu().numpy().astype(np.complex128), p.cpu().numpy().astype(np.complex128)) < 1e-6
     p = p.cpu().numpy().astype(np.complex128)
     otr = O.trace(w.scene, w.sources[0])
     po = O.gbs_sum(otr, recv, w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma, window=w.window)
@@ -270,8 +276,10 @@ def test_invalid_arguments_are_rejected_before_launch(G):
 
 @pytest.mark.parametrize("which", ["open_plane_large", "city"])
 def test_tile_cull_is_exact(G, which):
-    """The per-warp segment test is conservative: the same pairs survive and are summed in
-    the same order, so the field is bit-identical to testing every pair."""
+    """The pre-cull (per-tile segment lists, then the per-warp ball test) is conservative:
+    exactly the same pairs pass the prefilter and the same (pair, frequency) triples are
+    kept, so the field equals testing every pair up to the FP32 rounding of the
+    regrouped partial sums (the lists batch a tile's segments differently)."""
     import torch
     w = I.open_plane_large() if which == "open_plane_large" else I.city(n_rays=32768, n_recv_side=96)
     sc = G.Scene(w.scene)
@@ -282,7 +290,7 @@ def test_tile_cull_is_exact(G, which):
     args = (tr, r, list(w.freqs), list(w.beam_b[0]), gam)
     dense = G.gbs_sum(*args, order=o, window=w.window).cpu().numpy()
     cull = G.gbs_sum(*args, order=o, window=w.window, tile_cull=True).cpu().numpy()
-    assert np.array_equal(dense, cull)
+    assert rel_l2(cull.astype(np.complex128), dense.astype(np.complex128)) < 1e-6
     st_d = G.sum_stats(*args, order=o, window=w.window)
     st_c = G.sum_stats(*args, order=o, window=w.window, tile_cull=True)
     assert st_d["pairs_tested"] == st_d["pairs"]
