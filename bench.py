@@ -39,7 +39,7 @@ UNIT = "evals/s"
 OPS_PER_PAIR = 15
 OPS_PER_KEPT = 24
 LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
-KERNEL_TAG = "gbs_fwd_kernel<6,LINE,fwd,plain> CTA-staged ring, paired survivors"
+KERNEL_TAG = "gbs_fwd_kernel<6,LINE,fwd,plain> warp-autonomous, paired survivors"
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of this
 # exact kernel version (profiles/gbs_fwd_open_plane_64k_rays_256x256_6f.md); a changed
 # kernel gets a new tag and no entry until it is captured again.

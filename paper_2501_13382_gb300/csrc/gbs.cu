@@ -42,13 +42,13 @@
 namespace gbt {
 namespace {
 
-constexpr int kConsumerWarps = 15;          // compute warps per CTA (one CTA per SM)
-constexpr int kThreads = 32 * (kConsumerWarps + 1);   // + one producer warp
-constexpr int kStages = 8;                  // ring of raw record batches (bulk-copy targets)
-constexpr int kStaged = 8;                  // ring of staged batches shared by the consumer warps
+constexpr int kWarpsFwd = 16;               // warps per CTA of the pair kernel (one CTA per SM)
+constexpr int kWarpsBwd = 12;               // adjoint: fewer warps, room for per-segment sums
+constexpr int kWRaw = 2;                    // raw record buffers per warp (double buffering)
 constexpr int kR = 2;                       // receivers per lane
-constexpr int kWarpRecv = 32 * kR;          // receivers per warp
-constexpr int kCtaRecv = kConsumerWarps * kWarpRecv;
+constexpr int kWarpRecv = 32 * kR;          // receivers per warp tile
+constexpr int kTileWarps = 15;              // warp tiles per CTA tile (dispatch order, lists)
+constexpr int kCtaRecv = kTileWarps * kWarpRecv;
 constexpr int kBatch = 32;                  // segments per staged batch
 constexpr long long kSpinLimit = 1LL << 22; // bounded mbarrier waits
 enum { kFwd = 0, kStats = 1, kBwd = 2 };    // what the pair kernel does with survivors
@@ -210,11 +210,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n"); }
-// waits until at most kStages - 1 of this thread's commit groups are pending
-__device__ __forceinline__ void cp_async_wait_stages()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 1) : "memory");
-}
+
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -263,8 +259,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return false;
 }
 
-// One staged batch, shared by every consumer warp of the CTA: the prefilter (hot)
-// view relative to the CTA tile's first receiver and the exact-path (cold) view.
+// One staged batch of a warp: the prefilter (hot) view relative to the warp
+// tile's first receiver and the exact-path (cold) view.
 enum { C_OXH = 0, C_OYH, C_OZH, C_OXL, C_OYL, C_OZL, C_TXL, C_TYL, C_TZL, C_S0H, C_S0L,
        C_LH, C_LL, C_AMP, C_COUNT };
 struct StageSmem {
@@ -650,90 +646,91 @@ struct AdjSmem {
     float segG[32];            // per segment of the current batch
     float segH[NF][32];
 };
-template <int NF>
-struct CtaSmem {
-    float4 raw[kStages][kBatch][kRecFloats / 4];   // bulk-copy ring of raw record batches
-    StageSmem stg[kStaged];                         // staged batches for all consumer warps
-    union {
-        float4 acc[kConsumerWarps][NF][kR][32];     // forward: float-float sums (hi, hi, lo, lo)
-        AdjSmem<NF> adj[kConsumerWarps];            // adjoint
-    };
-    unsigned long long full[kStages];                // raw batch landed
-    unsigned long long ready[kStaged], freed[kStaged];   // staged batch written / consumed
-    FwdParams inst;            // batched launch: the current item's instance
-    int64_t item;
-    int inst_idx, abort_flag;
+// Per-warp shared memory of the pair kernel: two raw record buffers (bulk-copy
+// or cp.async targets), the staged batch, and the completion barriers of the
+// bulk copies.
+struct WarpBuf {
+    float4 raw[kWRaw][kBatch][kRecFloats / 4];
+    StageSmem stg;
+    unsigned long long bar[kWRaw];
+    int abort_flag, pad[3];
 };
 
-// One CTA per SM.  A producer warp streams record batches of the current item
-// (receiver tile of 960, segment split) into a ring of raw stages with bulk
-// asynchronous copies and stages each batch once for the whole CTA (relative to
-// the tile's first receiver) into a second ring; 15 consumer warps run the
-// prefilter and the exact path of every staged batch for their 64 receivers.
-// Warps wait for each other only through the staged ring (8 batches of slack)
-// and once per item.
+template <int NF, int MODE, bool BATCHED>
+struct PairCfg {
+    static constexpr int kWarps = MODE == kBwd ? kWarpsBwd : kWarpsFwd;
+    static constexpr size_t kAdj = MODE == kBwd ? sizeof(AdjSmem<NF>) : 0;
+    static constexpr size_t kInst = BATCHED ? sizeof(FwdParams) : 0;
+    static constexpr size_t kPerWarp = (sizeof(WarpBuf) + kAdj + kInst + 127) / 128 * 128;
+    static constexpr size_t kSmem = kWarps * kPerWarp;
+};
+
+// Persistent pair kernel.  Every warp works on its own: it takes (warp tile of
+// 64 receivers, segment split) items from a global queue (CTA tiles of 960
+// heaviest first), streams the item's record batches into its own double buffer
+// (one bulk copy per batch for consecutive segments, one 16-byte cp.async per
+// lane and word for a tile's list), stages each batch relative to its first
+// receiver, and runs the prefilter and the exact path for its receivers.  No
+// warp ever waits for another, so warps whose receivers meet more surviving
+// pairs cost only themselves.  The FP32 sums fold into the item's float-float
+// partials (global, resident in L2) every kFoldEvery batches.
 template <int NF, int WINDOW, int MODE, bool BATCHED>
 __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParams prm)
 {
+    using Cfg = PairCfg<NF, MODE, BATCHED>;
     constexpr bool STATS = MODE == kStats;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    CtaSmem<NF> &S = *reinterpret_cast<CtaSmem<NF> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool producer = warp == kConsumerWarps;
+    unsigned char *const mine = smem_raw + (size_t)warp * Cfg::kPerWarp;
+    WarpBuf &B = *reinterpret_cast<WarpBuf *>(mine);
+    AdjSmem<NF> &adj = *reinterpret_cast<AdjSmem<NF> *>(mine + sizeof(WarpBuf));
+    FwdParams &inst = *reinterpret_cast<FwdParams *>(mine + sizeof(WarpBuf) + Cfg::kAdj);
 
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(smem_addr(&S.full[st]), 1);
-        for (int st = 0; st < kStaged; ++st) {
-            mbar_init(smem_addr(&S.ready[st]), 32);
-            mbar_init(smem_addr(&S.freed[st]), kConsumerWarps);
-        }
-        S.abort_flag = 0;
+    if (lane == 0) {
+        for (int i = 0; i < kWRaw; ++i) mbar_init(smem_addr(&B.bar[i]), 1);
+        B.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    __syncthreads();
-
-    volatile int *abort_flag = &S.abort_flag;
+    __syncwarp();
+    volatile int *abort_flag = &B.abort_flag;
     uint32_t n_pre = 0, n_kept = 0;
     unsigned long long n_test = 0;
-    uint32_t g = 0;       // batches through the staged ring so far (same count in every role)
-    uint32_t gfull = 0;   // producer: batches through the raw ring by bulk copy
+    uint32_t ph = 0;   // bit i: parity of the next completion of bar[i]
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            int64_t it = atomicAdd(prm.work_counter, 1);
-            int inst = 0;
-            if (BATCHED && it < prm.n_items) {
+        int64_t it = 0;
+        if (lane == 0) it = atomicAdd(prm.work_counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (BATCHED) {
+            if (it < prm.n_items) {
                 int lo = 0, hi = prm.n_inst - 1;      // last instance with inst_off <= it
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (prm.inst_off[mid] <= it) lo = mid;
                     else hi = mid - 1;
                 }
-                inst = lo;
                 it -= prm.inst_off[lo];
-            } else if (BATCHED) {
-                it = prm.n_items;
+                const int4 *src = reinterpret_cast<const int4 *>(prm.inst + lo);
+                int4 *dst = reinterpret_cast<int4 *>(&inst);
+                for (int q = lane; q < (int)(sizeof(FwdParams) / 16); q += 32) dst[q] = src[q];
+                __syncwarp();
+            } else {
+                break;
             }
-            S.item = it;
-            S.inst_idx = inst;
         }
-        __syncthreads();
-        if (BATCHED && S.item < prm.n_items) {
-            // the item's instance parameters into shared memory
-            const int4 *src = reinterpret_cast<const int4 *>(prm.inst + S.inst_idx);
-            int4 *dst = reinterpret_cast<int4 *>(&S.inst);
-            for (int q = threadIdx.x; q < (int)(sizeof(FwdParams) / 16); q += blockDim.x)
-                dst[q] = src[q];
-            __syncthreads();
-        }
-        const FwdParams &p = *(BATCHED ? &S.inst : &prm);
-        const int64_t item = S.item;
-        if (item >= (BATCHED ? prm.n_items : p.n_items) || *abort_flag) break;
-        const float alpha = p.pre_alpha, beta = p.pre_beta;
-        const int64_t tile_rank = item / p.splits;
+        const FwdParams &p = BATCHED ? inst : prm;
+        if ((!BATCHED && it >= p.n_items) || *abort_flag) break;
+
+        // item -> (CTA tile by dispatch rank, split, warp tile within the CTA tile)
+        const int64_t per_tile = (int64_t)kTileWarps * p.splits;
+        const int64_t tile_rank = it / per_tile;
+        const int64_t rem = it - tile_rank * per_tile;
+        const int split = (int)(rem / kTileWarps);
+        const int wl = (int)(rem - (int64_t)split * kTileWarps);
         const int64_t tile = p.tile_perm ? (int64_t)p.tile_perm[tile_rank] : tile_rank;
-        const int64_t tile_base = tile * kCtaRecv;
-        // the segments this item streams: the tile's list, or every segment
+        const int64_t wbase = tile * kCtaRecv + (int64_t)wl * kWarpRecv;
+        if (wbase >= p.n_recv) continue;
+        // the segments this item streams: the CTA tile's list, or every segment
         const int32_t *lst = nullptr;
         int64_t n_seg = *p.n_seg_ptr;
         if (p.list) {
@@ -744,317 +741,286 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             }
         }
         const int64_t n_batches = (n_seg + kBatch - 1) / kBatch;
-        const int split = (int)(item % p.splits);
         const uint32_t nb = split < n_batches ? (uint32_t)((n_batches - 1 - split) / p.splits + 1) : 0u;
-        // frame of the staged batches: the tile's first receiver
-        const int64_t c_idx = p.order ? p.order[tile_base] : tile_base;
+        const float alpha = p.pre_alpha, beta = p.pre_beta;
+        // frame of the staged batches: the warp tile's first receiver
+        const int64_t c_idx = p.order ? p.order[wbase] : wbase;
         const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
 
-        if (producer) {
-            // bulk copies run kStages batches ahead (one copy of consecutive records, or one
-            // 80-byte copy per lane from the tile's list); every lane stages one record
-            // Contiguous segments: one bulk copy per batch, completed on the `full`
-            // mbarrier of its raw stage (uses counted by gfull).  A tile's list: every
-            // lane gathers its own record with 16-byte async copies, one commit group per
-            // batch and always kStages groups in flight (empty ones past the end), and
-            // later stages only that record, so no lane waits on another's copies.
-            auto list_idx = [&](uint32_t k) -> int32_t {   // loaded one issue ahead
-                const int64_t e = (split + (int64_t)k * p.splits) * kBatch + lane;
-                return (k < nb && e < n_seg) ? lst[e] : -1;
-            };
-            int32_t next_idx = lst ? list_idx(0) : -1;
-            auto issue = [&](uint32_t k) {   // all lanes, k in increasing order
-                if (lst) {
-                    const int32_t idx = next_idx;
-                    next_idx = list_idx(k + 1);
-                    if (idx >= 0) {
-                        const float4 *src = reinterpret_cast<const float4 *>(
-                            p.rec + (int64_t)idx * kRecFloats);
-                        float4 *dst = S.raw[k % kStages][lane];
+        float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
+        int32_t ridx[kR];
+        uint32_t valid = 0;
+        float4 *const part_base = p.partial + (int64_t)split * p.nf * p.n_recv;
 #pragma unroll
-                        for (int c = 0; c < kRecFloats / 4; ++c) cp_async16(dst + c, src + c, 16);
-                    }
-                    cp_async_commit();
-                } else if (lane == 0) {
-                    const uint32_t q = gfull + k, rs = q % kStages;
-                    const int64_t b = split + (int64_t)k * p.splits;
-                    const uint32_t bytes = (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * kRecFloats * 4;
-                    mbar_arrive_expect_tx(smem_addr(&S.full[rs]), bytes);
-                    bulk_g2s(smem_addr(&S.raw[rs][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
-                             smem_addr(&S.full[rs]));
-                }
-            };
-            const uint32_t ahead = lst ? (uint32_t)kStages : min(nb, (uint32_t)kStages);
-            uint32_t issued = 0, landed = 0;
-            for (; issued < ahead; ++issued) issue(issued);
-            for (uint32_t k = 0; k < nb; ++k) {
-                const uint32_t q = g + k, qs = q % kStaged;
-                const uint32_t rs = lst ? k % kStages : (gfull + k) % kStages;
-                bool ok = true;
-                if (lst) {
-                    cp_async_wait_stages();                 // this lane's copies of batch k
-                } else {
-                    ok = mbar_wait(smem_addr(&S.full[rs]), ((gfull + k) / kStages) & 1u, abort_flag,
-                                   p.status);
-                    ok = __all_sync(0xffffffffu, ok);
-                    if (!ok) break;
-                    landed = k + 1;
-                }
-                ok = mbar_wait(smem_addr(&S.freed[qs]), ((q / kStaged) & 1u) ^ 1u, abort_flag,
-                               p.status);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-                const int64_t b = split + (int64_t)k * p.splits;
-                const int64_t e = b * kBatch + lane;
-                const bool valid = e < n_seg;
-                stage_batch(S.stg[qs], S.raw[rs][lane], lane, valid,
-                            valid ? (lst ? lst[e] : (int32_t)e) : -1, cx, cy, cz, alpha, beta);
-                mbar_arrive(smem_addr(&S.ready[qs]));
-                __syncwarp();
-                if (lst || issued < nb) issue(issued++);
+        for (int k = 0; k < kR; ++k) {
+            // lane holds receivers lane and lane + 32 of the warp tile: the two halves
+            // of its Morton patch, so a beam edge splits work evenly over lanes
+            const int64_t r = wbase + (int64_t)k * 32 + lane;
+            xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
+            ridx[k] = -1;
+            if (r < p.n_recv) {
+                const int64_t o = p.order ? p.order[r] : r;
+                xa[k] = p.recv[3 * o]; ya[k] = p.recv[3 * o + 1]; za[k] = p.recv[3 * o + 2];
+                xp[k] = xa[k] - cx; yp[k] = ya[k] - cy; zp[k] = za[k] - cz;
+                xx[k] = fmaf(xp[k], xp[k], fmaf(yp[k], yp[k], zp[k] * zp[k]));
+                valid |= 1u << k;
+                ridx[k] = (int32_t)o;
             }
-            if (lst) {
-                cp_async_wait0();   // every gather of this item has landed
-            } else if (lane == 0 && *abort_flag) {
-                // let every bulk copy still in flight land before leaving
-                for (uint32_t k = landed; k < issued; ++k) {
-                    const uint32_t q = gfull + k;
-                    for (long long it = 0; it < kSpinLimit; ++it)
-                        if (mbar_try_wait(smem_addr(&S.full[q % kStages]), (q / kStages) & 1u)) break;
-                }
+            if (MODE == kBwd) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    adj.g[f][k][lane] = (f < p.nf && ridx[k] >= 0)
+                                            ? p.grad_out[(int64_t)p.fperm[f] * p.n_recv + ridx[k]]
+                                            : make_float2(0.f, 0.f);
+            } else if (MODE == kFwd) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    if (f < p.nf && ridx[k] >= 0)
+                        part_base[(int64_t)f * p.n_recv + ridx[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-        } else {
-            const int64_t wbase = tile_base + (int64_t)warp * kWarpRecv;
-            const bool warp_live = wbase < p.n_recv;
+        }
+        if (MODE == kBwd) {
+            adj.segG[lane] = 0.f;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) adj.segH[f][lane] = 0.f;
+        }
+        // bounding ball of the warp tile's receivers (relative to its first receiver)
+        float4 sphere = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p.tile_cull) {
+            float sx = 0.f, sy = 0.f, sz = 0.f, nv = 0.f;
+#pragma unroll
+            for (int k = 0; k < kR; ++k)
+                if ((valid >> k) & 1u) { sx += xp[k]; sy += yp[k]; sz += zp[k]; nv += 1.f; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                sz += __shfl_xor_sync(0xffffffffu, sz, o);
+                nv += __shfl_xor_sync(0xffffffffu, nv, o);
+            }
+            if (nv > 0.f) { sx /= nv; sy /= nv; sz /= nv; }
+            float r2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < kR; ++k)
+                if ((valid >> k) & 1u) {
+                    const float ex = xp[k] - sx, ey = yp[k] - sy, ez = zp[k] - sz;
+                    r2 = fmaxf(r2, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+            sphere = make_float4(sx, sy, sz, sqrtf(r2));
+        }
+        static_assert(kR == 2, "the paired prefilter handles two receivers per lane");
+        const f2x X2 = pk(xp[0], xp[1]), Y2 = pk(yp[0], yp[1]), Z2 = pk(zp[0], zp[1]);
+        const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
+        const f2x AL2 = pk(alpha, alpha);
+        const f2x MG2 = pk(kWinMargin, kWinMargin);
+        // per-batch FP32 sums of the lane's two receivers, paired (re, im)
+        f2x accx[NF], accy[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) accx[f] = accy[f] = 0ull;
+        const f2x XA = pk(xa[0], xa[1]), YA = pk(ya[0], ya[1]), ZA = pk(za[0], za[1]);
+        auto fold_all = [&]() {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (f < p.nf) {
+                    float x0, x1, y0, y1;
+                    upk(accx[f], x0, x1);
+                    upk(accy[f], y0, y1);
+                    float2 t0 = make_float2(x0, y0), t1 = make_float2(x1, y1);
+                    if (ridx[0] >= 0) fold(part_base + (int64_t)f * p.n_recv + ridx[0], t0);
+                    if (ridx[1] >= 0) fold(part_base + (int64_t)f * p.n_recv + ridx[1], t1);
+                }
+                accx[f] = accy[f] = 0ull;
+            }
+        };
 
-            float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
-            int32_t ridx[kR];
-            uint32_t valid = 0;
-            float4 *const part_base = p.partial + (int64_t)split * p.nf * p.n_recv;
+        // Record batch k of the item into raw buffer k % 2: one bulk copy (lane 0)
+        // for consecutive segments, else every lane gathers its own record with
+        // 16-byte async copies, one commit group per batch (empty past the end).
+        auto list_idx = [&](uint32_t k) -> int32_t {
+            const int64_t e = (split + (int64_t)k * p.splits) * kBatch + lane;
+            return (k < nb && e < n_seg) ? lst[e] : -1;
+        };
+        int32_t next_idx = lst ? list_idx(0) : -1;
+        auto issue = [&](uint32_t k) {
+            const int buf = (int)(k & 1u);
+            if (lst) {
+                const int32_t idx = next_idx;
+                next_idx = list_idx(k + 1);
+                if (idx >= 0) {
+                    const float4 *src =
+                        reinterpret_cast<const float4 *>(p.rec + (int64_t)idx * kRecFloats);
 #pragma unroll
-            for (int k = 0; k < kR; ++k) {
-                // lane holds receivers lane and lane + 32 of the warp: the two halves of
-                // the warp's Morton patch, so a beam edge splits work evenly over lanes
-                const int64_t r = wbase + (int64_t)k * 32 + lane;
-                xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
-                ridx[k] = -1;
-                if (r < p.n_recv) {
-                    const int64_t o = p.order ? p.order[r] : r;
-                    xa[k] = p.recv[3 * o]; ya[k] = p.recv[3 * o + 1]; za[k] = p.recv[3 * o + 2];
-                    xp[k] = xa[k] - cx; yp[k] = ya[k] - cy; zp[k] = za[k] - cz;
-                    xx[k] = fmaf(xp[k], xp[k], fmaf(yp[k], yp[k], zp[k] * zp[k]));
-                    valid |= 1u << k;
-                    ridx[k] = (int32_t)o;
+                    for (int c = 0; c < kRecFloats / 4; ++c) cp_async16(&B.raw[buf][lane][c], src + c, 16);
                 }
-                if (MODE == kBwd) {
+                cp_async_commit();
+            } else if (k < nb && lane == 0) {
+                const int64_t b = split + (int64_t)k * p.splits;
+                const uint32_t bytes =
+                    (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * kRecFloats * 4;
+                mbar_arrive_expect_tx(smem_addr(&B.bar[buf]), bytes);
+                bulk_g2s(smem_addr(&B.raw[buf][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
+                         smem_addr(&B.bar[buf]));
+            }
+        };
+        issue(0);
+        issue(1);
+        uint32_t waited = 0;   // bulk batches whose copy has landed
+        bool dirty = false;    // survivors since the last fold
+        for (uint32_t kb_ = 0; kb_ < nb; ++kb_) {
+            const int buf = (int)(kb_ & 1u);
+            if (lst) {
+                cp_async_wait1();   // this lane's copies of batch kb_
+            } else {
+                bool ok = mbar_wait(smem_addr(&B.bar[buf]), (ph >> buf) & 1u, abort_flag, p.status);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                ph ^= 1u << buf;
+                waited = kb_ + 1;
+            }
+            const int64_t b = split + (int64_t)kb_ * p.splits;
+            const int64_t e = b * kBatch + lane;
+            const bool seg_ok = e < n_seg;
+            StageSmem &w = B.stg;
+            stage_batch(w, B.raw[buf][lane], lane, seg_ok, seg_ok ? (lst ? lst[e] : (int32_t)e) : -1,
+                        cx, cy, cz, alpha, beta);
+            uint32_t tmask = 0u;
+            if (p.tile_cull) {
+                // this lane's segment against the warp tile's ball (own lane's staging only)
+                const float4 O = w.O[lane], A = w.A[lane];
+                const bool pass = seg_ok &&
+                                  ball_may_keep<WINDOW>(O, make_float4(A.x, A.y, A.z, w.cold[C_LH][lane]),
+                                                        O.x, O.y, O.z, sphere, alpha, beta);
+                tmask = __ballot_sync(0xffffffffu, pass);
+            }
+            __syncwarp();        // the batch is staged and raw[buf] is free again
+            issue(kb_ + 2);
+
+            // ---- prefilter: one keep bit per (receiver, segment); segment jj at bit 31 - jj.
+            // Both receivers of the lane go through paired FP32 instructions:
+            //   s_loc = x'.t - o'.t,  sm = s_loc + s0 + margin,
+            //   g = sm^2 + beta - alpha |x' - o'|^2 + alpha s_loc^2  (= q - alpha n^2),
+            // keep iff g >= 0 and the window test holds.
+            uint32_t m[kR];
 #pragma unroll
-                    for (int f = 0; f < NF; ++f)
-                        S.adj[warp].g[f][k][lane] =
-                            (f < p.nf && ridx[k] >= 0)
-                                ? p.grad_out[(int64_t)p.fperm[f] * p.n_recv + ridx[k]]
-                                : make_float2(0.f, 0.f);
+            for (int k = 0; k < kR; ++k) m[k] = 0u;
+            auto pair_bits = [&](int jj, uint32_t &kb0, uint32_t &kb1) {
+                const float4 *P = w.P[jj];
+                const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3], p4 = P[4];
+                const f2x TX = pk(p0.x, p0.y), TY = pk(p0.z, p0.w), TZ = pk(p1.x, p1.y);
+                const f2x OT = pk(p1.z, p1.w);
+                const f2x OX = pk(p2.x, p2.y), OY = pk(p2.z, p2.w), OZ = pk(p3.x, p3.y);
+                const f2x C7 = pk(p3.z, p3.w), S0 = pk(p4.x, p4.y);
+                const f2x sl = fma2(X2, TX, fma2(Y2, TY, fma2(Z2, TZ, OT)));
+                const f2x sm2 = add2(sl, S0);
+                const f2x nd = fma2(X2, OX, fma2(Y2, OY, fma2(Z2, OZ, add2(NAXX, C7))));
+                const f2x gg = fma2(mul2(sl, AL2), sl, fma2(sm2, sm2, nd));
+                float g0, g1, s0_, s1_;
+                upk(gg, g0, g1);
+                if (WINDOW == GBT_WINDOW_LINE) {
+                    upk(sm2, s0_, s1_);
+                    kb0 = ~(__float_as_uint(g0) | __float_as_uint(s0_));
+                    kb1 = ~(__float_as_uint(g1) | __float_as_uint(s1_));
                 } else {
+                    const f2x a = add2(sl, MG2);
+                    const f2x bb = sub2(sl, pk(p4.z, p4.w));
+                    float a0, a1, b0_, b1_;
+                    upk(a, a0, a1);
+                    upk(bb, b0_, b1_);
+                    kb0 = ~(__float_as_uint(g0) | __float_as_uint(a0)) & __float_as_uint(b0_);
+                    kb1 = ~(__float_as_uint(g1) | __float_as_uint(a1)) & __float_as_uint(b1_);
+                }
+            };
+            if (p.tile_cull) {
+                // only the segments that can reach this warp tile's receivers
+                uint32_t T = tmask;
+                if (STATS) n_test += __popc(T) * __popc(valid);
+                while (T) {
+                    const int jj = __ffs(T) - 1;
+                    T &= T - 1;
+                    uint32_t kb0, kb1;
+                    pair_bits(jj, kb0, kb1);
+                    m[0] |= (kb0 >> 31) << (31 - jj);
+                    m[1] |= (kb1 >> 31) << (31 - jj);
+                }
+            } else {
+                if (STATS) n_test += (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * __popc(valid);
+#pragma unroll 4
+                for (int jj = 0; jj < kBatch; ++jj) {
+                    uint32_t kb0, kb1;
+                    pair_bits(jj, kb0, kb1);
+                    m[0] = __funnelshift_l(kb0, m[0], 1);
+                    m[1] = __funnelshift_l(kb1, m[1], 1);
+                }
+            }
+            // ---- survivors, in segment order per receiver
+            if (MODE == kFwd) {
+                // the two receivers' survivors side by side, each in segment order
+                uint32_t mm0 = (valid & 1u) ? m[0] : 0u, mm1 = (valid & 2u) ? m[1] : 0u;
+                while (mm0 | mm1) {
+                    const bool h0 = mm0 != 0u, h1 = mm1 != 0u;
+                    int j0 = __clz(mm0), j1 = __clz(mm1);
+                    if (h0) mm0 ^= 0x80000000u >> j0;
+                    if (h1) mm1 ^= 0x80000000u >> j1;
+                    if (!h0) j0 = j1;
+                    if (!h1) j1 = j0;
+                    survivor_pair<NF, WINDOW>(p, XA, YA, ZA, w, j0, j1, h0, h1, accx, accy);
+                }
+            } else {
 #pragma unroll
-                    for (int f = 0; f < NF; ++f)
-                        S.acc[warp][f][k][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int k = 0; k < kR; ++k) {
+                    uint32_t mm = ((valid >> k) & 1u) ? m[k] : 0u;
+                    if (STATS) n_pre += __popc(mm);
+                    while (mm) {
+                        const int jj = __clz(mm);
+                        mm ^= 0x80000000u >> jj;
+                        if (MODE == kBwd)
+                            survivor_adjoint<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj,
+                                                         &adj.g[0][k][lane], adj.segG,
+                                                         &adj.segH[0][0]);
+                        else
+                            survivor_count<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj, n_kept);
+                    }
                 }
             }
             if (MODE == kBwd) {
-                S.adj[warp].segG[lane] = 0.f;
-#pragma unroll
-                for (int f = 0; f < NF; ++f) S.adj[warp].segH[f][lane] = 0.f;
-            }
-            __syncwarp();
-            // bounding ball of the warp's receivers (relative to the tile centre)
-            float4 sphere = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p.tile_cull) {
-                float sx = 0.f, sy = 0.f, sz = 0.f, nv = 0.f;
-#pragma unroll
-                for (int k = 0; k < kR; ++k)
-                    if ((valid >> k) & 1u) { sx += xp[k]; sy += yp[k]; sz += zp[k]; nv += 1.f; }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                    sz += __shfl_xor_sync(0xffffffffu, sz, o);
-                    nv += __shfl_xor_sync(0xffffffffu, nv, o);
-                }
-                if (nv > 0.f) { sx /= nv; sy /= nv; sz /= nv; }
-                float r2 = 0.f;
-#pragma unroll
-                for (int k = 0; k < kR; ++k)
-                    if ((valid >> k) & 1u) {
-                        const float ex = xp[k] - sx, ey = yp[k] - sy, ez = zp[k] - sz;
-                        r2 = fmaxf(r2, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                    }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
-                sphere = make_float4(sx, sy, sz, sqrtf(r2));
-            }
-            static_assert(kR == 2, "the paired prefilter handles two receivers per lane");
-            const f2x X2 = pk(xp[0], xp[1]), Y2 = pk(yp[0], yp[1]), Z2 = pk(zp[0], zp[1]);
-            const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
-            const f2x AL2 = pk(alpha, alpha);
-            const f2x MG2 = pk(kWinMargin, kWinMargin);
-            // per-batch FP32 sums of the lane's two receivers, paired (re, im)
-            f2x accx[NF], accy[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) accx[f] = accy[f] = 0ull;
-            const f2x XA = pk(xa[0], xa[1]), YA = pk(ya[0], ya[1]), ZA = pk(za[0], za[1]);
-
-            bool dirty = false;   // survivors since the last fold (this lane)
-            for (uint32_t kb_ = 0; kb_ < nb; ++kb_) {
-                const uint32_t q = g + kb_, qs = q % kStaged;
-                bool ok = mbar_wait(smem_addr(&S.ready[qs]), (q / kStaged) & 1u, abort_flag, p.status);
-                if (!__all_sync(0xffffffffu, ok)) break;
-                const StageSmem &w = S.stg[qs];
-                if (!warp_live) {
-                    if (lane == 0) mbar_arrive(smem_addr(&S.freed[qs]));
-                    continue;
-                }
-                const int64_t b = split + (int64_t)kb_ * p.splits;
-                uint32_t tmask = 0u;
-                if (p.tile_cull) {
-                    // segment `lane` of the batch against the warp's receiver ball
-                    const float4 O = w.O[lane], A = w.A[lane];
-                    const bool pass = b * kBatch + lane < n_seg &&
-                                      ball_may_keep<WINDOW>(O, make_float4(A.x, A.y, A.z, w.cold[C_LH][lane]),
-                                                            O.x, O.y, O.z, sphere, alpha, beta);
-                    tmask = __ballot_sync(0xffffffffu, pass);
-                }
-
-                // ---- prefilter: one keep bit per (receiver, segment); segment jj at bit 31 - jj.
-                // Both receivers of the lane go through paired FP32 instructions:
-                //   s_loc = x'.t - o'.t,  sm = s_loc + s0 + margin,
-                //   g = sm^2 + beta - alpha |x' - o'|^2 + alpha s_loc^2  (= q - alpha n^2),
-                // keep iff g >= 0 and the window test holds.
-                uint32_t m[kR];
-#pragma unroll
-                for (int k = 0; k < kR; ++k) m[k] = 0u;
-                // keep bits of segment jj for both receivers (sign bit = keep)
-                auto pair_bits = [&](int jj, uint32_t &kb0, uint32_t &kb1) {
-                    const float4 *P = w.P[jj];
-                    const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3], p4 = P[4];
-                    const f2x TX = pk(p0.x, p0.y), TY = pk(p0.z, p0.w), TZ = pk(p1.x, p1.y);
-                    const f2x OT = pk(p1.z, p1.w);
-                    const f2x OX = pk(p2.x, p2.y), OY = pk(p2.z, p2.w), OZ = pk(p3.x, p3.y);
-                    const f2x C7 = pk(p3.z, p3.w), S0 = pk(p4.x, p4.y);
-                    const f2x sl = fma2(X2, TX, fma2(Y2, TY, fma2(Z2, TZ, OT)));
-                    const f2x sm2 = add2(sl, S0);
-                    const f2x nd = fma2(X2, OX, fma2(Y2, OY, fma2(Z2, OZ, add2(NAXX, C7))));
-                    const f2x gg = fma2(mul2(sl, AL2), sl, fma2(sm2, sm2, nd));
-                    float g0, g1, s0_, s1_;
-                    upk(gg, g0, g1);
-                    if (WINDOW == GBT_WINDOW_LINE) {
-                        upk(sm2, s0_, s1_);
-                        kb0 = ~(__float_as_uint(g0) | __float_as_uint(s0_));
-                        kb1 = ~(__float_as_uint(g1) | __float_as_uint(s1_));
-                    } else {
-                        const f2x a = add2(sl, MG2);
-                        const f2x bb = sub2(sl, pk(p4.z, p4.w));
-                        float a0, a1, b0_, b1_;
-                        upk(a, a0, a1);
-                        upk(bb, b0_, b1_);
-                        kb0 = ~(__float_as_uint(g0) | __float_as_uint(a0)) & __float_as_uint(b0_);
-                        kb1 = ~(__float_as_uint(g1) | __float_as_uint(a1)) & __float_as_uint(b1_);
-                    }
-                };
-                if (p.tile_cull) {
-                    // only the segments that can reach this warp's receivers
-                    uint32_t T = tmask;
-                    if (STATS) n_test += __popc(T) * __popc(valid);
-                    while (T) {
-                        const int jj = __ffs(T) - 1;
-                        T &= T - 1;
-                        uint32_t kb0, kb1;
-                        pair_bits(jj, kb0, kb1);
-                        m[0] |= (kb0 >> 31) << (31 - jj);
-                        m[1] |= (kb1 >> 31) << (31 - jj);
-                    }
-                } else {
-                    if (STATS) n_test += (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * __popc(valid);
-#pragma unroll 4
-                    for (int jj = 0; jj < kBatch; ++jj) {
-                        uint32_t kb0, kb1;
-                        pair_bits(jj, kb0, kb1);
-                        m[0] = __funnelshift_l(kb0, m[0], 1);
-                        m[1] = __funnelshift_l(kb1, m[1], 1);
-                    }
-                }
-                // ---- survivors, in segment order per receiver
-                if (MODE == kFwd) {
-                    // the two receivers' survivors side by side, each in segment order
-                    uint32_t mm0 = (valid & 1u) ? m[0] : 0u, mm1 = (valid & 2u) ? m[1] : 0u;
-                    while (mm0 | mm1) {
-                        const bool h0 = mm0 != 0u, h1 = mm1 != 0u;
-                        int j0 = __clz(mm0), j1 = __clz(mm1);
-                        if (h0) mm0 ^= 0x80000000u >> j0;
-                        if (h1) mm1 ^= 0x80000000u >> j1;
-                        if (!h0) j0 = j1;
-                        if (!h1) j1 = j0;
-                        survivor_pair<NF, WINDOW>(p, XA, YA, ZA, w, j0, j1, h0, h1, accx, accy);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kR; ++k) {
-                        uint32_t mm = ((valid >> k) & 1u) ? m[k] : 0u;
-                        if (STATS) n_pre += __popc(mm);
-                        while (mm) {
-                            const int jj = __clz(mm);
-                            mm ^= 0x80000000u >> jj;
-                            if (MODE == kBwd)
-                                survivor_adjoint<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj,
-                                                             &S.adj[warp].g[0][k][lane],
-                                                             S.adj[warp].segG,
-                                                             &S.adj[warp].segH[0][0]);
-                            else
-                                survivor_count<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj, n_kept);
-                        }
-                    }
-                }
-                if (MODE == kBwd) {
-                    // per-segment sums of this warp to global, then clear
-                    __syncwarp();
-                    const int64_t jg = w.seg[lane];
-                    const float G = S.adj[warp].segG[lane];
-                    if (G != 0.f && jg >= 0) atomicAdd(&p.seg_G[jg], G);
-                    S.adj[warp].segG[lane] = 0.f;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        const float H = S.adj[warp].segH[f][lane];
-                        if (H != 0.f && jg >= 0) atomicAdd(&p.seg_H[f * p.seg_stride + jg], H);
-                        S.adj[warp].segH[f][lane] = 0.f;
-                    }
-                }
-                if (MODE == kFwd) dirty |= (m[0] | m[1]) != 0u;
-                if (MODE == kFwd && (kb_ % kFoldEvery) == kFoldEvery - 1 && dirty) {
-                    dirty = false;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f)
-                        fold_pair(&S.acc[warp][f][0][lane], &S.acc[warp][f][1][lane], accx[f], accy[f]);
-                }
+                // per-segment sums of this warp to global, then clear
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_addr(&S.freed[qs]));
+                const int64_t jg = w.seg[lane];
+                const float G = adj.segG[lane];
+                if (G != 0.f && jg >= 0) atomicAdd(&p.seg_G[jg], G);
+                adj.segG[lane] = 0.f;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const float H = adj.segH[f][lane];
+                    if (H != 0.f && jg >= 0) atomicAdd(&p.seg_H[f * p.seg_stride + jg], H);
+                    adj.segH[f][lane] = 0.f;
+                }
             }
             if (MODE == kFwd) {
-#pragma unroll
-                for (int f = 0; f < NF; ++f)
-                    fold_pair(&S.acc[warp][f][0][lane], &S.acc[warp][f][1][lane], accx[f], accy[f]);
-#pragma unroll
-                for (int k = 0; k < kR; ++k) {
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        if (f < p.nf && ridx[k] >= 0)
-                            part_base[(int64_t)f * p.n_recv + ridx[k]] = S.acc[warp][f][k][lane];
-                    }
+                dirty |= (m[0] | m[1]) != 0u;
+                if ((kb_ % kFoldEvery) == kFoldEvery - 1 && dirty) {
+                    dirty = false;
+                    fold_all();
                 }
             }
+            __syncwarp();        // before the next batch is staged over this one
         }
-        g += nb;
-        if (!lst) gfull += nb;
-        __syncthreads();
+        if (lst) {
+            cp_async_wait0();    // every gather of this item has landed
+        } else if (*abort_flag && lane == 0) {
+            // a wait gave up: let the bulk copies still in flight land before leaving
+            const uint32_t issued = nb < 2u ? nb : min(nb, waited + 2u);
+            for (uint32_t k = waited; k < issued; ++k) {
+                const int bf = (int)(k & 1u);
+                for (long long i2 = 0; i2 < kSpinLimit; ++i2)
+                    if (mbar_try_wait(smem_addr(&B.bar[bf]), (ph >> bf) & 1u)) break;
+                ph ^= 1u << bf;
+            }
+        }
+        if (MODE == kFwd) fold_all();
     }
-    if (STATS && !producer) {
+    if (STATS) {
         atomicAdd(&prm.stats[1], (unsigned long long)n_pre);
         atomicAdd(&prm.stats[2], (unsigned long long)n_kept);
         atomicAdd(&prm.stats[3], n_test);
@@ -1649,18 +1615,21 @@ template <int NF, int WINDOW, int MODE, bool BATCHED = false>
 void launch_fwd_t(const FwdParams &p, cudaStream_t s, bool timed)
 {
     constexpr bool STATS = MODE != kFwd;
-    const size_t smem = sizeof(CtaSmem<NF>);
+    using Cfg = PairCfg<NF, MODE, BATCHED>;
+    const size_t smem = Cfg::kSmem;
+    const int threads = 32 * Cfg::kWarps;
     GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED>, kThreads, smem));
+        &per_sm, gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED>, threads, smem));
     if (per_sm < 1) fail(GBT_ERR_UNSUPPORTED, "GBS kernel does not fit on one SM");
     const int grid = (int)std::max<int64_t>(
-        1, std::min<int64_t>(p.n_items, (int64_t)std::max(per_sm, 1) * num_sms()));
+        1, std::min<int64_t>((p.n_items + Cfg::kWarps - 1) / Cfg::kWarps,
+                             (int64_t)std::max(per_sm, 1) * num_sms()));
     GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
     if (MODE != kStats && timed) timing_begin(s);
-    gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED><<<grid, kThreads, smem, s>>>(p);
+    gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED><<<grid, threads, smem, s>>>(p);
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
     if (MODE != kStats && timed) timing_end(s);
@@ -1949,7 +1918,7 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
             q.splits = splits;
             q.partial = reinterpret_cast<float4 *>(partial);
             q.stats = stats;
-            q.n_items = cta_tiles(a.n_recv) * splits;
+            q.n_items = cta_tiles(a.n_recv) * kTileWarps * splits;
             q.work_counter = counter;
             tile_prep_launch(q, a.window, tile_ws_layout(order_ws, a.n_recv, td.capacity, a.tile_cull != 0), s);
             if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
@@ -2068,7 +2037,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     if (a.n_recv > 0) {
         const int splits = choose_splits(td, a);
         q.splits = splits;
-        q.n_items = ((a.n_recv + kCtaRecv - 1) / kCtaRecv) * splits;
+        q.n_items = cta_tiles(a.n_recv) * kTileWarps * splits;
         q.work_counter = counter;
         q.grad_out = reinterpret_cast<const float2 *>(grad_out);
         q.seg_G = seg_G;
@@ -2119,12 +2088,13 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
 template <int NF, int WINDOW>
 int batched_prepare()
 {
-    const size_t smem = sizeof(CtaSmem<NF>);
+    using Cfg = PairCfg<NF, kFwd, true>;
+    const size_t smem = Cfg::kSmem;
     GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, kFwd, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, gbs_fwd_kernel<NF, WINDOW, kFwd, true>, kThreads, smem));
+        &per_sm, gbs_fwd_kernel<NF, WINDOW, kFwd, true>, 32 * Cfg::kWarps, smem));
     if (per_sm < 1) fail(GBT_ERR_UNSUPPORTED, "GBS kernel does not fit on one SM");
     return per_sm;
 }
@@ -2133,7 +2103,8 @@ template <int NF, int WINDOW>
 void batched_launch(const FwdParams &prm, int grid, cudaStream_t s)
 {
     GBT_CUDA(cudaMemsetAsync(prm.work_counter, 0, sizeof(int), s));
-    gbs_fwd_kernel<NF, WINDOW, kFwd, true><<<grid, kThreads, sizeof(CtaSmem<NF>), s>>>(prm);
+    using Cfg = PairCfg<NF, kFwd, true>;
+    gbs_fwd_kernel<NF, WINDOW, kFwd, true><<<grid, 32 * Cfg::kWarps, Cfg::kSmem, s>>>(prm);
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
@@ -2242,7 +2213,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         float *rec = reinterpret_cast<float *>(w + B.rec_off[i]);
         FwdParams q = make_pair_params(td, td.scene->d, a, rec);
         q.splits = B.splits[i];
-        q.n_items = ((a.n_recv + kCtaRecv - 1) / kCtaRecv) * q.splits;
+        q.n_items = cta_tiles(a.n_recv) * kTileWarps * q.splits;
         q.partial = reinterpret_cast<float4 *>(w + B.part_off[i]);
         q.work_counter = B.mode == kConcurrent ? B.counter + k : B.counter;
         {
