@@ -90,6 +90,7 @@ struct alignas(16) FwdParams {
     const int32_t *list;       // segment indices, each tile's in segment order, or null
     const int64_t *list_off;   // per tile: first entry in list
     const int32_t *list_n;     // per tile: entries, or -1 (no list: stream every segment)
+    const uint16_t *list_mask; // per entry: bit w set if the segment can reach warp tile w
     float4 *partial;           // [splits][nf][n_recv]: re_hi, im_hi, re_lo, im_lo
     unsigned long long *stats; // counting mode when non-null: [1] prefiltered, [2] kept
     unsigned int *status;      // device status word (timeouts)
@@ -653,6 +654,7 @@ struct WarpBuf {
     float4 raw[kWRaw][kBatch][kRecFloats / 4];
     StageSmem stg;
     unsigned long long bar[kWRaw];
+    int32_t queue[2 * kBatch];       // list entries selected for this warp tile, not yet batched
     int abort_flag, pad[3];
 };
 
@@ -835,19 +837,43 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             }
         };
 
-        // Record batch k of the item into raw buffer k % 2: one bulk copy (lane 0)
-        // for consecutive segments, else every lane gathers its own record with
-        // 16-byte async copies, one commit group per batch (empty past the end).
-        auto list_idx = [&](uint32_t k) -> int32_t {
-            const int64_t e = (split + (int64_t)k * p.splits) * kBatch + lane;
-            return (k < nb && e < n_seg) ? lst[e] : -1;
+        // Batches of the item, double-buffered: raw buffer k % 2 receives batch k.  Consecutive
+        // segments: batch k is split + k * splits, one bulk copy (lane 0) on the buffer's
+        // mbarrier.  A tile list: the item scans the list's 32-entry chunks split, split +
+        // splits, ..., keeps the entries whose mask has this warp tile's bit, and every
+        // lane gathers its own record of each full batch of kept entries with 16-byte
+        // async copies (one commit group per batch, empty past the end).
+        // Per buffer: records in the batch, and this lane's segment index (or -1).
+        int nrec0 = 0, nrec1 = 0;
+        int32_t seg0 = -1, seg1 = -1;
+        const uint32_t wbit = 1u << wl;
+        const int64_t n_chunks = (n_seg + kBatch - 1) / kBatch;
+        int64_t chunk = split;   // list: next chunk to scan
+        int qlen = 0;            // list: entries queued for this warp tile (warp-uniform)
+        auto next_list_batch = [&](int32_t &idx) -> int {
+            while (qlen < kBatch && chunk < n_chunks) {
+                const int64_t e = chunk * kBatch + lane;
+                const bool sel = e < n_seg && (p.list_mask[lst - p.list + e] & wbit) != 0u;
+                const uint32_t m = __ballot_sync(0xffffffffu, sel);
+                if (sel) B.queue[qlen + __popc(m & ((1u << lane) - 1u))] = lst[e];
+                qlen += __popc(m);
+                chunk += p.splits;
+            }
+            __syncwarp();
+            const int n = min(qlen, kBatch);
+            idx = lane < n ? B.queue[lane] : -1;
+            __syncwarp();
+            if (lane + kBatch < qlen) B.queue[lane] = B.queue[lane + kBatch];
+            qlen -= n;
+            __syncwarp();
+            return n;
         };
-        int32_t next_idx = lst ? list_idx(0) : -1;
-        auto issue = [&](uint32_t k) {
+        auto issue = [&](uint32_t k) {   // all lanes, k in increasing order
             const int buf = (int)(k & 1u);
+            int n = 0;
+            int32_t idx = -1;
             if (lst) {
-                const int32_t idx = next_idx;
-                next_idx = list_idx(k + 1);
+                n = next_list_batch(idx);
                 if (idx >= 0) {
                     const float4 *src =
                         reinterpret_cast<const float4 *>(p.rec + (int64_t)idx * kRecFloats);
@@ -855,21 +881,28 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     for (int c = 0; c < kRecFloats / 4; ++c) cp_async16(&B.raw[buf][lane][c], src + c, 16);
                 }
                 cp_async_commit();
-            } else if (k < nb && lane == 0) {
+            } else if (k < nb) {
                 const int64_t b = split + (int64_t)k * p.splits;
-                const uint32_t bytes =
-                    (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * kRecFloats * 4;
-                mbar_arrive_expect_tx(smem_addr(&B.bar[buf]), bytes);
-                bulk_g2s(smem_addr(&B.raw[buf][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
-                         smem_addr(&B.bar[buf]));
+                n = (int)min((int64_t)kBatch, n_seg - b * kBatch);
+                idx = lane < n ? (int32_t)(b * kBatch + lane) : -1;
+                if (lane == 0) {
+                    const uint32_t bytes = (uint32_t)n * kRecFloats * 4;
+                    mbar_arrive_expect_tx(smem_addr(&B.bar[buf]), bytes);
+                    bulk_g2s(smem_addr(&B.raw[buf][0][0]), p.rec + b * kBatch * kRecFloats, bytes,
+                             smem_addr(&B.bar[buf]));
+                }
             }
+            if (buf) { nrec1 = n; seg1 = idx; } else { nrec0 = n; seg0 = idx; }
         };
         issue(0);
         issue(1);
         uint32_t waited = 0;   // bulk batches whose copy has landed
         bool dirty = false;    // survivors since the last fold
-        for (uint32_t kb_ = 0; kb_ < nb; ++kb_) {
+        for (uint32_t kb_ = 0;; ++kb_) {
             const int buf = (int)(kb_ & 1u);
+            const int nrec = buf ? nrec1 : nrec0;
+            if (nrec <= 0) break;
+            const int32_t my_seg = buf ? seg1 : seg0;
             if (lst) {
                 cp_async_wait1();   // this lane's copies of batch kb_
             } else {
@@ -878,12 +911,9 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 ph ^= 1u << buf;
                 waited = kb_ + 1;
             }
-            const int64_t b = split + (int64_t)kb_ * p.splits;
-            const int64_t e = b * kBatch + lane;
-            const bool seg_ok = e < n_seg;
+            const bool seg_ok = lane < nrec;
             StageSmem &w = B.stg;
-            stage_batch(w, B.raw[buf][lane], lane, seg_ok, seg_ok ? (lst ? lst[e] : (int32_t)e) : -1,
-                        cx, cy, cz, alpha, beta);
+            stage_batch(w, B.raw[buf][lane], lane, seg_ok, my_seg, cx, cy, cz, alpha, beta);
             uint32_t tmask = 0u;
             if (p.tile_cull) {
                 // this lane's segment against the warp tile's ball (own lane's staging only)
@@ -944,7 +974,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     m[1] |= (kb1 >> 31) << (31 - jj);
                 }
             } else {
-                if (STATS) n_test += (uint32_t)min((int64_t)kBatch, n_seg - b * kBatch) * __popc(valid);
+                if (STATS) n_test += (uint32_t)nrec * __popc(valid);
 #pragma unroll 4
                 for (int jj = 0; jj < kBatch; ++jj) {
                     uint32_t kb0, kb1;
@@ -1010,7 +1040,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             cp_async_wait0();    // every gather of this item has landed
         } else if (*abort_flag && lane == 0) {
             // a wait gave up: let the bulk copies still in flight land before leaving
-            const uint32_t issued = nb < 2u ? nb : min(nb, waited + 2u);
+            const uint32_t issued = min(nb, waited + 2u);
             for (uint32_t k = waited; k < issued; ++k) {
                 const int bf = (int)(k & 1u);
                 for (long long i2 = 0; i2 < kSpinLimit; ++i2)
@@ -1305,6 +1335,42 @@ __global__ void tile_ball_kernel(const float *recv, const int32_t *order, int64_
     }
 }
 
+// Bounding ball of each warp tile (64 receivers), one warp per warp tile.
+__global__ void warp_ball_kernel(const float *recv, const int32_t *order, int64_t n_recv,
+                                 int64_t n_wtiles, float4 *wball)
+{
+    const int64_t wt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wt >= n_wtiles) return;
+    float x[2] = {0.f, 0.f}, y[2] = {0.f, 0.f}, z[2] = {0.f, 0.f};
+    float sx = 0.f, sy = 0.f, sz = 0.f, nv = 0.f;
+    bool ok[2];
+    for (int k = 0; k < 2; ++k) {
+        const int64_t r = wt * kWarpRecv + k * 32 + lane;
+        ok[k] = r < n_recv;
+        if (ok[k]) {
+            const int64_t o = order ? order[r] : r;
+            x[k] = recv[3 * o]; y[k] = recv[3 * o + 1]; z[k] = recv[3 * o + 2];
+            sx += x[k]; sy += y[k]; sz += z[k]; nv += 1.f;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    }
+    if (nv > 0.f) { sx /= nv; sy /= nv; sz /= nv; }
+    float r2 = 0.f;
+    for (int k = 0; k < 2; ++k)
+        if (ok[k]) {
+            const float dx = x[k] - sx, dy = y[k] - sy, dz = z[k] - sz;
+            r2 = fmaxf(r2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    if (lane == 0) wball[wt] = make_float4(sx, sy, sz, sqrtf(r2));
+}
+
 template <int WINDOW>
 __global__ void tile_weight_kernel(const float *rec, const int32_t *n_seg_ptr, const float4 *ball,
                                    int64_t n_tiles, float alpha, float beta, unsigned int *weight)
@@ -1434,6 +1500,31 @@ __global__ void __launch_bounds__(1024) list_scan_chunks_kernel(int32_t *counts,
         carry += tot;
     }
     if (threadIdx.x == 0) total[blockIdx.x] = (unsigned int)carry;
+}
+
+// Per list entry, the warp tiles of its CTA tile whose balls the segment can reach.
+// Blocks (g, t) stride over tile t's entries.
+template <int WINDOW>
+__global__ void list_mask_kernel(const float *rec, const float4 *wball, int64_t n_wtiles,
+                                 float alpha, float beta, const int64_t *list_off,
+                                 const int32_t *list_n, const int32_t *list, uint16_t *list_mask)
+{
+    const int64_t t = blockIdx.y;
+    const int32_t n = list_n[t];
+    if (n <= 0) return;
+    const int64_t off = list_off[t];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 *R = reinterpret_cast<const float4 *>(rec + (int64_t)list[off + i] * kRecFloats);
+        const float4 r0 = R[0], r1 = R[1], r2 = R[2];
+        uint32_t wm = 0u;
+        for (int w = 0; w < kTileWarps; ++w) {
+            const int64_t wt = t * kTileWarps + w;
+            if (wt < n_wtiles && seg_reaches_ball<WINDOW>(r0, r1, r2, wball[wt], alpha, beta))
+                wm |= 1u << w;
+        }
+        list_mask[off + i] = (uint16_t)wm;
+    }
 }
 
 // One block: list ranges, tiles lightest first (perm lists them heaviest first).
@@ -1715,9 +1806,12 @@ int choose_splits(const TraceDev &td, const gbt_sum_args &a)
         s = std::max<int64_t>(1, std::min<int64_t>(s, (nseg_est + kTS64 - 1) / kTS64));
         return (int)std::min<int64_t>(s, 4096);
     }
-    const int64_t tiles = (a.n_recv + kCtaRecv - 1) / kCtaRecv;         // CTA tiles
-    const int64_t slots = (int64_t)num_sms();                           // resident CTAs
-    int64_t s = (8 * slots + tiles - 1) / (tiles > 0 ? tiles : 1);
+    // items are (warp tile, split): about 16 per resident warp, 32 with the pre-cull (its
+    // item costs vary more), so that the last items to finish are short ones
+    const int64_t wtiles = std::max<int64_t>(1, (a.n_recv + kCtaRecv - 1) / kCtaRecv) * kTileWarps;
+    const int64_t warps = (int64_t)num_sms() * kWarpsFwd;
+    const int64_t per_warp = a.tile_cull ? 32 : 16;
+    int64_t s = (per_warp * warps + wtiles - 1) / wtiles;
     s = std::max<int64_t>(1, std::min<int64_t>(s, (nseg_est + kBatch - 1) / kBatch));
     // partial sums stay under ~1 GiB
     const int64_t per_split = (int64_t)a.n_freq * std::max<int64_t>(a.n_recv, 1) * 16;
@@ -1737,7 +1831,9 @@ struct TileWs {
     int64_t *list_off = nullptr;
     int32_t *list_n = nullptr;
     int32_t *list = nullptr;
-    int64_t tiles = 0, chunks = 0, cap = 0;
+    uint16_t *mask = nullptr;      // per list entry: warp tiles it can reach
+    float4 *wball = nullptr;       // per warp tile: bounding ball
+    int64_t tiles = 0, chunks = 0, cap = 0, wtiles = 0;
     bool order = false, lists = false;
     size_t bytes = 0;              // workspace the layout needs
 };
@@ -1750,9 +1846,10 @@ static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, boo
     t.lists = tile_cull && t.tiles >= 1 && t.tiles <= kMaxOrderedTiles && seg_capacity > 0;
     if (!t.order && !t.lists) return t;
     t.chunks = t.lists ? (seg_capacity + kListChunk - 1) / kListChunk : 0;
-    // room for a quarter of all (tile, segment) pairs, at least 16M entries
+    // room for an eighth of all (tile, segment) pairs, at least 16M entries
     const int64_t all = t.tiles * seg_capacity;
-    t.cap = t.lists ? std::min<int64_t>(all, std::max<int64_t>(int64_t(1) << 24, all / 4)) : 0;
+    t.cap = t.lists ? std::min<int64_t>(all, std::max<int64_t>(int64_t(1) << 24, all / 8)) : 0;
+    t.wtiles = (n_recv + kWarpRecv - 1) / kWarpRecv;
     char *w = static_cast<char *>(ws);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -1768,6 +1865,8 @@ static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, boo
         t.list_off = reinterpret_cast<int64_t *>(take((size_t)t.tiles * sizeof(int64_t)));
         t.list_n = reinterpret_cast<int32_t *>(take((size_t)t.tiles * sizeof(int32_t)));
         t.list = reinterpret_cast<int32_t *>(take((size_t)t.cap * sizeof(int32_t)));
+        t.mask = reinterpret_cast<uint16_t *>(take((size_t)t.cap * sizeof(uint16_t)));
+        t.wball = reinterpret_cast<float4 *>(take((size_t)t.wtiles * sizeof(float4)));
     }
     t.bytes = off;
     return t;
@@ -1821,18 +1920,27 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
     if (t.lists) {
         list_layout_kernel<<<1, 1024, 0, s>>>(t.weight, t.order ? t.perm : nullptr, T, t.cap,
                                               t.list_off, t.list_n);
-        if (window == GBT_WINDOW_LINE)
+        warp_ball_kernel<<<(unsigned)((t.wtiles + 7) / 8), 256, 0, s>>>(q.recv, q.order, q.n_recv,
+                                                                         t.wtiles, t.wball);
+        const dim3 mgrid(32, (unsigned)T);
+        if (window == GBT_WINDOW_LINE) {
             list_write_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
                 q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                 t.list_off, t.list_n, t.list);
-        else
+            list_mask_kernel<GBT_WINDOW_LINE><<<mgrid, 256, 0, s>>>(
+                q.rec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
+        } else {
             list_write_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
                 q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                 t.list_off, t.list_n, t.list);
-        n += 2;
+            list_mask_kernel<GBT_WINDOW_SEGMENT><<<mgrid, 256, 0, s>>>(
+                q.rec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
+        }
+        n += 4;
         q.list = t.list;
         q.list_off = t.list_off;
         q.list_n = t.list_n;
+        q.list_mask = t.mask;
     }
     GBT_CUDA(cudaGetLastError());
     note_launches(n);
@@ -2222,6 +2330,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
             q.list = t.lists ? t.list : nullptr;
             q.list_off = t.lists ? t.list_off : nullptr;
             q.list_n = t.lists ? t.list_n : nullptr;
+            q.list_mask = t.lists ? t.mask : nullptr;
         }
         B.table.push_back(q);
         B.inst_off.push_back(B.inst_off.back() + q.n_items);

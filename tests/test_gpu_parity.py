@@ -183,8 +183,9 @@ def test_many_tiles_every_receiver_against_oracle(G):
     assert G.gbt_launches_read(reset=True) == 6
     pc = G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[0]), _dev(w.scene.gamma, torch.float32),
                    order=order, window=w.window, cutoff=w.cutoff, tile_cull=True)
-    # prepass, ball, list counts, count scan, rank, list layout, list write, pair kernel, merge
-    assert G.gbt_launches_read(reset=True) == 9
+    # prepass, ball, list counts, count scan, rank, list layout, warp-tile balls, list write,
+    # list masks, pair kernel, merge
+    assert G.gbt_launches_read(reset=True) == 11
     torch.cuda.synchronize()
     G.gbt_sync()
     # per-tile lists: the same terms, regrouped into other batches and splits
