@@ -43,7 +43,7 @@ KERNEL_TAG = "gbs_fwd_kernel<6,LINE,fwd,plain> warp-autonomous, paired survivors
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of this
 # exact kernel version (profiles/gbs_fwd_open_plane_64k_rays_256x256_6f.md); a changed
 # kernel gets a new tag and no entry until it is captured again.
-KERNEL_TRAFFIC = {"gbs_fwd_kernel<6,LINE,fwd,plain> ring-v2, heaviest tiles first": 63850496}
+KERNEL_TRAFFIC = {"gbs_fwd_kernel<6,LINE,fwd,plain> warp-autonomous, paired survivors": 194647296}
 
 
 def _env_int(name, default):

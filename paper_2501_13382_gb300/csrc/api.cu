@@ -351,6 +351,7 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
             sd.n_clusters = (d.n_tri + kTriCluster - 1) / kTriCluster;
             sd.cbox = static_cast<float *>(
                 dalloc((size_t)std::max<int64_t>(sd.n_clusters, 1) * 6 * sizeof(float), s));
+            sd.tbox = static_cast<float *>(dalloc(nt * 6 * sizeof(float), s));
             if (d.n_tri > 0) {
                 std::vector<int32_t> face(d.n_tri);
                 for (int64_t k = 0; k < d.n_tri; ++k) face[k] = d.tri_face ? d.tri_face[k] : (int32_t)k;
@@ -361,14 +362,13 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
                                          cudaMemcpyHostToDevice, s));
                 GBT_CUDA(cudaMemcpyAsync(sd.mat, d.tri_material, (size_t)d.n_tri * 4,
                                          cudaMemcpyHostToDevice, s));
-                // cluster boxes on the host: exact min/max, then an expansion (1 mm plus
-                // 2e-6 relative) far above the rounding of the FP32 slab test, rounded outward
-                std::vector<float> box((size_t)sd.n_clusters * 6);
-                for (int64_t c = 0; c < sd.n_clusters; ++c) {
+                // FP32 boxes of each cluster of kTriCluster triangles and of each triangle,
+                // on the host: exact min/max, then an expansion (1 mm plus 2e-6 relative)
+                // far above the rounding of the FP32 slab test, rounded outward
+                auto padded_box = [&](int64_t k0, int64_t k1, float *box) {
                     double lo[3] = {INFINITY, INFINITY, INFINITY};
                     double hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-                    const int64_t k1 = std::min<int64_t>(d.n_tri, (c + 1) * kTriCluster);
-                    for (int64_t k = c * kTriCluster; k < k1; ++k)
+                    for (int64_t k = k0; k < k1; ++k)
                         for (int v = 0; v < 3; ++v)
                             for (int a = 0; a < 3; ++a) {
                                 const double x = d.tri_xyz[9 * k + 3 * v + a];
@@ -377,11 +377,18 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
                             }
                     for (int a = 0; a < 3; ++a) {
                         const double pad = 1e-3 + 2e-6 * std::max(fabs(lo[a]), fabs(hi[a]));
-                        box[6 * c + a] = nextafterf((float)(lo[a] - pad), -INFINITY);
-                        box[6 * c + 3 + a] = nextafterf((float)(hi[a] + pad), INFINITY);
+                        box[a] = nextafterf((float)(lo[a] - pad), -INFINITY);
+                        box[3 + a] = nextafterf((float)(hi[a] + pad), INFINITY);
                     }
-                }
+                };
+                std::vector<float> box((size_t)sd.n_clusters * 6), tbox((size_t)d.n_tri * 6);
+                for (int64_t c = 0; c < sd.n_clusters; ++c)
+                    padded_box(c * kTriCluster, std::min<int64_t>(d.n_tri, (c + 1) * kTriCluster),
+                               &box[6 * c]);
+                for (int64_t k = 0; k < d.n_tri; ++k) padded_box(k, k + 1, &tbox[6 * k]);
                 GBT_CUDA(cudaMemcpyAsync(sd.cbox, box.data(), box.size() * sizeof(float),
+                                         cudaMemcpyHostToDevice, s));
+                GBT_CUDA(cudaMemcpyAsync(sd.tbox, tbox.data(), tbox.size() * sizeof(float),
                                          cudaMemcpyHostToDevice, s));
                 scene_prepare(sd, static_cast<const double *>(raw), s);
                 dfree(raw, s);
@@ -391,6 +398,7 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
         } catch (...) {
             if (raw) dfree(raw, s);
             dfree(sd.tri, s); dfree(sd.face, s); dfree(sd.mat, s); dfree(sd.cbox, s);
+            dfree(sd.tbox, s);
             delete sc;
             throw;
         }
@@ -407,6 +415,7 @@ gbt_status gbt_scene_destroy(gbt_scene_t *scene)
         dfree(scene->d.face, nullptr);
         dfree(scene->d.mat, nullptr);
         dfree(scene->d.cbox, nullptr);
+        dfree(scene->d.tbox, nullptr);
         delete scene;
     });
 }

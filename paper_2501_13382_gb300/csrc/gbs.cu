@@ -5,29 +5,29 @@
 // GB300 design of the FP32 pair kernel:
 //  * A prepass turns every traced segment into an 80-byte record (origin and
 //    start distance as float-float, direction, length, amplitude).
-//  * Receivers are visited in Morton order.  A CTA tile is 960 receivers: 15
-//    consumer warps x 64, each lane holding receivers lane and lane + 32 of its
-//    warp's patch, in registers, absolute (exact path) and relative to the
-//    warp's first receiver (prefilter).
-//  * One persistent CTA per SM takes (tile, split) items from an atomic
-//    counter; split s of a tile owns record batches s, s + splits, ...  Tiles
-//    are dispatched heaviest first (sampled estimate of the beams that reach
-//    them), so the queue drains on light items.
-//  * A producer warp streams 32-record batches into an 8-stage shared-memory
-//    ring with bulk asynchronous copies completed on mbarriers; every consumer
-//    warp re-expresses the batch relative to its own patch.  All waits are
-//    bounded and raise a status flag instead of hanging.
+//  * Receivers are visited in Morton order, in warp tiles of 64 (two per lane:
+//    receivers lane and lane + 32) held in registers, absolute (exact path) and
+//    relative to the warp tile's first receiver (prefilter).
+//  * Persistent CTAs of 16 warps, and every warp works on its own: it takes
+//    (warp tile, segment split) items from a global queue, split s owning record
+//    batches s, s + splits, ...  CTA tiles of 15 warp tiles are dispatched
+//    heaviest first and splits are sized for about 16 items per warp, so no warp
+//    waits for another and the queue drains on short items.
+//  * A warp double-buffers its own 32-record batches (a bulk asynchronous copy
+//    completed on a per-warp mbarrier, or per-lane cp.async gathers from the
+//    tile's segment list with the pre-cull) and stages each batch itself.  Every
+//    wait is bounded and raises a status flag instead of hanging.
 //  * Prefilter (every pair, frequency independent): a paired FP32 (f32x2)
 //    evaluation of the union of the per-frequency Gaussian cutoffs and the
 //    window, conservative by a margin, gives one keep bit per pair.  With the
-//    tile pre-cull, a batch's segments that cannot reach a warp's bounding ball
-//    are skipped first.
-//  * Survivors (typically a few percent of pairs) are evaluated exactly per
-//    lane: float-float s and phase (reduced in turns before the MUFU sin/cos),
-//    compensated cross product for n^2.  FP32 sums per lane are folded into
-//    float-float accumulators in shared memory every 16 batches, and the
-//    per-split partials are merged in FP64 in a fixed order by a second kernel,
-//    so results do not depend on scheduling.
+//    pre-cull, per-tile segment lists with per-entry warp-tile masks and a
+//    per-warp ball test skip segments that can reach none of its receivers.
+//  * Survivors (typically a few percent of pairs) are evaluated exactly, the two
+//    receivers of a lane side by side in paired FP32: float-float s and phase
+//    (reduced in turns before the MUFU sin/cos), compensated cross product for
+//    n^2.  FP32 sums per lane fold into the item's float-float partials every 16
+//    batches, and the per-split partials are merged in FP64 in a fixed order by
+//    a second kernel, so results do not depend on scheduling.
 
 #include <math.h>
 
@@ -1601,14 +1601,22 @@ __global__ void reduce_kernel(ReduceParams p)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= p.n) return;
+    // splits in order (the sums are the same whatever the unrolling); unrolled so the
+    // independent loads are in flight together
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < p.splits; ++s) {
-        if (p.p32) {
-            const float4 v = p.p32[(int64_t)s * p.n + i];
+    if (p.p32) {
+        const float4 *src = p.p32 + i;
+#pragma unroll 8
+        for (int s = 0; s < p.splits; ++s) {
+            const float4 v = __ldcs(src + (int64_t)s * p.n);
             re += (double)v.x + (double)v.z;
             im += (double)v.y + (double)v.w;
-        } else {
-            const double2 v = p.p64[(int64_t)s * p.n + i];
+        }
+    } else {
+        const double2 *src = p.p64 + i;
+#pragma unroll 8
+        for (int s = 0; s < p.splits; ++s) {
+            const double2 v = src[(int64_t)s * p.n];
             re += v.x;
             im += v.y;
         }

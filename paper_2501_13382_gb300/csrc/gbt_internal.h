@@ -66,7 +66,8 @@ struct SceneDev {
     // bounding boxes of consecutive triangle clusters (kTriCluster each), in FP32,
     // expanded far beyond FP32 rounding so a box test never rejects a hit:
     // per cluster xmin, ymin, zmin, xmax, ymax, zmax
-    float *cbox = nullptr;
+    float *cbox = nullptr;         // padded FP32 box per cluster of kTriCluster triangles
+    float *tbox = nullptr;         // padded FP32 box per triangle
     int64_t n_clusters = 0;
 };
 constexpr int kTriCluster = 8;

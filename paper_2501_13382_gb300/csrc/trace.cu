@@ -14,13 +14,15 @@
 // the segment count stays on the device (ray_off[n_rays]).
 #include <math.h>
 
+#include <algorithm>
+
 #include "gbt_internal.h"
 
 namespace gbt {
 namespace {
 
-constexpr int kTraceBlock = 128;
-constexpr int kTriChunk = 512;          // triangles per shared-memory chunk
+constexpr int kTraceBlock = 256;
+constexpr int kTriChunk = 1024;         // most triangles per shared-memory chunk (scene resident up to this)
 static_assert(kTriChunk % kTriCluster == 0, "chunks hold whole clusters");
 constexpr int kScanBlock = 1024;        // threads per scan block
 constexpr int kScanItems = 4;           // items per scan thread
@@ -58,7 +60,9 @@ struct TraceParams {
     const int32_t *mat;
     int64_t n_tri;
     const float *cbox;         // n_clusters * 6
+    const float *tbox;         // n_tri * 6
     int64_t n_clusters;
+    int chunk;                 // triangles per shared-memory chunk (a multiple of kTriCluster)
     int64_t stride;            // max_refl + 1
     double *po, *pt, *pL, *ps0;
     int32_t *pbmat, *phit, *cnt;
@@ -105,11 +109,14 @@ __device__ __forceinline__ bool slab(float o, float d, float inv, float lo, floa
     return true;
 }
 
-__device__ __forceinline__ void load_tri_chunk(double *st, float *sbox, int32_t *sface,
-                                               const TraceParams &p, int64_t base, int count)
+__device__ __forceinline__ void load_tri_chunk(double *st, float *sbox, float *stbox,
+                                               int32_t *sface, const TraceParams &p, int64_t base,
+                                               int count)
 {
     for (int idx = threadIdx.x; idx < count * 12; idx += blockDim.x)
         st[idx] = p.tri[base * 12 + idx];
+    for (int idx = threadIdx.x; idx < count * 6; idx += blockDim.x)
+        stbox[idx] = p.tbox[base * 6 + idx];
     const int c0 = (int)(base / kTriCluster), nc = (count + kTriCluster - 1) / kTriCluster;
     for (int idx = threadIdx.x; idx < nc * 6; idx += blockDim.x)
         sbox[idx] = p.cbox[(int64_t)c0 * 6 + idx];
@@ -120,9 +127,11 @@ __device__ __forceinline__ void load_tri_chunk(double *st, float *sbox, int32_t 
 __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
 {
     extern __shared__ double smem[];
-    double *st = smem;                                   // kTriChunk * 12
-    float *sbox = reinterpret_cast<float *>(smem + kTriChunk * 12);   // clusters * 6
-    int32_t *sface = reinterpret_cast<int32_t *>(sbox + (kTriChunk / kTriCluster) * 6);
+    const int chunk = p.chunk;
+    double *st = smem;                                              // chunk * 12
+    float *stbox = reinterpret_cast<float *>(smem + (size_t)chunk * 12);   // chunk * 6
+    float *sbox = stbox + (size_t)chunk * 6;                        // clusters * 6
+    int32_t *sface = reinterpret_cast<int32_t *>(sbox + (chunk / kTriCluster) * 6);
 
     const int64_t i = blockIdx.x * (int64_t)kTraceBlock + threadIdx.x;
     const bool active = i < p.n_rays;
@@ -149,10 +158,10 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
     int nref = 0, nseg = 0;
     bool alive = active;
 
-    const int64_t nchunk = (p.n_tri + kTriChunk - 1) / kTriChunk;
+    const int64_t nchunk = (p.n_tri + chunk - 1) / chunk;
     const bool resident = nchunk <= 1;
     if (resident && p.n_tri > 0) {
-        load_tri_chunk(st, sbox, sface, p, 0, (int)p.n_tri);
+        load_tri_chunk(st, sbox, stbox, sface, p, 0, (int)p.n_tri);
     }
     __syncthreads();
 
@@ -164,11 +173,11 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
             if (t > kTMin && t < tbest) { tbest = t; best = 0; }
         }
         for (int64_t c = 0; c < nchunk; ++c) {
-            const int64_t base = c * kTriChunk;
-            const int count = (int)min((int64_t)kTriChunk, p.n_tri - base);
+            const int64_t base = c * chunk;
+            const int count = (int)min((int64_t)chunk, p.n_tri - base);
             if (!resident) {
                 __syncthreads();
-                load_tri_chunk(st, sbox, sface, p, base, count);
+                load_tri_chunk(st, sbox, stbox, sface, p, base, count);
                 __syncthreads();
             }
             if (alive) {
@@ -189,6 +198,14 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
                     const int k1 = min(count, (c + 1) * kTriCluster);
                     for (int k = c * kTriCluster; k < k1; ++k) {
                         if (sface[k] == last_face) continue;
+                        // the triangle's own padded box first: the FP64 test only where it
+                        // could hit before the best hit so far
+                        const float *tb = stbox + 6 * k;
+                        float un = 0.0f, uf = (float)tbest * 1.000001f + 1e-3f;
+                        bool hit_tri = slab(of0, df0, id0, tb[0], tb[3], un, uf);
+                        hit_tri = hit_tri && slab(of1, df1, id1, tb[1], tb[4], un, uf);
+                        hit_tri = hit_tri && slab(of2, df2, id2, tb[2], tb[5], un, uf);
+                        if (!hit_tri || un > uf) continue;
                         double t = ray_triangle(o, d, st + 12 * k);
                         if (t > kTMin && t < tbest) { tbest = t; best = (int)(base + k + 1); }
                     }
@@ -418,7 +435,11 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     p.mat = sd.mat;
     p.n_tri = sd.n_tri;
     p.cbox = sd.cbox;
+    p.tbox = sd.tbox;
     p.n_clusters = sd.n_clusters;
+    // the whole scene resident in shared memory when it fits one chunk
+    const int64_t nt = std::max<int64_t>(sd.n_tri, 1);
+    p.chunk = (int)std::min<int64_t>(kTriChunk, (nt + kTriCluster - 1) / kTriCluster * kTriCluster);
     p.stride = stride;
     p.po = reinterpret_cast<double *>(take(cap * 3 * sizeof(double)));
     p.pt = reinterpret_cast<double *>(take(cap * 3 * sizeof(double)));
@@ -433,12 +454,15 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     if ((size_t)(w - static_cast<char *>(scratch)) > scratch_bytes)
         fail(GBT_ERR_INVALID_ARG, "trace scratch too small");
 
-    const size_t smem = kTriChunk * 12 * sizeof(double) +
-                        (kTriChunk / kTriCluster) * 6 * sizeof(float) + kTriChunk * sizeof(int32_t);
+    auto chunk_smem = [](size_t c) {
+        return c * 12 * sizeof(double) + c * 6 * sizeof(float) + (c / kTriCluster) * 6 * sizeof(float) +
+               c * sizeof(int32_t);
+    };
+    const size_t smem = chunk_smem((size_t)p.chunk);
     static bool attr_set = false;
     if (!attr_set) {
         GBT_CUDA(cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+                                      (int)chunk_smem(kTriChunk)));
         attr_set = true;
     }
     trace_kernel<<<(unsigned)((n + kTraceBlock - 1) / kTraceBlock), kTraceBlock, smem, s>>>(p);
