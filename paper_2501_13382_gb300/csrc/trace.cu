@@ -63,6 +63,7 @@ struct TraceParams {
     const float *tbox;         // n_tri * 6
     int64_t n_clusters;
     int chunk;                 // triangles per shared-memory chunk (a multiple of kTriCluster)
+    int64_t strip;             // Fibonacci fan: lattice step between a warp's rays (0: none)
     int64_t stride;            // max_refl + 1
     double *po, *pt, *pL, *ps0;
     int32_t *pbmat, *phit, *cnt;
@@ -133,7 +134,19 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
     float *sbox = stbox + (size_t)chunk * 6;                        // clusters * 6
     int32_t *sface = reinterpret_cast<int32_t *>(sbox + (chunk / kTriCluster) * 6);
 
-    const int64_t i = blockIdx.x * (int64_t)kTraceBlock + threadIdx.x;
+    // On the Fibonacci lattice ray g and ray g + F (F a Fibonacci number near sqrt(N))
+    // are neighbours, so a warp takes rays i0, i0 + F, ..., i0 + 31 F: the 32 x F index
+    // blocks are read transposed and a warp's rays meet the same boxes and triangles.
+    // Outputs stay at each ray's own index; the tail past whole blocks keeps its order.
+    const int64_t tid = blockIdx.x * (int64_t)kTraceBlock + threadIdx.x;
+    int64_t i = tid;
+    if (p.strip > 0) {
+        const int64_t blk = 32 * p.strip;
+        if (tid < p.n_rays / blk * blk) {
+            const int64_t r = tid % blk;
+            i = tid - r + (r & 31) * p.strip + (r >> 5);
+        }
+    }
     const bool active = i < p.n_rays;
     double o[3] = {p.src[0], p.src[1], p.src[2]};
     double d[3] = {0.0, 0.0, 1.0};
@@ -437,6 +450,13 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     p.cbox = sd.cbox;
     p.tbox = sd.tbox;
     p.n_clusters = sd.n_clusters;
+    // coherent warps on a Fibonacci fan: the largest Fibonacci number <= sqrt(N) / 2
+    p.strip = 0;
+    if (!p.dirs && td.n_fan >= 4096) {
+        int64_t f0 = 1, f1 = 2;   // lattice neighbours are set by the whole fan's size
+        while (f1 * f1 * 4 <= td.n_fan) { const int64_t f2 = f0 + f1; f0 = f1; f1 = f2; }
+        p.strip = f0;
+    }
     // the whole scene resident in shared memory when it fits one chunk
     const int64_t nt = std::max<int64_t>(sd.n_tri, 1);
     p.chunk = (int)std::min<int64_t>(kTriChunk, (nt + kTriCluster - 1) / kTriCluster * kTriCluster);
