@@ -282,23 +282,30 @@ def bench_fwd_bwd(G, torch, stream, steps=5):
     freqs, bb = list(w.freqs), list(w.beam_b[0])
     out = torch.empty((len(freqs), recv.shape[0]), dtype=torch.complex64, device="cuda")
     g = torch.ones_like(out)
-
-    def fwd():
-        G.gbs_sum(tr, recv, freqs, bb, gam, order=order, window=w.window, out=out)
-
-    def fwd_bwd():
-        fwd()
-        G.gbs_sum_backward(tr, recv, freqs, bb, gam, g, order=order, window=w.window)
-    fwd_bwd()
-    torch.cuda.synchronize()
-    t_f = _timed(torch, stream, fwd, steps) / steps
-    t_fb = _timed(torch, stream, fwd_bwd, steps) / steps
     evals = float(recv.shape[0]) * n_seg * len(freqs)
+    res = {"workload": w.name, "evals": evals}
+    for name, cull in (("dense", False), ("tile_cull", True)):
+        def fwd():
+            G.gbs_sum(tr, recv, freqs, bb, gam, order=order, window=w.window, out=out,
+                      tile_cull=cull)
+
+        def fwd_bwd():
+            fwd()
+            G.gbs_sum_backward(tr, recv, freqs, bb, gam, g, order=order, window=w.window,
+                               tile_cull=cull)
+        fwd_bwd()
+        torch.cuda.synchronize()
+        t_f = _timed(torch, stream, fwd, steps) / steps
+        t_fb = _timed(torch, stream, fwd_bwd, steps) / steps
+        r = {"forward": {"value": evals / (t_f * 1e-3), "ms": t_f},
+             "forward_backward": {"value": evals / (t_fb * 1e-3), "ms": t_fb},
+             "backward_over_forward": (t_fb - t_f) / t_f}
+        if cull:
+            res["tile_cull"] = r
+        else:
+            res.update(r)
     tr.close()
-    return {"workload": w.name, "evals": evals,
-            "forward": {"value": evals / (t_f * 1e-3), "ms": t_f},
-            "forward_backward": {"value": evals / (t_fb * 1e-3), "ms": t_fb},
-            "backward_over_forward": (t_fb - t_f) / t_f}
+    return res
 
 
 def main():

@@ -43,7 +43,7 @@ namespace gbt {
 namespace {
 
 constexpr int kWarpsFwd = 16;               // warps per CTA of the pair kernel (one CTA per SM)
-constexpr int kWarpsBwd = 12;               // adjoint: fewer warps, room for per-segment sums
+constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory of one pair-kernel CTA
 constexpr int kWRaw = 2;                    // raw record buffers per warp (double buffering)
 constexpr int kR = 2;                       // receivers per lane
 constexpr int kWarpRecv = 32 * kR;          // receivers per warp tile
@@ -514,16 +514,15 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, 
     }
 }
 
-// Adjoint of one surviving pair: per-segment sums in shared memory (gk: this
-// receiver's g per sorted frequency, stride 32 floats2).
+// Adjoint terms of one surviving pair added into G and H[f] (gk: this receiver's
+// g per sorted frequency, stride kR * 32 float2).
 template <int NF, int WINDOW>
 __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, float y, float z,
                                                  const StageSmem &w, int j, const float2 *gk,
-                                                 float *segG, float *segH)
+                                                 float &G, float (&H)[NF])
 {
     float sh, sl, n2;
     if (!exact_geometry<WINDOW>(x, y, z, w, j, sh, sl, n2)) return;
-    float G = 0.f;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
@@ -533,11 +532,15 @@ __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, fl
             if (p.uniform_b) break;
             continue;
         }
-        float H = 0.f;
-        beam_adjoint(q, sh, sl, n2, rcp_approx(D), gk[f * (kR * 32)], G, H);
-        atomicAdd(&segH[f * 32 + j], H);
+        beam_adjoint(q, sh, sl, n2, rcp_approx(D), gk[f * (kR * 32)], G, H[f]);
     }
-    if (G != 0.f) atomicAdd(&segG[j], G);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // Folds the two halves of a paired FP32 sum into two float-float accumulators.
@@ -644,8 +647,6 @@ __device__ __forceinline__ void stage_batch(StageSmem &w, const float4 (&raw)[kR
 template <int NF>
 struct AdjSmem {
     float2 g[NF][kR][32];      // the warp's receivers' g, per sorted frequency
-    float segG[32];            // per segment of the current batch
-    float segH[NF][32];
 };
 // Per-warp shared memory of the pair kernel: two raw record buffers (bulk-copy
 // or cp.async targets), the staged batch, and the completion barriers of the
@@ -660,10 +661,12 @@ struct WarpBuf {
 
 template <int NF, int MODE, bool BATCHED>
 struct PairCfg {
-    static constexpr int kWarps = MODE == kBwd ? kWarpsBwd : kWarpsFwd;
     static constexpr size_t kAdj = MODE == kBwd ? sizeof(AdjSmem<NF>) : 0;
     static constexpr size_t kInst = BATCHED ? sizeof(FwdParams) : 0;
     static constexpr size_t kPerWarp = (sizeof(WarpBuf) + kAdj + kInst + 127) / 128 * 128;
+    // as many warps as fit in the shared memory budget, at most kWarpsFwd
+    static constexpr int kFit = (int)(kSmemBudget / kPerWarp);
+    static constexpr int kWarps = kFit < kWarpsFwd ? kFit : kWarpsFwd;
     static constexpr size_t kSmem = kWarps * kPerWarp;
 };
 
@@ -780,11 +783,6 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     if (f < p.nf && ridx[k] >= 0)
                         part_base[(int64_t)f * p.n_recv + ridx[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-        }
-        if (MODE == kBwd) {
-            adj.segG[lane] = 0.f;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) adj.segH[f][lane] = 0.f;
         }
         // bounding ball of the warp tile's receivers (relative to its first receiver)
         float4 sphere = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -996,6 +994,34 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     if (!h1) j1 = j0;
                     survivor_pair<NF, WINDOW>(p, XA, YA, ZA, w, j0, j1, h0, h1, accx, accy);
                 }
+            } else if (MODE == kBwd) {
+                // segment by segment: the lanes holding a survivor of segment jj add their
+                // receivers' terms, the warp sums them, and one lane adds the sums to the
+                // segment's global G and H (no shared-memory atomics between lanes)
+                const uint32_t mm0 = (valid & 1u) ? m[0] : 0u, mm1 = (valid & 2u) ? m[1] : 0u;
+                uint32_t any = __reduce_or_sync(0xffffffffu, mm0 | mm1);
+                while (any) {
+                    const int jj = __clz(any);
+                    any ^= 0x80000000u >> jj;
+                    float G = 0.f, H[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) H[f] = 0.f;
+                    if ((mm0 << jj) >> 31)
+                        survivor_adjoint<NF, WINDOW>(p, xa[0], ya[0], za[0], w, jj, &adj.g[0][0][lane], G, H);
+                    if ((mm1 << jj) >> 31)
+                        survivor_adjoint<NF, WINDOW>(p, xa[1], ya[1], za[1], w, jj, &adj.g[0][1][lane], G, H);
+                    G = warp_sum(G);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        if (f < p.nf) H[f] = warp_sum(H[f]);
+                    const int32_t jg = w.seg[jj];
+                    if (lane == 0 && jg >= 0) {
+                        if (G != 0.f) atomicAdd(&p.seg_G[jg], G);
+#pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            if (f < p.nf && H[f] != 0.f) atomicAdd(&p.seg_H[(int64_t)f * p.seg_stride + jg], H[f]);
+                    }
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < kR; ++k) {
@@ -1004,27 +1030,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     while (mm) {
                         const int jj = __clz(mm);
                         mm ^= 0x80000000u >> jj;
-                        if (MODE == kBwd)
-                            survivor_adjoint<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj,
-                                                         &adj.g[0][k][lane], adj.segG,
-                                                         &adj.segH[0][0]);
-                        else
-                            survivor_count<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj, n_kept);
+                        survivor_count<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj, n_kept);
                     }
-                }
-            }
-            if (MODE == kBwd) {
-                // per-segment sums of this warp to global, then clear
-                __syncwarp();
-                const int64_t jg = w.seg[lane];
-                const float G = adj.segG[lane];
-                if (G != 0.f && jg >= 0) atomicAdd(&p.seg_G[jg], G);
-                adj.segG[lane] = 0.f;
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const float H = adj.segH[f][lane];
-                    if (H != 0.f && jg >= 0) atomicAdd(&p.seg_H[f * p.seg_stride + jg], H);
-                    adj.segH[f][lane] = 0.f;
                 }
             }
             if (MODE == kFwd) {
