@@ -31,13 +31,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GBS segment x receiver evals/s at <=1e-4 rel L2; batched & fwd+bwd vs plain"
 UNIT = "evals/s"
-# Algorithmic lane-operations (FP32 / integer / MUFU issue slots) the method needs:
-# per (receiver, segment) pair: x - o (3), s_loc (3), s (1), n^2 = |x-o|^2 - s_loc^2 (4),
-# cutoff test (3), window test (1) = 15; per kept (pair, frequency): 1/E (3),
-# Gaussian amplitude (2 + EX2), phase k s + k n^2 s / 2D with range reduction (6 + SIN + COS),
-# complex product and scale (6), accumulation (2) = 22 + 3 MUFU -> 24 counted.
-OPS_PER_PAIR = 15
-OPS_PER_KEPT = 24
+# Algorithmic work of the method, in FP32/ALU lane issue slots:
+# per tested (receiver, segment) pair about 20 (projection onto the segment, s, n^2, window,
+# the frequency-independent cutoff); per kept (pair, frequency) about 45 FP32 slots for the
+# beam term (1/E, Gaussian amplitude, phase with its range reduction, complex product) plus
+# about 12 for the compensated accumulation, i.e. 57, and 4 MUFU operations (RCP, EX2, SIN,
+# COS) on the separate special-function pipe, whose time at 16-32 lanes per clock per SM
+# stays below the FP32 time on every workload here (open plane: 7 %), so the FP32/ALU issue
+# rate is the roofline.
+OPS_PER_PAIR = 20
+OPS_PER_KEPT = 57
 LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
 KERNEL_TAG = "gbs_fwd_kernel<6,LINE,fwd,plain> warp-autonomous, paired survivors"
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of this
@@ -136,6 +139,18 @@ def _oracle_sample(w, budget_s: float, seed: int = 17):
     evals = float(len(idx)) * tr.n_seg * len(w.freqs)
     return {"idx": idx, "p": p, "evals": evals, "t_sum": dt, "t_trace": t_trace,
             "n_seg": tr.n_seg}
+
+
+def aggregate_ranks(torch, ms, e2e_ms, evals, steps, world, dist=None, device="cuda"):
+    """Whole-job rates over `world` replicas: the slowest rank's timed totals (max over ranks)
+    and every rank's `evals` per step.  Returns (ms_per_step, value, e2e_value)."""
+    if dist is not None:
+        t = torch.tensor([ms, e2e_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    ms_per_step = ms / steps
+    return (ms_per_step, world * evals / (ms_per_step * 1e-3),
+            world * evals / (e2e_ms / steps * 1e-3))
 
 
 def run_reference(args):
@@ -423,13 +438,8 @@ def main():
     clk.stop()
     G.gbt_sync()
 
-    if dist:
-        t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
-    ms_per_step = ms / args.steps
-    value = world * evals / (ms_per_step * 1e-3)
-    e2e_value = world * evals / (e2e_ms / args.steps * 1e-3)
+    ms_per_step, value, e2e_value = aggregate_ranks(torch, ms, e2e_ms, evals, args.steps, world,
+                                                    dist)
 
     if rank != 0:
         if dist:
