@@ -227,9 +227,11 @@ gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
 /* --------------------------------------------------------------- solve --
  * RT + GBS for one source with the ray range split into chunks so that one
  * chunk's trace fits args->max_device_bytes (the paper's chunking when rays
- * exceed device memory, Sec. 4.5.1).  Chunks are traced and summed in ray
- * order and accumulated into args->out; the result equals one unchunked
- * trace + sum up to rounding.  src->ray_begin / ray_count must be 0. */
+ * exceed device memory, Sec. 4.5.1).  Chunks are summed in ray order and
+ * accumulated into args->out; with more than one chunk, chunk i + 1 is traced
+ * on a private stream while chunk i is summed on `stream` (two trace slots,
+ * ordered by events; the call returns without waiting).  The result equals one
+ * unchunked trace + sum up to rounding.  src->ray_begin / ray_count must be 0. */
 gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src,
                      const gbt_sum_args *args, void *stream);
 

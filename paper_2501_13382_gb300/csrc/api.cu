@@ -217,36 +217,44 @@ static void validate_source(const gbt_source_desc &src)
                 "segment capacity exceeds 2^31 - 1: trace fewer rays at a time");
 }
 
-static gbt_trace_t *make_trace(const gbt_scene_t *scene, const gbt_source_desc &src, cudaStream_t s)
+// Device buffers of a trace of up to cnt rays (one allocation); td's ray range is set
+// by the caller before each trace_launch into it.
+static void alloc_trace_block(TraceDev &td, const gbt_scene_t *scene, const gbt_source_desc &src,
+                              int64_t cnt, cudaStream_t s)
 {
-    validate_source(src);
-    const int64_t cnt = src.ray_count == 0 ? src.n_rays - src.ray_begin : src.ray_count;
-    gbt_trace_t *tr = new gbt_trace_s();
-    TraceDev &td = tr->d;
     td.scene = scene;
     td.n_fan = src.n_rays;
-    td.ray_begin = src.ray_begin;
-    td.n_rays = cnt;
     td.max_refl = src.max_reflections;
     td.max_path = src.max_path;
     td.capacity = cnt * (int64_t)(src.max_reflections + 1);
     const size_t cap = (size_t)td.capacity;
     size_t bytes = align_up((size_t)(cnt + 1) * 4, 256) + 2 * align_up(cap * 24, 256) +
                    2 * align_up(cap * 8, 256) + 4 * align_up(cap * 4, 256);
+    td.block = dalloc(bytes, s);
+    char *w = static_cast<char *>(td.block);
+    auto take = [&](size_t b) { char *p = w; w += align_up(b, 256); return p; };
+    td.ray_off = reinterpret_cast<int32_t *>(take((size_t)(cnt + 1) * 4));
+    td.o = reinterpret_cast<double *>(take(cap * 24));
+    td.t = reinterpret_cast<double *>(take(cap * 24));
+    td.L = reinterpret_cast<double *>(take(cap * 8));
+    td.s0 = reinterpret_cast<double *>(take(cap * 8));
+    td.ray = reinterpret_cast<int32_t *>(take(cap * 4));
+    td.depth = reinterpret_cast<int32_t *>(take(cap * 4));
+    td.bmat = reinterpret_cast<int32_t *>(take(cap * 4));
+    td.hit = reinterpret_cast<int32_t *>(take(cap * 4));
+}
+
+static gbt_trace_t *make_trace(const gbt_scene_t *scene, const gbt_source_desc &src, cudaStream_t s)
+{
+    validate_source(src);
+    const int64_t cnt = src.ray_count == 0 ? src.n_rays - src.ray_begin : src.ray_count;
+    gbt_trace_t *tr = new gbt_trace_s();
+    TraceDev &td = tr->d;
     void *scratch = nullptr;
     try {
-        td.block = dalloc(bytes, s);
-        char *w = static_cast<char *>(td.block);
-        auto take = [&](size_t b) { char *p = w; w += align_up(b, 256); return p; };
-        td.ray_off = reinterpret_cast<int32_t *>(take((size_t)(cnt + 1) * 4));
-        td.o = reinterpret_cast<double *>(take(cap * 24));
-        td.t = reinterpret_cast<double *>(take(cap * 24));
-        td.L = reinterpret_cast<double *>(take(cap * 8));
-        td.s0 = reinterpret_cast<double *>(take(cap * 8));
-        td.ray = reinterpret_cast<int32_t *>(take(cap * 4));
-        td.depth = reinterpret_cast<int32_t *>(take(cap * 4));
-        td.bmat = reinterpret_cast<int32_t *>(take(cap * 4));
-        td.hit = reinterpret_cast<int32_t *>(take(cap * 4));
+        alloc_trace_block(td, scene, src, cnt, s);
+        td.ray_begin = src.ray_begin;
+        td.n_rays = cnt;
         const size_t sb = trace_scratch_bytes(cnt, src.max_reflections);
         scratch = dalloc(sb, s);
         trace_launch(scene->d, td, src, scratch, sb, s);
@@ -545,12 +553,9 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
         }
         chunk = std::min<int64_t>(chunk, (int64_t)(2147483646LL / (src->max_reflections + 1)));
         gbt_sum_args a = *args;
-        for (int64_t b = 0; b < N; b += chunk) {
-            gbt_source_desc cs = *src;
-            cs.ray_begin = b;
-            cs.ray_count = std::min<int64_t>(chunk, N - b);
-            gbt_trace_t *tr = make_trace(scene, cs, s);
-            a.accumulate = (b == 0) ? args->accumulate : 1;
+        if (chunk >= N) {
+            // one pass: trace and sum on the caller's stream
+            gbt_trace_t *tr = make_trace(scene, *src, s);
             try {
                 validate_sum(tr, &a);
                 const int splits = choose_splits(tr->d, a);
@@ -565,7 +570,72 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
             tr->d.work.release(s);
             dfree(tr->d.block, s);
             delete tr;
+            return;
         }
+        // Chunks of rays, double-buffered: chunk i is traced on a private stream into slot
+        // i % 2 while the caller's stream sums chunk i - 1 from the other slot; every sum
+        // accumulates into out in chunk order on the caller's stream.
+        validate_source(*src);
+        const int nslot = 2;
+        TraceDev slot[nslot];
+        void *scratch[nslot] = {nullptr, nullptr};
+        cudaStream_t ts = nullptr;
+        cudaEvent_t ready = nullptr, traced[nslot] = {nullptr, nullptr}, summed[nslot] = {nullptr, nullptr};
+        const size_t sb = trace_scratch_bytes(chunk, src->max_reflections);
+        // Frees are ordered on s after the last sum, and every trace precedes a sum on s; a
+        // failed call may leave a trace in flight, so that path waits for the trace stream.
+        auto cleanup = [&](bool failed) {
+            if (ts && failed) cudaStreamSynchronize(ts);
+            for (int k = 0; k < nslot; ++k) {
+                slot[k].work.release(s);
+                if (slot[k].block) dfree(slot[k].block, s);
+                if (scratch[k]) dfree(scratch[k], s);
+                if (traced[k]) cudaEventDestroy(traced[k]);
+                if (summed[k]) cudaEventDestroy(summed[k]);
+            }
+            if (ready) cudaEventDestroy(ready);
+            if (ts) cudaStreamDestroy(ts);
+        };
+        try {
+            GBT_CUDA(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+            for (int k = 0; k < nslot; ++k) {
+                GBT_CUDA(cudaEventCreateWithFlags(&traced[k], cudaEventDisableTiming));
+                GBT_CUDA(cudaEventCreateWithFlags(&summed[k], cudaEventDisableTiming));
+                alloc_trace_block(slot[k], scene, *src, chunk, s);
+                scratch[k] = dalloc(sb, s);
+                // the sum workspace for a full chunk, sized once
+                slot[k].ray_begin = 0;
+                slot[k].n_rays = chunk;
+                slot[k].work.ensure(sum_workspace_bytes(slot[k], a, choose_splits(slot[k], a)), s);
+            }
+            GBT_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+            GBT_CUDA(cudaEventRecord(ready, s));          // allocations above are ordered on s
+            GBT_CUDA(cudaStreamWaitEvent(ts, ready, 0));
+            const int64_t nchunks = (N + chunk - 1) / chunk;
+            for (int64_t i = 0; i < nchunks; ++i) {
+                const int k = (int)(i % nslot);
+                TraceDev &td = slot[k];
+                gbt_source_desc cs = *src;
+                cs.ray_begin = i * chunk;
+                cs.ray_count = std::min<int64_t>(chunk, N - cs.ray_begin);
+                if (i >= nslot) GBT_CUDA(cudaStreamWaitEvent(ts, summed[k], 0));   // slot free
+                td.ray_begin = cs.ray_begin;
+                td.n_rays = cs.ray_count;
+                td.n_seg_host = -1;
+                trace_launch(scene->d, td, cs, scratch[k], sb, ts);
+                GBT_CUDA(cudaEventRecord(traced[k], ts));
+                GBT_CUDA(cudaStreamWaitEvent(s, traced[k], 0));
+                a.accumulate = (i == 0) ? args->accumulate : 1;
+                const int splits = choose_splits(td, a);
+                sum_launch(td, scene->d, a, splits, td.work.ensure(sum_workspace_bytes(td, a, splits), s), s);
+                GBT_CUDA(cudaEventRecord(summed[k], s));
+            }
+            // the caller's stream is last: every trace was waited for by a sum on it
+        } catch (...) {
+            cleanup(true);
+            throw;
+        }
+        cleanup(false);
     });
 }
 

@@ -249,8 +249,15 @@ def test_chunked_solve_equals_single_pass(G):
     args = (sc, w.sources[0], r, list(w.freqs), list(w.beam_b[0]), gam)
     one = G.gbs_solve(*args, window=w.window).cpu().numpy()
     per_ray = (w.sources[0].max_reflections + 1) * (80 + 80 + 4 * 20 + 16)
+    # 8 chunks: chunk i + 1 is traced on a second stream while chunk i is summed
     many = G.gbs_solve(*args, window=w.window, max_device_bytes=per_ray * 1700).cpu().numpy()
     assert rel_l2(many, one) < 1e-6
+    # accumulators persist across chunks; the pre-cull lists are rebuilt per chunk
+    out = _dev(one)
+    G.gbs_solve(*args, window=w.window, max_device_bytes=per_ray * 1700, out=out, accumulate=True,
+                tile_cull=True)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), 2 * one) < 1e-6
     _, po = O.solve(w)
     assert rel_l2(one.astype(np.complex128), po) <= TOL_L2
 
