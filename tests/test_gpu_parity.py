@@ -373,3 +373,77 @@ def test_fp32_path_keeps_float_float_phase_precision(G, window):
                    window=window, cutoff=w.cutoff)
     assert rel_l2(p[:, idx], po) <= 1e-6
     assert rel_l2(pb[:, idx], po) <= 1e-6
+
+
+def test_single_beam_closed_form_on_gpu(G):
+    """One ray (explicit direction +x, no reflector), one segment: the GPU field at
+    receivers placed at arclength s and normal offset n against the closed form of the
+    summand, c = W (k b / 8 pi^2) exp(i k s + i k n^2 / (2 E)) / E with E = s - i b,
+    W = 4 pi for a one-ray fan.  FP32 bar 1e-5 relative to the on-axis amplitude."""
+    import torch
+    from paper_2501_13382_gb300.inputs import Scene, Source
+    c0, f, b = 343.0, 1000.0, 40.0
+    k = 2 * math.pi * f / c0
+    sc0 = Scene(c0, False, 0.0, 0, np.zeros((0, 3, 3)), np.zeros(0, np.int32), np.zeros(0, np.int32),
+                np.array([1.0], np.float32))
+    src = Source(np.array([1.5, -2.0, 3.0]), 1, 0, 2000.0)
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src, dirs=_dev(np.array([[1.0, 0.0, 0.0]]), torch.float64))
+    pts = []
+    for s in (0.5, 10.0, 55.5, 300.0, 1500.0):
+        wid = math.sqrt(2 * (s * s + b * b) / (k * b))
+        for n, ang in ((0.0, 0.0), (0.5 * wid, 0.3), (wid, 1.9), (2.0 * wid, -2.2)):
+            pts.append([1.5 + s, -2.0 + n * math.cos(ang), 3.0 + n * math.sin(ang)])
+    recv = np.array(pts, np.float32)
+    for window in (0, 1):
+        p = G.gbs_sum(tr, _dev(recv), [f], [b], _dev(np.array([1.0], np.float32)), window=window,
+                      cutoff=1e6)
+        torch.cuda.synchronize()
+        p = p.cpu().numpy()[0].astype(np.complex128)
+        x = recv.astype(np.float64) - np.array([1.5, -2.0, 3.0])
+        s = x[:, 0]
+        n2 = x[:, 1] ** 2 + x[:, 2] ** 2
+        E = s - 1j * b
+        want = 4 * math.pi * (k * b / (8 * math.pi ** 2)) * np.exp(1j * k * s + 1j * k * n2 / (2 * E)) / E
+        scale = np.abs(want).max()
+        assert np.abs(p - want).max() <= 1e-5 * scale
+
+
+def test_gpu_trace_csr_invariants(G):
+    """Offsets monotone, 1 <= segments per ray <= reflections + 1, each ray's segments
+    chained (a segment starts where the previous one ends, s0 accumulates L), total path
+    within the limit, directions unit length."""
+    w = I.city(n_rays=8192, n_recv_side=8)
+    src = w.sources[0]
+    sc = G.Scene(w.scene)
+    seg = G.Trace(sc, src).segments()
+    off = seg["ray_off"].cpu().numpy().astype(np.int64)
+    cnt = np.diff(off)
+    assert off[0] == 0 and np.all(cnt >= 1) and np.all(cnt <= src.max_reflections + 1)
+    o, t, L, s0 = (seg[k].cpu().numpy() for k in ("o", "t", "L", "s0"))
+    ray = seg["ray"].cpu().numpy()
+    assert np.array_equal(ray, np.repeat(np.arange(len(cnt)), cnt))
+    assert np.allclose(np.linalg.norm(t, axis=1), 1.0, atol=1e-12)
+    first = off[:-1]
+    assert np.all(s0[first] == 0.0)
+    nxt = np.setdiff1d(np.arange(off[-1]), first)          # segments after the first of a ray
+    end = o[nxt - 1] + L[nxt - 1, None] * t[nxt - 1]
+    assert np.allclose(o[nxt], end, rtol=0, atol=1e-9 * max(1.0, np.abs(o).max()))
+    assert np.allclose(s0[nxt], s0[nxt - 1] + L[nxt - 1], rtol=1e-14, atol=1e-9)
+    last = off[1:] - 1
+    assert np.all(s0[last] + L[last] <= src.max_path * (1 + 1e-12))
+
+
+@pytest.mark.parametrize("chunks", [2, 7, 64])
+def test_forced_chunk_counts_equal_one_pass(G, chunks):
+    import torch
+    w = I.city(n_rays=6400, n_recv_side=24)
+    sc = G.Scene(w.scene)
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    args = (sc, w.sources[0], r, list(w.freqs), list(w.beam_b[0]), gam)
+    one = G.gbs_solve(*args, window=w.window).cpu().numpy()
+    per_ray = (w.sources[0].max_reflections + 1) * (80 + 80 + 4 * 20 + 16)
+    rays = -(-w.sources[0].n_rays // chunks)
+    many = G.gbs_solve(*args, window=w.window, max_device_bytes=per_ray * rays).cpu().numpy()
+    assert rel_l2(many, one) < 1e-6
