@@ -1709,6 +1709,78 @@ __global__ void bitonic_step(unsigned long long *keys, int64_t npad, int64_t j, 
     }
 }
 
+// ---- stable LSD radix sort of the (Morton code, index) keys on the code's 30 bits,
+// 8 bits per pass: the same order as sorting the whole keys, in O(n) per pass
+constexpr int kRadixBlock = 1024;   // keys per block, one per thread
+constexpr int kRadixBuckets = 256;
+
+__device__ __forceinline__ unsigned int radix_digit(unsigned long long key, int shift)
+{
+    return (unsigned int)(key >> (32 + shift)) & (kRadixBuckets - 1);
+}
+
+// counts[d * nblocks + block]: keys of the block with digit d
+__global__ void __launch_bounds__(kRadixBlock) radix_count_kernel(const unsigned long long *keys,
+                                                                  int64_t n, int shift,
+                                                                  uint32_t *counts, int64_t nblocks)
+{
+    __shared__ uint32_t c[kRadixBuckets];
+    if (threadIdx.x < kRadixBuckets) c[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kRadixBlock + threadIdx.x;
+    if (i < n) atomicAdd(&c[radix_digit(keys[i], shift)], 1u);
+    __syncthreads();
+    if (threadIdx.x < kRadixBuckets) counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = c[threadIdx.x];
+}
+
+// One block: exclusive scan of the counts in place (digit-major, then block).
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *counts, int64_t total)
+{
+    __shared__ int64_t ws[33];
+    int64_t carry = 0;
+    for (int64_t base = 0; base < total; base += 1024) {
+        const int64_t c = base + threadIdx.x;
+        const int64_t v = c < total ? counts[c] : 0;
+        int64_t excl;
+        const int64_t tot = block_scan_1024(v, excl, ws);
+        if (c < total) counts[c] = (uint32_t)(carry + excl);
+        carry += tot;
+    }
+}
+
+// Stable scatter: rank within the warp from the lanes holding the same digit, then the
+// counts of earlier warps of the block, then the scanned offset of (digit, block).
+__global__ void __launch_bounds__(kRadixBlock) radix_scatter_kernel(const unsigned long long *in,
+                                                                    unsigned long long *out,
+                                                                    int64_t n, int shift,
+                                                                    const uint32_t *offs,
+                                                                    int64_t nblocks)
+{
+    __shared__ uint32_t wc[kRadixBlock / 32][kRadixBuckets];
+    for (int q = threadIdx.x; q < (kRadixBlock / 32) * kRadixBuckets; q += kRadixBlock)
+        (&wc[0][0])[q] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kRadixBlock + threadIdx.x;
+    const bool ok = i < n;
+    const unsigned long long key = ok ? in[i] : 0ull;
+    const unsigned int d = ok ? radix_digit(key, shift) : (unsigned int)kRadixBuckets;
+    const unsigned int same = __match_any_sync(0xffffffffu, d);
+    const unsigned int rank = __popc(same & ((1u << lane) - 1u));
+    if (ok && rank == 0) wc[wid][d] = __popc(same);
+    __syncthreads();
+    if (threadIdx.x < kRadixBuckets) {
+        uint32_t run = 0u;
+        for (int w = 0; w < kRadixBlock / 32; ++w) {
+            const uint32_t c = wc[w][threadIdx.x];
+            wc[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (ok) out[offs[(int64_t)d * nblocks + blockIdx.x] + wc[wid][d] + rank] = key;
+}
+
 __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t *order)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -2066,31 +2138,37 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
 
 size_t recv_order_scratch_bytes(int64_t n)
 {
-    int64_t npad = 1;
-    while (npad < n) npad <<= 1;
-    return align_up((size_t)npad * sizeof(unsigned long long), 256) + 256;
+    const int64_t nblocks = (n + kRadixBlock - 1) / kRadixBlock;
+    return 2 * align_up((size_t)n * sizeof(unsigned long long), 256) +
+           align_up((size_t)kRadixBuckets * nblocks * sizeof(uint32_t), 256) + 256;
 }
 
 void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scratch, cudaStream_t s)
 {
     if (n <= 0) return;
-    int64_t npad = 1;
-    while (npad < n) npad <<= 1;
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch);
-    unsigned int *bb = reinterpret_cast<unsigned int *>(
-        static_cast<char *>(scratch) + align_up((size_t)npad * sizeof(unsigned long long), 256));
+    const int64_t nblocks = (n + kRadixBlock - 1) / kRadixBlock;
+    char *w = static_cast<char *>(scratch);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(w);
+    w += align_up((size_t)n * sizeof(unsigned long long), 256);
+    unsigned long long *tmp = reinterpret_cast<unsigned long long *>(w);
+    w += align_up((size_t)n * sizeof(unsigned long long), 256);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(w);
+    w += align_up((size_t)kRadixBuckets * nblocks * sizeof(uint32_t), 256);
+    unsigned int *bb = reinterpret_cast<unsigned int *>(w);
     GBT_CUDA(cudaMemsetAsync(bb, 0xff, 3 * sizeof(unsigned int), s));
     GBT_CUDA(cudaMemsetAsync(bb + 3, 0x00, 3 * sizeof(unsigned int), s));
     bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(recv, n, bb);
     note_launches(1);
-    const unsigned g = (unsigned)((npad + 255) / 256);
-    morton_kernel<<<g, 256, 0, s>>>(recv, n, npad, bb, keys);
+    morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(recv, n, n, bb, keys);
     note_launches(1);
-    for (int64_t k = 2; k <= npad; k <<= 1)
-        for (int64_t j = k >> 1; j > 0; j >>= 1) {
-            bitonic_step<<<g, 256, 0, s>>>(keys, npad, j, k);
-            note_launches(1);
-        }
+    for (int shift = 0; shift < 30; shift += 8) {   // 30-bit codes: four passes
+        radix_count_kernel<<<(unsigned)nblocks, kRadixBlock, 0, s>>>(keys, n, shift, counts, nblocks);
+        radix_scan_kernel<<<1, 1024, 0, s>>>(counts, (int64_t)kRadixBuckets * nblocks);
+        radix_scatter_kernel<<<(unsigned)nblocks, kRadixBlock, 0, s>>>(keys, tmp, n, shift, counts,
+                                                                         nblocks);
+        note_launches(3);
+        std::swap(keys, tmp);
+    }
     extract_order<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, order);
     note_launches(1);
     GBT_CUDA(cudaGetLastError());

@@ -174,9 +174,8 @@ def test_many_tiles_every_receiver_against_oracle(G):
     assert G.gbt_launches_read(reset=True) == 5    # tracer, 3 scan passes, compaction
     r = _dev(recv, torch.float32)
     order = G.recv_order(r)
-    lg = int(np.ceil(np.log2(recv.shape[0])))
-    # bounding box, Morton codes, bitonic passes, extraction
-    assert G.gbt_launches_read(reset=True) == 3 + lg * (lg + 1) // 2
+    # bounding box, Morton codes, four radix passes (count, scan, scatter), extraction
+    assert G.gbt_launches_read(reset=True) == 3 + 4 * 3
     p = G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[0]), _dev(w.scene.gamma, torch.float32),
                   order=order, window=w.window, cutoff=w.cutoff)
     # prepass, tile order (ball, weight, rank), pair kernel, merge
