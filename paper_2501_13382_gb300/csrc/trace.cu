@@ -64,6 +64,7 @@ struct TraceParams {
     int64_t n_clusters;
     int chunk;                 // triangles per shared-memory chunk (a multiple of kTriCluster)
     int64_t strip;             // Fibonacci fan: lattice step between a warp's rays (0: none)
+    unsigned long long *counter;   // resident scene: next strip of 32 ray slots (zeroed)
     int64_t stride;            // max_refl + 1
     double *po, *pt, *pL, *ps0;
     int32_t *pbmat, *phit, *cnt;
@@ -125,6 +126,136 @@ __device__ __forceinline__ void load_tri_chunk(double *st, float *sbox, float *s
         sface[idx] = p.face ? p.face[base + idx] : (int32_t)(base + idx);
 }
 
+// Ray index of thread slot tid.  On the Fibonacci lattice ray g and ray g + F (F a
+// Fibonacci number near sqrt(N)) are neighbours, so a warp takes rays i0, i0 + F, ...,
+// i0 + 31 F: the 32 x F index blocks are read transposed and a warp's rays meet the
+// same boxes and triangles.  Outputs stay at each ray's own index; the tail past whole
+// blocks keeps its order.
+__device__ __forceinline__ int64_t ray_of_slot(const TraceParams &p, int64_t tid)
+{
+    if (p.strip > 0) {
+        const int64_t blk = 32 * p.strip;
+        if (tid < p.n_rays / blk * blk) {
+            const int64_t r = tid % blk;
+            return tid - r + (r & 31) * p.strip + (r >> 5);
+        }
+    }
+    return tid;
+}
+
+// Take-off direction of ray i (explicit, or the Fibonacci fan of the whole source).
+__device__ __forceinline__ void ray_direction(const TraceParams &p, int64_t i, double d[3])
+{
+    if (p.dirs) {
+        d[0] = p.dirs[3 * i]; d[1] = p.dirs[3 * i + 1]; d[2] = p.dirs[3 * i + 2];
+    } else {
+        const int64_t g = p.ray_begin + i;
+        const double golden = kPi * (3.0 - sqrt(5.0));
+        double z = 1.0 - (2.0 * (double)g + 1.0) / (double)p.n_fan;
+        double r = sqrt(1.0 - z * z);
+        double phi = (double)g * golden;
+        d[0] = r * cos(phi);
+        d[1] = r * sin(phi);
+        d[2] = z;
+    }
+}
+
+// Nearest hit among the triangles of one staged chunk (base .. base + count), with
+// tbest / best carrying the nearest so far.  Clusters in index order; a cluster whose
+// (expanded) box the ray misses, or enters only beyond the best hit so far, holds no
+// hit that could win, and likewise each triangle's own padded box before its FP64 test.
+__device__ __forceinline__ void nearest_in_chunk(const double o[3], const double d[3], int last_face,
+                                                 const double *st, const float *stbox,
+                                                 const float *sbox, const int32_t *sface,
+                                                 int64_t base, int count, double &tbest, int &best)
+{
+    const float of0 = (float)o[0], of1 = (float)o[1], of2 = (float)o[2];
+    const float df0 = (float)d[0], df1 = (float)d[1], df2 = (float)d[2];
+    const float id0 = 1.0f / df0, id1 = 1.0f / df1, id2 = 1.0f / df2;
+    const int nc = (count + kTriCluster - 1) / kTriCluster;
+    for (int c = 0; c < nc; ++c) {
+        const float *bx = sbox + 6 * c;
+        // upper bound: the best hit so far, widened like the boxes
+        float tn = 0.0f, tf = (float)tbest * 1.000001f + 1e-3f;
+        bool hit_box = slab(of0, df0, id0, bx[0], bx[3], tn, tf);
+        hit_box = hit_box && slab(of1, df1, id1, bx[1], bx[4], tn, tf);
+        hit_box = hit_box && slab(of2, df2, id2, bx[2], bx[5], tn, tf);
+        if (!hit_box || tn > tf) continue;
+        const int k1 = min(count, (c + 1) * kTriCluster);
+        for (int k = c * kTriCluster; k < k1; ++k) {
+            if (sface[k] == last_face) continue;
+            const float *tb = stbox + 6 * k;
+            float un = 0.0f, uf = (float)tbest * 1.000001f + 1e-3f;
+            bool hit_tri = slab(of0, df0, id0, tb[0], tb[3], un, uf);
+            hit_tri = hit_tri && slab(of1, df1, id1, tb[1], tb[4], un, uf);
+            hit_tri = hit_tri && slab(of2, df2, id2, tb[2], tb[5], un, uf);
+            if (!hit_tri || un > uf) continue;
+            double t = ray_triangle(o, d, st + 12 * k);
+            if (t > kTMin && t < tbest) { tbest = t; best = (int)(base + k + 1); }
+        }
+    }
+}
+
+// Ground plane candidate (best 0) before any triangle.
+__device__ __forceinline__ void nearest_ground(const TraceParams &p, const double o[3],
+                                               const double d[3], int last_face, double &tbest,
+                                               int &best)
+{
+    if (p.ground && last_face != -2 && d[2] != 0.0) {
+        double t = (p.ground_z - o[2]) / d[2];
+        if (t > kTMin && t < tbest) { tbest = t; best = 0; }
+    }
+}
+
+// Writes the segment from o along d ending at the nearest hit (or the path limit) and,
+// unless the ray ends there, reflects it.  Returns whether the ray continues.
+__device__ __forceinline__ bool record_and_reflect(const TraceParams &p, int64_t i, double o[3],
+                                                   double d[3], double &s0, int &last_face,
+                                                   int &bmat, int &nref, int &nseg, double tbest,
+                                                   int best)
+{
+    const double remaining = p.max_path - s0;
+    const int64_t row = i * p.stride + nseg;
+    p.po[3 * row + 0] = o[0]; p.po[3 * row + 1] = o[1]; p.po[3 * row + 2] = o[2];
+    p.pt[3 * row + 0] = d[0]; p.pt[3 * row + 1] = d[1]; p.pt[3 * row + 2] = d[2];
+    p.ps0[row] = s0;
+    p.pbmat[row] = bmat;
+    ++nseg;
+    if (best < 0 || tbest >= remaining) {
+        p.pL[row] = remaining;
+        p.phit[row] = -1;
+        return false;
+    }
+    p.pL[row] = tbest;
+    p.phit[row] = best;
+    if (nref == p.max_refl) return false;
+    double n0, n1, n2;
+    int face, mat;
+    if (best == 0) {
+        n0 = 0.0; n1 = 0.0; n2 = 1.0;
+        face = -2; mat = p.ground_mat;
+    } else {
+        const int64_t k = best - 1;
+        n0 = p.tri[12 * k + 9]; n1 = p.tri[12 * k + 10]; n2 = p.tri[12 * k + 11];
+        face = p.face ? p.face[k] : (int)k;
+        mat = p.mat[k];
+    }
+    o[0] = o[0] + tbest * d[0];
+    o[1] = o[1] + tbest * d[1];
+    o[2] = o[2] + tbest * d[2];
+    double dn = d[0] * n0 + d[1] * n1 + d[2] * n2;
+    d[0] = d[0] - 2.0 * dn * n0;
+    d[1] = d[1] - 2.0 * dn * n1;
+    d[2] = d[2] - 2.0 * dn * n2;
+    s0 = s0 + tbest;
+    last_face = face;
+    bmat = mat;
+    ++nref;
+    return true;
+}
+
+// Scene too large for one shared-memory chunk: the block streams the triangle chunks
+// for every bounce, so its rays advance bounce by bounce together.
 __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
 {
     extern __shared__ double smem[];
@@ -134,143 +265,69 @@ __global__ void __launch_bounds__(kTraceBlock) trace_kernel(TraceParams p)
     float *sbox = stbox + (size_t)chunk * 6;                        // clusters * 6
     int32_t *sface = reinterpret_cast<int32_t *>(sbox + (chunk / kTriCluster) * 6);
 
-    // On the Fibonacci lattice ray g and ray g + F (F a Fibonacci number near sqrt(N))
-    // are neighbours, so a warp takes rays i0, i0 + F, ..., i0 + 31 F: the 32 x F index
-    // blocks are read transposed and a warp's rays meet the same boxes and triangles.
-    // Outputs stay at each ray's own index; the tail past whole blocks keeps its order.
-    const int64_t tid = blockIdx.x * (int64_t)kTraceBlock + threadIdx.x;
-    int64_t i = tid;
-    if (p.strip > 0) {
-        const int64_t blk = 32 * p.strip;
-        if (tid < p.n_rays / blk * blk) {
-            const int64_t r = tid % blk;
-            i = tid - r + (r & 31) * p.strip + (r >> 5);
-        }
-    }
+    const int64_t i = ray_of_slot(p, blockIdx.x * (int64_t)kTraceBlock + threadIdx.x);
     const bool active = i < p.n_rays;
     double o[3] = {p.src[0], p.src[1], p.src[2]};
     double d[3] = {0.0, 0.0, 1.0};
-    if (active) {
-        if (p.dirs) {
-            d[0] = p.dirs[3 * i]; d[1] = p.dirs[3 * i + 1]; d[2] = p.dirs[3 * i + 2];
-        } else {
-            // Fibonacci sphere, ray index g in the whole fan
-            const int64_t g = p.ray_begin + i;
-            const double golden = kPi * (3.0 - sqrt(5.0));
-            double z = 1.0 - (2.0 * (double)g + 1.0) / (double)p.n_fan;
-            double r = sqrt(1.0 - z * z);
-            double phi = (double)g * golden;
-            d[0] = r * cos(phi);
-            d[1] = r * sin(phi);
-            d[2] = z;
-        }
-    }
+    if (active) ray_direction(p, i, d);
     double s0 = 0.0;
-    int last_face = -1;
-    int bmat = -1;
-    int nref = 0, nseg = 0;
+    int last_face = -1, bmat = -1, nref = 0, nseg = 0;
     bool alive = active;
-
     const int64_t nchunk = (p.n_tri + chunk - 1) / chunk;
-    const bool resident = nchunk <= 1;
-    if (resident && p.n_tri > 0) {
-        load_tri_chunk(st, sbox, stbox, sface, p, 0, (int)p.n_tri);
-    }
-    __syncthreads();
-
     for (int bounce = 0; bounce <= p.max_refl; ++bounce) {
         double tbest = INFINITY;
         int best = -1;
-        if (alive && p.ground && last_face != -2 && d[2] != 0.0) {
-            double t = (p.ground_z - o[2]) / d[2];
-            if (t > kTMin && t < tbest) { tbest = t; best = 0; }
-        }
+        if (alive) nearest_ground(p, o, d, last_face, tbest, best);
         for (int64_t c = 0; c < nchunk; ++c) {
             const int64_t base = c * chunk;
             const int count = (int)min((int64_t)chunk, p.n_tri - base);
-            if (!resident) {
-                __syncthreads();
-                load_tri_chunk(st, sbox, stbox, sface, p, base, count);
-                __syncthreads();
-            }
-            if (alive) {
-                // clusters in index order; a cluster whose (expanded) box the ray misses,
-                // or enters only beyond the best hit so far, holds no hit that could win
-                const float of0 = (float)o[0], of1 = (float)o[1], of2 = (float)o[2];
-                const float df0 = (float)d[0], df1 = (float)d[1], df2 = (float)d[2];
-                const float id0 = 1.0f / df0, id1 = 1.0f / df1, id2 = 1.0f / df2;
-                const int nc = (count + kTriCluster - 1) / kTriCluster;
-                for (int c = 0; c < nc; ++c) {
-                    const float *bx = sbox + 6 * c;
-                    // upper bound: the best hit so far, widened like the boxes
-                    float tn = 0.0f, tf = (float)tbest * 1.000001f + 1e-3f;
-                    bool hit_box = slab(of0, df0, id0, bx[0], bx[3], tn, tf);
-                    hit_box = hit_box && slab(of1, df1, id1, bx[1], bx[4], tn, tf);
-                    hit_box = hit_box && slab(of2, df2, id2, bx[2], bx[5], tn, tf);
-                    if (!hit_box || tn > tf) continue;
-                    const int k1 = min(count, (c + 1) * kTriCluster);
-                    for (int k = c * kTriCluster; k < k1; ++k) {
-                        if (sface[k] == last_face) continue;
-                        // the triangle's own padded box first: the FP64 test only where it
-                        // could hit before the best hit so far
-                        const float *tb = stbox + 6 * k;
-                        float un = 0.0f, uf = (float)tbest * 1.000001f + 1e-3f;
-                        bool hit_tri = slab(of0, df0, id0, tb[0], tb[3], un, uf);
-                        hit_tri = hit_tri && slab(of1, df1, id1, tb[1], tb[4], un, uf);
-                        hit_tri = hit_tri && slab(of2, df2, id2, tb[2], tb[5], un, uf);
-                        if (!hit_tri || un > uf) continue;
-                        double t = ray_triangle(o, d, st + 12 * k);
-                        if (t > kTMin && t < tbest) { tbest = t; best = (int)(base + k + 1); }
-                    }
-                }
-            }
+            __syncthreads();
+            load_tri_chunk(st, sbox, stbox, sface, p, base, count);
+            __syncthreads();
+            if (alive) nearest_in_chunk(o, d, last_face, st, stbox, sbox, sface, base, count, tbest, best);
         }
-        if (alive) {
-            const double remaining = p.max_path - s0;
-            const int64_t row = i * p.stride + nseg;
-            p.po[3 * row + 0] = o[0]; p.po[3 * row + 1] = o[1]; p.po[3 * row + 2] = o[2];
-            p.pt[3 * row + 0] = d[0]; p.pt[3 * row + 1] = d[1]; p.pt[3 * row + 2] = d[2];
-            p.ps0[row] = s0;
-            p.pbmat[row] = bmat;
-            ++nseg;
-            if (best < 0 || tbest >= remaining) {
-                p.pL[row] = remaining;
-                p.phit[row] = -1;
-                alive = false;
-            } else {
-                p.pL[row] = tbest;
-                p.phit[row] = best;
-                if (nref == p.max_refl) {
-                    alive = false;
-                } else {
-                    double n0, n1, n2;
-                    int face, mat;
-                    if (best == 0) {
-                        n0 = 0.0; n1 = 0.0; n2 = 1.0;
-                        face = -2; mat = p.ground_mat;
-                    } else {
-                        const int64_t k = best - 1;
-                        n0 = p.tri[12 * k + 9]; n1 = p.tri[12 * k + 10]; n2 = p.tri[12 * k + 11];
-                        face = p.face ? p.face[k] : (int)k;
-                        mat = p.mat[k];
-                    }
-                    o[0] = o[0] + tbest * d[0];
-                    o[1] = o[1] + tbest * d[1];
-                    o[2] = o[2] + tbest * d[2];
-                    double dn = d[0] * n0 + d[1] * n1 + d[2] * n2;
-                    d[0] = d[0] - 2.0 * dn * n0;
-                    d[1] = d[1] - 2.0 * dn * n1;
-                    d[2] = d[2] - 2.0 * dn * n2;
-                    s0 = s0 + tbest;
-                    last_face = face;
-                    bmat = mat;
-                    ++nref;
-                }
-            }
-        }
+        if (alive) alive = record_and_reflect(p, i, o, d, s0, last_face, bmat, nref, nseg, tbest, best);
         if (!__syncthreads_or(alive)) break;
     }
     if (active) p.cnt[i] = nseg;
+}
+
+// Scene resident in shared memory: after the one load, every warp takes strips of 32
+// ray slots from an atomic counter and traces each ray to its end on its own, with no
+// block barrier per bounce, so a long ray delays only its own warp.
+__global__ void __launch_bounds__(kTraceBlock) trace_resident_kernel(TraceParams p)
+{
+    extern __shared__ double smem[];
+    const int chunk = p.chunk;
+    double *st = smem;
+    float *stbox = reinterpret_cast<float *>(smem + (size_t)chunk * 12);
+    float *sbox = stbox + (size_t)chunk * 6;
+    int32_t *sface = reinterpret_cast<int32_t *>(sbox + (chunk / kTriCluster) * 6);
+    if (p.n_tri > 0) load_tri_chunk(st, sbox, stbox, sface, p, 0, (int)p.n_tri);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int64_t q = 0;
+        if (lane == 0) q = atomicAdd(p.counter, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q * 32 >= p.n_rays) break;
+        const int64_t i = ray_of_slot(p, q * 32 + lane);
+        if (i >= p.n_rays) continue;
+        double o[3] = {p.src[0], p.src[1], p.src[2]};
+        double d[3];
+        ray_direction(p, i, d);
+        double s0 = 0.0;
+        int last_face = -1, bmat = -1, nref = 0, nseg = 0;
+        for (bool alive = true; alive;) {
+            double tbest = INFINITY;
+            int best = -1;
+            nearest_ground(p, o, d, last_face, tbest, best);
+            if (p.n_tri > 0)
+                nearest_in_chunk(o, d, last_face, st, stbox, sbox, sface, 0, (int)p.n_tri, tbest, best);
+            alive = record_and_reflect(p, i, o, d, s0, last_face, bmat, nref, nseg, tbest, best);
+        }
+        p.cnt[i] = nseg;
+    }
 }
 
 // ---- exclusive scan of per-ray counts (3 phases, deterministic) ----
@@ -417,6 +474,7 @@ size_t trace_scratch_bytes(int64_t n_rays, int max_refl)
     b += align_up(cap * sizeof(int32_t), 256) * 2;      // pbmat, phit
     b += align_up((size_t)n_rays * sizeof(int32_t), 256);   // cnt
     b += align_up((nb + 1) * sizeof(int32_t), 256);     // block sums
+    b += 256;                                           // strip counter
     return b;
 }
 
@@ -471,6 +529,7 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     const int64_t per = (int64_t)kScanBlock * kScanItems;
     const int64_t nb = (n + per - 1) / per;
     int32_t *bsum = reinterpret_cast<int32_t *>(take((size_t)(nb + 1) * sizeof(int32_t)));
+    p.counter = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
     if ((size_t)(w - static_cast<char *>(scratch)) > scratch_bytes)
         fail(GBT_ERR_INVALID_ARG, "trace scratch too small");
 
@@ -483,9 +542,25 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     if (!attr_set) {
         GBT_CUDA(cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)chunk_smem(kTriChunk)));
+        GBT_CUDA(cudaFuncSetAttribute(trace_resident_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)chunk_smem(kTriChunk)));
         attr_set = true;
     }
-    trace_kernel<<<(unsigned)((n + kTraceBlock - 1) / kTraceBlock), kTraceBlock, smem, s>>>(p);
+    if (sd.n_tri <= p.chunk) {
+        // resident scene: a persistent grid whose warps take strips of rays
+        int per_sm = 0;
+        GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_resident_kernel,
+                                                               kTraceBlock, smem));
+        const int64_t strips = (n + 31) / 32;
+        const int64_t blocks = std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * num_sms(),
+                                 (strips + kTraceBlock / 32 - 1) / (kTraceBlock / 32)));
+        GBT_CUDA(cudaMemsetAsync(p.counter, 0, sizeof(unsigned long long), s));
+        trace_resident_kernel<<<(unsigned)blocks, kTraceBlock, smem, s>>>(p);
+    } else {
+        trace_kernel<<<(unsigned)((n + kTraceBlock - 1) / kTraceBlock), kTraceBlock, smem, s>>>(p);
+    }
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
 
