@@ -86,3 +86,24 @@ def test_batch_graph_replay_sees_new_gamma(G, form):
     po = O.gbs_sum(otr, recv_np, freqs, b, w.scene.c, new_gamma, window=w.window)
     got = batch.outputs[1].cpu().numpy().astype(np.complex128)
     assert rel_l2(got, po) < 1e-4
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_batch_with_tile_cull_equals_per_instance_sums(G, form):
+    """Both batch forms with the pre-cull (per-instance tile lists in one workspace) against
+    one pre-culled gbt_sum per instance."""
+    import torch
+    w, sc, gam, insts, _ = _batch_setup(G, n_src=4, side=48, seed=8)
+    batch = G.Batch(insts, window=w.window, use_graph=True, form=form, tile_cull=True)
+    for rep in range(2):
+        batch.submit()
+        torch.cuda.synchronize()
+        G.gbt_sync()
+        for d, out in zip(batch.instances, batch.outputs):
+            ref = G.gbs_sum(d["trace"], d["recv"], d["freqs"], d["beam_b"], gam, order=d["order"],
+                            window=w.window, tile_cull=True)
+            torch.cuda.synchronize()
+            e = rel_l2(out.cpu().numpy().astype(np.complex128),
+                       ref.cpu().numpy().astype(np.complex128))
+            assert e < 1e-6, (rep, e)
+    batch.close()
