@@ -162,6 +162,9 @@ gbt_status gbt_trace_destroy(gbt_trace_t *trace);
  * F32 precision: FP32 arithmetic with float-float arclength and phase
  * reduction, FP32 MUFU exp/sin/cos, compensated per-receiver accumulation;
  * relative L2 error against an FP64 evaluation is about 1e-6..1e-5.
+ * With more than 8 frequencies the F32 path runs one pair launch per group of
+ * at most 8 (frequencies sorted by value when every b_f is equal, otherwise in
+ * the given order); each group costs a full pass over the pairs.
  * `out` (n_freq * n_recv complex64, frequency-major) is overwritten, or added
  * to when `accumulate` is 1.  Scratch comes from the trace's workspace, so
  * calls on one trace must not overlap on different streams. */
@@ -291,7 +294,9 @@ gbt_status gbt_launches_read(int64_t *launches, int32_t reset);
 /* Work statistics of one gbt_sum call (same arguments): number of
  * (receiver, segment) pairs, pairs kept by the frequency-union prefilter, and
  * (receiver, segment, frequency) triples whose beam contributes (window and
- * cutoff met).  Runs a counting variant of the F32 kernel; synchronises. */
+ * cutoff met).  Runs a counting variant of the F32 kernel; synchronises.
+ * With more than 8 frequencies, pairs_prefiltered and pairs_tested add up the
+ * counts of each group of at most 8 frequencies (see gbt_sum). */
 typedef struct gbt_sum_stats {
     int64_t n_segments;
     int64_t pairs;

@@ -1829,34 +1829,49 @@ void launch_fwd_nf(const FwdParams &p, cudaStream_t s, bool timed = true)
     else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, s, timed);
     else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, s, timed);
     else if (p.nf <= 6) launch_fwd<6, WINDOW>(p, s, timed);
-    else launch_fwd<8, WINDOW>(p, s, timed);
+    else if (p.nf <= 8) launch_fwd<8, WINDOW>(p, s, timed);
+    else fail(GBT_ERR_UNSUPPORTED, "pair kernel launched with more than 8 frequencies");
 }
 
-// Kernel parameters shared by the forward, counting and adjoint launches.
-FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
-                                  const float *rec)
+// Frequency processing order: when every b is equal, sorted by k so that the kept
+// frequencies of a pair form a prefix (wider beams first); otherwise as given.
+// perm[slot] = user frequency index.  Returns whether b is uniform.
+bool freq_order(const gbt_sum_args &a, int (&perm)[GBT_MAX_FREQ])
 {
-    FwdParams q{};
-    q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
-    q.n_seg_ptr = td.ray_off + td.n_rays;
-    q.rec = rec;
-    q.nf = a.n_freq;
-    q.cutoff = (float)a.cutoff;
-    q.tile_cull = a.tile_cull ? 1 : 0;
-    // frequency order: when every b is equal, sort by k so that the kept
-    // frequencies of a pair form a prefix (wider beams first)
-    int perm[GBT_MAX_FREQ];
-    for (int f = 0; f < a.n_freq; ++f) perm[f] = f;
+    for (int f = 0; f < GBT_MAX_FREQ; ++f) perm[f] = f;
     bool uniform = true;
     for (int f = 1; f < a.n_freq; ++f) uniform = uniform && a.beam_b[f] == a.beam_b[0];
     if (uniform)
         std::stable_sort(perm, perm + a.n_freq,
                          [&](int x, int y) { return a.freq_hz[x] < a.freq_hz[y]; });
-    q.uniform_b = uniform ? 1 : 0;
+    return uniform;
+}
+
+// Frequencies go through the pair kernel in groups of at most kGroupFreq slots of
+// the processing order; the kernel is instantiated for up to that many.
+constexpr int kGroupFreq = 8;
+
+int freq_groups(const gbt_sum_args &a) { return (a.n_freq + kGroupFreq - 1) / kGroupFreq; }
+
+// Kernel parameters shared by the forward, counting and adjoint launches, for the
+// frequency group that starts at processing slot g0 (fperm maps the group's slots to
+// user frequency indices).
+FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
+                           const float *rec, int g0 = 0)
+{
+    FwdParams q{};
+    q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
+    q.n_seg_ptr = td.ray_off + td.n_rays;
+    q.rec = rec;
+    q.nf = std::min(kGroupFreq, a.n_freq - g0);
+    q.cutoff = (float)a.cutoff;
+    q.tile_cull = a.tile_cull ? 1 : 0;
+    int perm[GBT_MAX_FREQ];
+    q.uniform_b = freq_order(a, perm) ? 1 : 0;
     double amin = 1e300, bmax = 0.0;
     for (int f = 0; f < GBT_MAX_FREQ; ++f) q.fperm[f] = f;
-    for (int f = 0; f < a.n_freq; ++f) {
-        const int g = perm[f];
+    for (int f = 0; f < q.nf; ++f) {
+        const int g = perm[g0 + f];
         q.fperm[f] = g;
         const double K = a.freq_hz[g] / sd.c;       // turns per metre
         const double k = 2.0 * kPi * K;
@@ -2084,55 +2099,60 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         GBT_CUDA(cudaGetLastError());
     }
 
-    const int64_t nout = (int64_t)a.n_freq * a.n_recv;
-    int fperm[GBT_MAX_FREQ];
-    for (int f = 0; f < GBT_MAX_FREQ; ++f) fperm[f] = f;
-    if (a.n_recv > 0) {
-        if (a.precision == GBT_PRECISION_F64) {
-            F64Params q{};
-            q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
-            q.n_seg_ptr = n_seg_ptr;
-            q.o = td.o; q.t = td.t; q.L = td.L; q.s0 = td.s0; q.amp = amp64;
-            q.nf = a.n_freq;
-            q.cutoff = a.cutoff;
-            for (int f = 0; f < a.n_freq; ++f) {
-                q.k[f] = 2.0 * kPi * a.freq_hz[f] / sd.c;
-                q.b[f] = a.beam_b[f];
-            }
-            q.splits = splits;
-            q.partial = reinterpret_cast<double2 *>(partial);
-            dim3 grid((unsigned)((a.n_recv + kThreads64 - 1) / kThreads64), (unsigned)splits);
-            if (a.window == GBT_WINDOW_LINE)
-                gbs_fwd_f64_kernel<GBT_WINDOW_LINE><<<grid, kThreads64, 0, s>>>(q);
-            else
-                gbs_fwd_f64_kernel<GBT_WINDOW_SEGMENT><<<grid, kThreads64, 0, s>>>(q);
-            note_launches(1);
-            GBT_CUDA(cudaGetLastError());
-        } else {
-            FwdParams q = make_pair_params(td, sd, a, rec);
-            q.splits = splits;
-            q.partial = reinterpret_cast<float4 *>(partial);
-            q.stats = stats;
-            q.n_items = cta_tiles(a.n_recv) * kTileWarps * splits;
-            q.work_counter = counter;
-            tile_prep_launch(q, a.window, tile_ws_layout(order_ws, a.n_recv, td.capacity, a.tile_cull != 0), s);
-            if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
-            else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
-            if (stats) return;
-            for (int f = 0; f < a.n_freq; ++f) fperm[f] = q.fperm[f];
-        }
-        ReduceParams rp{};
-        rp.n = nout;
-        rp.n_recv = a.n_recv;
-        for (int f = 0; f < GBT_MAX_FREQ; ++f) rp.perm[f] = fperm[f];
-        rp.splits = splits;
-        rp.p32 = a.precision == GBT_PRECISION_F64 ? nullptr : reinterpret_cast<float4 *>(partial);
-        rp.p64 = a.precision == GBT_PRECISION_F64 ? reinterpret_cast<double2 *>(partial) : nullptr;
-        rp.out = reinterpret_cast<float2 *>(a.out);
-        rp.accumulate = a.accumulate;
-        reduce_kernel<<<(unsigned)((nout + 255) / 256), 256, 0, s>>>(rp);
+    if (a.n_recv <= 0) return;
+    ReduceParams rp{};
+    rp.n_recv = a.n_recv;
+    rp.out = reinterpret_cast<float2 *>(a.out);
+    rp.accumulate = a.accumulate;
+    rp.splits = splits;
+    auto reduce = [&]() {
+        reduce_kernel<<<(unsigned)((rp.n + 255) / 256), 256, 0, s>>>(rp);
         note_launches(1);
         GBT_CUDA(cudaGetLastError());
+    };
+    if (a.precision == GBT_PRECISION_F64) {
+        F64Params q{};
+        q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
+        q.n_seg_ptr = n_seg_ptr;
+        q.o = td.o; q.t = td.t; q.L = td.L; q.s0 = td.s0; q.amp = amp64;
+        q.nf = a.n_freq;
+        q.cutoff = a.cutoff;
+        for (int f = 0; f < a.n_freq; ++f) {
+            q.k[f] = 2.0 * kPi * a.freq_hz[f] / sd.c;
+            q.b[f] = a.beam_b[f];
+        }
+        q.splits = splits;
+        q.partial = reinterpret_cast<double2 *>(partial);
+        dim3 grid((unsigned)((a.n_recv + kThreads64 - 1) / kThreads64), (unsigned)splits);
+        if (a.window == GBT_WINDOW_LINE)
+            gbs_fwd_f64_kernel<GBT_WINDOW_LINE><<<grid, kThreads64, 0, s>>>(q);
+        else
+            gbs_fwd_f64_kernel<GBT_WINDOW_SEGMENT><<<grid, kThreads64, 0, s>>>(q);
+        note_launches(1);
+        GBT_CUDA(cudaGetLastError());
+        rp.n = (int64_t)a.n_freq * a.n_recv;
+        for (int f = 0; f < GBT_MAX_FREQ; ++f) rp.perm[f] = f;
+        rp.p64 = reinterpret_cast<double2 *>(partial);
+        reduce();
+        return;
+    }
+    // F32: one pair launch and one merge per group of at most 8 frequencies, each
+    // group with its own partials (split-major within the group) and output rows
+    for (int g0 = 0; g0 < a.n_freq; g0 += kGroupFreq) {
+        FwdParams q = make_pair_params(td, sd, a, rec, g0);
+        q.splits = splits;
+        q.partial = reinterpret_cast<float4 *>(partial) + (int64_t)splits * g0 * a.n_recv;
+        q.stats = stats;
+        q.n_items = cta_tiles(a.n_recv) * kTileWarps * splits;
+        q.work_counter = counter;
+        tile_prep_launch(q, a.window, tile_ws_layout(order_ws, a.n_recv, td.capacity, a.tile_cull != 0), s);
+        if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
+        else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
+        if (stats) continue;
+        rp.n = (int64_t)q.nf * a.n_recv;
+        for (int f = 0; f < GBT_MAX_FREQ; ++f) rp.perm[f] = q.fperm[f];
+        rp.p32 = q.partial;
+        reduce();
     }
 }
 
@@ -2234,20 +2254,26 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
         note_launches(1);
         GBT_CUDA(cudaGetLastError());
     }
-    FwdParams q = make_pair_params(td, sd, a, rec);
+    // per frequency group: seg_G gathers every frequency's terms, seg_H the group's rows
+    // (processing slots g0 .. g0 + nf - 1)
     if (a.n_recv > 0) {
         const int splits = choose_splits(td, a);
-        q.splits = splits;
-        q.n_items = cta_tiles(a.n_recv) * kTileWarps * splits;
-        q.work_counter = counter;
-        q.grad_out = reinterpret_cast<const float2 *>(grad_out);
-        q.seg_G = seg_G;
-        q.seg_H = seg_H;
-        q.seg_stride = td.capacity;
-        tile_prep_launch(q, a.window, tile_ws_layout(w + off[6], a.n_recv, td.capacity, a.tile_cull != 0), s);
-        if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
-        else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
+        for (int g0 = 0; g0 < a.n_freq; g0 += kGroupFreq) {
+            FwdParams q = make_pair_params(td, sd, a, rec, g0);
+            q.splits = splits;
+            q.n_items = cta_tiles(a.n_recv) * kTileWarps * splits;
+            q.work_counter = counter;
+            q.grad_out = reinterpret_cast<const float2 *>(grad_out);
+            q.seg_G = seg_G;
+            q.seg_H = seg_H + (int64_t)g0 * td.capacity;
+            q.seg_stride = td.capacity;
+            tile_prep_launch(q, a.window, tile_ws_layout(w + off[6], a.n_recv, td.capacity, a.tile_cull != 0), s);
+            if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
+            else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
+        }
     }
+    int fperm[GBT_MAX_FREQ];
+    freq_order(a, fperm);
     RayGradParams r{};
     r.n_rays = td.n_rays;
     r.ray_begin = td.ray_begin;
@@ -2272,7 +2298,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     g.acc = acc;
     g.n_materials = sd.n_materials;
     g.nf = a.n_freq;
-    for (int f = 0; f < GBT_MAX_FREQ; ++f) g.fperm[f] = q.fperm[f];
+    for (int f = 0; f < GBT_MAX_FREQ; ++f) g.fperm[f] = fperm[f];
     g.grad_gamma = grad_gamma;
     g.grad_b = grad_b;
     const int nk = sd.n_materials + a.n_freq;

@@ -128,3 +128,35 @@ def test_backward_tile_cull_matches_dense(G):
     torch.cuda.synchronize()
     for x, y in zip(d, c):
         assert _rel(y.cpu().numpy(), x.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("nf", [11, 16])
+def test_backward_more_than_eight_frequencies(G, nf):
+    """The adjoint in frequency groups of at most 8: dL/dgamma, dL/dW and every dL/db_f
+    against the oracle's adjoint (frequencies unsorted, b per frequency and uniform)."""
+    import torch
+    sc0, src, recv, _, _, gamma, win = _problem(n_rays=4096, side=24, seed=nf)
+    rng = np.random.default_rng(nf)
+    freqs = rng.permutation(125.0 * 2.0 ** (np.arange(nf) / 3.0))
+    if nf == 16:
+        b = np.full(nf, I.beam_b_rule(src.n_rays, 700.0))
+    else:
+        b = np.array([I.beam_b_rule(src.n_rays, f) for f in freqs])
+    otr = O.trace(sc0, src)
+    po = O.gbs_sum(otr, recv, freqs, b, sc0.c, gamma, window=win)
+    g = (rng.normal(size=po.shape) + 1j * rng.normal(size=po.shape)) * np.abs(po).mean()
+    dg_o, dw_o, db_o = O.gbs_adjoint(otr, recv, freqs, b, sc0.c, gamma, g, window=win)
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src)
+    r = torch.as_tensor(recv, device="cuda")
+    dg, dw, db = G.gbs_sum_backward(tr, r, list(freqs), list(b),
+                                    torch.as_tensor(gamma, device="cuda"),
+                                    torch.as_tensor(g.astype(np.complex64), device="cuda"),
+                                    order=G.recv_order(r), window=win)
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    assert _rel(dg.cpu().numpy(), dg_o) < TOL
+    assert _rel(dw.cpu().numpy(), dw_o) < TOL
+    db = db.cpu().numpy()
+    for f in range(nf):
+        assert abs(db[f] - db_o[f]) < TOL * np.abs(db_o).max(), (f, db[f], db_o[f])

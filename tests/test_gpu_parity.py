@@ -446,3 +446,52 @@ def test_forced_chunk_counts_equal_one_pass(G, chunks):
     rays = -(-w.sources[0].n_rays // chunks)
     many = G.gbs_solve(*args, window=w.window, max_device_bytes=per_ray * rays).cpu().numpy()
     assert rel_l2(many, one) < 1e-6
+
+
+@pytest.mark.parametrize("nf,uniform_b,tile_cull", [(9, False, True), (12, False, False),
+                                                    (16, True, False), (16, True, True)])
+def test_more_than_eight_frequencies_against_oracle(G, nf, uniform_b, tile_cull):
+    """More frequencies than one pair launch takes (8): they go through in groups, each
+    group writing its own output rows.  Every row against the oracle (the F64 path too),
+    and the kept-triple count against one call per frequency and the oracle's count."""
+    import torch
+    w = I.city(n_rays=8192, n_recv_side=32)
+    src = w.sources[0]
+    rng = np.random.default_rng(100 + nf)
+    freqs = rng.permutation(100.0 * 2.0 ** (np.arange(nf) / 3.0))
+    if uniform_b:
+        b = np.full(nf, I.beam_b_rule(src.n_rays, 500.0, w.scene.c))
+    else:
+        b = np.array([I.beam_b_rule(src.n_rays, f, w.scene.c) for f in freqs])
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, src)
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    o = G.recv_order(r)
+    args = (tr, r, list(freqs), list(b), gam)
+    p = G.gbs_sum(*args, order=o, window=w.window, cutoff=w.cutoff, tile_cull=tile_cull)
+    p64 = G.gbs_sum(*args, order=o, window=w.window, cutoff=w.cutoff, precision=1)
+    st = G.sum_stats(*args, order=o, window=w.window, cutoff=w.cutoff, tile_cull=tile_cull)
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    p = p.cpu().numpy().astype(np.complex128)
+    p64 = p64.cpu().numpy().astype(np.complex128)
+    otr = O.trace(w.scene, src)
+    po = O.gbs_sum(otr, w.receivers, freqs, b, w.scene.c, w.scene.gamma, window=w.window,
+                   cutoff=w.cutoff)
+    assert p.shape == po.shape == (nf, w.receivers.shape[0])
+    for f in range(nf):
+        assert rel_l2(p[f], po[f]) <= TOL_L2, (f, rel_l2(p[f], po[f]))
+        assert rel_l2(p64[f], po[f]) < 1e-7, f
+    # the kept test of a (pair, frequency) does not depend on the group it runs in; the
+    # oracle decides in FP64, so a triple on the cutoff boundary may go the other way
+    per_f = sum(G.sum_stats(tr, r, [freqs[f]], [b[f]], gam, order=o, window=w.window,
+                            cutoff=w.cutoff, tile_cull=tile_cull)["triples_kept"]
+                for f in range(nf))
+    assert st["triples_kept"] == per_f
+    kept_o = O.count_kept(otr, w.receivers, freqs, b, w.scene.c, window=w.window, cutoff=w.cutoff)
+    assert abs(st["triples_kept"] - kept_o) <= 1e-5 * kept_o
+    for f in (0, nf // 2, nf - 1):
+        one = G.gbs_sum(tr, r, [freqs[f]], [b[f]], gam, order=o, window=w.window,
+                        cutoff=w.cutoff, tile_cull=tile_cull).cpu().numpy()
+        assert rel_l2(p[f], one[0].astype(np.complex128)) < 1e-6, f
