@@ -17,7 +17,8 @@
  *  1. Fan of rays (Sec. 3.3: each ray's initial direction is set by its
  *     take-off angles; Eq. 3 integrates over these take-off parameters).
  *     A Fibonacci sphere: z_i = 1 - (2i+1)/N, phi_i = i * pi (3 - sqrt 5),
- *     each ray carrying the solid-angle weight 4 pi / N.
+ *     each ray carrying the solid-angle weight 4 pi / N; or the paper's grid
+ *     of elevation x azimuth angles, each ray carrying its cell's solid angle.
  *  2. Ray tracing (Sec. 2 and Sec. 3.1: rays and their specular interactions
  *     with planar facets).  Homogeneous medium, so rays are straight lines;
  *     nearest hit over the ground plane and the triangles (Moller-Trumbore),
@@ -66,6 +67,35 @@ void orc_fan_fibonacci(int64_t n, double *dirs)
         dirs[3 * i + 0] = r * cos(phi);
         dirs[3 * i + 1] = r * sin(phi);
         dirs[3 * i + 2] = z;
+    }
+}
+
+/* Latitude-longitude fan: the paper sets each ray's initial direction by a
+ * pair of take-off angles over an elevation range and an azimuth range (its
+ * input tables give 0..180 and 0..360 degrees).  Reading: the elevation is
+ * the polar angle from +z; ray g = it * n_phi + ip sits at the centre of its
+ * (theta, phi) cell, theta = th0 + (it + 1/2) dth, phi = ph0 + (ip + 1/2) dph,
+ * and carries the cell's solid angle, the integral of sin(theta) over the
+ * cell:  w = dph * (cos theta_lo - cos theta_hi). */
+void orc_fan_latlong(int64_t n_theta, int64_t n_phi, double th0_deg, double th1_deg,
+                     double ph0_deg, double ph1_deg, double *dirs, double *w)
+{
+    const double deg = ORC_PI / 180.0;
+    const double th0 = th0_deg * deg, ph0 = ph0_deg * deg;
+    const double dth = (th1_deg - th0_deg) * deg / (double)n_theta;
+    const double dph = (ph1_deg - ph0_deg) * deg / (double)n_phi;
+    for (int64_t it = 0; it < n_theta; ++it) {
+        const double th = th0 + ((double)it + 0.5) * dth;
+        const double lo = th0 + (double)it * dth, hi = th0 + (double)(it + 1) * dth;
+        const double cell = dph * (cos(lo) - cos(hi));
+        for (int64_t ip = 0; ip < n_phi; ++ip) {
+            const double ph = ph0 + ((double)ip + 0.5) * dph;
+            const int64_t g = it * n_phi + ip;
+            dirs[3 * g + 0] = sin(th) * cos(ph);
+            dirs[3 * g + 1] = sin(th) * sin(ph);
+            dirs[3 * g + 2] = cos(th);
+            w[g] = cell;
+        }
     }
 }
 

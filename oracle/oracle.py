@@ -7,6 +7,8 @@ shares no code with the CUDA path.  Inputs come from
 
 Functions and the passages they follow (arXiv 2501.13382):
   fan_fibonacci  -- the ray fan over take-off angles (Sec. 3.3, Eq. 3's gamma1, gamma2)
+  fan_latlong    -- the paper's grid of elevation x azimuth take-off angles, with
+                    each ray's cell solid angle as its weight
   trace          -- straight-ray tracing with specular reflection (Sec. 2, Sec. 3.1)
   gbs_sum        -- Gaussian beam summation, Eq. 3 with the beam of Eq. 1 / Eq. 2
   gbs_adjoint    -- gradient of a real loss through gbs_sum
@@ -125,6 +127,32 @@ def fan_fibonacci(n: int) -> np.ndarray:
     return d
 
 
+FAN_FIBONACCI, FAN_LATLONG = 0, 2
+
+
+def fan_latlong(n_theta: int, n_phi: int, theta_deg=(0.0, 180.0), phi_deg=(0.0, 360.0)):
+    """Grid of take-off angles (Sec. 3.3; the input tables' elevation and azimuth
+    ranges): directions (N, 3) at the cell centres and per-ray cell solid angles (N,)."""
+    n = int(n_theta) * int(n_phi)
+    d = np.empty((n, 3), np.float64)
+    w = np.empty(n, np.float64)
+    _load().orc_fan_latlong(C.c_int64(n_theta), C.c_int64(n_phi), C.c_double(theta_deg[0]),
+                            C.c_double(theta_deg[1]), C.c_double(phi_deg[0]),
+                            C.c_double(phi_deg[1]), _p(d), _p(w))
+    return d, w
+
+
+def fan(source):
+    """Directions and weights of a source's fan: Fibonacci (4 pi / N each) or the
+    latitude-longitude grid (n_theta rows of n_rays / n_theta azimuths)."""
+    n = int(source.n_rays)
+    if getattr(source, "fan", FAN_FIBONACCI) == FAN_LATLONG:
+        nt = int(source.n_theta)
+        assert nt >= 1 and n % nt == 0, "n_rays must be a multiple of n_theta"
+        return fan_latlong(nt, n // nt, source.theta_deg, source.phi_deg)
+    return fan_fibonacci(n), default_weight(n)
+
+
 @dataclass
 class Trace:
     n_rays: int
@@ -138,6 +166,7 @@ class Trace:
     depth: np.ndarray     # (S,) int32
     bmat: np.ndarray      # (S,) int32
     hit: np.ndarray       # (S,) int32  0 ground, 1+k triangle k, -1 none
+    w: np.ndarray | None = None   # (N_fan,) the fan's ray weights (None: 4 pi / N)
 
     @property
     def n_seg(self) -> int:
@@ -147,7 +176,7 @@ class Trace:
         a, b = int(self.ray_off[lo]), int(self.ray_off[hi])
         return Trace(hi - lo, self.ray_off[lo:hi + 1] - a, self.cnt[lo:hi], self.o[a:b],
                      self.t[a:b], self.L[a:b], self.s0[a:b], self.ray[a:b], self.depth[a:b],
-                     self.bmat[a:b], self.hit[a:b])
+                     self.bmat[a:b], self.hit[a:b], self.w)
 
 
 def _scene_struct(scene):
@@ -162,8 +191,9 @@ def _scene_struct(scene):
 def trace(scene, source, dirs: np.ndarray | None = None) -> Trace:
     lib = _load()
     n = int(source.n_rays)
+    w = None
     if dirs is None:
-        dirs = fan_fibonacci(n)
+        dirs, w = fan(source)
     dirs = np.ascontiguousarray(dirs, np.float64)
     R = int(source.max_reflections)
     cap = n * (R + 1)
@@ -182,7 +212,7 @@ def trace(scene, source, dirs: np.ndarray | None = None) -> Trace:
     ray_off[1:] = np.cumsum(cnt)
     ray = np.repeat(np.arange(n, dtype=np.int32), cnt)
     depth = (np.arange(idx.shape[0]) - ray_off[ray]).astype(np.int32)
-    return Trace(n, ray_off, cnt, o[idx], t[idx], L[idx], s0[idx], ray, depth, bm[idx], hit[idx])
+    return Trace(n, ray_off, cnt, o[idx], t[idx], L[idx], s0[idx], ray, depth, bm[idx], hit[idx], w)
 
 
 def _segs_struct(tr: Trace):
@@ -205,6 +235,12 @@ def default_weight(n_rays: int) -> np.ndarray:
     return np.full(n_rays, 4.0 * np.pi / n_rays)
 
 
+def _weights(tr: Trace, weight):
+    if weight is not None:
+        return np.ascontiguousarray(weight, np.float64)
+    return default_weight(tr.n_rays) if tr.w is None else np.ascontiguousarray(tr.w, np.float64)
+
+
 def gbs_sum(tr: Trace, receivers: np.ndarray, freqs, b, c: float, gamma, weight=None,
             window: int = 1, cutoff: float = 16.0, b_mask=None) -> np.ndarray:
     """Complex pressure p[f, r] (complex128)."""
@@ -212,7 +248,7 @@ def gbs_sum(tr: Trace, receivers: np.ndarray, freqs, b, c: float, gamma, weight=
     recv = np.ascontiguousarray(np.asarray(receivers, np.float32).astype(np.float64))
     nr = recv.shape[0]
     gam = np.ascontiguousarray(gamma, np.float64)
-    w = default_weight(tr.n_rays) if weight is None else np.ascontiguousarray(weight, np.float64)
+    w = _weights(tr, weight)
     segs, k1 = _segs_struct(tr)
     args, k2 = _args_struct(c, freqs, b, cutoff, window, b_mask)
     out = np.zeros((len(freqs), nr, 2), np.float64)
@@ -227,7 +263,7 @@ def gbs_adjoint(tr: Trace, receivers, freqs, b, c, gamma, g, weight=None, window
     recv = np.ascontiguousarray(np.asarray(receivers, np.float32).astype(np.float64))
     nr = recv.shape[0]
     gam = np.ascontiguousarray(gamma, np.float64)
-    w = default_weight(tr.n_rays) if weight is None else np.ascontiguousarray(weight, np.float64)
+    w = _weights(tr, weight)
     gg = np.ascontiguousarray(np.stack([np.real(g), np.imag(g)], -1), np.float64)
     segs, k1 = _segs_struct(tr)
     args, k2 = _args_struct(c, freqs, b, cutoff, window, b_mask)

@@ -53,12 +53,19 @@ class Scene:
         return int(self.gamma.shape[0])
 
 
+FAN_FIBONACCI, FAN_LATLONG = 0, 2
+
+
 @dataclass
 class Source:
     pos: np.ndarray              # (3,) float64
     n_rays: int
     max_reflections: int
     max_path: float              # m
+    fan: int = FAN_FIBONACCI     # FAN_LATLONG: n_theta rows of n_rays / n_theta azimuths
+    n_theta: int = 0
+    theta_deg: tuple = (0.0, 180.0)   # polar angle range from +z, degrees
+    phi_deg: tuple = (0.0, 360.0)     # azimuth range, degrees
 
 
 @dataclass
@@ -210,6 +217,17 @@ def open_plane_large() -> Workload:
     freqs = 125.0 * 2.0 ** np.arange(6)
     return _with_b(Workload("open_plane_64k_rays_256x256_6f", sc, [src],
                             receiver_grid(256, 500.0, 1.5), freqs, WINDOW_LINE))
+
+
+def open_plane_latlong(n_theta: int = 128, n_phi: int = 256) -> Workload:
+    """Open plane with the take-off grid of the paper's input tables (polar angle 0-180,
+    azimuth 0-360 degrees): 128 x 256 rays, <=2 reflections, 400 m, 96x96 receivers,
+    two bands."""
+    sc = _ground_scene(0.9)
+    src = Source(np.array([0.0, 0.0, 10.0]), n_theta * n_phi, 2, 400.0, FAN_LATLONG, n_theta)
+    return _with_b(Workload(f"open_plane_latlong_{n_theta}x{n_phi}_96x96_2f", sc, [src],
+                            receiver_grid(96, 150.0, 1.5), np.array([250.0, 500.0]),
+                            WINDOW_LINE))
 
 
 CITY_MAX_PATH = 1000.0

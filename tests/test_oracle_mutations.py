@@ -29,6 +29,12 @@ MUTATIONS = {
     "fan_offset": ("double z = 1.0 - (2.0 * (double)i + 1.0) / (double)n;",
                    "double z = 1.0 - (2.0 * (double)i) / (double)n;"),
     "gaussian_exponent_half": ("I * k * n2 / (2.0 * E)", "I * k * n2 / E"),
+    "latlong_midpoint_weight": ("const double cell = dph * (cos(lo) - cos(hi));",
+                                "const double cell = dph * dth * sin(th);"),
+    "latlong_cell_edge": ("const double th = th0 + ((double)it + 0.5) * dth;",
+                          "const double th = th0 + (double)it * dth;"),
+    "latlong_sin_cos_swapped": ("dirs[3 * g + 0] = sin(th) * cos(ph);",
+                                "dirs[3 * g + 0] = cos(th) * cos(ph);"),
 }
 
 
@@ -38,6 +44,14 @@ def _battery():
     # fan: equal-area z bands
     d = O.fan_fibonacci(1024)
     ok &= bool(np.allclose(d[:, 2], 1.0 - (2.0 * np.arange(1024) + 1.0) / 1024, atol=1e-15))
+    # lat-long fan: cell centres and cell solid angles (quadrature of sin(theta))
+    from scipy.integrate import quad
+    dl, wl = O.fan_latlong(6, 4, (20.0, 140.0), (0.0, 360.0))
+    ok &= bool(np.allclose(np.linalg.norm(dl, axis=1), 1.0, atol=1e-15))
+    ok &= bool(np.allclose(np.degrees(np.arccos(dl[::4, 2])), 20.0 + 20.0 * (np.arange(6) + 0.5)))
+    cells = [quad(math.sin, math.radians(20.0 + 20.0 * i), math.radians(40.0 + 20.0 * i))[0] *
+             math.pi / 2 for i in range(6)]
+    ok &= bool(np.allclose(wl[::4], cells, rtol=1e-12))
     # free field, point source with the paraxial law p/p_exact - 1 = i r / (k b^2)
     sc = I.Scene(C, False, 0.0, 0, np.zeros((0, 3, 3)), np.zeros(0, np.int32),
                  np.zeros(0, np.int32), np.array([1.0], np.float32))
