@@ -52,7 +52,8 @@ enum { GBT_WINDOW_SEGMENT = 0,   /* a beam acts on 0 <= s_loc < L of its segment
 enum { GBT_PRECISION_F32 = 0,    /* FP32 arithmetic, float-float phase, compensated sums */
        GBT_PRECISION_F64 = 1 };  /* FP64 everywhere (comparison path; slow on GB300) */
 enum { GBT_FAN_FIBONACCI = 0,    /* directions generated on the device */
-       GBT_FAN_EXPLICIT = 1 };   /* directions supplied by the caller */
+       GBT_FAN_EXPLICIT = 1,     /* directions supplied by the caller */
+       GBT_FAN_LATLONG = 2 };    /* grid of polar x azimuth take-off angles, on the device */
 
 typedef struct gbt_scene_s gbt_scene_t;   /* opaque handles */
 typedef struct gbt_trace_s gbt_trace_t;
@@ -105,6 +106,15 @@ gbt_status gbt_scene_destroy(gbt_scene_t *scene);
  * after max_reflections reflections.  The Fibonacci fan is
  * z_i = 1 - (2i+1)/N, phi_i = i pi (3 - sqrt 5); every ray carries the
  * solid-angle weight 4 pi / N unless the sum supplies per-ray weights.
+ * The latitude-longitude fan is the paper's grid of take-off angles (Sec. 3.3;
+ * its input tables give the elevation range 0..180 and the azimuth range
+ * 0..360 degrees): n_theta rows of n_phi = N / n_theta rays, ray
+ * g = it * n_phi + ip at the centre of its cell,
+ *   theta = theta_deg[0] + (it + 1/2) dtheta   (polar angle from +z),
+ *   phi   = phi_deg[0]   + (ip + 1/2) dphi,
+ *   d = (sin theta cos phi, sin theta sin phi, cos theta),
+ * carrying its cell's solid angle dphi (cos theta_lo - cos theta_hi) as weight
+ * (explicit fans carry 4 pi / N).
  * FP64 throughout, without fused multiply-add, in a fixed operation order.
  *
  * The result is a CSR list of straight segments in ray order (ray_off over
@@ -118,10 +128,14 @@ typedef struct gbt_source_desc {
     int64_t n_rays;               /* fan size N (>= 1) */
     int64_t ray_begin;            /* first ray traced (chunking), 0 normally */
     int64_t ray_count;            /* rays traced; 0 = n_rays - ray_begin */
-    int32_t fan;                  /* GBT_FAN_FIBONACCI or GBT_FAN_EXPLICIT */
+    int32_t fan;                  /* GBT_FAN_FIBONACCI, GBT_FAN_EXPLICIT or GBT_FAN_LATLONG */
     int32_t max_reflections;      /* >= 0 */
     const double *dirs;           /* device, ray_count * 3 unit vectors (EXPLICIT only) */
     double max_path;              /* m (> 0) */
+    /* GBT_FAN_LATLONG only: n_rays = n_theta * n_phi */
+    int64_t n_theta;              /* polar rows (>= 1, divides n_rays) */
+    double theta_deg[2];          /* polar range, 0 <= [0] < [1] <= 180 */
+    double phi_deg[2];            /* azimuth range, [0] < [1] <= [0] + 360 */
 } gbt_source_desc;
 
 gbt_status gbt_trace(const gbt_scene_t *scene, const gbt_source_desc *src, void *stream,
@@ -178,7 +192,8 @@ typedef struct gbt_sum_args {
     double freq_hz[GBT_MAX_FREQ]; /* > 0 */
     double beam_b[GBT_MAX_FREQ];  /* beam parameter b_f, m (> 0) */
     const float *gamma;           /* device, n_materials reflection coefficients */
-    const float *ray_weight;      /* device, n_fan per-ray weights, or NULL (4 pi / N) */
+    const float *ray_weight;      /* device, n_fan per-ray weights, or NULL (the fan's own:
+                                     4 pi / N, or the lat-long cell solid angles) */
     float *out;                   /* device, n_freq * n_recv * 2 floats */
     double cutoff;                /* C (> 0); 16 drops less than 1.2e-7 of a beam */
     int32_t precision;            /* GBT_PRECISION_F32 / GBT_PRECISION_F64 */

@@ -211,8 +211,18 @@ static void validate_source(const gbt_source_desc &src)
     GBT_REQUIRE(src.max_path > 0 && isfinite(src.max_path), "max_path must be finite and > 0");
     GBT_REQUIRE(isfinite(src.pos[0]) && isfinite(src.pos[1]) && isfinite(src.pos[2]),
                 "source position must be finite");
-    GBT_REQUIRE(src.fan == GBT_FAN_FIBONACCI || src.fan == GBT_FAN_EXPLICIT, "unknown fan");
+    GBT_REQUIRE(src.fan == GBT_FAN_FIBONACCI || src.fan == GBT_FAN_EXPLICIT ||
+                    src.fan == GBT_FAN_LATLONG, "unknown fan");
     GBT_REQUIRE(src.fan != GBT_FAN_EXPLICIT || src.dirs, "explicit fan needs dirs");
+    if (src.fan == GBT_FAN_LATLONG) {
+        GBT_REQUIRE(src.n_theta >= 1 && src.n_rays % src.n_theta == 0,
+                    "lat-long fan: n_theta must be >= 1 and divide n_rays");
+        const double *th = src.theta_deg, *ph = src.phi_deg;
+        GBT_REQUIRE(isfinite(th[0]) && isfinite(th[1]) && th[0] >= 0.0 && th[0] < th[1] &&
+                        th[1] <= 180.0, "lat-long fan: need 0 <= theta_deg[0] < theta_deg[1] <= 180");
+        GBT_REQUIRE(isfinite(ph[0]) && isfinite(ph[1]) && ph[0] < ph[1] && ph[1] - ph[0] <= 360.0,
+                    "lat-long fan: need phi_deg[0] < phi_deg[1] <= phi_deg[0] + 360");
+    }
     GBT_REQUIRE((double)cnt * (src.max_reflections + 1) < 2147483647.0,
                 "segment capacity exceeds 2^31 - 1: trace fewer rays at a time");
 }
@@ -224,6 +234,16 @@ static void alloc_trace_block(TraceDev &td, const gbt_scene_t *scene, const gbt_
 {
     td.scene = scene;
     td.n_fan = src.n_rays;
+    td.fan = FanDev{};
+    td.fan.kind = src.fan;
+    if (src.fan == GBT_FAN_LATLONG) {
+        const double deg = kPi / 180.0;
+        td.fan.n_phi = src.n_rays / src.n_theta;
+        td.fan.th0 = src.theta_deg[0] * deg;
+        td.fan.dth = (src.theta_deg[1] - src.theta_deg[0]) * deg / (double)src.n_theta;
+        td.fan.ph0 = src.phi_deg[0] * deg;
+        td.fan.dph = (src.phi_deg[1] - src.phi_deg[0]) * deg / (double)td.fan.n_phi;
+    }
     td.max_refl = src.max_reflections;
     td.max_path = src.max_path;
     td.capacity = cnt * (int64_t)(src.max_reflections + 1);
@@ -541,7 +561,8 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
         GBT_REQUIRE(scene && src && args, "scene, src and args must be non-NULL");
         GBT_REQUIRE(src->ray_begin == 0 && src->ray_count == 0,
                     "gbt_solve traces the whole fan: ray_begin and ray_count must be 0");
-        GBT_REQUIRE(src->fan == GBT_FAN_FIBONACCI, "gbt_solve supports the Fibonacci fan");
+        GBT_REQUIRE(src->fan != GBT_FAN_EXPLICIT,
+                    "gbt_solve generates its fan: Fibonacci or lat-long, not explicit");
         GBT_REQUIRE(args->max_device_bytes >= 0, "max_device_bytes must be >= 0");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const int64_t N = src->n_rays;

@@ -1071,8 +1071,9 @@ struct PrepParams {
     const double *o, *t, *L, *s0;
     const int32_t *ray, *depth, *bmat;
     const float *gamma;
-    const float *weight;       // per global ray, or nullptr -> 4 pi / N
-    double w_default;
+    const float *weight;       // per global ray, or nullptr -> the fan's own weight
+    FanDev fan;
+    int64_t n_fan;
     int n_materials;
     float *rec;
     // F64 path records (nullptr when not needed)
@@ -1102,7 +1103,7 @@ __global__ void prepass_kernel(PrepParams p)
         }
         g *= (double)p.gamma[m];
     }
-    const double w = p.weight ? (double)p.weight[p.ray[j]] : p.w_default;
+    const double w = p.weight ? (double)p.weight[p.ray[j]] : fan_weight(p.fan, p.n_fan, p.ray[j]);
     const double amp = w * g;
     float4 *R = reinterpret_cast<float4 *>(p.rec + j * kRecFloats);
     float oh[3], ol[3], th[3], tl[3], s0h, s0l, Lh, Ll;
@@ -1216,7 +1217,8 @@ struct RayGradParams {
     int64_t n_rays, ray_begin;
     const int32_t *ray_off, *bmat;
     const float *gamma, *weight;
-    double w_default;
+    FanDev fan;
+    int64_t n_fan;
     const float *seg_G, *seg_H;
     int64_t seg_stride;
     int nf, n_materials;
@@ -1237,7 +1239,8 @@ __global__ void ray_grad_kernel(RayGradParams p)
     if (i < p.n_rays) {
         const int64_t a = p.ray_off[i];
         const int cnt = (int)(p.ray_off[i + 1] - a);
-        const double W = p.weight ? (double)p.weight[p.ray_begin + i] : p.w_default;
+        const double W = p.weight ? (double)p.weight[p.ray_begin + i]
+                                  : fan_weight(p.fan, p.n_fan, p.ray_begin + i);
         double gams[kMaxDepth];
         int mats[kMaxDepth];
         double gp = 1.0, gw = 0.0;
@@ -2089,7 +2092,8 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
         pp.gamma = a.gamma;
         pp.weight = a.ray_weight;
-        pp.w_default = 4.0 * kPi / (double)td.n_fan;
+        pp.fan = td.fan;
+        pp.n_fan = td.n_fan;
         pp.n_materials = sd.n_materials;
         pp.rec = rec;
         pp.amp64 = amp64;
@@ -2245,7 +2249,8 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
         pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
         pp.gamma = a.gamma;
         pp.weight = a.ray_weight;
-        pp.w_default = 4.0 * kPi / (double)td.n_fan;
+        pp.fan = td.fan;
+        pp.n_fan = td.n_fan;
         pp.n_materials = sd.n_materials;
         pp.rec = rec;
         pp.amp64 = amp64;
@@ -2281,7 +2286,8 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     r.bmat = td.bmat;
     r.gamma = a.gamma;
     r.weight = a.ray_weight;
-    r.w_default = 4.0 * kPi / (double)td.n_fan;
+    r.fan = td.fan;
+    r.n_fan = td.n_fan;
     r.seg_G = seg_G;
     r.seg_H = seg_H;
     r.seg_stride = td.capacity;
@@ -2472,7 +2478,8 @@ static void batch_prepass(BatchImpl &B, int i, cudaStream_t s)
     pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
     pp.gamma = a.gamma;
     pp.weight = a.ray_weight;
-    pp.w_default = 4.0 * kPi / (double)td.n_fan;
+    pp.fan = td.fan;
+    pp.n_fan = td.n_fan;
     pp.n_materials = td.scene->d.n_materials;
     pp.rec = reinterpret_cast<float *>(static_cast<char *>(B.work) + B.rec_off[i]);
     pp.amp64 = nullptr;

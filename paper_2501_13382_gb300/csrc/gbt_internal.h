@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <stdexcept>
@@ -84,9 +85,28 @@ enum RecField {
     kRecFloats = 20
 };
 
+// Fan of take-off directions of a trace (angles in radians).
+struct FanDev {
+    int kind = GBT_FAN_FIBONACCI;
+    int64_t n_phi = 0;                   // GBT_FAN_LATLONG: rays per polar row
+    double th0 = 0, dth = 0, ph0 = 0, dph = 0;
+};
+
+// Default weight of global ray g of a fan of n_fan rays: 4 pi / N, or for the
+// lat-long grid its cell's solid angle dphi (cos th_lo - cos th_hi), written
+// 2 dphi sin(th_mid) sin(dth / 2).
+__host__ __device__ inline double fan_weight(const FanDev &f, int64_t n_fan, int64_t g)
+{
+    if (f.kind != GBT_FAN_LATLONG) return 4.0 * 3.14159265358979323846 / (double)n_fan;
+    const int64_t it = g / f.n_phi;
+    const double th = f.th0 + ((double)it + 0.5) * f.dth;
+    return 2.0 * f.dph * sin(th) * sin(0.5 * f.dth);
+}
+
 struct TraceDev {
     const gbt_scene_t *scene = nullptr;
     int64_t n_fan = 0, ray_begin = 0, n_rays = 0, capacity = 0;
+    FanDev fan;
     int max_refl = 0;
     double max_path = 0;
     int32_t *ray_off = nullptr;  // n_rays + 1 (device); ray_off[n_rays] = segment count

@@ -50,6 +50,7 @@ struct TraceParams {
     double src[3];
     int64_t n_fan, ray_begin, n_rays;
     const double *dirs;        // explicit directions (n_rays * 3) or nullptr
+    FanDev fan;                // generated fan when dirs is nullptr
     int max_refl;
     double max_path;
     int ground;
@@ -143,11 +144,20 @@ __device__ __forceinline__ int64_t ray_of_slot(const TraceParams &p, int64_t tid
     return tid;
 }
 
-// Take-off direction of ray i (explicit, or the Fibonacci fan of the whole source).
+// Take-off direction of ray i (explicit, or the generated fan of the whole source:
+// the lat-long grid's cell centre, or the Fibonacci lattice).
 __device__ __forceinline__ void ray_direction(const TraceParams &p, int64_t i, double d[3])
 {
     if (p.dirs) {
         d[0] = p.dirs[3 * i]; d[1] = p.dirs[3 * i + 1]; d[2] = p.dirs[3 * i + 2];
+    } else if (p.fan.kind == GBT_FAN_LATLONG) {
+        const int64_t g = p.ray_begin + i;
+        const int64_t it = g / p.fan.n_phi, ip = g - it * p.fan.n_phi;
+        const double th = p.fan.th0 + ((double)it + 0.5) * p.fan.dth;
+        const double ph = p.fan.ph0 + ((double)ip + 0.5) * p.fan.dph;
+        d[0] = sin(th) * cos(ph);
+        d[1] = sin(th) * sin(ph);
+        d[2] = cos(th);
     } else {
         const int64_t g = p.ray_begin + i;
         const double golden = kPi * (3.0 - sqrt(5.0));
@@ -496,6 +506,7 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     p.ray_begin = td.ray_begin;
     p.n_rays = n;
     p.dirs = src.fan == GBT_FAN_EXPLICIT ? src.dirs : nullptr;
+    p.fan = td.fan;
     p.max_refl = td.max_refl;
     p.max_path = td.max_path;
     p.ground = sd.ground;
@@ -510,7 +521,7 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     p.n_clusters = sd.n_clusters;
     // coherent warps on a Fibonacci fan: the largest Fibonacci number <= sqrt(N) / 2
     p.strip = 0;
-    if (!p.dirs && td.n_fan >= 4096) {
+    if (!p.dirs && td.fan.kind == GBT_FAN_FIBONACCI && td.n_fan >= 4096) {
         int64_t f0 = 1, f1 = 2;   // lattice neighbours are set by the whole fan's size
         while (f1 * f1 * 4 <= td.n_fan) { const int64_t f2 = f0 + f1; f0 = f1; f1 = f2; }
         p.strip = f0;

@@ -24,7 +24,7 @@ MAX_FREQ = 16
 WINDOW_SEGMENT, WINDOW_LINE = 0, 1
 BATCH_AUTO, BATCH_FUSED, BATCH_CONCURRENT = 0, 1, 2
 PRECISION_F32, PRECISION_F64 = 0, 1
-FAN_FIBONACCI, FAN_EXPLICIT = 0, 1
+FAN_FIBONACCI, FAN_EXPLICIT, FAN_LATLONG = 0, 1, 2
 
 STATUS_NAMES = {0: "GBT_OK", 1: "GBT_ERR_INVALID_ARG", 2: "GBT_ERR_OOM", 3: "GBT_ERR_CUDA",
                 4: "GBT_ERR_TIMEOUT", 5: "GBT_ERR_DEVICE_STATUS", 6: "GBT_ERR_UNSUPPORTED"}
@@ -50,7 +50,8 @@ class gbt_scene_desc(C.Structure):
 class gbt_source_desc(C.Structure):
     _fields_ = [("pos", C.c_double * 3), ("n_rays", C.c_int64), ("ray_begin", C.c_int64),
                 ("ray_count", C.c_int64), ("fan", C.c_int32), ("max_reflections", C.c_int32),
-                ("dirs", C.c_void_p), ("max_path", C.c_double)]
+                ("dirs", C.c_void_p), ("max_path", C.c_double), ("n_theta", C.c_int64),
+                ("theta_deg", C.c_double * 2), ("phi_deg", C.c_double * 2)]
 
 
 class gbt_trace_info(C.Structure):
@@ -336,10 +337,14 @@ def source_desc(source, ray_begin: int = 0, ray_count: int = 0, dirs=None) -> gb
     s.n_rays = int(source.n_rays)
     s.ray_begin = int(ray_begin)
     s.ray_count = int(ray_count)
-    s.fan = FAN_EXPLICIT if dirs is not None else FAN_FIBONACCI
+    s.fan = FAN_EXPLICIT if dirs is not None else int(getattr(source, "fan", FAN_FIBONACCI))
     s.max_reflections = int(source.max_reflections)
     s.dirs = _ptr(dirs)
     s.max_path = float(source.max_path)
+    if s.fan == FAN_LATLONG:
+        s.n_theta = int(source.n_theta)
+        s.theta_deg[:] = [float(v) for v in source.theta_deg]
+        s.phi_deg[:] = [float(v) for v in source.phi_deg]
     return s
 
 

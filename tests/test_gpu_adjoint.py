@@ -160,3 +160,29 @@ def test_backward_more_than_eight_frequencies(G, nf):
     db = db.cpu().numpy()
     for f in range(nf):
         assert abs(db[f] - db_o[f]) < TOL * np.abs(db_o).max(), (f, db[f], db_o[f])
+
+
+def test_backward_latlong_fan_default_weights(G):
+    """Adjoint on the paper's take-off grid with the cells' solid angles as the default
+    ray weights: dL/dgamma, dL/dW and dL/db against the oracle's adjoint."""
+    import torch
+    sc0, _, recv, freqs, b, gamma, win = _problem(n_rays=4096, side=24, seed=21)
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 64 * 96, 6, 1000.0, I.FAN_LATLONG, 64)
+    b = np.array([I.beam_b_rule(src.n_rays, f) for f in freqs])
+    otr = O.trace(sc0, src)
+    po = O.gbs_sum(otr, recv, freqs, b, sc0.c, gamma, window=win)
+    rng = np.random.default_rng(21)
+    g = (rng.normal(size=po.shape) + 1j * rng.normal(size=po.shape)) * np.abs(po).mean()
+    dg_o, dw_o, db_o = O.gbs_adjoint(otr, recv, freqs, b, sc0.c, gamma, g, window=win)
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src)
+    r = torch.as_tensor(recv, device="cuda")
+    dg, dw, db = G.gbs_sum_backward(tr, r, list(freqs), list(b),
+                                    torch.as_tensor(gamma, device="cuda"),
+                                    torch.as_tensor(g.astype(np.complex64), device="cuda"),
+                                    order=G.recv_order(r), window=win)
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    assert _rel(dg.cpu().numpy(), dg_o) < TOL
+    assert _rel(db.cpu().numpy(), db_o) < TOL
+    assert _rel(dw.cpu().numpy(), dw_o) < TOL

@@ -278,6 +278,15 @@ def test_invalid_arguments_are_rejected_before_launch(G):
     bad = I.Source(np.array([0.0, 0.0, 2.0]), 0, 2, 200.0)
     with pytest.raises(G.GBTError):
         G.Trace(sc, bad)
+    pos = np.array([0.0, 0.0, 2.0])
+    for bad in (I.Source(pos, 1000, 2, 200.0, I.FAN_LATLONG, 7),                  # 7 does not divide
+                I.Source(pos, 1000, 2, 200.0, I.FAN_LATLONG, 0),
+                I.Source(pos, 1000, 2, 200.0, I.FAN_LATLONG, 10, (90.0, 90.0)),
+                I.Source(pos, 1000, 2, 200.0, I.FAN_LATLONG, 10, (0.0, 181.0)),
+                I.Source(pos, 1000, 2, 200.0, I.FAN_LATLONG, 10, (0.0, 180.0), (0.0, 361.0))):
+        with pytest.raises(G.GBTError) as e:
+            G.Trace(sc, bad)
+        assert e.value.status == 1
     G.gbt_sync()
 
 
@@ -495,3 +504,66 @@ def test_more_than_eight_frequencies_against_oracle(G, nf, uniform_b, tile_cull)
         one = G.gbs_sum(tr, r, [freqs[f]], [b[f]], gam, order=o, window=w.window,
                         cutoff=w.cutoff, tile_cull=tile_cull).cpu().numpy()
         assert rel_l2(p[f], one[0].astype(np.complex128)) < 1e-6, f
+
+
+def _latlong_city_source(nt=64, nph=128, th=(0.0, 180.0), ph=(0.0, 360.0)):
+    return I.Source(np.array([0.0, 0.0, 5.0]), nt * nph, 8, 1000.0, I.FAN_LATLONG, nt, th, ph)
+
+
+@pytest.mark.parametrize("th,ph", [((0.0, 180.0), (0.0, 360.0)), ((20.0, 160.0), (-45.0, 135.0))])
+def test_trace_latlong_fan_matches_oracle(G, th, ph):
+    """The paper's take-off grid generated on the device: hit sequences, counts and
+    offsets identical to the oracle's trace, geometry to FP64 rounding (the two sides'
+    sin/cos may differ in the last bit)."""
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    src = _latlong_city_source(th=th, ph=ph)
+    sc = G.Scene(sc0)
+    _compare_trace(G.Trace(sc, src).segments(), O.trace(sc0, src))
+    # a ray range of the grid is a slice of the whole
+    full = G.Trace(sc, src).segments()
+    part = G.Trace(sc, src, ray_begin=1000, ray_count=3000).segments()
+    off = full["ray_off"].cpu().numpy()
+    a, b = off[1000], off[4000]
+    for k in ("o", "t", "L", "s0", "ray", "hit", "bmat", "depth"):
+        assert np.array_equal(part[k].cpu().numpy(), full[k].cpu().numpy()[a:b]), k
+
+
+@pytest.mark.parametrize("tile_cull", [False, True])
+def test_sum_latlong_fan_against_oracle(G, tile_cull):
+    """Sum over the grid with each ray's cell solid angle as its default weight (no
+    per-ray weights passed), F32 and F64 paths, against the oracle."""
+    import torch
+    w = I.open_plane_latlong()
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, w.sources[0])
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    o = G.recv_order(r)
+    args = (tr, r, list(w.freqs), list(w.beam_b[0]), gam)
+    p = G.gbs_sum(*args, order=o, window=w.window, tile_cull=tile_cull)
+    p64 = G.gbs_sum(*args, order=o, window=w.window, precision=1)
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    _, po = O.solve(w)
+    for f in range(len(w.freqs)):
+        assert rel_l2(p[f].cpu().numpy().astype(np.complex128), po[f]) <= TOL_L2, f
+        assert rel_l2(p64[f].cpu().numpy().astype(np.complex128), po[f]) < 1e-7, f
+
+
+def test_solve_latlong_fan_chunked_equals_one_pass(G):
+    import torch
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    src = _latlong_city_source(48, 96)
+    recv = I.receiver_grid(24, 250.0, 1.5)
+    freqs = [500.0, 1000.0]
+    b = [I.beam_b_rule(src.n_rays, f) for f in freqs]
+    sc = G.Scene(sc0)
+    r = _dev(recv, torch.float32)
+    gam = _dev(sc0.gamma, torch.float32)
+    one = G.gbs_solve(sc, src, r, freqs, b, gam, window=I.WINDOW_SEGMENT).cpu().numpy()
+    per_ray = (src.max_reflections + 1) * (80 + 80 + 4 * 20 + 16)
+    many = G.gbs_solve(sc, src, r, freqs, b, gam, window=I.WINDOW_SEGMENT,
+                       max_device_bytes=per_ray * 700).cpu().numpy()
+    assert rel_l2(many, one) < 1e-6
+    po = O.gbs_sum(O.trace(sc0, src), recv, freqs, b, sc0.c, sc0.gamma, window=I.WINDOW_SEGMENT)
+    assert rel_l2(one.astype(np.complex128), po) <= TOL_L2
