@@ -323,6 +323,37 @@ def bench_fwd_bwd(G, torch, stream, steps=5):
     return res
 
 
+def bench_trace(G, torch, stream, steps=5):
+    """The tracer alone (fan, nearest hits, reflections, scan and compaction into the
+    segment list) for each nearest-hit search: the synthetic city (768 triangles, kept in
+    shared memory, 1,048,576 rays) and the large city (12,288 triangles, 262,144 rays)."""
+    from paper_2501_13382_gb300 import inputs as I
+    res = {}
+    for name, w in (("city_768_tris_1M_rays", I.city()),
+                    ("big_city_12k_tris_256k_rays", I.big_city())):
+        src = w.sources[0]
+        r = {"triangles": int(w.scene.n_tri), "rays": int(src.n_rays)}
+        accels = [("auto", G.ACCEL_AUTO), ("bvh", G.ACCEL_BVH)]
+        if w.scene.n_tri > 1024:
+            accels.append(("linear", G.ACCEL_LINEAR))
+        for an, a in accels:
+            sc = G.Scene(w.scene, accel=a)
+            t = G.Trace(sc, src)
+            n_seg = int(t.info().n_segments)
+            t.close()
+            ev = _events(torch, steps)
+            for i in range(steps):
+                ev[i][0].record(stream)
+                t = G.Trace(sc, src)
+                ev[i][1].record(stream)
+                t.close()
+            ms = float(np.median([a0.elapsed_time(b0) for a0, b0 in ev]))
+            r[an] = {"ms": ms, "rays_per_s": src.n_rays / (ms * 1e-3), "segments": n_seg}
+            sc.close()
+        res[name] = r
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,6 +514,7 @@ def main():
                                          min(args.steps, 50), n_seg),
             "batched": bench_batched(G, torch, stream),
             "fwd_bwd": bench_fwd_bwd(G, torch, stream),
+            "trace": bench_trace(G, torch, stream),
         }
         # the forms overwrite `out`; recompute the measured workload's field for the check
         G.gbs_solve(sc, src, recv, list(w.freqs), list(w.beam_b[0]), gam, order=order,

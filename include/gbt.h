@@ -81,7 +81,20 @@ gbt_status gbt_set_allocator(const gbt_allocator *allocator);
  * one planar facet: a ray leaving a facet cannot hit it again.  A reflection
  * off primitive p multiplies the beam by gamma[material(p)] (supplied at sum
  * time).  Host arrays are copied; the caller may free them on return.
- * Synchronises `stream` once (upload). */
+ * Synchronises `stream` once (upload).
+ *
+ * Nearest-hit search (`accel`; every choice finds the same hits, bit for bit):
+ *   GBT_ACCEL_AUTO    the BVH below (the faster search on every scene measured,
+ *                     from 768 triangles up);
+ *   GBT_ACCEL_BVH     a bounding-volume hierarchy built on the host at creation
+ *                     (binned surface-area heuristic over triangle centroids,
+ *                     leaves of at most 4 triangles, each node holding its two
+ *                     children's padded FP32 boxes), traversed near child first
+ *                     with a per-ray stack;
+ *   GBT_ACCEL_LINEAR  padded FP32 boxes of clusters of 8 triangles and of each
+ *                     triangle tested in index order: the whole scene resident
+ *                     in shared memory up to 1,024 triangles, staged through it
+ *                     in chunks of 1,024 above. */
 typedef struct gbt_scene_desc {
     double c;                     /* speed of sound, m/s (> 0) */
     int32_t ground_enabled;       /* 0 / 1 */
@@ -92,7 +105,10 @@ typedef struct gbt_scene_desc {
     const int32_t *tri_material;  /* host, n_tri, each in [0, n_materials) */
     const int32_t *tri_face;      /* host, n_tri facet ids >= 0, or NULL (own facet each) */
     int32_t n_materials;          /* >= 1 */
+    int32_t accel;                /* GBT_ACCEL_AUTO (0), GBT_ACCEL_BVH, GBT_ACCEL_LINEAR */
 } gbt_scene_desc;
+
+enum { GBT_ACCEL_AUTO = 0, GBT_ACCEL_BVH = 1, GBT_ACCEL_LINEAR = 2 };
 
 gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_t **out);
 gbt_status gbt_scene_destroy(gbt_scene_t *scene);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -52,6 +53,19 @@ struct DeviceBuffer {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTMin = 1e-9;   // smallest accepted hit distance, m
 
+// BVH node: the padded FP32 boxes of its two children (lo xyz, hi xyz each) and their
+// references: >= 0 an inner node, kBvhNone no child, otherwise a leaf of 1..8
+// consecutive entries of the triangle permutation, encoded -(first * 8 + count - 1) - 1.
+struct alignas(16) BvhNode {
+    float box[2][6];
+    int32_t ref[2];
+    int32_t pad[2];
+};
+static_assert(sizeof(BvhNode) == 64, "BVH node is four 16-byte words");
+constexpr int32_t kBvhNone = INT32_MIN;
+constexpr int kBvhLeaf = 4;          // most triangles per leaf
+constexpr int kBvhStack = 64;        // traversal stack entries (build depth is at most 58)
+
 // Scene on the device.  Per triangle 12 doubles: v0, e1 = v1 - v0, e2 = v2 - v0,
 // unit normal (e1 x e2 normalised).
 struct SceneDev {
@@ -70,6 +84,11 @@ struct SceneDev {
     float *cbox = nullptr;         // padded FP32 box per cluster of kTriCluster triangles
     float *tbox = nullptr;         // padded FP32 box per triangle
     int64_t n_clusters = 0;
+    int accel = GBT_ACCEL_AUTO;
+    BvhNode *bvh = nullptr;        // nodes (root 0), or nullptr when not built
+    int32_t *bvh_perm = nullptr;   // triangle index of each leaf entry
+    int64_t n_bvh_nodes = 0;
+    int bvh_depth = 0;
 };
 constexpr int kTriCluster = 8;
 

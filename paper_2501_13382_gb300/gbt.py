@@ -25,6 +25,7 @@ WINDOW_SEGMENT, WINDOW_LINE = 0, 1
 BATCH_AUTO, BATCH_FUSED, BATCH_CONCURRENT = 0, 1, 2
 PRECISION_F32, PRECISION_F64 = 0, 1
 FAN_FIBONACCI, FAN_EXPLICIT, FAN_LATLONG = 0, 1, 2
+ACCEL_AUTO, ACCEL_BVH, ACCEL_LINEAR = 0, 1, 2
 
 STATUS_NAMES = {0: "GBT_OK", 1: "GBT_ERR_INVALID_ARG", 2: "GBT_ERR_OOM", 3: "GBT_ERR_CUDA",
                 4: "GBT_ERR_TIMEOUT", 5: "GBT_ERR_DEVICE_STATUS", 6: "GBT_ERR_UNSUPPORTED"}
@@ -44,7 +45,7 @@ class gbt_scene_desc(C.Structure):
     _fields_ = [("c", C.c_double), ("ground_enabled", C.c_int32), ("ground_material", C.c_int32),
                 ("ground_z", C.c_double), ("n_tri", C.c_int64), ("tri_xyz", C.c_void_p),
                 ("tri_material", C.c_void_p), ("tri_face", C.c_void_p),
-                ("n_materials", C.c_int32)]
+                ("n_materials", C.c_int32), ("accel", C.c_int32)]
 
 
 class gbt_source_desc(C.Structure):
@@ -305,7 +306,7 @@ def gbt_sum_stats_get(trace: int, args: gbt_sum_args, stream: int = 0) -> gbt_su
 class Scene:
     """Device-resident scene built from ``inputs.Scene``."""
 
-    def __init__(self, scene):
+    def __init__(self, scene, accel: int = ACCEL_AUTO):
         self.src = scene
         tri = np.ascontiguousarray(scene.tri_xyz.reshape(-1, 9), np.float64)
         mat = np.ascontiguousarray(scene.tri_material, np.int32)
@@ -314,7 +315,8 @@ class Scene:
                            float(scene.ground_z), int(tri.shape[0]),
                            tri.ctypes.data if tri.size else 0,
                            mat.ctypes.data if mat.size else 0,
-                           face.ctypes.data if face.size else 0, int(scene.n_materials))
+                           face.ctypes.data if face.size else 0, int(scene.n_materials),
+                           int(accel))
         self.handle = gbt_scene_create(d, _stream_ptr())
         self.c = float(scene.c)
         self.n_materials = int(scene.n_materials)

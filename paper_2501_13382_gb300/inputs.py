@@ -173,14 +173,15 @@ def synthetic_city(seed: int, n_side: int = 8, extent: float = 500.0):
             np.concatenate(bidx), np.array(foot), heights, gammas)
 
 
-def city_scene(seed: int, material_of_building=None, gamma_buildings=None) -> Scene:
+def city_scene(seed: int, material_of_building=None, gamma_buildings=None, n_side: int = 8,
+               extent: float = 500.0) -> Scene:
     """Ground (material 0, gamma 1.0: hard surface) plus the synthetic city.
 
     By default each building is its own material 1+b with its seeded gamma.
     ``material_of_building`` (B,) maps building -> material index >= 1 and
     ``gamma_buildings`` gives gamma per such material (index 1..).
     """
-    tris, faces, bidx, foot, heights, gam = synthetic_city(seed)
+    tris, faces, bidx, foot, heights, gam = synthetic_city(seed, n_side, extent)
     nb = foot.shape[0]
     if material_of_building is None:
         mat = (1 + bidx).astype(np.int32)
@@ -239,6 +240,17 @@ def city(n_rays: int = 1 << 20, n_recv_side: int = 512) -> Workload:
     src = Source(np.array([0.0, 0.0, 5.0]), n_rays, 8, CITY_MAX_PATH)
     w = Workload("city_1M_rays_512x512_1kHz", sc, [src],
                  receiver_grid(n_recv_side, 250.0, 1.5), np.array([1000.0]),
+                 WINDOW_SEGMENT, extra=ex)
+    return _with_b(w)
+
+
+def big_city(n_rays: int = 1 << 18, n_recv_side: int = 256) -> Workload:
+    """Large synthetic city for the BVH: 32 x 32 boxes over 2 km (12,288 triangles),
+    262,144 rays from (0,0,5), <=8 reflections, 1 km paths, 256^2 receivers, 1 kHz."""
+    sc, ex = city_scene(SEED_BASE + 6, n_side=32, extent=2000.0)
+    src = Source(np.array([0.0, 0.0, 5.0]), n_rays, 8, CITY_MAX_PATH)
+    w = Workload("big_city_12k_tris_256k_rays_256x256_1kHz", sc, [src],
+                 receiver_grid(n_recv_side, 1000.0, 1.5), np.array([1000.0]),
                  WINDOW_SEGMENT, extra=ex)
     return _with_b(w)
 

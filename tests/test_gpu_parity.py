@@ -567,3 +567,55 @@ def test_solve_latlong_fan_chunked_equals_one_pass(G):
     assert rel_l2(many, one) < 1e-6
     po = O.gbs_sum(O.trace(sc0, src), recv, freqs, b, sc0.c, sc0.gamma, window=I.WINDOW_SEGMENT)
     assert rel_l2(one.astype(np.complex128), po) <= TOL_L2
+
+
+def _big_city_scene():
+    sc0, _ = I.city_scene(I.SEED_BASE + 6, n_side=32, extent=2000.0)
+    return sc0
+
+
+def test_bvh_trace_large_city_matches_oracle(G):
+    """12,288 triangles (above the 1,024 a block keeps in shared memory): the BVH's hit
+    sequences, counts and offsets equal the oracle's brute-force trace."""
+    sc0 = _big_city_scene()
+    assert sc0.n_tri == 12288
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 8192, 8, 1000.0)
+    gt = G.Trace(G.Scene(sc0), src).segments()
+    ot = O.trace(sc0, src)
+    _compare_trace(gt, ot)
+    assert np.diff(ot.ray_off).max() >= 6
+
+
+@pytest.mark.parametrize("which", ["city", "big_city"])
+def test_accel_choices_give_identical_traces(G, which):
+    """Resident boxes, BVH and linear chunks find the same nearest hits bit for bit."""
+    sc0 = I.city_scene(I.SEED_BASE + 3)[0] if which == "city" else _big_city_scene()
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 16384, 8, 1000.0)
+    runs = [G.Trace(G.Scene(sc0, accel=a), src).segments()
+            for a in (G.ACCEL_AUTO, G.ACCEL_BVH, G.ACCEL_LINEAR)]
+    for other in runs[1:]:
+        assert other["n_segments"] == runs[0]["n_segments"]
+        for k in ("ray_off", "o", "t", "L", "s0", "ray", "hit", "bmat", "depth"):
+            assert np.array_equal(other[k].cpu().numpy(), runs[0][k].cpu().numpy()), k
+
+
+@pytest.mark.parametrize("accel", ["bvh", "linear"])
+def test_equal_distance_hits_go_to_the_lowest_primitive(G, accel):
+    """Every triangle of the city twice (the copy after all originals, same facet, other
+    material): each hit is at the same t on both copies, and the original (lower id)
+    must win, as in the oracle, whatever order the BVH meets its leaves in."""
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    n = sc0.n_tri
+    nm = sc0.n_materials
+    dup = I.Scene(sc0.c, sc0.ground, sc0.ground_z, sc0.ground_material,
+                  np.concatenate([sc0.tri_xyz, sc0.tri_xyz]),
+                  np.concatenate([sc0.tri_material, sc0.tri_material * 0 + nm]).astype(np.int32),
+                  np.concatenate([sc0.tri_face, sc0.tri_face]).astype(np.int32),
+                  np.concatenate([sc0.gamma, [0.5]]).astype(np.float32))
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 8192, 8, 1000.0)
+    a = {"bvh": G.ACCEL_BVH, "linear": G.ACCEL_LINEAR}[accel]
+    gt = G.Trace(G.Scene(dup, accel=a), src).segments()
+    ot = O.trace(dup, src)
+    _compare_trace(gt, ot)
+    hit = gt["hit"].cpu().numpy()
+    assert hit.max() <= n and (hit > 0).sum() > 1000     # only originals are ever hit
