@@ -26,8 +26,9 @@
 //    receivers of a lane side by side in paired FP32: float-float s and phase
 //    (reduced in turns before the MUFU sin/cos), compensated cross product for
 //    n^2.  FP32 sums per lane fold into the item's float-float partials every 16
-//    batches, and the per-split partials are merged in FP64 in a fixed order by
-//    a second kernel, so results do not depend on scheduling.
+//    batches, and the per-split partials are merged in float-float (error-free
+//    FP32 sums) in a fixed order by a second kernel, so results do not depend on
+//    scheduling.
 
 #include <math.h>
 
@@ -1613,16 +1614,40 @@ __global__ void reduce_kernel(ReduceParams p)
     if (i >= p.n) return;
     // splits in order (the sums are the same whatever the unrolling); unrolled so the
     // independent loads are in flight together
-    double re = 0.0, im = 0.0;
+    const int64_t f = i / p.n_recv, r = i - f * p.n_recv;
+    const int64_t oi = (int64_t)p.perm[f] * p.n_recv + r;
     if (p.p32) {
+        // float-float partials (hi, running FP32 sum of errors) merged into a float-float
+        // total with error-free FP32 sums: about 44 bits, far beyond the complex64 output,
+        // and no FP64 arithmetic (GB300 issues FP64 at a small fraction of the FP32 rate)
         const float4 *src = p.p32 + i;
+        float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
 #pragma unroll 8
         for (int s = 0; s < p.splits; ++s) {
             const float4 v = __ldcs(src + (int64_t)s * p.n);
-            re += (double)v.x + (double)v.z;
-            im += (double)v.y + (double)v.w;
+            float t, e;
+            two_sum(rh, v.x, t, e);
+            rh = t;
+            rl = __fadd_rn(rl, __fadd_rn(e, v.z));
+            two_sum(ih, v.y, t, e);
+            ih = t;
+            il = __fadd_rn(il, __fadd_rn(e, v.w));
         }
-    } else {
+        if (p.accumulate) {
+            const float2 o = p.out[oi];
+            float t, e;
+            two_sum(rh, o.x, t, e);
+            rh = t;
+            rl = __fadd_rn(rl, e);
+            two_sum(ih, o.y, t, e);
+            ih = t;
+            il = __fadd_rn(il, e);
+        }
+        p.out[oi] = make_float2(__fadd_rn(rh, rl), __fadd_rn(ih, il));
+        return;
+    }
+    double re = 0.0, im = 0.0;
+    {
         const double2 *src = p.p64 + i;
 #pragma unroll 8
         for (int s = 0; s < p.splits; ++s) {
@@ -1631,8 +1656,6 @@ __global__ void reduce_kernel(ReduceParams p)
             im += v.y;
         }
     }
-    const int64_t f = i / p.n_recv, r = i - f * p.n_recv;
-    const int64_t oi = (int64_t)p.perm[f] * p.n_recv + r;
     if (p.accumulate) {
         const float2 o = p.out[oi];
         re += (double)o.x;
