@@ -107,7 +107,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-WORKLOADS = ("open_plane_large", "open_plane_small", "city", "diff_city")
+WORKLOADS = ("open_plane_large", "open_plane_small", "city", "diff_city", "big_city")
 
 
 def _workload(name: str = "open_plane_large"):
@@ -115,7 +115,7 @@ def _workload(name: str = "open_plane_large"):
     request with --workload (the batched city is measured as a form)."""
     from paper_2501_13382_gb300 import inputs as I
     return {"open_plane_large": I.open_plane_large, "open_plane_small": I.open_plane_small,
-            "city": I.city, "diff_city": I.diff_city}[name]()
+            "city": I.city, "diff_city": I.diff_city, "big_city": I.big_city}[name]()
 
 
 def _oracle_sample(w, budget_s: float, seed: int = 17):
@@ -333,9 +333,7 @@ def bench_trace(G, torch, stream, steps=5):
                     ("big_city_12k_tris_256k_rays", I.big_city())):
         src = w.sources[0]
         r = {"triangles": int(w.scene.n_tri), "rays": int(src.n_rays)}
-        accels = [("auto", G.ACCEL_AUTO), ("bvh", G.ACCEL_BVH)]
-        if w.scene.n_tri > 1024:
-            accels.append(("linear", G.ACCEL_LINEAR))
+        accels = [("auto", G.ACCEL_AUTO), ("bvh", G.ACCEL_BVH), ("linear", G.ACCEL_LINEAR)]
         for an, a in accels:
             sc = G.Scene(w.scene, accel=a)
             t = G.Trace(sc, src)
