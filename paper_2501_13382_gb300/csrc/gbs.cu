@@ -1877,8 +1877,6 @@ bool freq_order(const gbt_sum_args &a, int (&perm)[GBT_MAX_FREQ])
 // the processing order; the kernel is instantiated for up to that many.
 constexpr int kGroupFreq = 8;
 
-int freq_groups(const gbt_sum_args &a) { return (a.n_freq + kGroupFreq - 1) / kGroupFreq; }
-
 // Kernel parameters shared by the forward, counting and adjoint launches, for the
 // frequency group that starts at processing slot g0 (fperm maps the group's slots to
 // user frequency indices).
