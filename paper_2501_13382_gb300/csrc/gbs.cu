@@ -222,11 +222,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar)
-                 : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
 {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
@@ -321,26 +316,6 @@ __device__ __forceinline__ bool exact_geometry(float x, float y, float z, const 
     return true;
 }
 
-// One beam's contribution at frequency f given D = s^2 + b^2 and 1/D.
-__device__ __forceinline__ void beam_term(const FreqConst &q, float sh, float sl, float n2,
-                                          float invD, float amp, float2 &acc)
-{
-    const float n2invD = n2 * invD;
-    const float ga = ex2_approx(-q.kb2l2e * n2invD);  // exp(-k b n^2 / (2 D))
-    // phase in turns: frac(K s) in float-float, plus K n^2 s / (2 D)
-    const float ph = __fmul_rn(q.K_hi, sh);       // rounded: pe below is its exact error
-    const float pe = fmaf(q.K_hi, sh, -ph);
-    const float corr = fmaf(q.K_hi, sl, fmaf(q.K_lo, sh, pe));
-    float tau = __fsub_rn(ph, rintf(ph)) + corr;
-    tau = fmaf(q.halfK * n2invD, sh, tau);
-    tau = tau - rintf(tau);
-    float sn, cs;
-    __sincosf(6.283185307179586f * tau, &sn, &cs);
-    const float g = q.scale * amp * ga * invD;      // (s + i b) / D = 1 / E
-    acc.x = fmaf(g, fmaf(sh, cs, -q.b * sn), acc.x);
-    acc.y = fmaf(g, fmaf(sh, sn, q.b * cs), acc.y);
-}
-
 // Adjoint terms of one beam: with c~ the contribution without W Gamma_path,
 // G += Re(conj(g) c~) and H += Re(conj(g) dc~/db), where
 // d log c / db = 1/b + i/E - k n^2 / (2 E^2), E = s - i b.
@@ -398,8 +373,9 @@ __device__ __forceinline__ void survivor_count(const FwdParams &p, float x, floa
 // Two surviving pairs at once in paired FP32: receiver 0 of the lane with
 // segment j0 and receiver 1 with segment j1 (a side without a survivor repeats
 // the other side's segment and is masked out).  Every operation is the paired
-// twin of the single-pair path's (exact_geometry, beam_term), so each half
-// rounds identically to it; only the MUFU operations run per half.  accx / accy
+// twin of one pair's evaluation (exact_geometry, then per frequency the Gaussian,
+// the phase reduced in turns and the 1/E factor), so each half rounds as that
+// evaluation would; only the MUFU operations run per half.  accx / accy
 // hold the two receivers' real / imaginary sums per sorted frequency.
 template <int NF, int WINDOW>
 __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, f2x Z,
@@ -544,9 +520,6 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// Folds the two halves of a paired FP32 sum into two float-float accumulators.
-__device__ __forceinline__ void fold_pair(float4 *acc0, float4 *acc1, f2x &sx, f2x &sy);
-
 // Adds an FP32 partial sum into a float-float accumulator (hi, hi, lo, lo).
 __device__ __forceinline__ void fold(float4 *acc, float2 &t)
 {
@@ -564,16 +537,6 @@ __device__ __forceinline__ void fold(float4 *acc, float2 &t)
     }
 }
 
-__device__ __forceinline__ void fold_pair(float4 *acc0, float4 *acc1, f2x &sx, f2x &sy)
-{
-    float x0, x1, y0, y1;
-    upk(sx, x0, x1);
-    upk(sy, y0, y1);
-    float2 t0 = make_float2(x0, y0), t1 = make_float2(x1, y1);
-    fold(acc0, t0);
-    fold(acc1, t1);
-    sx = sy = 0ull;
-}
 
 // Conservative test: can the segment (origin (ox, oy, oz) relative to the frame
 // of `sphere`, record words r0 / r1) keep any receiver inside the ball `sphere`
