@@ -45,6 +45,13 @@ def test_invalid_scene_rejected_on_host(lib):
     assert e.value.status == 1 and b"tri_material" in lib.gbt_last_error()
 
 
+def test_unknown_accel_rejected_on_host(lib):
+    d = G.gbt_scene_desc(343.0, 1, 0, 0.0, 0, 0, 0, 0, 1, 7)
+    with pytest.raises(G.GBTError) as e:
+        G.gbt_scene_create(d, 0)
+    assert e.value.status == 1 and b"accel" in lib.gbt_last_error()
+
+
 def test_null_handles_rejected(lib):
     st = lib.gbt_sum(None, None, None)
     assert st == 1
