@@ -238,7 +238,8 @@ def bench_tile_cull(G, torch, stream, sc, w, recv, gam, order, out, flush, steps
 def bench_batched(G, torch, stream, steps=5):
     """Batched city: 32 sources (log-uniform 4,096-262,144 rays), 8 frequencies, receivers
     128 x 128.  One graph-replayed batch submit (form chosen by the autotuner, and each form
-    on its own) vs one gbt_sum launch per source."""
+    on its own) vs one gbt_sum launch per source (8 frequencies each) and vs one launch per
+    (source, frequency)."""
     from paper_2501_13382_gb300 import inputs as I
     w = I.batched_city()
     recv_np = I.receiver_grid(128, 250.0, 1.5)
@@ -260,9 +261,21 @@ def bench_batched(G, torch, stream, steps=5):
         for d, o in zip(insts, outs):
             G.gbs_sum(d["trace"], recv, d["freqs"], d["beam_b"], gam, order=order,
                       window=w.window, out=o)
+
+    outs_f = [torch.empty_like(o) for o in outs]
+
+    def plain_per_frequency():
+        for d, o in zip(insts, outs_f):
+            for fi in range(len(d["freqs"])):
+                G.gbs_sum(d["trace"], recv, [d["freqs"][fi]], [d["beam_b"][fi]], gam,
+                          order=order, window=w.window, out=o[fi:fi + 1])
+    plain_per_frequency()
     plain()
     torch.cuda.synchronize()
     t_p = _timed(torch, stream, plain, steps) / steps
+    t_pf = _timed(torch, stream, plain_per_frequency, max(1, steps // 2)) / max(1, steps // 2)
+    err_pf = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+                 for a, b in zip(outs_f, outs))
     forms = {}
     for name, form in (("auto", G.BATCH_AUTO), ("fused", G.BATCH_FUSED),
                        ("concurrent", G.BATCH_CONCURRENT)):
@@ -278,13 +291,18 @@ def bench_batched(G, torch, stream, steps=5):
             "batched": forms["auto"], "fused_autotuned": forms["fused"],
             "concurrent": forms["concurrent"],
             "plain_per_instance": {"value": evals / (t_p * 1e-3), "ms": t_p},
-            "speedup": t_p / forms["auto"]["ms"]}
+            "plain_per_source_frequency": {"value": evals / (t_pf * 1e-3), "ms": t_pf,
+                                           "launches_of_gbs_sum": len(insts) * len(w.freqs),
+                                           "rel_l2_vs_plain": err_pf},
+            "speedup": t_p / forms["auto"]["ms"],
+            "speedup_vs_per_source_frequency": t_pf / forms["auto"]["ms"]}
 
 
 def bench_fwd_bwd(G, torch, stream, steps=5):
     """Differentiable city: 262,144 rays, <= 6 reflections, 128 x 128 receivers, 4 frequencies;
     forward + backward (gradients for 9 reflection coefficients and 4 beam parameters) vs
-    forward alone."""
+    forward alone, and the training step of the workload (L2 loss against the seeded target
+    field, through the torch.autograd.Function)."""
     from paper_2501_13382_gb300 import inputs as I
     w = I.diff_city()
     sc = G.Scene(w.scene)
@@ -315,6 +333,23 @@ def bench_fwd_bwd(G, torch, stream, steps=5):
         r = {"forward": {"value": evals / (t_f * 1e-3), "ms": t_f},
              "forward_backward": {"value": evals / (t_fb * 1e-3), "ms": t_fb},
              "backward_over_forward": (t_fb - t_f) / t_f}
+        # the training step of the workload: L2 loss against the field of the seeded target
+        # coefficients, forward and backward through the torch.autograd.Function
+        from paper_2501_13382_gb300.autograd import gbs_field
+        target = G.gbs_sum(tr, recv, freqs, bb,
+                           torch.as_tensor(w.extra["target_gamma"], device="cuda"),
+                           order=order, window=w.window)
+        gam_p = torch.tensor(w.scene.gamma, device="cuda", requires_grad=True)
+
+        def train_step():
+            gam_p.grad = None
+            p = gbs_field(tr, recv, freqs, bb, gam_p, order=order, window=w.window,
+                          tile_cull=cull)
+            (p - target).abs().pow(2).sum().backward()
+        train_step()
+        torch.cuda.synchronize()
+        t_a = _timed(torch, stream, train_step, steps) / steps
+        r["autograd_loss_step"] = {"value": evals / (t_a * 1e-3), "ms": t_a}
         if cull:
             res["tile_cull"] = r
         else:

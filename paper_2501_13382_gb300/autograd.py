@@ -21,15 +21,16 @@ from . import gbt as G
 
 class GBTSum(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, gamma, ray_weight, beam_b, trace, recv, freqs, order, window, cutoff):
+    def forward(ctx, gamma, ray_weight, beam_b, trace, recv, freqs, order, window, cutoff,
+                tile_cull=False):
         b = [float(v) for v in beam_b.detach().cpu().tolist()]
         p = G.gbs_sum(trace, recv, list(freqs), b, gamma.detach().contiguous(),
                       ray_weight=None if ray_weight is None else ray_weight.detach().contiguous(),
-                      order=order, window=window, cutoff=cutoff)
+                      order=order, window=window, cutoff=cutoff, tile_cull=tile_cull)
         ctx.save_for_backward(gamma, ray_weight if ray_weight is not None else torch.empty(0))
         ctx.has_w = ray_weight is not None
         ctx.trace, ctx.recv, ctx.freqs, ctx.b, ctx.order = trace, recv, list(freqs), b, order
-        ctx.window, ctx.cutoff = window, cutoff
+        ctx.window, ctx.cutoff, ctx.tile_cull = window, cutoff, tile_cull
         ctx.b_dtype, ctx.b_device = beam_b.dtype, beam_b.device
         return p
 
@@ -44,16 +45,19 @@ class GBTSum(torch.autograd.Function):
                                         grad_p.to(torch.complex64).contiguous(),
                                         ray_weight=None if w is None else w.detach().contiguous(),
                                         order=ctx.order, window=ctx.window, cutoff=ctx.cutoff,
-                                        need_weight=need_w, need_b=need_b)
+                                        need_weight=need_w, need_b=need_b,
+                                        tile_cull=ctx.tile_cull)
         gw = dw if (need_w and w is not None) else None
         gb = db.to(device=ctx.b_device, dtype=ctx.b_dtype) if need_b else None
-        return dg if ctx.needs_input_grad[0] else None, gw, gb, None, None, None, None, None, None
+        return (dg if ctx.needs_input_grad[0] else None, gw, gb,
+                None, None, None, None, None, None, None)
 
 
 def gbs_field(trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
-              window: int = G.WINDOW_LINE, cutoff: float = 16.0):
-    """Differentiable complex pressure p[f, r] (complex64)."""
+              window: int = G.WINDOW_LINE, cutoff: float = 16.0, tile_cull: bool = False):
+    """Differentiable complex pressure p[f, r] (complex64); ``tile_cull`` runs forward and
+    backward with the exact tile pre-cull."""
     if not torch.is_tensor(beam_b):
         beam_b = torch.tensor(list(beam_b), dtype=torch.float64, device=recv.device)
     return GBTSum.apply(gamma, ray_weight, beam_b, trace, recv, tuple(freqs), order, window,
-                        float(cutoff))
+                        float(cutoff), bool(tile_cull))

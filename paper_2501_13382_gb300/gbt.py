@@ -444,6 +444,13 @@ def _check_tensors(recv, gamma, ray_weight, order):
         assert order.is_cuda and order.dtype == torch.int32 and order.is_contiguous()
 
 
+def _check_out(out, nf: int, nr: int):
+    import torch
+    assert out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous(), \
+        "out must be a contiguous complex64 CUDA tensor"
+    assert tuple(out.shape) == (nf, nr), f"out must have shape ({nf}, {nr})"
+
+
 def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
             window: int = WINDOW_LINE, cutoff: float = 16.0, precision: int = PRECISION_F32,
             out=None, accumulate: bool = False, seg_split: int = 0, tile_cull: bool = False):
@@ -453,6 +460,7 @@ def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=Non
     nr = int(recv.shape[0])
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
+    _check_out(out, len(freqs), nr)
     a = sum_args(recv, freqs, beam_b, gamma, out, ray_weight, order, window, cutoff, precision,
                  accumulate, seg_split, tile_cull=tile_cull)
     gbt_sum(trace.handle, a, _stream_ptr())
@@ -479,6 +487,7 @@ def gbs_solve(scene: Scene, source, recv, freqs, beam_b, gamma, ray_weight=None,
     nr = int(recv.shape[0])
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
+    _check_out(out, len(freqs), nr)
     a = sum_args(recv, freqs, beam_b, gamma, out, ray_weight, order, window, cutoff,
                  PRECISION_F32, accumulate, 0, max_device_bytes, tile_cull=tile_cull)
     gbt_solve(scene.handle, source_desc(source), a, _stream_ptr())

@@ -86,9 +86,10 @@ def test_backward_line_window_open_plane(G):
     assert _rel(dw.cpu().numpy(), dw_o) < TOL
 
 
-def test_autograd_loss_gradients(G):
-    """L = sum |p - p_target|^2 through torch autograd; gradients vs the oracle adjoint
-    (the oracle adjoint is pinned to central differences)."""
+@pytest.mark.parametrize("tile_cull", [False, True])
+def test_autograd_loss_gradients(G, tile_cull):
+    """L = sum |p - p_target|^2 through torch autograd (testing every pair, and with the
+    tile pre-cull); gradients vs the oracle adjoint (pinned to central differences)."""
     import torch
     from paper_2501_13382_gb300.autograd import gbs_field
     sc0, src, recv, freqs, b, gamma_t, win = _problem(n_rays=8192, side=32, seed=7)
@@ -101,7 +102,7 @@ def test_autograd_loss_gradients(G):
     r = torch.as_tensor(recv, device="cuda")
     gam = torch.tensor(gamma0, device="cuda", requires_grad=True)
     bt = torch.tensor(b, device="cuda", dtype=torch.float64, requires_grad=True)
-    p = gbs_field(tr, r, freqs, bt, gam, order=G.recv_order(r), window=win)
+    p = gbs_field(tr, r, freqs, bt, gam, order=G.recv_order(r), window=win, tile_cull=tile_cull)
     tt = torch.as_tensor(target.astype(np.complex64), device="cuda")
     loss = (p - tt).abs().pow(2).sum()
     loss.backward()
