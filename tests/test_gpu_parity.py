@@ -619,3 +619,17 @@ def test_equal_distance_hits_go_to_the_lowest_primitive(G, accel):
     _compare_trace(gt, ot)
     hit = gt["hit"].cpu().numpy()
     assert hit.max() <= n and (hit > 0).sum() > 1000     # only originals are ever hit
+
+
+@pytest.mark.parametrize("n_tri", [1, 2, 4, 5, 12])
+def test_tiny_scenes_every_search_matches_oracle(G, n_tri):
+    """Scenes of a few triangles (the BVH's root then holds a single leaf up to 4) next to
+    the ground: every nearest-hit search against the oracle."""
+    tris, faces = I.box_triangles(8.0, 20.0, -6.0, 6.0, 15.0)
+    sc0 = I.Scene(343.0, True, 0.0, 0, tris[:n_tri], np.ones(n_tri, np.int32), faces[:n_tri],
+                  np.array([1.0, 0.8], np.float32))
+    src = I.Source(np.array([0.0, 0.0, 3.0]), 4096, 4, 300.0)
+    ot = O.trace(sc0, src)
+    for a in (G.ACCEL_AUTO, G.ACCEL_BVH, G.ACCEL_LINEAR):
+        _compare_trace(G.Trace(G.Scene(sc0, accel=a), src).segments(), ot)
+    assert (ot.hit > 0).sum() > 0                 # the triangles are really hit
