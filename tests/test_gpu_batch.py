@@ -107,3 +107,37 @@ def test_batch_with_tile_cull_equals_per_instance_sums(G, form):
                        ref.cpu().numpy().astype(np.complex128))
             assert e < 1e-6, (rep, e)
     batch.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_batch_with_latlong_fans_against_oracle(G, form):
+    """Instances traced with the paper's take-off grid (cell solid-angle weights, no
+    per-ray weights passed) mixed with Fibonacci ones: each batch output against the
+    oracle."""
+    import torch
+    w = I.batched_city(n_sources=4)
+    sc = G.Scene(w.scene)
+    gam = torch.as_tensor(w.scene.gamma, device="cuda")
+    recv_np = I.receiver_grid(24, 250.0, 1.5)
+    recv = torch.as_tensor(recv_np, device="cuda")
+    order = G.recv_order(recv)
+    freqs = [500.0, 1000.0]
+    insts, srcs = [], []
+    for i, s in enumerate(w.sources):
+        if i % 2 == 0:
+            src = I.Source(s.pos, 48 * 96, s.max_reflections, s.max_path, I.FAN_LATLONG, 48)
+        else:
+            src = I.Source(s.pos, 4096, s.max_reflections, s.max_path)
+        b = [I.beam_b_rule(src.n_rays, f) for f in freqs]
+        insts.append(dict(trace=G.Trace(sc, src), recv=recv, freqs=freqs, beam_b=b, gamma=gam,
+                          order=order))
+        srcs.append((src, b))
+    batch = G.Batch(insts, window=w.window, use_graph=True, form=form)
+    batch.submit()
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    for (src, b), out in zip(srcs, batch.outputs):
+        po = O.gbs_sum(O.trace(w.scene, src), recv_np, freqs, b, w.scene.c, w.scene.gamma,
+                       window=w.window)
+        assert rel_l2(out.cpu().numpy().astype(np.complex128), po) <= 1e-4
+    batch.close()
