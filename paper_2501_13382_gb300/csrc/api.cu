@@ -534,6 +534,7 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
         try {
             const size_t nt = (size_t)std::max<int64_t>(d.n_tri, 1);
             sd.tri = static_cast<double *>(dalloc(nt * 12 * sizeof(double), s));
+            sd.trif = static_cast<float *>(dalloc(nt * 9 * sizeof(float), s));
             sd.face = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
             sd.mat = static_cast<int32_t *>(dalloc(nt * sizeof(int32_t), s));
             sd.n_clusters = (d.n_tri + kTriCluster - 1) / kTriCluster;
@@ -598,7 +599,7 @@ gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_
             }
         } catch (...) {
             if (raw) dfree(raw, s);
-            dfree(sd.tri, s); dfree(sd.face, s); dfree(sd.mat, s); dfree(sd.cbox, s);
+            dfree(sd.tri, s); dfree(sd.trif, s); dfree(sd.face, s); dfree(sd.mat, s); dfree(sd.cbox, s);
             dfree(sd.tbox, s);
             if (sd.bvh) dfree(sd.bvh, s);
             if (sd.bvh_perm) dfree(sd.bvh_perm, s);
@@ -615,6 +616,7 @@ gbt_status gbt_scene_destroy(gbt_scene_t *scene)
         if (!scene) return;
         GBT_CUDA(cudaDeviceSynchronize());
         dfree(scene->d.tri, nullptr);
+        dfree(scene->d.trif, nullptr);
         dfree(scene->d.face, nullptr);
         dfree(scene->d.mat, nullptr);
         dfree(scene->d.cbox, nullptr);

@@ -76,6 +76,7 @@ struct SceneDev {
     int64_t n_tri = 0;
     int n_materials = 0;
     double *tri = nullptr;       // n_tri * 12
+    float *trif = nullptr;       // n_tri * 9: v0, e1, e2 rounded to FP32 (BVH screen)
     int32_t *face = nullptr;     // n_tri
     int32_t *mat = nullptr;      // n_tri
     // bounding boxes of consecutive triangle clusters (kTriCluster each), in FP32,

@@ -30,7 +30,7 @@ constexpr int kScanBlock = 1024;        // threads per scan block
 constexpr int kScanItems = 4;           // items per scan thread
 
 __global__ void scene_prep_kernel(const double *__restrict__ raw, int64_t n,
-                                  double *__restrict__ tri)
+                                  double *__restrict__ tri, float *__restrict__ trif)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -46,6 +46,8 @@ __global__ void scene_prep_kernel(const double *__restrict__ raw, int64_t n,
     o[3] = e1x; o[4] = e1y; o[5] = e1z;
     o[6] = e2x; o[7] = e2y; o[8] = e2z;
     o[9] = nx / len; o[10] = ny / len; o[11] = nz / len;
+    float *f = trif + 9 * k;
+    for (int q = 0; q < 9; ++q) f[q] = (float)o[q];
 }
 
 struct TraceParams {
@@ -59,6 +61,7 @@ struct TraceParams {
     double ground_z;
     int ground_mat;
     const double *tri;         // n_tri * 12
+    const float *trif;         // n_tri * 9 (v0, e1, e2 in FP32)
     const int32_t *face;
     const int32_t *mat;
     int64_t n_tri;
@@ -211,6 +214,44 @@ __device__ __forceinline__ void nearest_in_chunk(const double o[3], const double
     }
 }
 
+// Conservative FP32 screen in front of the exact FP64 test: false only when that test
+// is certain to reject the triangle.  With eps = 2^-24 the FP32 rounding of the inputs
+// (origin, direction, v0, e1, e2) and of these operations moves u's numerator (o - v0).p
+// by at most 9 eps sum_i (|o_i| + |v0_i|) |p|_i, the determinant by 8 eps sum |e1_i| |p|_i
+// and v's numerator by 9 eps sum |d_i| |q|_i (|p|_i, |q|_i: the sums of the absolute
+// products forming p = d x e2 and q = (o - v0) x e1); the margins below use 1e-5 in place
+// of those 9 eps and 8 eps, covering also the rounding of the comparisons and the FP64
+// test's own (about 1e-15 relative).  Outside the margins u < 0, u > 1, v < 0 or u + v > 1
+// holds in exact arithmetic, and so in FP64; where the determinant's sign is uncertain the
+// FP64 test decides.
+__device__ __forceinline__ bool tri_may_hit(float of0, float of1, float of2, float df0, float df1,
+                                            float df2, const float *__restrict__ f)
+{
+    const float v0x = f[0], v0y = f[1], v0z = f[2];
+    const float e1x = f[3], e1y = f[4], e1z = f[5];
+    const float e2x = f[6], e2y = f[7], e2z = f[8];
+    const float px = df1 * e2z - df2 * e2y, py = df2 * e2x - df0 * e2z, pz = df0 * e2y - df1 * e2x;
+    const float pax = fabsf(df1 * e2z) + fabsf(df2 * e2y), pay = fabsf(df2 * e2x) + fabsf(df0 * e2z),
+                paz = fabsf(df0 * e2y) + fabsf(df1 * e2x);
+    const float det = e1x * px + e1y * py + e1z * pz;
+    const float bd = 1e-5f * (fabsf(e1x) * pax + fabsf(e1y) * pay + fabsf(e1z) * paz) + 1e-30f;
+    const float adet = fabsf(det);
+    if (!(adet > bd)) return true;
+    const float tx = of0 - v0x, ty = of1 - v0y, tz = of2 - v0z;
+    const float ax = fabsf(of0) + fabsf(v0x), ay = fabsf(of1) + fabsf(v0y), az = fabsf(of2) + fabsf(v0z);
+    const float bu = 1e-5f * (ax * pax + ay * pay + az * paz) + 1e-30f;
+    const float sgn = det > 0.0f ? 1.0f : -1.0f;
+    const float su = sgn * (tx * px + ty * py + tz * pz);
+    if (su < -bu || su - adet > bu + bd) return false;
+    const float qx = ty * e1z - tz * e1y, qy = tz * e1x - tx * e1z, qz = tx * e1y - ty * e1x;
+    const float qax = ay * fabsf(e1z) + az * fabsf(e1y), qay = az * fabsf(e1x) + ax * fabsf(e1z),
+                qaz = ax * fabsf(e1y) + ay * fabsf(e1x);
+    const float bv = 1e-5f * (fabsf(df0) * qax + fabsf(df1) * qay + fabsf(df2) * qaz) + 1e-30f;
+    const float sv = sgn * (df0 * qx + df1 * qy + df2 * qz);
+    if (sv < -bv || su + sv - adet > bu + bv + bd) return false;
+    return true;
+}
+
 // Nearest hit among all triangles through the BVH.  Same candidates and the same
 // winner as testing every triangle in index order: a child whose padded box the ray
 // misses, or enters only beyond the best hit so far (widened like the boxes), holds
@@ -247,6 +288,7 @@ __device__ __forceinline__ void nearest_in_bvh(const TraceParams &p, const doubl
                 hit_tri = hit_tri && slab(of1, df1, id1, tb[1], tb[4], un, uf);
                 hit_tri = hit_tri && slab(of2, df2, id2, tb[2], tb[5], un, uf);
                 if (!hit_tri || un > uf) continue;
+                if (!tri_may_hit(of0, of1, of2, df0, df1, df2, p.trif + 9 * (int64_t)k)) continue;
                 const double t = ray_triangle(o, d, p.tri + 12 * (int64_t)k);
                 if (t > kTMin && (t < tbest || (t == tbest && k + 1 < best))) {
                     tbest = t;
@@ -580,7 +622,7 @@ void scene_prepare(SceneDev &sd, const double *tri_raw_dev, cudaStream_t s)
     if (sd.n_tri == 0) return;
     const int bs = 128;
     scene_prep_kernel<<<(unsigned)((sd.n_tri + bs - 1) / bs), bs, 0, s>>>(tri_raw_dev, sd.n_tri,
-                                                                          sd.tri);
+                                                                          sd.tri, sd.trif);
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
@@ -624,6 +666,7 @@ void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src, 
     p.ground_z = sd.ground_z;
     p.ground_mat = sd.ground_material;
     p.tri = sd.tri;
+    p.trif = sd.trif;
     p.face = sd.face;
     p.mat = sd.mat;
     p.n_tri = sd.n_tri;
