@@ -177,6 +177,33 @@ typedef struct gbt_trace_info {
 gbt_status gbt_trace_info_get(const gbt_trace_t *trace, gbt_trace_info *info);
 gbt_status gbt_trace_destroy(gbt_trace_t *trace);
 
+/* Segment list of a trace computed elsewhere (a saved trace, another tracer), in
+ * the layout gbt_trace_info exposes.  Device arrays; they are copied, so the
+ * caller may free them when gbt_trace_import returns. */
+typedef struct gbt_segments {
+    int64_t n_segments;           /* >= 0 */
+    const int32_t *ray_off;       /* n_rays + 1 offsets: ray_off[0] = 0, non-decreasing, at
+                                     most max_reflections + 1 segments per ray,
+                                     ray_off[n_rays] = n_segments */
+    const double *seg_o;          /* n_segments * 3, segment origins, m */
+    const double *seg_t;          /* n_segments * 3, unit directions */
+    const double *seg_L;          /* n_segments, lengths, m */
+    const double *seg_s0;         /* n_segments, unfolded arclength at the segment start, m */
+    const int32_t *seg_bmat;      /* n_segments, material of the reflection that starts the
+                                     segment (-1 for a ray's first); out-of-range materials
+                                     are flagged by the sums' status word */
+    const int32_t *seg_hit;       /* n_segments end primitives, or NULL (-1 each) */
+} gbt_segments;
+
+/* Trace handle over such a segment list, for the sums and the adjoint as if
+ * gbt_trace had produced it: `src` as for gbt_trace (fan size and kind, which set
+ * the default ray weights, traced ray range, max_reflections); segment j of ray
+ * i gets ray index ray_begin + i and depth j - ray_off[i].  The offsets are
+ * checked on the host (one synchronisation of `stream`); GBT_ERR_INVALID_ARG if
+ * they do not describe such a list. */
+gbt_status gbt_trace_import(const gbt_scene_t *scene, const gbt_source_desc *src,
+                            const gbt_segments *segs, void *stream, gbt_trace_t **out);
+
 /* ----------------------------------------------------------------- sum --
  * GBS process (Eq. 3): for every receiver x, frequency f and segment j with
  *   s_loc = (x - o_j).t_j,  s = s0_j + s_loc,  n^2 = |(x - o_j) x t_j|^2,

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbt_internal.h"
 
 namespace gbt {
@@ -317,6 +319,16 @@ static void validate_sum(const gbt_trace_t *trace, const gbt_sum_args *a, bool n
 }  // namespace gbt
 
 using namespace gbt;
+
+// Named NVTX range around each public entry point (trace, sum, adjoint, solve, batch,
+// receiver order), so profilers can attribute device work to the call that launched it;
+// free when no profiling tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 extern "C" {
 
@@ -630,10 +642,66 @@ gbt_status gbt_scene_destroy(gbt_scene_t *scene)
 gbt_status gbt_trace(const gbt_scene_t *scene, const gbt_source_desc *src, void *stream,
                      gbt_trace_t **out)
 {
+    NvtxRange nvtx_range("gbt_trace");
     return guarded([&] {
         GBT_REQUIRE(scene && src && out, "scene, src and out must be non-NULL");
         *out = nullptr;
         *out = make_trace(scene, *src, static_cast<cudaStream_t>(stream));
+    });
+}
+
+gbt_status gbt_trace_import(const gbt_scene_t *scene, const gbt_source_desc *src,
+                            const gbt_segments *segs, void *stream, gbt_trace_t **out)
+{
+    NvtxRange nvtx_range("gbt_trace_import");
+    return guarded([&] {
+        GBT_REQUIRE(scene && src && segs && out, "scene, src, segs and out must be non-NULL");
+        *out = nullptr;
+        validate_source(*src);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int64_t cnt = src->ray_count == 0 ? src->n_rays - src->ray_begin : src->ray_count;
+        const int64_t per_ray = (int64_t)src->max_reflections + 1;
+        const int64_t n = segs->n_segments;
+        GBT_REQUIRE(n >= 0 && n <= cnt * per_ray, "n_segments out of range for the ray range");
+        GBT_REQUIRE(segs->ray_off, "ray_off must be non-NULL");
+        GBT_REQUIRE(n == 0 || (segs->seg_o && segs->seg_t && segs->seg_L && segs->seg_s0 &&
+                               segs->seg_bmat),
+                    "segment arrays must be non-NULL");
+        std::vector<int32_t> off((size_t)cnt + 1);
+        GBT_CUDA(cudaMemcpyAsync(off.data(), segs->ray_off, off.size() * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+        GBT_CUDA(cudaStreamSynchronize(s));
+        GBT_REQUIRE(off[0] == 0 && off[(size_t)cnt] == n, "ray_off must run from 0 to n_segments");
+        for (int64_t i = 0; i < cnt; ++i) {
+            const int64_t c = (int64_t)off[i + 1] - off[i];
+            GBT_REQUIRE(c >= 0 && c <= per_ray,
+                        "ray_off: each ray needs 0 .. max_reflections + 1 segments");
+        }
+        gbt_trace_t *tr = new gbt_trace_s();
+        TraceDev &td = tr->d;
+        try {
+            alloc_trace_block(td, scene, *src, cnt, s);
+            td.ray_begin = src->ray_begin;
+            td.n_rays = cnt;
+            auto copy = [&](void *dst, const void *from, size_t bytes) {
+                if (bytes) GBT_CUDA(cudaMemcpyAsync(dst, from, bytes, cudaMemcpyDeviceToDevice, s));
+            };
+            copy(td.ray_off, segs->ray_off, ((size_t)cnt + 1) * sizeof(int32_t));
+            copy(td.o, segs->seg_o, (size_t)n * 3 * sizeof(double));
+            copy(td.t, segs->seg_t, (size_t)n * 3 * sizeof(double));
+            copy(td.L, segs->seg_L, (size_t)n * sizeof(double));
+            copy(td.s0, segs->seg_s0, (size_t)n * sizeof(double));
+            copy(td.bmat, segs->seg_bmat, (size_t)n * sizeof(int32_t));
+            if (segs->seg_hit) copy(td.hit, segs->seg_hit, (size_t)n * sizeof(int32_t));
+            else if (n) GBT_CUDA(cudaMemsetAsync(td.hit, 0xff, (size_t)n * sizeof(int32_t), s));
+            csr_ray_depth_launch(td, s);
+            td.n_seg_host = n;
+        } catch (...) {
+            if (td.block) dfree(td.block, s);
+            delete tr;
+            throw;
+        }
+        *out = tr;
     });
 }
 
@@ -675,6 +743,7 @@ gbt_status gbt_trace_destroy(gbt_trace_t *trace)
 
 gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *stream)
 {
+    NvtxRange nvtx_range("gbt_sum");
     return guarded([&] {
         validate_sum(trace, args);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -688,6 +757,7 @@ gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *str
 
 gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out, void *stream)
 {
+    NvtxRange nvtx_range("gbt_recv_order");
     return guarded([&] {
         GBT_REQUIRE(n_recv >= 0 && n_recv < 2147483647LL, "n_recv out of range");
         if (n_recv == 0) return;
@@ -720,6 +790,7 @@ gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
                             const float *grad_out, float *grad_gamma, float *grad_ray_weight,
                             double *grad_b, void *stream)
 {
+    NvtxRange nvtx_range("gbt_sum_backward");
     return guarded([&] {
         validate_sum(trace, args, false);
         GBT_REQUIRE(args->precision == GBT_PRECISION_F32, "backward supports F32 precision only");
@@ -736,6 +807,7 @@ gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
 gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const gbt_sum_args *args,
                      void *stream)
 {
+    NvtxRange nvtx_range("gbt_solve");
     return guarded([&] {
         GBT_REQUIRE(scene && src && args, "scene, src and args must be non-NULL");
         GBT_REQUIRE(src->ray_begin == 0 && src->ray_count == 0,
@@ -938,6 +1010,7 @@ gbt_status gbt_batch_create(const gbt_batch_desc *desc, void *stream, gbt_batch_
 
 gbt_status gbt_batch_submit(gbt_batch_t *batch, void *stream)
 {
+    NvtxRange nvtx_range("gbt_batch_submit");
     return guarded([&] {
         GBT_REQUIRE(batch && batch->impl, "batch is NULL");
         batch_submit(batch->impl, static_cast<cudaStream_t>(stream));

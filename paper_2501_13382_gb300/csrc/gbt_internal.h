@@ -142,6 +142,8 @@ void scene_prepare(SceneDev &sd, const double *tri_raw_dev, cudaStream_t s);
 void trace_launch(const SceneDev &sd, TraceDev &td, const gbt_source_desc &src,
                   void *scratch, size_t scratch_bytes, cudaStream_t s);
 size_t trace_scratch_bytes(int64_t n_rays, int max_refl);
+// Fills each segment's ray index and depth from the trace's offsets (imported traces).
+void csr_ray_depth_launch(TraceDev &td, cudaStream_t s);
 
 // ---- GBS launchers (gbs.cu) ----
 size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits);

@@ -615,7 +615,28 @@ __global__ void compact_kernel(CompactParams p)
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+__global__ void csr_ray_depth_kernel(const int32_t *__restrict__ off, int64_t n_rays,
+                                     int64_t ray_begin, int32_t *__restrict__ ray,
+                                     int32_t *__restrict__ depth)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_rays) return;
+    for (int32_t j = off[i], d = 0; j < off[i + 1]; ++j, ++d) {
+        ray[j] = (int32_t)(ray_begin + i);
+        depth[j] = d;
+    }
+}
+
 }  // namespace
+
+void csr_ray_depth_launch(TraceDev &td, cudaStream_t s)
+{
+    if (td.n_rays == 0) return;
+    csr_ray_depth_kernel<<<(unsigned)((td.n_rays + 255) / 256), 256, 0, s>>>(
+        td.ray_off, td.n_rays, td.ray_begin, td.ray, td.depth);
+    note_launches(1);
+    GBT_CUDA(cudaGetLastError());
+}
 
 void scene_prepare(SceneDev &sd, const double *tri_raw_dev, cudaStream_t s)
 {

@@ -55,6 +55,12 @@ class gbt_source_desc(C.Structure):
                 ("theta_deg", C.c_double * 2), ("phi_deg", C.c_double * 2)]
 
 
+class gbt_segments(C.Structure):
+    _fields_ = [("n_segments", C.c_int64), ("ray_off", C.c_void_p), ("seg_o", C.c_void_p),
+                ("seg_t", C.c_void_p), ("seg_L", C.c_void_p), ("seg_s0", C.c_void_p),
+                ("seg_bmat", C.c_void_p), ("seg_hit", C.c_void_p)]
+
+
 class gbt_trace_info(C.Structure):
     _fields_ = [("n_fan", C.c_int64), ("ray_begin", C.c_int64), ("n_rays", C.c_int64),
                 ("seg_capacity", C.c_int64), ("n_segments", C.c_int64),
@@ -95,6 +101,8 @@ _SIGS = {
     "gbt_trace": (C.c_int, [C.c_void_p, C.POINTER(gbt_source_desc), C.c_void_p,
                             C.POINTER(C.c_void_p)]),
     "gbt_trace_info_get": (C.c_int, [C.c_void_p, C.POINTER(gbt_trace_info)]),
+    "gbt_trace_import": (C.c_int, [C.c_void_p, C.POINTER(gbt_source_desc), C.POINTER(gbt_segments),
+                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "gbt_trace_destroy": (C.c_int, [C.c_void_p]),
     "gbt_sum": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.c_void_p]),
     "gbt_recv_order": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -180,6 +188,13 @@ def gbt_trace(scene: int, src: gbt_source_desc, stream: int = 0) -> int:
     h = C.c_void_p()
     _check(load().gbt_trace(C.c_void_p(scene), C.byref(src), C.c_void_p(stream), C.byref(h)),
            "gbt_trace")
+    return h.value
+
+
+def gbt_trace_import(scene: int, src: gbt_source_desc, segs: gbt_segments, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().gbt_trace_import(C.c_void_p(scene), C.byref(src), C.byref(segs),
+                                   C.c_void_p(stream), C.byref(h)), "gbt_trace_import")
     return h.value
 
 
@@ -359,13 +374,54 @@ class _CudaView:
 class Trace:
     """Traced fan (CSR of segments) living on the device."""
 
-    def __init__(self, scene: Scene, source, ray_begin: int = 0, ray_count: int = 0, dirs=None):
+    def __init__(self, scene: Scene, source, ray_begin: int = 0, ray_count: int = 0, dirs=None,
+                 segments: dict | None = None):
+        """Traces `source` through `scene`, or, with `segments` (device tensors in the layout
+        of `segments()`: ray_off, o, t, L, s0, bmat, optional hit), wraps a segment list
+        computed elsewhere (gbt_trace_import)."""
         self.scene = scene
         self.source = source
         self._dirs = dirs
-        self.handle = gbt_trace(scene.handle, source_desc(source, ray_begin, ray_count, dirs),
-                                _stream_ptr())
+        self.ray_begin, self.ray_count = int(ray_begin), int(ray_count)
+        desc = source_desc(source, ray_begin, ray_count, dirs)
+        if segments is None:
+            self.handle = gbt_trace(scene.handle, desc, _stream_ptr())
+        else:
+            sg = {k: v.contiguous() for k, v in segments.items() if k != "n_segments"}
+            s = gbt_segments(int(sg["L"].shape[0]), _ptr(sg["ray_off"]), _ptr(sg["o"]),
+                             _ptr(sg["t"]), _ptr(sg["L"]), _ptr(sg["s0"]), _ptr(sg["bmat"]),
+                             _ptr(sg.get("hit")))
+            self.handle = gbt_trace_import(scene.handle, desc, s, _stream_ptr())
         self.n_fan = int(source.n_rays)
+
+    def save(self, path: str):
+        """Writes the segment list and the source parameters to an .npz file (synchronises),
+        so that sums can be rerun later without tracing (`Trace.load`)."""
+        sg = {k: v.cpu().numpy() for k, v in self.segments().items() if k != "n_segments"}
+        s = self.source
+        np.savez(path, pos=np.asarray(s.pos, np.float64), n_rays=s.n_rays,
+                 max_reflections=s.max_reflections, max_path=s.max_path,
+                 fan=int(getattr(s, "fan", FAN_FIBONACCI)), n_theta=int(getattr(s, "n_theta", 0)),
+                 theta_deg=np.asarray(getattr(s, "theta_deg", (0.0, 180.0)), np.float64),
+                 phi_deg=np.asarray(getattr(s, "phi_deg", (0.0, 360.0)), np.float64),
+                 ray_begin=self.ray_begin, ray_count=self.ray_count, **sg)
+
+    @classmethod
+    def load(cls, scene: Scene, path: str) -> "Trace":
+        """A trace handle over a segment list written by `save` (gbt_trace_import)."""
+        import torch
+        from types import SimpleNamespace
+        z = np.load(path)
+        fan = int(z["fan"])
+        src = SimpleNamespace(pos=z["pos"], n_rays=int(z["n_rays"]),
+                              max_reflections=int(z["max_reflections"]),
+                              max_path=float(z["max_path"]),
+                              fan=FAN_FIBONACCI if fan == FAN_EXPLICIT else fan,
+                              n_theta=int(z["n_theta"]), theta_deg=tuple(z["theta_deg"]),
+                              phi_deg=tuple(z["phi_deg"]))
+        seg = {k: torch.as_tensor(z[k], device="cuda")
+               for k in ("ray_off", "o", "t", "L", "s0", "bmat", "hit")}
+        return cls(scene, src, int(z["ray_begin"]), int(z["ray_count"]), segments=seg)
 
     def info(self) -> gbt_trace_info:
         return gbt_trace_info_get(self.handle)

@@ -633,3 +633,60 @@ def test_tiny_scenes_every_search_matches_oracle(G, n_tri):
     for a in (G.ACCEL_AUTO, G.ACCEL_BVH, G.ACCEL_LINEAR):
         _compare_trace(G.Trace(G.Scene(sc0, accel=a), src).segments(), ot)
     assert (ot.hit > 0).sum() > 0                 # the triangles are really hit
+
+
+def test_trace_save_load_roundtrip_gives_identical_sums(G, tmp_path):
+    """A trace written to .npz and imported again (gbt_trace_import) holds the same
+    segments and gives bit-identical sums, for a ray range of the paper's take-off grid
+    (whose default weights come back with the fan)."""
+    import torch
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 64 * 96, 6, 1000.0, I.FAN_LATLONG, 64)
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src, ray_begin=1000, ray_count=3000)
+    path = str(tmp_path / "trace.npz")
+    tr.save(path)
+    tr2 = G.Trace.load(sc, path)
+    a, b = tr.segments(), tr2.segments()
+    for k in ("ray_off", "o", "t", "L", "s0", "ray", "depth", "bmat", "hit"):
+        assert np.array_equal(a[k].cpu().numpy(), b[k].cpu().numpy()), k
+    r = _dev(I.receiver_grid(24, 250.0, 1.5), torch.float32)
+    gam = _dev(sc0.gamma, torch.float32)
+    freqs, bb = [500.0, 1000.0], [60.0, 80.0]
+    p1 = G.gbs_sum(tr, r, freqs, bb, gam, window=I.WINDOW_SEGMENT).cpu().numpy()
+    p2 = G.gbs_sum(tr2, r, freqs, bb, gam, window=I.WINDOW_SEGMENT).cpu().numpy()
+    assert np.array_equal(p1, p2)
+
+
+def test_sum_over_imported_oracle_segments(G):
+    """GBS over ray paths traced elsewhere: the oracle's segment list imported as a trace,
+    summed on the GPU, against the oracle's sum; malformed offsets are rejected."""
+    import torch
+    sc0, _ = I.city_scene(I.SEED_BASE + 3)
+    src = I.Source(np.array([0.0, 0.0, 5.0]), 8192, 8, 1000.0)
+    ot = O.trace(sc0, src)
+    seg = {"ray_off": _dev(ot.ray_off.astype(np.int32)), "o": _dev(ot.o), "t": _dev(ot.t),
+           "L": _dev(ot.L), "s0": _dev(ot.s0), "bmat": _dev(ot.bmat.astype(np.int32)),
+           "hit": _dev(ot.hit.astype(np.int32))}
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src, segments=seg)
+    got = tr.segments()
+    assert np.array_equal(got["ray"].cpu().numpy(), ot.ray)
+    assert np.array_equal(got["depth"].cpu().numpy(), ot.depth)
+    recv = I.receiver_grid(32, 250.0, 1.5)
+    freqs, bb = [1000.0], [I.beam_b_rule(src.n_rays, 1000.0)]
+    p = G.gbs_sum(tr, _dev(recv, torch.float32), freqs, bb, _dev(sc0.gamma, torch.float32),
+                  window=I.WINDOW_SEGMENT)
+    po = O.gbs_sum(ot, recv, freqs, bb, sc0.c, sc0.gamma, window=I.WINDOW_SEGMENT)
+    assert rel_l2(p.cpu().numpy().astype(np.complex128), po) <= TOL_L2
+    bad = dict(seg)
+    off = ot.ray_off.astype(np.int32).copy()
+    off[10], off[11] = off[11], off[10] - 1           # decreasing offsets
+    bad["ray_off"] = _dev(off)
+    with pytest.raises(G.GBTError) as e:
+        G.Trace(sc, src, segments=bad)
+    assert e.value.status == 1
+    too_long = I.Source(src.pos, src.n_rays, 0, src.max_path)   # at most 1 segment per ray
+    with pytest.raises(G.GBTError):
+        G.Trace(sc, too_long, segments=seg)
+    G.gbt_sync()
