@@ -111,6 +111,8 @@ typedef struct gbt_scene_desc {
 enum { GBT_ACCEL_AUTO = 0, GBT_ACCEL_BVH = 1, GBT_ACCEL_LINEAR = 2 };
 
 gbt_status gbt_scene_create(const gbt_scene_desc *desc, void *stream, gbt_scene_t **out);
+/* Waits for the device (every stream), then frees the scene; its traces must be
+ * destroyed first.  NULL is a no-op. */
 gbt_status gbt_scene_destroy(gbt_scene_t *scene);
 
 /* --------------------------------------------------------------- trace --
@@ -175,6 +177,8 @@ typedef struct gbt_trace_info {
 } gbt_trace_info;
 
 gbt_status gbt_trace_info_get(const gbt_trace_t *trace, gbt_trace_info *info);
+/* Waits for the device (every stream), then frees the trace and its workspace.
+ * NULL is a no-op. */
 gbt_status gbt_trace_destroy(gbt_trace_t *trace);
 
 /* Segment list of a trace computed elsewhere (a saved trace, another tracer), in
@@ -218,7 +222,10 @@ gbt_status gbt_trace_import(const gbt_scene_t *scene, const gbt_source_desc *src
  *
  * F32 precision: FP32 arithmetic with float-float arclength and phase
  * reduction, FP32 MUFU exp/sin/cos, compensated per-receiver accumulation;
- * relative L2 error against an FP64 evaluation is about 1e-6..1e-5.
+ * relative L2 error against an FP64 evaluation measured at 1e-7..4e-7 on the
+ * synthetic open-plane and city workloads (tested to 1e-6 with 4 kHz phases
+ * over 1 km paths).  F64 precision: every step in FP64 (2.6e-8, the rounding of
+ * the complex64 output), at FP64 speed.
  * With more than 8 frequencies the F32 path runs one pair launch per group of
  * at most 8 (frequencies sorted by value when every b_f is equal, otherwise in
  * the given order); each group costs a full pass over the pairs.
