@@ -324,7 +324,9 @@ typedef struct gbt_batch_desc {
     int32_t n_instances;              /* >= 1 */
     const gbt_trace_t *const *traces; /* host array of n_instances handles */
     const gbt_sum_args *args;         /* host array of n_instances argument sets; all F32,
-                                         one window, n_freq <= 8 */
+                                         one window; an instance with more than 8
+                                         frequencies runs as one instance per group of 8
+                                         consecutive ones, each writing its rows of out */
     int32_t use_graph;                /* 1: capture on first submit, then replay */
     int32_t autotune;                 /* 1: time the candidate forms / work splittings at
                                          create (running the batch a few times), keep the best */

@@ -2564,16 +2564,29 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
 {
     BatchImpl *B = new BatchImpl();
     try {
-        const int n = d.n_instances;
-        B->traces.assign(d.traces, d.traces + n);
-        B->args.assign(d.args, d.args + n);
+        // an instance with more than kGroupFreq frequencies becomes one instance per group of
+        // consecutive frequencies, each writing its own rows of the caller's output
+        for (int i = 0; i < d.n_instances; ++i) {
+            const gbt_sum_args &a = d.args[i];
+            for (int g0 = 0; g0 < a.n_freq; g0 += kGroupFreq) {
+                gbt_sum_args sa = a;
+                sa.n_freq = std::min(kGroupFreq, a.n_freq - g0);
+                for (int f = 0; f < GBT_MAX_FREQ; ++f) {
+                    sa.freq_hz[f] = f < sa.n_freq ? a.freq_hz[g0 + f] : 0.0;
+                    sa.beam_b[f] = f < sa.n_freq ? a.beam_b[g0 + f] : 0.0;
+                }
+                sa.out = a.out + (size_t)g0 * (size_t)a.n_recv * 2;
+                B->traces.push_back(d.traces[i]);
+                B->args.push_back(sa);
+            }
+        }
+        const int n = (int)B->args.size();
         B->use_graph = d.use_graph != 0;
-        B->window = d.args[0].window;
+        B->window = B->args[0].window;
         for (int i = 0; i < n; ++i) {
-            GBT_REQUIRE(d.args[i].window == B->window, "batch instances must share one window");
-            GBT_REQUIRE(d.args[i].precision == GBT_PRECISION_F32, "batches are F32 only");
-            GBT_REQUIRE(d.args[i].n_freq <= 8, "batches support up to 8 frequencies");
-            B->nf_max = std::max(B->nf_max, (int)d.args[i].n_freq);
+            GBT_REQUIRE(B->args[i].window == B->window, "batch instances must share one window");
+            GBT_REQUIRE(B->args[i].precision == GBT_PRECISION_F32, "batches are F32 only");
+            B->nf_max = std::max(B->nf_max, (int)B->args[i].n_freq);
         }
         status_word();   // allocate before any capture
         // one synchronisation: segment counts of every trace
@@ -2582,10 +2595,10 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
         B->cost.resize(n);
         for (int i = 0; i < n; ++i) {
             int32_t ns = 0;
-            const TraceDev &td = d.traces[i]->d;
+            const TraceDev &td = B->traces[i]->d;
             GBT_CUDA(cudaMemcpy(&ns, td.ray_off + td.n_rays, sizeof(int32_t), cudaMemcpyDeviceToHost));
             B->n_seg[i] = ns;
-            B->cost[i] = (int64_t)ns * d.args[i].n_recv * d.args[i].n_freq;
+            B->cost[i] = (int64_t)ns * B->args[i].n_recv * B->args[i].n_freq;
         }
         B->order.resize(n);
         for (int i = 0; i < n; ++i) B->order[i] = i;

@@ -141,3 +141,27 @@ def test_batch_with_latlong_fans_against_oracle(G, form):
                        window=w.window)
         assert rel_l2(out.cpu().numpy().astype(np.complex128), po) <= 1e-4
     batch.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_batch_instances_with_more_than_eight_frequencies(G, form):
+    """Instances of 12 and 16 frequencies next to one of 3: the batch splits them into groups
+    of 8 consecutive frequencies; every output row against gbt_sum on the whole instance."""
+    import torch
+    w, sc, gam, insts, _ = _batch_setup(G, n_src=3, side=32, seed=8)
+    rng = np.random.default_rng(8)
+    for d, nf in zip(insts, (12, 3, 16)):
+        d["freqs"] = list(rng.permutation(125.0 * 2.0 ** (np.arange(nf) / 3.0)))
+        d["beam_b"] = [I.beam_b_rule(4096, f) for f in d["freqs"]]
+    batch = G.Batch(insts, window=w.window, use_graph=True, form=form)
+    batch.submit()
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    for d, out in zip(batch.instances, batch.outputs):
+        ref = G.gbs_sum(d["trace"], d["recv"], d["freqs"], d["beam_b"], gam, order=d["order"],
+                        window=w.window).cpu().numpy().astype(np.complex128)
+        got = out.cpu().numpy().astype(np.complex128)
+        assert got.shape == ref.shape
+        for f in range(ref.shape[0]):
+            assert rel_l2(got[f], ref[f]) < 1e-6, f
+    batch.close()
