@@ -2040,6 +2040,29 @@ static size_t records_bytes(const TraceDev &td)
     return align_up((size_t)kRecFloats * (size_t)td.capacity * sizeof(float), 256);
 }
 
+// Prepass of a trace's segments into kernel records (and FP64 amplitudes when amp64 is
+// set), with the sum's reflection coefficients and ray weights.
+static void prepass_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
+                           float *rec, double *amp64, cudaStream_t s)
+{
+    if (td.capacity == 0) return;
+    PrepParams pp{};
+    pp.n_seg_ptr = td.ray_off + td.n_rays;
+    pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
+    pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
+    pp.gamma = a.gamma;
+    pp.weight = a.ray_weight;
+    pp.fan = td.fan;
+    pp.n_fan = td.n_fan;
+    pp.n_materials = sd.n_materials;
+    pp.rec = rec;
+    pp.amp64 = amp64;
+    pp.status = status_word();
+    prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
+    note_launches(1);
+    GBT_CUDA(cudaGetLastError());
+}
+
 size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits)
 {
     size_t b = records_bytes(td);
@@ -2069,23 +2092,7 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
     void *order_ws = w;
     const int32_t *n_seg_ptr = td.ray_off + td.n_rays;
 
-    if (td.capacity > 0) {
-        PrepParams pp{};
-        pp.n_seg_ptr = n_seg_ptr;
-        pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
-        pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
-        pp.gamma = a.gamma;
-        pp.weight = a.ray_weight;
-        pp.fan = td.fan;
-        pp.n_fan = td.n_fan;
-        pp.n_materials = sd.n_materials;
-        pp.rec = rec;
-        pp.amp64 = amp64;
-        pp.status = status_word();
-        prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
-        note_launches(1);
-        GBT_CUDA(cudaGetLastError());
-    }
+    prepass_launch(td, sd, a, rec, amp64, s);
 
     if (a.n_recv <= 0) return;
     ReduceParams rp{};
@@ -2219,30 +2226,13 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     float *seg_G = reinterpret_cast<float *>(w + off[3]);
     float *seg_H = reinterpret_cast<float *>(w + off[4]);
     double *acc = reinterpret_cast<double *>(w + off[5]);
-    const int32_t *n_seg_ptr = td.ray_off + td.n_rays;
 
     GBT_CUDA(cudaMemsetAsync(seg_G, 0, (size_t)td.capacity * sizeof(float), s));
     GBT_CUDA(cudaMemsetAsync(seg_H, 0, (size_t)a.n_freq * td.capacity * sizeof(float), s));
     GBT_CUDA(cudaMemsetAsync(acc, 0, (size_t)(sd.n_materials + GBT_MAX_FREQ) * sizeof(double), s));
     if (grad_w) GBT_CUDA(cudaMemsetAsync(grad_w, 0, (size_t)td.n_fan * sizeof(float), s));
 
-    if (td.capacity > 0) {
-        PrepParams pp{};
-        pp.n_seg_ptr = n_seg_ptr;
-        pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
-        pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
-        pp.gamma = a.gamma;
-        pp.weight = a.ray_weight;
-        pp.fan = td.fan;
-        pp.n_fan = td.n_fan;
-        pp.n_materials = sd.n_materials;
-        pp.rec = rec;
-        pp.amp64 = amp64;
-        pp.status = status_word();
-        prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
-        note_launches(1);
-        GBT_CUDA(cudaGetLastError());
-    }
+    prepass_launch(td, sd, a, rec, amp64, s);
     // per frequency group: seg_G gathers every frequency's terms, seg_H the group's rows
     // (processing slots g0 .. g0 + nf - 1)
     if (a.n_recv > 0) {
@@ -2454,23 +2444,8 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
 static void batch_prepass(BatchImpl &B, int i, cudaStream_t s)
 {
     const TraceDev &td = B.traces[i]->d;
-    const gbt_sum_args &a = B.args[i];
-    if (td.capacity == 0) return;
-    PrepParams pp{};
-    pp.n_seg_ptr = td.ray_off + td.n_rays;
-    pp.o = td.o; pp.t = td.t; pp.L = td.L; pp.s0 = td.s0;
-    pp.ray = td.ray; pp.depth = td.depth; pp.bmat = td.bmat;
-    pp.gamma = a.gamma;
-    pp.weight = a.ray_weight;
-    pp.fan = td.fan;
-    pp.n_fan = td.n_fan;
-    pp.n_materials = td.scene->d.n_materials;
-    pp.rec = reinterpret_cast<float *>(static_cast<char *>(B.work) + B.rec_off[i]);
-    pp.amp64 = nullptr;
-    pp.status = status_word();
-    prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
-    note_launches(1);
-    GBT_CUDA(cudaGetLastError());
+    prepass_launch(td, td.scene->d, B.args[i],
+                   reinterpret_cast<float *>(static_cast<char *>(B.work) + B.rec_off[i]), nullptr, s);
 }
 
 // Merge of instance i (processing index k) into its output.
