@@ -29,6 +29,12 @@ MUTATIONS = {
     "fan_offset": ("double z = 1.0 - (2.0 * (double)i + 1.0) / (double)n;",
                    "double z = 1.0 - (2.0 * (double)i) / (double)n;"),
     "gaussian_exponent_half": ("I * k * n2 / (2.0 * E)", "I * k * n2 / E"),
+    "adjoint_weight_without_gamma_path": ("mw[ray] += creal(gc * gpath[j] * cu);",
+                                          "mw[ray] += creal(gc * cu);"),
+    "adjoint_gamma_product_includes_self": ("if (q2 != q) other *= gamma[S->bmat[q2]];",
+                                            "other *= gamma[S->bmat[q2]];"),
+    "adjoint_gamma_without_weight": ("mg[S->bmat[q]] += creal(gc * weight[ray] * other * cu);",
+                                     "mg[S->bmat[q]] += creal(gc * other * cu);"),
     "latlong_midpoint_weight": ("const double cell = dph * (cos(lo) - cos(hi));",
                                 "const double cell = dph * dth * sin(th);"),
     "latlong_cell_edge": ("const double th = th0 + ((double)it + 0.5) * dth;",
@@ -99,6 +105,19 @@ def _battery():
     lm = np.real(np.conj(g) * O.gbs_sum(tg, recv, [800.0], bb - h, C, [0.6], window=1,
                                         b_mask=bb)).sum()
     ok &= bool(math.isclose(db[0], (lp - lm) / (2 * h), rel_tol=1e-5))
+    # adjoint in gamma and in the ray weights against central differences (the field is
+    # linear in both over a single reflection, so the differences are exact up to rounding)
+    rng = np.random.default_rng(3)
+    w0 = (4 * math.pi / tg.n_rays) * rng.uniform(0.5, 1.5, tg.n_rays)
+    dg, dw, _ = O.gbs_adjoint(tg, recv, [800.0], bb, C, [0.6], g, weight=w0, window=1)
+    loss = lambda gam, w: np.real(np.conj(g) * O.gbs_sum(tg, recv, [800.0], bb, C, [gam],
+                                                          weight=w, window=1)).sum()
+    hg = 1e-3
+    ok &= bool(math.isclose(dg[0], (loss(0.6 + hg, w0) - loss(0.6 - hg, w0)) / (2 * hg),
+                            rel_tol=1e-6))
+    v = rng.normal(size=tg.n_rays) * (4 * math.pi / tg.n_rays)
+    fd = (loss(0.6, w0 + v) - loss(0.6, w0 - v)) / 2
+    ok &= bool(math.isclose(float(dw @ v), fd, rel_tol=1e-6))
     return ok
 
 
