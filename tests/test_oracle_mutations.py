@@ -35,6 +35,10 @@ MUTATIONS = {
                                             "other *= gamma[S->bmat[q2]];"),
     "adjoint_gamma_without_weight": ("mg[S->bmat[q]] += creal(gc * weight[ray] * other * cu);",
                                      "mg[S->bmat[q]] += creal(gc * other * cu);"),
+    "cutoff_without_b": ("return k * n2 * bm / (2.0 * (s * s + bm * bm)) <= A->cutoff;",
+                         "return k * n2 / (2.0 * (s * s + bm * bm)) <= A->cutoff;"),
+    "segment_window_closed_end": ("if (!(s_loc >= 0.0 && s_loc < S->L[j])) return 0;",
+                                  "if (!(s_loc >= 0.0 && s_loc <= S->L[j])) return 0;"),
     "latlong_midpoint_weight": ("const double cell = dph * (cos(lo) - cos(hi));",
                                 "const double cell = dph * dth * sin(th);"),
     "latlong_cell_edge": ("const double th = th0 + ((double)it + 0.5) * dth;",
@@ -105,6 +109,10 @@ def _battery():
     lm = np.real(np.conj(g) * O.gbs_sum(tg, recv, [800.0], bb - h, C, [0.6], window=1,
                                         b_mask=bb)).sum()
     ok &= bool(math.isclose(db[0], (lp - lm) / (2 * h), rel_tol=1e-5))
+    # cutoff and window against the beam amplitude (one segment, a grid of receivers)
+    from tests.test_oracle_pins import _cutoff_window_case
+    kept, expect, undecided = _cutoff_window_case()[:3]
+    ok &= bool(np.array_equal(kept[~undecided], expect[~undecided]))
     # adjoint in gamma and in the ray weights against central differences (the field is
     # linear in both over a single reflection, so the differences are exact up to rounding)
     rng = np.random.default_rng(3)

@@ -298,6 +298,41 @@ def test_summand_matches_matrix_form_of_eq1():
         assert abs(p - ref) <= 1e-10 * abs(ref)       # |phase| ~ 1e4 rad in FP64
 
 
+def _cutoff_window_case(cutoff=16.0):
+    """One segment along +x (s0 = 20 m, L = 50 m) and receivers at s_loc in {-5, 0, 25, 50,
+    60} m times normal offsets 0 .. 60 m: for each receiver the culled SEGMENT-window sum
+    and the unculled LINE-window beam.  Returns (kept?, expected?, undecided?)."""
+    f, b, s0, L = 800.0, 40.0, 20.0, 50.0
+    k = 2 * math.pi * f / C
+    tr = _one_segment_trace([0, 0, 0], [1.0, 0, 0], L=L, s0=s0)
+    xs = np.array([-5.0, 0.0, 25.0, 50.0, 60.0])
+    ns = np.linspace(0.0, 60.0, 241)
+    recv = np.array([[x, n, 0.0] for x in xs for n in ns], np.float32)
+    cut = O.gbs_sum(tr, recv, [f], [b], C, [1.0], weight=[1.0], window=0, cutoff=cutoff)[0]
+    full = O.gbs_sum(tr, recv, [f], [b], C, [1.0], weight=[1.0], window=1, cutoff=1e30)[0]
+    x = recv[:, 0].astype(float)
+    s = s0 + x
+    # the beam's Gaussian factor, read from the unculled field: |c| |E| / (k b / (8 pi^2))
+    gauss = np.abs(full) * np.abs(s - 1j * b) / (k * b / (8 * math.pi ** 2))
+    in_window = (x >= 0.0) & (x < L)
+    expect = in_window & (gauss >= math.exp(-cutoff))
+    undecided = np.abs(np.log(np.maximum(gauss, 1e-300)) + cutoff) < 1e-9
+    return cut != 0, expect, undecided, cut, full, tr, recv, f, b
+
+
+def test_cutoff_and_window_against_the_beam_amplitude():
+    """A pair is kept iff its beam's Gaussian factor exp(-k n^2 b / (2 (s^2 + b^2))), taken
+    from the magnitude of the unculled field, is at least exp(-C), and (SEGMENT window) its
+    projection lies in [0, L): half-open, so a receiver abreast of the segment's end belongs
+    to the next segment.  Kept pairs contribute exactly the unculled beam."""
+    kept, expect, undecided, cut, full, tr, recv, f, b = _cutoff_window_case()
+    assert np.array_equal(kept[~undecided], expect[~undecided])
+    assert np.array_equal(cut[kept], full[kept])
+    assert kept.sum() > 50 and (~kept & (recv[:, 0] >= 0) & (recv[:, 0] < 50)).sum() > 50
+    assert not kept[recv[:, 0] == 50.0].any() and kept[recv[:, 0] == 0.0].any()
+    assert O.count_kept(tr, recv, [f], [b], C, window=0) == int(kept.sum())
+
+
 def test_single_beam_profile_closed_form():
     """On-axis |c| = W k b / (8 pi^2 sqrt(s^2+b^2)); 1/e half-width w^2 = 2(s^2+b^2)/(k b);
     on-axis phase advances at k per metre (plus the Gouy term atan(s/b))."""
