@@ -187,3 +187,30 @@ def test_backward_latlong_fan_default_weights(G):
     assert _rel(dg.cpu().numpy(), dg_o) < TOL
     assert _rel(db.cpu().numpy(), db_o) < TOL
     assert _rel(dw.cpu().numpy(), dw_o) < TOL
+
+
+def test_backward_over_an_imported_trace(G):
+    """The adjoint over a trace imported from the oracle's segment list (gbt_trace_import)
+    against the oracle's adjoint."""
+    import torch
+    sc0, src, recv, freqs, b, gamma, win = _problem(n_rays=4096, side=20, seed=31)
+    otr = O.trace(sc0, src)
+    po = O.gbs_sum(otr, recv, freqs, b, sc0.c, gamma, window=win)
+    rng = np.random.default_rng(31)
+    g = (rng.normal(size=po.shape) + 1j * rng.normal(size=po.shape)) * np.abs(po).mean()
+    dg_o, dw_o, db_o = O.gbs_adjoint(otr, recv, freqs, b, sc0.c, gamma, g, window=win)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    seg = {"ray_off": dev(otr.ray_off.astype(np.int32)), "o": dev(otr.o), "t": dev(otr.t),
+           "L": dev(otr.L), "s0": dev(otr.s0), "bmat": dev(otr.bmat.astype(np.int32))}
+    sc = G.Scene(sc0)
+    tr = G.Trace(sc, src, segments=seg)
+    r = torch.as_tensor(recv, device="cuda")
+    dg, dw, db = G.gbs_sum_backward(tr, r, list(freqs), list(b),
+                                    torch.as_tensor(gamma, device="cuda"),
+                                    torch.as_tensor(g.astype(np.complex64), device="cuda"),
+                                    order=G.recv_order(r), window=win)
+    torch.cuda.synchronize()
+    G.gbt_sync()
+    assert _rel(dg.cpu().numpy(), dg_o) < TOL
+    assert _rel(db.cpu().numpy(), db_o) < TOL
+    assert _rel(dw.cpu().numpy(), dw_o) < TOL

@@ -690,3 +690,25 @@ def test_sum_over_imported_oracle_segments(G):
     with pytest.raises(G.GBTError):
         G.Trace(sc, too_long, segments=seg)
     G.gbt_sync()
+
+
+def test_chunked_accumulating_solve_with_twelve_frequencies(G):
+    """gbt_solve in 5 chunks with 12 frequencies (two pair launches per chunk), added to a
+    field already in `out`: equals the field plus one unchunked 12-frequency sum."""
+    import torch
+    w = I.city(n_rays=6400, n_recv_side=24)
+    src = w.sources[0]
+    sc = G.Scene(w.scene)
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    freqs = list(125.0 * 2.0 ** (np.arange(12) / 3.0))
+    b = [I.beam_b_rule(src.n_rays, f) for f in freqs]
+    one = G.gbs_solve(sc, src, r, freqs, b, gam, window=w.window).cpu().numpy()
+    base = torch.randn(12, r.shape[0], dtype=torch.complex64, device="cuda") * float(np.abs(one).mean())
+    out = base.clone()
+    per_ray = (src.max_reflections + 1) * (80 + 80 + 4 * 20 + 16)
+    G.gbs_solve(sc, src, r, freqs, b, gam, window=w.window, out=out, accumulate=True,
+                max_device_bytes=per_ray * (src.n_rays // 5 + 1))
+    got = (out - base).cpu().numpy()
+    for f in range(12):
+        assert rel_l2(got[f].astype(np.complex128), one[f].astype(np.complex128)) < 1e-5, f
