@@ -29,6 +29,8 @@
 //    batches, and the per-split partials are merged in float-float (error-free
 //    FP32 sums) in a fixed order by a second kernel, so results do not depend on
 //    scheduling.
+//  * The kernel holds the sums of up to 8 frequencies in registers; more (up to 16)
+//    run as one launch per group of 8, each with its own partials and output rows.
 
 #include <math.h>
 
