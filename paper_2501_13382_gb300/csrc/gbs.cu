@@ -1405,7 +1405,7 @@ __device__ __forceinline__ bool seg_reaches_ball(const float4 &r0, const float4 
 template <int WINDOW>
 __global__ void __launch_bounds__(kListChunk) list_count_kernel(
     const float *rec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
-    int64_t n_chunks, float alpha, float beta, int32_t *counts)
+    int64_t n_chunks, float alpha, float beta, int32_t *counts, uint32_t *bits)
 {
     extern __shared__ int32_t cnt_s[];
     for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) cnt_s[t] = 0;
@@ -1423,7 +1423,10 @@ __global__ void __launch_bounds__(kListChunk) list_count_kernel(
         for (int64_t t = 0; t < n_tiles; ++t) {
             const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, r2, ball[t], alpha, beta);
             const unsigned int m = __ballot_sync(0xffffffffu, pass);
-            if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt_s[t], (int32_t)__popc(m));
+            if ((threadIdx.x & 31) == 0) {
+                if (m) atomicAdd(&cnt_s[t], (int32_t)__popc(m));
+                if (bits) bits[t * n_chunks * 32 + c * 32 + (threadIdx.x >> 5)] = m;
+            }
         }
     }
     __syncthreads();
@@ -1559,6 +1562,33 @@ __global__ void __launch_bounds__(kListChunk) list_write_kernel(
             list[list_off[t] + chunk_off[t * n_chunks + c] + before +
                  __popc(m & ((1u << lane) - 1u))] = (int32_t)j;
         __syncthreads();
+    }
+}
+
+// The same lists from the ballots the counting pass stored (one 32-bit word per tile and
+// warp of 32 segments): no ball test is repeated, and each warp finds its place within
+// the chunk from the earlier warps' words, so there is no block barrier per tile.  Entry
+// order is the same (chunk, then warp, then lane).
+__global__ void __launch_bounds__(kListChunk) list_write_bits_kernel(
+    const int32_t *n_seg_ptr, int64_t n_tiles, int64_t n_chunks, const uint32_t *bits,
+    const int32_t *chunk_off, const int64_t *list_off, const int32_t *list_n, int32_t *list)
+{
+    const int64_t ns = *n_seg_ptr;
+    const int64_t c = blockIdx.x;
+    if (c * kListChunk >= ns) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t j = c * kListChunk + threadIdx.x;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        if (list_n[t] < 0) continue;
+        const uint32_t *row = bits + t * n_chunks * 32 + c * 32;
+        const uint32_t m = row[wid];
+        if (m == 0u) continue;
+        int before = lane < wid ? __popc(row[lane]) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+        if ((m >> lane) & 1u)
+            list[list_off[t] + chunk_off[t * n_chunks + c] + before +
+                 __popc(m & ((1u << lane) - 1u))] = (int32_t)j;
     }
 }
 
@@ -1924,6 +1954,7 @@ struct TileWs {
     int32_t *list = nullptr;
     uint16_t *mask = nullptr;      // per list entry: warp tiles it can reach
     float4 *wball = nullptr;       // per warp tile: bounding ball
+    uint32_t *bits = nullptr;      // [tiles][chunks * 32]: the counting pass's ballots, or null
     int64_t tiles = 0, chunks = 0, cap = 0, wtiles = 0;
     bool order = false, lists = false;
     size_t bytes = 0;              // workspace the layout needs
@@ -1958,6 +1989,10 @@ static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, boo
         t.list = reinterpret_cast<int32_t *>(take((size_t)t.cap * sizeof(int32_t)));
         t.mask = reinterpret_cast<uint16_t *>(take((size_t)t.cap * sizeof(uint16_t)));
         t.wball = reinterpret_cast<float4 *>(take((size_t)t.wtiles * sizeof(float4)));
+        // the ballots, unless they would take more than 4 GiB (then the write pass repeats
+        // the ball tests)
+        const size_t bb = (size_t)t.tiles * (size_t)t.chunks * 32 * sizeof(uint32_t);
+        if (bb <= (size_t(1) << 32)) t.bits = reinterpret_cast<uint32_t *>(take(bb));
     }
     t.bytes = off;
     return t;
@@ -1985,12 +2020,12 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
             GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_LINE>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             list_count_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, sm, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts);
+                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
         } else {
             GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_SEGMENT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             list_count_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, sm, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts);
+                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
         }
         list_scan_chunks_kernel<<<(unsigned)T, 1024, 0, s>>>(t.counts, t.chunks, t.weight);
         n += 2;
@@ -2015,15 +2050,23 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
                                                                          t.wtiles, t.wball);
         const dim3 mgrid(32, (unsigned)T);
         if (window == GBT_WINDOW_LINE) {
-            list_write_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
-                t.list_off, t.list_n, t.list);
+            if (t.bits)
+                list_write_bits_kernel<<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                    q.n_seg_ptr, T, t.chunks, t.bits, t.counts, t.list_off, t.list_n, t.list);
+            else
+                list_write_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                    q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                    t.list_off, t.list_n, t.list);
             list_mask_kernel<GBT_WINDOW_LINE><<<mgrid, 256, 0, s>>>(
                 q.rec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
         } else {
-            list_write_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
-                t.list_off, t.list_n, t.list);
+            if (t.bits)
+                list_write_bits_kernel<<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                    q.n_seg_ptr, T, t.chunks, t.bits, t.counts, t.list_off, t.list_n, t.list);
+            else
+                list_write_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                    q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                    t.list_off, t.list_n, t.list);
             list_mask_kernel<GBT_WINDOW_SEGMENT><<<mgrid, 256, 0, s>>>(
                 q.rec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
         }
