@@ -1488,20 +1488,22 @@ __global__ void list_mask_kernel(const float *rec, const float4 *wball, int64_t 
                                  float alpha, float beta, const int64_t *list_off,
                                  const int32_t *list_n, const int32_t *list, uint16_t *list_mask)
 {
+    __shared__ float4 sball[kTileWarps];
     const int64_t t = blockIdx.y;
     const int32_t n = list_n[t];
-    if (n <= 0) return;
+    if (n <= 0) return;                    // uniform over the block
+    const int nw = (int)min((int64_t)kTileWarps, n_wtiles - t * kTileWarps);
+    if (threadIdx.x < nw) sball[threadIdx.x] = wball[t * kTileWarps + threadIdx.x];
+    __syncthreads();
     const int64_t off = list_off[t];
+#pragma unroll 2
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float4 *R = reinterpret_cast<const float4 *>(rec + (int64_t)list[off + i] * kRecFloats);
         const float4 r0 = R[0], r1 = R[1], r2 = R[2];
         uint32_t wm = 0u;
-        for (int w = 0; w < kTileWarps; ++w) {
-            const int64_t wt = t * kTileWarps + w;
-            if (wt < n_wtiles && seg_reaches_ball<WINDOW>(r0, r1, r2, wball[wt], alpha, beta))
-                wm |= 1u << w;
-        }
+        for (int w = 0; w < nw; ++w)
+            if (seg_reaches_ball<WINDOW>(r0, r1, r2, sball[w], alpha, beta)) wm |= 1u << w;
         list_mask[off + i] = (uint16_t)wm;
     }
 }
