@@ -27,7 +27,7 @@ SOURCES = {
     "trace.cu": ["--fmad=false"],
     "gbs.cu": [],
 }
-HEADERS = ["gbt_internal.h"]
+HEADERS = ["gbt_internal.h", "bvh_build.h"]
 
 
 def _nvcc():
