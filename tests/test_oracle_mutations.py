@@ -109,6 +109,9 @@ def _battery():
     lm = np.real(np.conj(g) * O.gbs_sum(tg, recv, [800.0], bb - h, C, [0.6], window=1,
                                         b_mask=bb)).sum()
     ok &= bool(math.isclose(db[0], (lp - lm) / (2 * h), rel_tol=1e-5))
+    # Eq. 3 as a plain triple loop on a tiny traced scene
+    from tests.test_oracle_pins import _brute_force_mismatches
+    ok &= not _brute_force_mismatches()
     # cutoff and window against the beam amplitude (one segment, a grid of receivers)
     from tests.test_oracle_pins import _cutoff_window_case
     kept, expect, undecided = _cutoff_window_case()[:3]

@@ -277,6 +277,57 @@ def _eq1_matrix_form(x, o, t, s0, k, b, W, Gam):
     return Phi * Gam * amp * np.exp(phase)
 
 
+def _brute_force_mismatches():
+    """Eq. 3 as a plain triple loop on a tiny traced scene (8 rays off a box and the ground,
+    12 receivers, 2 frequencies, per-ray weights, two materials): every (receiver,
+    segment, frequency) term from the matrix form of Eq. 1 with Gamma_path the product of
+    the coefficients of the reflections before the segment, kept where the segment's
+    window holds and the beam's Gaussian factor is at least exp(-C); summed exactly."""
+    tris, faces = I.box_triangles(10.0, 16.0, -5.0, 5.0, 12.0)
+    sc = _scene(ground=True, tris=tris, faces=faces, mats=np.ones(12, np.int32),
+                gammas=[0.9, 0.7])
+    dirs = np.array([[1, 0, 0.1], [1, 0.3, -0.2], [1, -0.2, 0.4], [0.2, 1, -0.5],
+                     [1, 0.1, -0.6], [-1, 0.2, -0.3], [0.9, -0.4, 0.05], [0.5, 0.5, -1]], float)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    src = I.Source(np.array([0.0, 0.0, 3.0]), len(dirs), 3, 120.0)
+    tr = O.trace(sc, src, dirs=dirs)
+    assert tr.hit.max() >= 1 and (tr.hit == 0).any()             # box and ground both hit
+    rng = np.random.default_rng(4)
+    recv = np.concatenate([rng.uniform([-20, -15, 0.5], [8, 15, 10], (9, 3)),
+                           [[20.0, 0.0, 2.0], [5.0, 8.0, 1.0], [-8.0, -4.0, 6.0]]]).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, len(dirs)) * 4 * math.pi / len(dirs)
+    freqs, bb, cutoff = [400.0, 900.0], [20.0, 35.0], 16.0
+    got = O.gbs_sum(tr, recv, freqs, bb, C, sc.gamma, weight=w, window=0, cutoff=cutoff)
+    bad = []
+    for fi, (f, b) in enumerate(zip(freqs, bb)):
+        k = 2 * math.pi * f / C
+        for r, x in enumerate(recv.astype(float)):
+            re, im = [], []
+            for j in range(tr.n_seg):
+                o, t = tr.o[j], tr.t[j]
+                s_loc = (x - o) @ t
+                if not (0.0 <= s_loc < tr.L[j]):
+                    continue
+                first = j - tr.depth[j]
+                gam = math.prod(float(sc.gamma[tr.bmat[q]]) for q in range(first + 1, j + 1))
+                c = _eq1_matrix_form(x, o, t, tr.s0[j], k, b, w[tr.ray[j]], gam)
+                s = tr.s0[j] + s_loc
+                gauss = abs(c) * abs(s - 1j * b) / (w[tr.ray[j]] * gam * k * b / (8 * math.pi ** 2))
+                if gauss < math.exp(-cutoff):
+                    continue
+                re.append(c.real)
+                im.append(c.imag)
+            ref = math.fsum(re) + 1j * math.fsum(im)
+            if not abs(got[fi, r] - ref) <= 1e-12 * max(abs(ref), 1e-30) + 1e-18:
+                bad.append((fi, r, got[fi, r], ref))
+    assert np.count_nonzero(got) > 10
+    return bad
+
+
+def test_sum_brute_force_on_tiny_inputs():
+    assert _brute_force_mismatches() == []
+
+
 def test_summand_matches_matrix_form_of_eq1():
     rng = np.random.default_rng(1)
     for _ in range(40):
