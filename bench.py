@@ -13,6 +13,13 @@ and excluded from the per-step CUDA-event times.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own
 replica of the workload (weak scaling, no collective on the data path).
+On the default workload the line also carries `forms` (rank 0, outside the
+timed steps): the same step with the exact tile pre-cull; the 32-source
+batch against one launch per source and per (source, frequency); the
+differentiable city's forward, forward + backward and autograd training
+step; the tracer alone for each nearest-hit search.  `--workload` selects
+another workload (open_plane_small, city, diff_city, big_city) and
+`--tile-cull` times the pre-culled step as the main one.
 """
 from __future__ import annotations
 
