@@ -44,7 +44,7 @@ typedef enum gbt_status {
     GBT_ERR_CUDA = 3,            /* a CUDA runtime call failed */
     GBT_ERR_TIMEOUT = 4,         /* a bounded device wait ran out (via gbt_sync) */
     GBT_ERR_DEVICE_STATUS = 5,   /* a kernel flagged an internal error (via gbt_sync) */
-    GBT_ERR_UNSUPPORTED = 6      /* valid request this build does not handle */
+    GBT_ERR_UNSUPPORTED = 6      /* valid request the library does not handle */
 } gbt_status;
 
 enum { GBT_WINDOW_SEGMENT = 0,   /* a beam acts on 0 <= s_loc < L of its segment */
