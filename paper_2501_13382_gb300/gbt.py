@@ -490,21 +490,39 @@ def sum_args(recv, freqs: Sequence[float], beam_b: Sequence[float], gamma, out,
     return a
 
 
-def _check_tensors(recv, gamma, ray_weight, order):
+def _require(cond: bool, msg: str):
+    if not cond:
+        raise ValueError(msg)
+
+
+def _check_tensors(recv, gamma, ray_weight, order, n_materials: int | None = None,
+                   n_fan: int | None = None):
+    """The library reads these device arrays by index (gamma per material, ray_weight per
+    ray of the fan, order per receiver) and cannot see their sizes: check them here."""
     import torch
-    assert recv.is_cuda and recv.dtype == torch.float32 and recv.is_contiguous() and recv.dim() == 2
-    assert gamma.is_cuda and gamma.dtype == torch.float32 and gamma.is_contiguous()
+    _require(recv.is_cuda and recv.dtype == torch.float32 and recv.is_contiguous()
+             and recv.dim() == 2 and recv.shape[1] == 3,
+             "recv must be a contiguous float32 CUDA tensor of shape (n_recv, 3)")
+    _require(gamma.is_cuda and gamma.dtype == torch.float32 and gamma.is_contiguous(),
+             "gamma must be a contiguous float32 CUDA tensor")
+    if n_materials is not None:
+        _require(gamma.numel() == n_materials, f"gamma must hold {n_materials} coefficients")
     if ray_weight is not None:
-        assert ray_weight.is_cuda and ray_weight.dtype == torch.float32 and ray_weight.is_contiguous()
+        _require(ray_weight.is_cuda and ray_weight.dtype == torch.float32
+                 and ray_weight.is_contiguous(), "ray_weight must be a contiguous float32 CUDA tensor")
+        if n_fan is not None:
+            _require(ray_weight.numel() == n_fan, f"ray_weight must hold {n_fan} weights")
     if order is not None:
-        assert order.is_cuda and order.dtype == torch.int32 and order.is_contiguous()
+        _require(order.is_cuda and order.dtype == torch.int32 and order.is_contiguous()
+                 and order.numel() == recv.shape[0],
+                 "order must be a contiguous int32 CUDA tensor with one entry per receiver")
 
 
 def _check_out(out, nf: int, nr: int):
     import torch
-    assert out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous(), \
-        "out must be a contiguous complex64 CUDA tensor"
-    assert tuple(out.shape) == (nf, nr), f"out must have shape ({nf}, {nr})"
+    _require(out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous(),
+             "out must be a contiguous complex64 CUDA tensor")
+    _require(tuple(out.shape) == (nf, nr), f"out must have shape ({nf}, {nr})")
 
 
 def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
@@ -512,7 +530,7 @@ def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=Non
             out=None, accumulate: bool = False, seg_split: int = 0, tile_cull: bool = False):
     """Complex pressure p[f, r] (torch complex64 on the device)."""
     import torch
-    _check_tensors(recv, gamma, ray_weight, order)
+    _check_tensors(recv, gamma, ray_weight, order, trace.scene.n_materials, trace.n_fan)
     nr = int(recv.shape[0])
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
@@ -525,7 +543,7 @@ def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=Non
 
 def sum_stats(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
               window: int = WINDOW_LINE, cutoff: float = 16.0, tile_cull: bool = False) -> dict:
-    _check_tensors(recv, gamma, ray_weight, order)
+    _check_tensors(recv, gamma, ray_weight, order, trace.scene.n_materials, trace.n_fan)
     a = sum_args(recv, freqs, beam_b, gamma, None, ray_weight, order, window, cutoff,
                  tile_cull=tile_cull)
     st = gbt_sum_stats_get(trace.handle, a, _stream_ptr())
@@ -539,7 +557,7 @@ def gbs_solve(scene: Scene, source, recv, freqs, beam_b, gamma, ray_weight=None,
               out=None, accumulate: bool = False, tile_cull: bool = False):
     """Trace + sum of one source, chunked over rays under a device-byte budget."""
     import torch
-    _check_tensors(recv, gamma, ray_weight, order)
+    _check_tensors(recv, gamma, ray_weight, order, scene.n_materials, int(source.n_rays))
     nr = int(recv.shape[0])
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
@@ -566,7 +584,8 @@ class Batch:
         args = []
         for inst in instances:
             recv = inst["recv"]
-            _check_tensors(recv, inst["gamma"], inst.get("ray_weight"), inst.get("order"))
+            _check_tensors(recv, inst["gamma"], inst.get("ray_weight"), inst.get("order"),
+                           inst["trace"].scene.n_materials, inst["trace"].n_fan)
             out = inst.get("out")
             if out is None:
                 out = torch.empty((len(inst["freqs"]), recv.shape[0]), dtype=torch.complex64,
@@ -608,9 +627,11 @@ def gbs_sum_backward(trace: Trace, recv, freqs, beam_b, gamma, grad_out, ray_wei
                      need_weight: bool = True, need_b: bool = True, tile_cull: bool = False):
     """(d gamma, d ray_weight, d b) of a real loss with dL/dp = grad_out (complex64 [F, Nr])."""
     import torch
-    _check_tensors(recv, gamma, ray_weight, order)
+    _check_tensors(recv, gamma, ray_weight, order, trace.scene.n_materials, trace.n_fan)
     go = grad_out.contiguous()
-    assert go.dtype == torch.complex64 and go.is_cuda
+    _require(go.dtype == torch.complex64 and go.is_cuda
+             and tuple(go.shape) == (len(freqs), int(recv.shape[0])),
+             f"grad_out must be a complex64 CUDA tensor of shape ({len(freqs)}, {int(recv.shape[0])})")
     dg = torch.empty_like(gamma)
     dw = torch.empty(trace.n_fan, dtype=torch.float32, device=recv.device) if need_weight else None
     db = torch.empty(len(freqs), dtype=torch.float64, device=recv.device) if need_b else None

@@ -107,3 +107,27 @@ def test_torch_caching_allocator_as_library_allocator(lib):
     finally:
         G.gbt_set_allocator(None)
     assert torch.equal(ref, got)
+
+
+def test_binding_checks_tensors_before_any_call():
+    """The binding rejects tensors the library would read out of bounds or cannot use
+    (host tensors, wrong dtypes, gamma or ray_weight of the wrong length) before any
+    library call: the C ABI cannot see the sizes of device arrays."""
+    import torch
+    from types import SimpleNamespace
+    tr = SimpleNamespace(scene=SimpleNamespace(n_materials=2), n_fan=8, handle=0)
+    recv = torch.zeros(4, 3)
+    with pytest.raises(ValueError, match="recv"):
+        G.gbs_sum(tr, recv, [500.0], [10.0], torch.ones(2))
+    with pytest.raises(ValueError, match="recv"):
+        G._check_tensors(torch.zeros(4, 2), torch.ones(2), None, None)
+    if not torch.cuda.is_available():
+        return
+    r = torch.zeros(4, 3, device="cuda")
+    with pytest.raises(ValueError, match="gamma must hold 2"):
+        G._check_tensors(r, torch.ones(3, device="cuda"), None, None, 2, 8)
+    with pytest.raises(ValueError, match="ray_weight must hold 8"):
+        G._check_tensors(r, torch.ones(2, device="cuda"), torch.ones(7, device="cuda"), None, 2, 8)
+    with pytest.raises(ValueError, match="order"):
+        G._check_tensors(r, torch.ones(2, device="cuda"), None,
+                         torch.zeros(3, dtype=torch.int32, device="cuda"), 2, 8)
