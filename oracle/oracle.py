@@ -12,6 +12,8 @@ Functions and the passages they follow (arXiv 2501.13382):
   trace          -- straight-ray tracing with specular reflection (Sec. 2, Sec. 3.1)
   gbs_sum        -- Gaussian beam summation, Eq. 3 with the beam of Eq. 1 / Eq. 2
   gbs_adjoint    -- gradient of a real loss through gbs_sum
+  synthesize     -- time signals from per-frequency fields (superposition of the
+                    time-harmonic fields of Eq. 1 under the exp(-i omega t) convention)
 Parity unpinned (definitions with no external check): the Fibonacci variant,
 the beam-parameter rule, the cutoff C and the window choice.
 """
@@ -272,6 +274,16 @@ def gbs_adjoint(tr: Trace, receivers, freqs, b, c, gamma, g, weight=None, window
                         C.c_int(gam.shape[0]), _p(w), C.c_int64(tr.n_rays), _p(gg), _p(dg),
                         _p(dw), _p(db))
     return dg, dw, db
+
+
+def synthesize(p, freqs, amp, t0: float, dt: float, n_t: int) -> np.ndarray:
+    """Time signals of a superposition of time-harmonic fields (exp(-i omega t) convention):
+    h[n, r] = Re sum_f amp_f p[f, r] exp(-i 2 pi freq_f (t0 + n dt)), in FP64; with
+    amp_f = S(freq_f) df this is the Fourier synthesis of a source spectrum S."""
+    p = np.asarray(p, np.complex128)
+    t = t0 + dt * np.arange(int(n_t), dtype=np.float64)
+    ph = np.exp(-2j * np.pi * np.outer(t, np.asarray(freqs, np.float64)))      # (n_t, F)
+    return np.real((ph * np.asarray(amp, np.complex128)[None, :]) @ p)
 
 
 def count_kept(tr: Trace, receivers, freqs, b, c, window=1, cutoff=16.0) -> int:

@@ -437,6 +437,32 @@ def test_free_field_point_source(free65k, f, b):
         assert np.all(np.abs(resid) <= 0.05 * np.abs(law) + np.abs(law) ** 2 + 2e-5), (r, np.abs(resid))
 
 
+def test_broadband_synthesis_of_the_free_field_arrives_at_r_over_c(free65k):
+    """Time synthesis of the oracle's GBS fields: 16 equally weighted frequencies of a
+    free-field point source superpose to a pulse that peaks at the travel time r / c with
+    the height sum_f 1 / (4 pi r) (to the paraxial error of the beams), the arrival the
+    exp(-i omega t) convention fixes (the other sign would put it at -r / c)."""
+    freqs = np.linspace(250.0, 4000.0, 16)
+    recv = np.array([[40.0, 20.0, -10.0], [-30.0, 50.0, 25.0]], np.float32)
+    rr = np.linalg.norm(recv.astype(float), axis=1)
+    b = [min(100.0, I.beam_b_rule(65536, f)) for f in freqs]
+    p = O.gbs_sum(free65k, recv, freqs, b, C, [1.0], window=1)
+    dt = 1e-6
+    for r in range(2):
+        # the 250 Hz comb repeats the pulse every 4 ms: look within +-1.8 ms of r / c
+        t0 = rr[r] / C - 1.8e-3
+        h = O.synthesize(p[:, r:r + 1], freqs, np.ones(16), t0, dt, 3600)[:, 0]
+        n = int(np.argmax(h))
+        assert abs(t0 + n * dt - rr[r] / C) <= 2 * dt, (r, t0 + n * dt, rr[r] / C)
+        assert math.isclose(h[n], 16 / (4 * math.pi * rr[r]), rel_tol=2e-2)
+    # one frequency: a cosine of the field's phase running backwards in time
+    h1 = O.synthesize(p[:1], freqs[:1], [0.5 - 0.25j], 0.0, 1e-4, 50)
+    t = 1e-4 * np.arange(50)
+    a = (0.5 - 0.25j) * p[0]
+    assert np.allclose(h1, np.abs(a)[None, :] * np.cos(np.angle(a)[None, :] - 2 * np.pi * freqs[0] * t[:, None]),
+                       rtol=0, atol=1e-14 * np.abs(a).max())
+
+
 def test_free_field_error_does_not_depend_on_fan_once_resolved():
     recv = np.array([[60.0, 20.0, -30.0], [-100.0, 5.0, 40.0]], np.float32)
     k = 2 * math.pi * 500 / C
