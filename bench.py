@@ -17,7 +17,8 @@ On the default workload the line also carries `forms` (rank 0, outside the
 timed steps): the same step with the exact tile pre-cull; the 32-source
 batch against one launch per source and per (source, frequency); the
 differentiable city's forward, forward + backward and autograd training
-step; the tracer alone for each nearest-hit search.  `--workload` selects
+step; the tracer alone for each nearest-hit search; the time synthesis of
+the field into 2,048 samples.  `--workload` selects
 another workload (open_plane_small, city, diff_city, big_city) and
 `--tile-cull` times the pre-culled step as the main one.
 """
@@ -394,6 +395,32 @@ def bench_trace(G, torch, stream, steps=5):
     return res
 
 
+def bench_synthesis(G, torch, stream, field, freqs, steps=5):
+    """Time synthesis of the open-plane field (6 bands x 65,536 receivers) into 2,048
+    samples at 16 kHz: the kernel writes 2,048 x 65,536 floats, so it is bound by HBM."""
+    n_t, dt = 2048, 1.0 / 16000.0
+    out = torch.empty((n_t, field.shape[1]), dtype=torch.float32, device="cuda")
+    amp = [1.0] * len(freqs)
+
+    def step():
+        G.synthesize(field, list(freqs), amp, 0.0, dt, n_t, out=out)
+    step()
+    torch.cuda.synchronize()
+    ms = _timed(torch, stream, step, steps) / steps
+    bytes_out = out.numel() * 4
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f).get("hbm_gbs"))
+    except Exception:
+        pass
+    gbs = bytes_out / (ms * 1e-3) / 1e9
+    return {"samples": n_t, "receivers": int(field.shape[1]), "freqs": len(freqs), "ms": ms,
+            "output_GB_per_s": gbs, "hbm_peak_GB_per_s": peak,
+            "frac": (gbs / peak) if peak else None,
+            "note": "ms includes forming the FP64 phasors on the host and their upload"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,6 +582,7 @@ def main():
             "batched": bench_batched(G, torch, stream),
             "fwd_bwd": bench_fwd_bwd(G, torch, stream),
             "trace": bench_trace(G, torch, stream),
+            "synthesis": bench_synthesis(G, torch, stream, out, w.freqs),
         }
         # the forms overwrite `out`; recompute the measured workload's field for the check
         G.gbs_solve(sc, src, recv, list(w.freqs), list(w.beam_b[0]), gam, order=order,

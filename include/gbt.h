@@ -343,6 +343,23 @@ gbt_status gbt_batch_create(const gbt_batch_desc *desc, void *stream, gbt_batch_
 gbt_status gbt_batch_submit(gbt_batch_t *batch, void *stream);
 gbt_status gbt_batch_destroy(gbt_batch_t *batch);
 
+/* ------------------------------------------------------------ synthesis --
+ * Time signals from per-frequency fields: the superposition of the
+ * time-harmonic fields of Eq. 1 under the exp(-i omega t) convention.  For
+ * receiver r and t_n = t0 + n dt,
+ *   h[n, r] = Re sum_f A_f p[f, r] exp(-i 2 pi freq_f t_n),
+ * with complex amplitudes A_f (A_f = S(freq_f) df synthesises a source
+ * spectrum S).  p: device, n_freq * n_recv complex64, frequency-major (the
+ * layout of gbt_sum's out); freq_hz: host, n_freq values; amp: host, n_freq
+ * complex amplitudes as (re, im) doubles; out: device, n_t * n_recv float32,
+ * time-major, overwritten, or added to when accumulate is 1 (more than
+ * GBT_MAX_FREQ frequencies: several accumulating calls).  The phasors
+ * A_f exp(-i 2 pi freq_f t_n) are formed in FP64 on the host, the sums in FP32.
+ * n_freq 1 .. GBT_MAX_FREQ, n_t 1 .. 2^20, n_recv >= 0; asynchronous. */
+gbt_status gbt_synthesize(const float *p, int32_t n_freq, int64_t n_recv, const double *freq_hz,
+                          const double *amp, double t0, double dt, int64_t n_t, float *out,
+                          int32_t accumulate, void *stream);
+
 /* ---------------------------------------------------------- measurement --
  * Kernel timing: while enabled, each launch of the GBS pair kernel (forward
  * or backward) is bracketed by CUDA events recorded on its launch stream.

@@ -603,6 +603,51 @@ gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *str
     });
 }
 
+gbt_status gbt_synthesize(const float *p, int32_t n_freq, int64_t n_recv, const double *freq_hz,
+                          const double *amp, double t0, double dt, int64_t n_t, float *out,
+                          int32_t accumulate, void *stream)
+{
+    NvtxRange nvtx_range("gbt_synthesize");
+    return guarded([&] {
+        GBT_REQUIRE(n_freq >= 1 && n_freq <= GBT_MAX_FREQ, "n_freq must be in [1, 16]");
+        GBT_REQUIRE(n_recv >= 0, "n_recv must be >= 0");
+        GBT_REQUIRE(n_t >= 1 && n_t <= (int64_t(1) << 20), "n_t must be in [1, 2^20]");
+        GBT_REQUIRE(freq_hz && amp, "freq_hz and amp must be non-NULL");
+        GBT_REQUIRE(isfinite(t0) && isfinite(dt), "t0 and dt must be finite");
+        for (int f = 0; f < n_freq; ++f)
+            GBT_REQUIRE(isfinite(freq_hz[f]) && isfinite(amp[2 * f]) && isfinite(amp[2 * f + 1]),
+                        "freq_hz and amp must be finite");
+        GBT_REQUIRE(accumulate == 0 || accumulate == 1, "accumulate must be 0 or 1");
+        if (n_recv == 0) return;
+        GBT_REQUIRE(p && out, "p and out must be non-NULL");
+        // phasors A_f exp(-i 2 pi f t_n) in FP64: the phase in turns, reduced before the trig
+        std::vector<float2> ph((size_t)n_t * n_freq);
+        for (int64_t n = 0; n < n_t; ++n) {
+            const double t = t0 + (double)n * dt;
+            for (int f = 0; f < n_freq; ++f) {
+                double turns = freq_hz[f] * t;
+                turns -= floor(turns);
+                const double c = cos(2.0 * kPi * turns), sn = -sin(2.0 * kPi * turns);
+                const double re = amp[2 * f] * c - amp[2 * f + 1] * sn;
+                const double im = amp[2 * f] * sn + amp[2 * f + 1] * c;
+                ph[(size_t)n * n_freq + f] = make_float2((float)re, (float)im);
+            }
+        }
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        void *dev = dalloc(ph.size() * sizeof(float2), s);
+        try {
+            // from pageable memory: the copy is staged before the call returns
+            GBT_CUDA(cudaMemcpyAsync(dev, ph.data(), ph.size() * sizeof(float2),
+                                     cudaMemcpyHostToDevice, s));
+            synth_launch(p, n_freq, n_recv, static_cast<const float2 *>(dev), n_t, out, accumulate, s);
+        } catch (...) {
+            dfree(dev, s);
+            throw;
+        }
+        dfree(dev, s);
+    });
+}
+
 gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out, void *stream)
 {
     NvtxRange nvtx_range("gbt_recv_order");

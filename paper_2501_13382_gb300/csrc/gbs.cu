@@ -1594,6 +1594,41 @@ __global__ void __launch_bounds__(kListChunk) list_write_bits_kernel(
     }
 }
 
+// Time synthesis: out[n, r] (+)= Re sum_f ph[n, f] p[f, r], ph[n, f] = A_f exp(-i omega_f t_n).
+// Threads run over receivers (coalesced), a block row over kSynthTile time samples whose
+// phasors sit in shared memory; each thread holds its receiver's field in registers.
+// Memory-bound: it writes n_t * n_recv floats and reads the field once per time tile.
+constexpr int kSynthTile = 32;
+
+__global__ void __launch_bounds__(256) synth_kernel(const float2 *__restrict__ p, int nf,
+                                                    int64_t n_recv, const float2 *__restrict__ ph,
+                                                    int64_t n_t, float *__restrict__ out,
+                                                    int accumulate)
+{
+    __shared__ float2 sph[kSynthTile][GBT_MAX_FREQ];
+    const int64_t n0 = (int64_t)blockIdx.y * kSynthTile;
+    for (int i = threadIdx.x; i < kSynthTile * GBT_MAX_FREQ; i += blockDim.x) {
+        const int a = i / GBT_MAX_FREQ, f = i - a * GBT_MAX_FREQ;
+        sph[a][f] = (f < nf && n0 + a < n_t) ? ph[(n0 + a) * nf + f] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_recv) return;
+    float2 pr[GBT_MAX_FREQ];
+#pragma unroll
+    for (int f = 0; f < GBT_MAX_FREQ; ++f)
+        pr[f] = f < nf ? p[(int64_t)f * n_recv + r] : make_float2(0.f, 0.f);
+    const int na = (int)min((int64_t)kSynthTile, n_t - n0);
+    for (int a = 0; a < na; ++a) {
+        float acc = 0.f;
+#pragma unroll
+        for (int f = 0; f < GBT_MAX_FREQ; ++f)
+            acc = fmaf(sph[a][f].x, pr[f].x, fmaf(-sph[a][f].y, pr[f].y, acc));
+        float *o = out + (n0 + a) * n_recv + r;
+        *o = accumulate ? *o + acc : acc;
+    }
+}
+
 struct ReduceParams {
     int64_t n;                 // nf * n_recv
     int64_t n_recv;
@@ -2196,6 +2231,17 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         rp.p32 = q.partial;
         reduce();
     }
+}
+
+void synth_launch(const float *p, int nf, int64_t n_recv, const float2 *ph, int64_t n_t,
+                  float *out, int accumulate, cudaStream_t s)
+{
+    if (n_recv <= 0 || n_t <= 0) return;
+    const dim3 grid((unsigned)((n_recv + 255) / 256), (unsigned)((n_t + kSynthTile - 1) / kSynthTile));
+    synth_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(p), nf, n_recv, ph, n_t,
+                                      out, accumulate);
+    note_launches(1);
+    GBT_CUDA(cudaGetLastError());
 }
 
 size_t recv_order_scratch_bytes(int64_t n)

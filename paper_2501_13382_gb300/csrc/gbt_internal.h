@@ -162,6 +162,10 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s);
 void batch_submit(BatchImpl *b, cudaStream_t s);
 void batch_destroy(BatchImpl *b);
 
+// ---- time synthesis (gbs.cu): ph holds n_t * nf phasors A_f exp(-i omega_f t_n) ----
+void synth_launch(const float *p, int nf, int64_t n_recv, const float2 *ph, int64_t n_t,
+                  float *out, int accumulate, cudaStream_t s);
+
 // ---- backward (gbs.cu) ----
 size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a);
 void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,

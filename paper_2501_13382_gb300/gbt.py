@@ -105,6 +105,9 @@ _SIGS = {
                                    C.c_void_p, C.POINTER(C.c_void_p)]),
     "gbt_trace_destroy": (C.c_int, [C.c_void_p]),
     "gbt_sum": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.c_void_p]),
+    "gbt_synthesize": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                                 C.c_double, C.c_double, C.c_int64, C.c_void_p, C.c_int32,
+                                 C.c_void_p]),
     "gbt_recv_order": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "gbt_recv_order_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "gbt_sum_backward": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.c_void_p, C.c_void_p,
@@ -620,6 +623,28 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def synthesize(p, freqs, amp, t0: float, dt: float, n_t: int, out=None, accumulate: bool = False):
+    """Time signals h[n, r] = Re sum_f amp_f p[f, r] exp(-i 2 pi freq_f (t0 + n dt)) from
+    per-frequency fields p (complex64 [F, Nr] on the device, as gbs_sum returns them);
+    float32 [n_t, Nr] (gbt_synthesize)."""
+    import torch
+    nf = len(freqs)
+    _require(p.is_cuda and p.dtype == torch.complex64 and p.is_contiguous()
+             and p.dim() == 2 and p.shape[0] == nf,
+             f"p must be a contiguous complex64 CUDA tensor of shape ({nf}, n_recv)")
+    _require(len(amp) == nf, "one amplitude per frequency")
+    nr = int(p.shape[1])
+    if out is None:
+        out = torch.empty((int(n_t), nr), dtype=torch.float32, device=p.device)
+    _require(out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+             and tuple(out.shape) == (int(n_t), nr), f"out must be float32 of shape ({n_t}, {nr})")
+    fr = (C.c_double * nf)(*[float(f) for f in freqs])
+    am = (C.c_double * (2 * nf))(*[v for a in amp for v in (complex(a).real, complex(a).imag)])
+    _check(load().gbt_synthesize(_ptr(p), nf, nr, fr, am, float(t0), float(dt), int(n_t),
+                                 _ptr(out), 1 if accumulate else 0, _stream_ptr()), "gbt_synthesize")
+    return out
 
 
 def gbs_sum_backward(trace: Trace, recv, freqs, beam_b, gamma, grad_out, ray_weight=None,

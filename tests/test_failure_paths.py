@@ -131,3 +131,11 @@ def test_binding_checks_tensors_before_any_call():
     with pytest.raises(ValueError, match="order"):
         G._check_tensors(r, torch.ones(2, device="cuda"), None,
                          torch.zeros(3, dtype=torch.int32, device="cuda"), 2, 8)
+
+
+def test_synthesis_rejects_bad_arguments_on_host(lib):
+    fr = (ctypes.c_double * 17)(*([500.0] * 17))
+    am = (ctypes.c_double * 34)(*([1.0] * 34))
+    for nf, n_t in ((0, 10), (17, 10), (4, 0), (4, (1 << 20) + 1)):
+        assert lib.gbt_synthesize(None, nf, 0, fr, am, 0.0, 1e-4, n_t, None, 0, None) == 1
+    assert lib.gbt_synthesize(None, 4, 10, fr, am, 0.0, 1e-4, 10, None, 0, None) == 1   # NULL p

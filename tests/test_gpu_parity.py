@@ -712,3 +712,29 @@ def test_chunked_accumulating_solve_with_twelve_frequencies(G):
     got = (out - base).cpu().numpy()
     for f in range(12):
         assert rel_l2(got[f].astype(np.complex128), one[f].astype(np.complex128)) < 1e-5, f
+
+
+@pytest.mark.parametrize("nf,n_t", [(1, 1), (12, 777), (16, 64)])
+def test_synthesis_against_oracle(G, nf, n_t):
+    """Time synthesis on the GPU (FP64 phasors, FP32 sums) against the oracle's FP64
+    definition, sample by sample: |error| <= 2e-6 of the summed magnitudes of the terms
+    (a ragged last time tile, one and sixteen frequencies), and added into `out`."""
+    import torch
+    rng = np.random.default_rng(nf)
+    nr = 1000
+    p = (rng.normal(size=(nf, nr)) + 1j * rng.normal(size=(nf, nr))).astype(np.complex64)
+    freqs = rng.uniform(100.0, 4000.0, nf)
+    amp = rng.normal(size=nf) + 1j * rng.normal(size=nf)
+    t0, dt = 0.0123, 2.3e-5
+    h = G.synthesize(_dev(p), list(freqs), list(amp), t0, dt, n_t)
+    torch.cuda.synchronize()
+    ho = O.synthesize(p.astype(np.complex128), freqs, amp, t0, dt, n_t)
+    scale = (np.abs(amp)[:, None] * np.abs(p.astype(np.complex128))).sum(0)[None, :]
+    assert np.all(np.abs(h.cpu().numpy() - ho) <= 2e-6 * scale)
+    base = torch.randn(n_t, nr, device="cuda")
+    out = base.clone()
+    G.synthesize(_dev(p), list(freqs), list(amp), t0, dt, n_t, out=out, accumulate=True)
+    b = base.cpu().numpy()
+    assert np.all(np.abs(out.cpu().numpy() - b - ho) <= 2e-6 * scale + 1e-6 * np.abs(b))
+    G.gbt_sync()
+
