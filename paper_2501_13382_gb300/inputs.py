@@ -234,11 +234,20 @@ def open_plane_latlong(n_theta: int = 128, n_phi: int = 256) -> Workload:
 CITY_MAX_PATH = 1000.0
 
 
+def _count_name(n: int) -> str:
+    """1048576 -> '1M', 262144 -> '256k', 1000 -> '1000'."""
+    if n % (1 << 20) == 0:
+        return f"{n >> 20}M"
+    if n % 1024 == 0:
+        return f"{n >> 10}k"
+    return str(n)
+
+
 def city(n_rays: int = 1 << 20, n_recv_side: int = 512) -> Workload:
     """Synthetic city: 64 boxes, 1,048,576 rays from (0,0,5), <=8 reflections, 512^2 receivers, 1 kHz."""
     sc, ex = city_scene(SEED_BASE + 3)
     src = Source(np.array([0.0, 0.0, 5.0]), n_rays, 8, CITY_MAX_PATH)
-    w = Workload("city_1M_rays_512x512_1kHz", sc, [src],
+    w = Workload(f"city_{_count_name(n_rays)}_rays_{n_recv_side}x{n_recv_side}_1kHz", sc, [src],
                  receiver_grid(n_recv_side, 250.0, 1.5), np.array([1000.0]),
                  WINDOW_SEGMENT, extra=ex)
     return _with_b(w)
