@@ -156,7 +156,7 @@ def oracle_rate(w, budget_s: float, seed: int = 17, tr=None):
         tr = O.trace(w.scene, src)
         t_trace = time.perf_counter() - t0
     nr = int(w.receivers.shape[0])
-    n = min(nr, 8 * O.num_threads())    # OpenMP runs over receivers: keep every core busy
+    n = min(nr, 32 * O.num_threads())   # OpenMP: chunks of 16 receivers; keep every core busy
     while True:
         idx = I.receiver_subset(w.receivers, n, seed)
         t0 = time.perf_counter()
@@ -200,8 +200,9 @@ def run_reference(args):
     tr = O.trace(w.scene, src)
     t_trace = time.perf_counter() - t0
     nr = int(w.receivers.shape[0])
-    # sample size: every core busy (OpenMP runs over receivers), at least 0.1 s per step
-    n = min(nr, 8 * O.num_threads())
+    # sample size: every core busy (OpenMP hands out receivers in chunks of 16), at least
+    # 0.1 s per step
+    n = min(nr, 32 * O.num_threads())
     while n < nr:
         idx = I.receiver_subset(w.receivers, n, 23)
         t0 = time.perf_counter()

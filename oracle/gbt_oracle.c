@@ -42,6 +42,17 @@
  *  4. Adjoint of the sum for a real loss L with g = dL/dRe p + i dL/dIm p:
  *     dL/dtheta = sum Re(conj(g) dp/dtheta) for theta = per-material gamma,
  *     per-ray weight and per-frequency beam parameter b (cull mask held fixed).
+ *  5. Propagation losses.  The paper's input tables (Sec. 4.5, Tables 2-3) give
+ *     the air temperature, relative humidity and pressure and a flow-impedance
+ *     setting of the surfaces, and say they shape the field, but give no
+ *     formula.  Standard published ones are used: the pure-tone absorption of
+ *     air of ISO 9613-1, applied as the amplitude factor exp(-a s) over the
+ *     unfolded arclength s of the beam; and, for a porous surface of effective
+ *     flow resistivity sigma, the normalised impedance of Delany and Bazley
+ *     (1970) with the plane-wave reflection factor of a locally reacting
+ *     surface at each reflection's angle of incidence, multiplying the
+ *     material's gamma.  A surface with sigma <= 0 is hard (the paper's
+ *     negative setting): its reflection is gamma alone.
  */
 #include <complex.h>
 #include <math.h>
@@ -230,6 +241,109 @@ void orc_trace(const orc_scene *sc, const double *src, const double *dirs,
     }
 }
 
+/* ---------------------------------------------------- propagation losses -- */
+
+/* Pure-tone attenuation coefficient of air in dB per metre (ISO 9613-1): the
+ * saturation vapour pressure over the triple-point temperature, the molar
+ * concentration h of water vapour from the relative humidity, the relaxation
+ * frequencies of oxygen and nitrogen, and the classical-plus-rotational term
+ * with the two vibrational relaxation terms.  T_c in degrees Celsius, rh in
+ * percent, p_kpa the ambient pressure in kPa. */
+double orc_air_absorption_db(double f, double T_c, double rh, double p_kpa)
+{
+    const double T0 = 293.15;            /* reference temperature, K */
+    const double T01 = 273.16;           /* triple-point isotherm temperature, K */
+    const double pr = 101.325;           /* reference pressure, kPa */
+    const double T = T_c + 273.15;
+    const double prel = p_kpa / pr;
+    const double C = -6.8346 * pow(T01 / T, 1.261) + 4.6151;
+    const double psat_rel = pow(10.0, C);               /* p_sat / p_r */
+    const double h = rh * psat_rel / prel;              /* percent */
+    const double frO = prel * (24.0 + 4.04e4 * h * (0.02 + h) / (0.391 + h));
+    const double frN = prel * pow(T / T0, -0.5) *
+                       (9.0 + 280.0 * h * exp(-4.170 * (pow(T / T0, -1.0 / 3.0) - 1.0)));
+    const double classical = 1.84e-11 / prel * sqrt(T / T0);
+    const double oxygen = 0.01275 * exp(-2239.1 / T) / (frO + f * f / frO);
+    const double nitrogen = 0.1068 * exp(-3352.0 / T) / (frN + f * f / frN);
+    return 8.686 * f * f * (classical + pow(T / T0, -2.5) * (oxygen + nitrogen));
+}
+
+/* The same attenuation as a pressure-amplitude decay rate a (Np/m): the amplitude
+ * falls as exp(-a s) over a path of length s, and 20 log10(e) dB = 1 Np. */
+double orc_air_absorption_np(double f, double T_c, double rh, double p_kpa)
+{
+    return orc_air_absorption_db(f, T_c, rh, p_kpa) / (20.0 / log(10.0));
+}
+
+/* Normalised surface impedance Z / (rho c) of a porous surface of effective flow
+ * resistivity sigma (kPa s m^-2) at frequency f (Hz): Delany and Bazley's
+ * one-parameter model, written for the exp(-i omega t) convention. */
+static double complex orc_delany_bazley(double f, double sigma)
+{
+    const double x = f / sigma;
+    return 1.0 + 9.08 * pow(x, -0.75) + I * 11.9 * pow(x, -0.73);
+}
+
+void orc_delany_bazley_z(double f, double sigma, double *z)
+{
+    const double complex Z = orc_delany_bazley(f, sigma);
+    z[0] = creal(Z);
+    z[1] = cimag(Z);
+}
+
+/* Reflection factor of a plane wave meeting a locally reacting surface of
+ * normalised impedance Z at incidence angle theta (cos_theta = cos theta). */
+static double complex orc_plane_wave_reflection(double complex Z, double cos_theta)
+{
+    return (Z * cos_theta - 1.0) / (Z * cos_theta + 1.0);
+}
+
+void orc_plane_wave_reflection_r(const double *z, double cos_theta, double *r)
+{
+    const double complex R = orc_plane_wave_reflection(z[0] + I * z[1], cos_theta);
+    r[0] = creal(R);
+    r[1] = cimag(R);
+}
+
+/* Cosine of the angle of incidence at the reflection that starts each segment:
+ * |t_j . n| with n the unit normal of the primitive that ended segment j - 1
+ * (a mirror reflection keeps |d . n|, so the reflected direction gives it);
+ * 1 for the first segment of a ray. */
+void orc_incidence_cos(const orc_scene *sc, int64_t n_seg, const double *t,
+                       const int32_t *depth, const int32_t *hit, double *cosi)
+{
+    for (int64_t j = 0; j < n_seg; ++j) {
+        if (depth[j] == 0) { cosi[j] = 1.0; continue; }
+        const int32_t prim = hit[j - 1];
+        double nrm[3] = {0.0, 0.0, 1.0};
+        if (prim >= 1) orc_triangle_normal(sc->tri + 9 * (int64_t)(prim - 1), nrm);
+        cosi[j] = fabs(t[3 * j] * nrm[0] + t[3 * j + 1] * nrm[1] + t[3 * j + 2] * nrm[2]);
+    }
+}
+
+/* Per frequency f and segment j: the product, over the reflections before j off a
+ * porous material (sigma[m] > 0), of the plane-wave reflection factor of the
+ * material's Delany-Bazley impedance at that reflection's incidence; 1 where the
+ * path met none.  out: interleaved complex, [n_freq][n_seg]. */
+void orc_path_factor(int64_t n_seg, const int32_t *depth, const int32_t *bmat,
+                     const double *cosi, const double *sigma, const double *freq, int n_freq,
+                     double *out)
+{
+    for (int f = 0; f < n_freq; ++f) {
+        for (int64_t j = 0; j < n_seg; ++j) {
+            double complex F = 1.0;
+            const int64_t first = j - depth[j];
+            for (int64_t q = first + 1; q <= j; ++q) {
+                const double sg = sigma[bmat[q]];
+                if (sg > 0.0)
+                    F *= orc_plane_wave_reflection(orc_delany_bazley(freq[f], sg), cosi[q]);
+            }
+            out[2 * ((int64_t)f * n_seg + j) + 0] = creal(F);
+            out[2 * ((int64_t)f * n_seg + j) + 1] = cimag(F);
+        }
+    }
+}
+
 /* ------------------------------------------------------------------ sum -- */
 
 typedef struct {
@@ -251,6 +365,9 @@ typedef struct {
     const double *b_mask;   /* b used by the cull test (NULL -> b) */
     double cutoff;          /* C */
     int window;             /* 0 SEGMENT, 1 LINE */
+    const double *absorb;   /* amplitude attenuation of air per frequency, Np/m (NULL: none) */
+    const double *seg_factor; /* complex reflection factors of porous surfaces per frequency and
+                                 segment, interleaved [n_freq][n_seg] (NULL: none) */
 } orc_sum_args;
 
 /* Gamma_path of segment j: product of gamma over the reflections before it. */
@@ -311,6 +428,20 @@ static void orc_acc_add(orc_acc *a, double complex v)
     orc_acc_add1(&a->si, &a->ci, cimag(v));
 }
 
+/* Losses of segment j at frequency f and arclength s: the porous reflections'
+ * factor times the air's amplitude decay exp(-a s) (1 without losses). */
+static double complex orc_losses(const orc_segments *S, const orc_sum_args *A, int f, int64_t j,
+                                 double s)
+{
+    double complex L = 1.0;
+    if (A->seg_factor) {
+        const double *F = A->seg_factor + 2 * ((int64_t)f * S->n_seg + j);
+        L = F[0] + I * F[1];
+    }
+    if (A->absorb) L *= exp(-A->absorb[f] * s);
+    return L;
+}
+
 /*
  * p[f][r] = sum over segments j (in order) of the kept contributions (Eq. 3).
  * recv: n_recv*3 doubles (the float32 receiver positions widened).
@@ -334,7 +465,7 @@ void orc_sum(const orc_segments *S, const orc_sum_args *A, const double *recv,
                 orc_geometry(S, j, recv + 3 * r, &s_loc, &s, &n2);
                 if (!orc_keep(S, j, A, k, bm, s_loc, s, n2)) continue;
                 double w = weight[S->ray[j]] * gpath[j];
-                orc_acc_add(&acc, w * orc_beam(k, b, s, n2));
+                orc_acc_add(&acc, w * orc_losses(S, A, f, j, s) * orc_beam(k, b, s, n2));
             }
             out[2 * (f * n_recv + r) + 0] = acc.sr + acc.cr;
             out[2 * (f * n_recv + r) + 1] = acc.si + acc.ci;
@@ -392,7 +523,8 @@ void orc_sum_adjoint(const orc_segments *S, const orc_sum_args *A, const double 
                     orc_geometry(S, j, recv + 3 * r, &s_loc, &s, &n2);
                     if (!orc_keep(S, j, A, k, bm, s_loc, s, n2)) continue;
                     const int32_t ray = S->ray[j];
-                    double complex cu = orc_beam(k, b, s, n2);      /* W = Gamma = 1 */
+                    /* W = Gamma = 1; the losses do not depend on W, gamma or b */
+                    double complex cu = orc_losses(S, A, f, j, s) * orc_beam(k, b, s, n2);
                     double complex E = s - I * b;
                     /* weight */
                     mw[ray] += creal(gc * gpath[j] * cu);

@@ -14,6 +14,11 @@ Functions and the passages they follow (arXiv 2501.13382):
   gbs_adjoint    -- gradient of a real loss through gbs_sum
   synthesize     -- time signals from per-frequency fields (superposition of the
                     time-harmonic fields of Eq. 1 under the exp(-i omega t) convention)
+  air_absorption, delany_bazley, plane_wave_reflection, incidence_cos, path_factor
+                 -- propagation losses for the atmospheric conditions and surface flow
+                    impedance of the paper's input tables (Sec. 4.5, Tables 2-3), which
+                    give no formula: ISO 9613-1 absorption of air, Delany-Bazley impedance
+                    and the plane-wave reflection factor of a locally reacting surface
 Parity unpinned (definitions with no external check): the Fibonacci variant,
 the beam-parameter rule, the cutoff C and the window choice.
 """
@@ -51,6 +56,9 @@ def _open(path):
     lib = C.CDLL(path)
     lib.orc_count_kept.restype = C.c_int64
     lib.orc_num_threads.restype = C.c_int
+    for fn in ("orc_air_absorption_db", "orc_air_absorption_np"):
+        getattr(lib, fn).restype = C.c_double
+        getattr(lib, fn).argtypes = [C.c_double] * 4
     return lib
 
 
@@ -112,7 +120,8 @@ class _Segs(C.Structure):
 
 class _SumArgs(C.Structure):
     _fields_ = [("c", C.c_double), ("n_freq", C.c_int), ("freq", C.c_void_p), ("b", C.c_void_p),
-                ("b_mask", C.c_void_p), ("cutoff", C.c_double), ("window", C.c_int)]
+                ("b_mask", C.c_void_p), ("cutoff", C.c_double), ("window", C.c_int),
+                ("absorb", C.c_void_p), ("seg_factor", C.c_void_p)]
 
 
 def _p(a):
@@ -225,12 +234,89 @@ def _segs_struct(tr: Trace):
     return s, arrs
 
 
-def _args_struct(c, freqs, b, cutoff, window, b_mask):
+def _args_struct(c, freqs, b, cutoff, window, b_mask, absorption=None, seg_factor=None):
     fr = np.ascontiguousarray(freqs, np.float64)
     bb = np.ascontiguousarray(b, np.float64)
     bmk = None if b_mask is None else np.ascontiguousarray(b_mask, np.float64)
-    a = _SumArgs(float(c), int(fr.shape[0]), _p(fr), _p(bb), _p(bmk), float(cutoff), int(window))
-    return a, (fr, bb, bmk)
+    ab = None if absorption is None else np.ascontiguousarray(absorption, np.float64)
+    sf = None
+    if seg_factor is not None:
+        sf = np.ascontiguousarray(np.stack([np.real(seg_factor), np.imag(seg_factor)], -1),
+                                  np.float64)
+    a = _SumArgs(float(c), int(fr.shape[0]), _p(fr), _p(bb), _p(bmk), float(cutoff), int(window),
+                 _p(ab), _p(sf))
+    return a, (fr, bb, bmk, ab, sf)
+
+
+# ------------------------------------------------------- propagation losses --
+
+def air_absorption_db(freqs, temperature_c: float = 20.0, humidity_pct: float = 70.0,
+                      pressure_kpa: float = 101.325) -> np.ndarray:
+    """Pure-tone attenuation coefficient of air, dB per metre (ISO 9613-1)."""
+    lib = _load()
+    return np.array([lib.orc_air_absorption_db(float(f), float(temperature_c),
+                                               float(humidity_pct), float(pressure_kpa))
+                     for f in np.atleast_1d(freqs)])
+
+
+def air_absorption(freqs, temperature_c: float = 20.0, humidity_pct: float = 70.0,
+                   pressure_kpa: float = 101.325) -> np.ndarray:
+    """Pressure-amplitude decay rate of air a (Np/m; the amplitude falls as exp(-a s)),
+    ISO 9613-1.  The paper's cases use 20 C, 70 % and 1 atm (Tables 2-3)."""
+    lib = _load()
+    return np.array([lib.orc_air_absorption_np(float(f), float(temperature_c),
+                                               float(humidity_pct), float(pressure_kpa))
+                     for f in np.atleast_1d(freqs)])
+
+
+def delany_bazley(freq: float, sigma_kpa: float) -> complex:
+    """Normalised surface impedance Z / (rho c) of a porous surface of effective flow
+    resistivity sigma (kPa s m^-2), Delany and Bazley's model, exp(-i omega t)."""
+    z = np.zeros(2)
+    _load().orc_delany_bazley_z(C.c_double(freq), C.c_double(sigma_kpa), _p(z))
+    return complex(z[0], z[1])
+
+
+def plane_wave_reflection(Z: complex, cos_theta: float) -> complex:
+    """(Z cos theta - 1) / (Z cos theta + 1): plane wave on a locally reacting surface."""
+    z = np.array([complex(Z).real, complex(Z).imag])
+    r = np.zeros(2)
+    _load().orc_plane_wave_reflection_r(_p(z), C.c_double(cos_theta), _p(r))
+    return complex(r[0], r[1])
+
+
+def incidence_cos(scene, tr: "Trace") -> np.ndarray:
+    """Per segment: cosine of the incidence angle at the reflection that starts it (1 for
+    each ray's first segment)."""
+    sc, keep = _scene_struct(scene)
+    t = np.ascontiguousarray(tr.t, np.float64)
+    dep = np.ascontiguousarray(tr.depth, np.int32)
+    hit = np.ascontiguousarray(tr.hit, np.int32)
+    out = np.zeros(tr.n_seg)
+    _load().orc_incidence_cos(C.byref(sc), C.c_int64(tr.n_seg), _p(t), _p(dep), _p(hit), _p(out))
+    return out
+
+
+def path_factor(scene, tr: "Trace", sigma, freqs) -> np.ndarray:
+    """Complex (F, S): per frequency and segment, the product of the plane-wave reflection
+    factors of the porous surfaces (sigma[m] > 0, Delany-Bazley) met before the segment."""
+    cosi = incidence_cos(scene, tr)
+    sg = np.ascontiguousarray(sigma, np.float64)
+    fr = np.ascontiguousarray(freqs, np.float64)
+    dep = np.ascontiguousarray(tr.depth, np.int32)
+    bm = np.ascontiguousarray(tr.bmat, np.int32)
+    out = np.zeros((fr.shape[0], tr.n_seg, 2))
+    _load().orc_path_factor(C.c_int64(tr.n_seg), _p(dep), _p(bm), _p(cosi), _p(sg), _p(fr),
+                            C.c_int(fr.shape[0]), _p(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def _losses(tr, freqs, absorption, sigma, scene):
+    seg_factor = None
+    if sigma is not None:
+        assert scene is not None, "porous surfaces need the scene (normals at the reflections)"
+        seg_factor = path_factor(scene, tr, sigma, freqs)
+    return absorption, seg_factor
 
 
 def default_weight(n_rays: int) -> np.ndarray:
@@ -244,22 +330,26 @@ def _weights(tr: Trace, weight):
 
 
 def gbs_sum(tr: Trace, receivers: np.ndarray, freqs, b, c: float, gamma, weight=None,
-            window: int = 1, cutoff: float = 16.0, b_mask=None) -> np.ndarray:
-    """Complex pressure p[f, r] (complex128)."""
+            window: int = 1, cutoff: float = 16.0, b_mask=None, absorption=None, sigma=None,
+            scene=None) -> np.ndarray:
+    """Complex pressure p[f, r] (complex128).  absorption: per-frequency amplitude decay of
+    air (Np/m); sigma: per-material flow resistivity (kPa s m^-2, <= 0 hard), which needs
+    the scene the trace came from."""
     lib = _load()
     recv = np.ascontiguousarray(np.asarray(receivers, np.float32).astype(np.float64))
     nr = recv.shape[0]
     gam = np.ascontiguousarray(gamma, np.float64)
     w = _weights(tr, weight)
     segs, k1 = _segs_struct(tr)
-    args, k2 = _args_struct(c, freqs, b, cutoff, window, b_mask)
+    args, k2 = _args_struct(c, freqs, b, cutoff, window, b_mask,
+                            *_losses(tr, freqs, absorption, sigma, scene))
     out = np.zeros((len(freqs), nr, 2), np.float64)
     lib.orc_sum(C.byref(segs), C.byref(args), _p(recv), C.c_int64(nr), _p(gam), _p(w), _p(out))
     return out[..., 0] + 1j * out[..., 1]
 
 
 def gbs_adjoint(tr: Trace, receivers, freqs, b, c, gamma, g, weight=None, window: int = 1,
-                cutoff: float = 16.0, b_mask=None):
+                cutoff: float = 16.0, b_mask=None, absorption=None, sigma=None, scene=None):
     """Gradients (d gamma[M], d weight[N], d b[F]) of a real loss with dL/dp = g (F, Nr)."""
     lib = _load()
     recv = np.ascontiguousarray(np.asarray(receivers, np.float32).astype(np.float64))
@@ -268,7 +358,8 @@ def gbs_adjoint(tr: Trace, receivers, freqs, b, c, gamma, g, weight=None, window
     w = _weights(tr, weight)
     gg = np.ascontiguousarray(np.stack([np.real(g), np.imag(g)], -1), np.float64)
     segs, k1 = _segs_struct(tr)
-    args, k2 = _args_struct(c, freqs, b, cutoff, window, b_mask)
+    args, k2 = _args_struct(c, freqs, b, cutoff, window, b_mask,
+                            *_losses(tr, freqs, absorption, sigma, scene))
     dg = np.zeros(gam.shape[0]); dw = np.zeros(tr.n_rays); db = np.zeros(len(freqs))
     lib.orc_sum_adjoint(C.byref(segs), C.byref(args), _p(recv), C.c_int64(nr), _p(gam),
                         C.c_int(gam.shape[0]), _p(w), C.c_int64(tr.n_rays), _p(gg), _p(dg),

@@ -12,6 +12,9 @@ Cases (arXiv 2501.13382):
                  the synthetic city: segment count, per-ray counts, hit primitives
   city_sum       the same trace summed at 8 receivers, 2 frequencies, SEGMENT window
   city_adjoint   gradients of Re sum conj(g) p (derivatives of Eq. 1) for that sum
+  city_lossy     the same sum with the atmosphere of the paper's Tables 2-3 (20 C, 70 %,
+                 1 atm; ISO 9613-1 absorption) and a porous ground (Delany-Bazley, 200 kPa s
+                 m^-2) under hard buildings
 """
 import json
 import os
@@ -52,6 +55,13 @@ def cases():
     dg, dw, db = O.gbs_adjoint(tc, recv, freqs, b, sc.c, sc.gamma, g, window=I.WINDOW_SEGMENT)
     out["city_adjoint"] = {"grad_gamma": dg.tolist(), "grad_weight_sum": float(dw.sum()),
                            "grad_weight_norm": float(np.linalg.norm(dw)), "grad_b": db.tolist()}
+    absorb = O.air_absorption(freqs, 20.0, 70.0, 101.325)
+    sigma = np.full(sc.n_materials, -10.0)
+    sigma[0] = 200.0
+    pl = O.gbs_sum(tc, recv, freqs, b, sc.c, sc.gamma, window=I.WINDOW_SEGMENT,
+                   absorption=absorb, sigma=sigma, scene=sc)
+    out["city_lossy"] = {"absorption": absorb.tolist(), "re": pl.real.tolist(),
+                         "im": pl.imag.tolist()}
     return out
 
 

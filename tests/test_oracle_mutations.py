@@ -45,6 +45,25 @@ MUTATIONS = {
                           "const double th = th0 + (double)it * dth;"),
     "latlong_sin_cos_swapped": ("dirs[3 * g + 0] = sin(th) * cos(ph);",
                                 "dirs[3 * g + 0] = cos(th) * cos(ph);"),
+    # propagation losses (the loss battery below)
+    "absorption_local_arclength": ("orc_acc_add(&acc, w * orc_losses(S, A, f, j, s) * orc_beam",
+                                   "orc_acc_add(&acc, w * orc_losses(S, A, f, j, s - S->s0[j]) * orc_beam"),
+    "absorption_sign": ("if (A->absorb) L *= exp(-A->absorb[f] * s);",
+                        "if (A->absorb) L *= exp(A->absorb[f] * s);"),
+    "absorption_db_not_np": ("return orc_air_absorption_db(f, T_c, rh, p_kpa) / (20.0 / log(10.0));",
+                             "return orc_air_absorption_db(f, T_c, rh, p_kpa);"),
+    "iso_oxygen_humidity": ("h * (0.02 + h) / (0.391 + h)", "h * (0.2 + h) / (0.391 + h)"),
+    "iso_nitrogen_temperature": ("pow(T / T0, -1.0 / 3.0) - 1.0", "pow(T / T0, 1.0 / 3.0) - 1.0"),
+    "reflection_inverted": ("return (Z * cos_theta - 1.0) / (Z * cos_theta + 1.0);",
+                            "return (Z - cos_theta) / (Z + cos_theta);"),
+    "delany_bazley_imag_sign": ("+ I * 11.9 * pow(x, -0.73)", "- I * 11.9 * pow(x, -0.73)"),
+    "incidence_sine": ("cosi[j] = fabs(t[3 * j] * nrm[0] + t[3 * j + 1] * nrm[1] + t[3 * j + 2] * nrm[2]);",
+                       "cosi[j] = sqrt(1.0 - pow(t[3 * j] * nrm[0] + t[3 * j + 1] * nrm[1] + "
+                       "t[3 * j + 2] * nrm[2], 2.0));"),
+    "path_factor_skips_first_bounce": ("for (int64_t q = first + 1; q <= j; ++q) {\n                const double sg",
+                                       "for (int64_t q = first + 2; q <= j; ++q) {\n                const double sg"),
+    "adjoint_without_losses": ("double complex cu = orc_losses(S, A, f, j, s) * orc_beam(k, b, s, n2);",
+                               "double complex cu = orc_beam(k, b, s, n2);"),
 }
 
 
@@ -132,8 +151,54 @@ def _battery():
     return ok
 
 
+def _loss_battery():
+    """The loss pins (tests/test_oracle_losses.py) on small cases; True iff all pass."""
+    from tests import test_oracle_losses as TL
+    ok = not TL.iso_table_mismatches()
+    sc0 = I.Scene(C, False, 0.0, 0, np.zeros((0, 3, 3)), np.zeros(0, np.int32),
+                  np.zeros(0, np.int32), np.array([1.0], np.float32))
+    tr = O.trace(sc0, I.Source(np.zeros(3), 16384, 0, 1e4))
+    res, corr = TL.free_field_absorption_residual(tr, 500.0, 100.0, 0.01, 120.0)
+    ok &= bool(res <= 0.05 * corr + corr ** 2 + 1e-6)
+    # the level drop of the paper's atmosphere at 4 kHz over 300 m
+    a = O.air_absorption([4000.0])[0]
+    alpha = O.air_absorption_db([4000.0])[0]
+    recv = np.array([[300.0, 0.0, 0.0]], np.float32)
+    p0 = O.gbs_sum(tr, recv, [4000.0], [100.0], C, [1.0], window=1)[0, 0]
+    pa = O.gbs_sum(tr, recv, [4000.0], [100.0], C, [1.0], window=1, absorption=[a])[0, 0]
+    ok &= bool(abs(20 * math.log10(abs(p0) / abs(pa)) - alpha * 300.0) < 2e-3 * alpha * 300.0)
+    ok &= bool(TL.image_field_with_absorption_error() < 3e-4)
+    # reflection factor against the impedance boundary condition
+    Z, th, k = 5.57 + 6.1j, 0.7, 2.0
+    R = O.plane_wave_reflection(Z, math.cos(th))
+    pz = lambda z: np.exp(-1j * k * z * math.cos(th)) + R * np.exp(1j * k * z * math.cos(th))
+    h = 1e-5
+    ok &= bool(abs(pz(0.0) / (-(pz(h) - pz(-h)) / (2 * h) / (1j * k)) - Z) < 1e-6 * abs(Z))
+    # Delany-Bazley against the Rayleigh model's sign and size
+    zd = O.delany_bazley(500.0, 200.0)
+    zr = np.sqrt(1 + 1j * 200e3 / (2 * math.pi * 500.0 * 1.2))
+    ok &= bool(zd.real > 1 and zd.imag > 0 and 0.6 < abs(zd) / abs(zr) < 1.6 and
+               abs(np.angle(zd) - np.angle(zr)) < math.radians(12.0))
+    ok &= not TL.hand_traced_path_factor_errors()
+    for f, sig, z, e0, e1, c in TL.porous_ground_image_errors(((1000.0, 200.0),)):
+        ok &= bool(e1 < e0 and e1 <= 0.35 * c + 2e-4)
+    from tests.test_oracle_pins import _box
+    ta, fa = _box(20, 40, -30, 10, 25, 0)
+    sc = I.Scene(C, True, 0.0, 0, ta, np.ones(12, np.int32), fa, np.array([0.9, 0.7], np.float32))
+    trc = O.trace(sc, I.Source(np.array([0.0, 0.0, 4.0]), 512, 3, 300.0))
+    rng = np.random.default_rng(5)
+    prob = (sc, trc, I.random_receivers(rng, 8, [-60, -60, 1], [60, 60, 20]),
+            np.array([400.0]), np.array([35.0]),
+            (rng.normal(size=(1, 8)) + 1j * rng.normal(size=(1, 8))) * 1e-3,
+            np.array([150.0, 40.0]), np.array([0.015]))
+    errs = TL.lossy_adjoint_errors(prob)
+    ok &= bool(max(errs) < 1e-5)
+    return ok
+
+
 def test_unmutated_oracle_passes_battery():
     assert _battery()
+    assert _loss_battery()
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
@@ -143,4 +208,4 @@ def test_planted_mistake_is_caught(name, tmp_path):
     assert src.count(old) >= 1, f"mutation anchor not found: {name}"
     lib = O.compile_source(src.replace(old, new), str(tmp_path / f"liboracle_{name}.so"))
     with O.use_library(lib):
-        assert not _battery(), f"planted mistake {name} went undetected"
+        assert not (_battery() and _loss_battery()), f"planted mistake {name} went undetected"
