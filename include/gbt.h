@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define GBT_VERSION 1
+#define GBT_VERSION 2
 #define GBT_MAX_FREQ 16          /* frequencies per sum call */
 
 typedef enum gbt_status {
@@ -231,7 +231,24 @@ gbt_status gbt_trace_import(const gbt_scene_t *scene, const gbt_source_desc *src
  * the given order); each group costs a full pass over the pairs.
  * `out` (n_freq * n_recv complex64, frequency-major) is overwritten, or added
  * to when `accumulate` is 1.  Scratch comes from the trace's workspace, so
- * calls on one trace must not overlap on different streams. */
+ * calls on one trace must not overlap on different streams.
+ *
+ * Propagation losses (optional).  The paper's input tables (Sec. 4.5, Tables
+ * 2-3) give the air temperature, humidity and pressure and a flow-impedance
+ * setting of the surfaces, with no formulas; the library takes standard ones:
+ *  - absorption of air: every beam is scaled by exp(-a_f s) over its unfolded
+ *    arclength s, with a_f = absorption[f] (Np/m, the pressure-amplitude decay
+ *    rate; gbt_air_absorption gives the ISO 9613-1 value);
+ *  - porous surfaces: a material m with flow_resistivity[m] = sigma > 0
+ *    (kPa s m^-2) reflects with gamma_m times the plane-wave reflection factor
+ *    R = (Z cos(theta) - 1) / (Z cos(theta) + 1) of a locally reacting surface
+ *    at the reflection's angle of incidence theta, Z / (rho c) = 1 +
+ *    9.08 (f / sigma)^-0.75 + i 11.9 (f / sigma)^-0.73 (Delany and Bazley,
+ *    exp(-i omega t)); sigma <= 0 (the paper's negative setting) or a NULL array
+ *    is a hard surface, whose reflection is gamma_m alone.
+ * The losses change no cull decision (the cutoff tests the Gaussian alone).
+ * Batches with losses run in the CONCURRENT form; the FUSED form rejects them
+ * (GBT_ERR_UNSUPPORTED). */
 typedef struct gbt_sum_args {
     const float *recv;            /* device, n_recv * 3 (x, y, z), m */
     int64_t n_recv;               /* >= 0 */
@@ -253,6 +270,10 @@ typedef struct gbt_sum_args {
                                      provably reach none of them (same result, less work);
                                      0: test every pair */
     int64_t max_device_bytes;     /* gbt_solve only: device budget for one chunk; 0 = auto */
+    double absorption[GBT_MAX_FREQ]; /* air's amplitude decay rate per frequency, Np/m
+                                     (>= 0; all 0 = lossless air) */
+    const float *flow_resistivity; /* device, n_materials effective flow resistivities,
+                                     kPa s m^-2 (<= 0: hard), or NULL: every surface hard */
 } gbt_sum_args;
 
 gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *stream);
@@ -279,6 +300,17 @@ gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out,
 gbt_status gbt_recv_order_noalloc(const float *recv, int64_t n_recv, int32_t *order_out,
                                   void *stream);
 
+/* Amplitude decay rate of air (Np/m) for pure tones at freq_hz[0 .. n) in an
+ * atmosphere at temperature_c (degrees C), relative humidity humidity_pct (%)
+ * and pressure pressure_kpa (kPa): the attenuation coefficient of ISO 9613-1
+ * (classical and rotational absorption plus the vibrational relaxation of
+ * oxygen and nitrogen) divided by 20 log10(e) dB per neper.  The paper's cases
+ * use 20 C, 70 % and 1 atm (Tables 2-3).  Host arrays; no GPU work.
+ * GBT_ERR_INVALID_ARG for n < 0, NULL arrays, non-positive frequencies or
+ * pressure, humidity outside [0, 100] or temperature outside [-50, 60] C. */
+gbt_status gbt_air_absorption(int32_t n, const double *freq_hz, double temperature_c,
+                              double humidity_pct, double pressure_kpa, double *np_per_m);
+
 /* ------------------------------------------------------------ backward --
  * Adjoint of gbt_sum for a real loss L.  grad_out (device, n_freq * n_recv
  * complex64) holds g = dL/dRe p + i dL/dIm p.  Writes (overwrites)
@@ -287,7 +319,9 @@ gbt_status gbt_recv_order_noalloc(const float *recv, int64_t n_recv, int32_t *or
  *   grad_b[f]          = dL/db_f            (device, n_freq doubles; NULL to skip)
  * using dL/dtheta = sum Re(conj(g) dp/dtheta).  The cull mask and window are
  * held fixed (the summand is differentiated where it is kept).  Contributions
- * are recomputed, never stored per (receiver, segment).  F32 only. */
+ * are recomputed, never stored per (receiver, segment).  F32 only.  With
+ * losses the contributions carry them; the losses depend on none of the
+ * differentiated parameters. */
 gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
                             const float *grad_out, float *grad_gamma, float *grad_ray_weight,
                             double *grad_b, void *stream);

@@ -10,7 +10,12 @@ cull mask and window are held fixed: the summand is differentiated where it is
 kept.  The backward pass recomputes every kept contribution in the library's
 kernel (nothing is stored per receiver and segment).  For a real loss torch
 hands the backward ``g = dL/dRe p + i dL/dIm p``, which is the convention of
-gbt_sum_backward, so the gradients are ``sum Re(conj(g) dp/dtheta)``.
+gbt_sum_backward, so the gradients are ``sum Re(conj(g) dp/dtheta)``.  Optional
+propagation losses (``absorption`` per frequency in Np/m, ``flow_resistivity`` per
+material) enter the field and its gradients but are not differentiated.  The backward
+pass ends by reading the library's device status word (gbt_sync on the current
+stream), so a kernel that flagged a problem (a bounded wait that ran out) raises
+instead of leaving a partial gradient.
 """
 from __future__ import annotations
 
@@ -22,11 +27,13 @@ from . import gbt as G
 class GBTSum(torch.autograd.Function):
     @staticmethod
     def forward(ctx, gamma, ray_weight, beam_b, trace, recv, freqs, order, window, cutoff,
-                tile_cull=False):
+                tile_cull=False, absorption=None, flow_resistivity=None):
         b = [float(v) for v in beam_b.detach().cpu().tolist()]
         p = G.gbs_sum(trace, recv, list(freqs), b, gamma.detach().contiguous(),
                       ray_weight=None if ray_weight is None else ray_weight.detach().contiguous(),
-                      order=order, window=window, cutoff=cutoff, tile_cull=tile_cull)
+                      order=order, window=window, cutoff=cutoff, tile_cull=tile_cull,
+                      absorption=absorption, flow_resistivity=flow_resistivity)
+        ctx.absorption, ctx.flow_resistivity = absorption, flow_resistivity
         ctx.save_for_backward(gamma, ray_weight if ray_weight is not None else torch.empty(0))
         ctx.has_w = ray_weight is not None
         ctx.trace, ctx.recv, ctx.freqs, ctx.b, ctx.order = trace, recv, list(freqs), b, order
@@ -46,18 +53,22 @@ class GBTSum(torch.autograd.Function):
                                         ray_weight=None if w is None else w.detach().contiguous(),
                                         order=ctx.order, window=ctx.window, cutoff=ctx.cutoff,
                                         need_weight=need_w, need_b=need_b,
-                                        tile_cull=ctx.tile_cull)
+                                        tile_cull=ctx.tile_cull, absorption=ctx.absorption,
+                                        flow_resistivity=ctx.flow_resistivity)
+        G.gbt_sync(G._stream_ptr())    # raises if a kernel of this step flagged a problem
         gw = dw if (need_w and w is not None) else None
         gb = db.to(device=ctx.b_device, dtype=ctx.b_dtype) if need_b else None
         return (dg if ctx.needs_input_grad[0] else None, gw, gb,
-                None, None, None, None, None, None, None)
+                None, None, None, None, None, None, None, None, None)
 
 
 def gbs_field(trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
-              window: int = G.WINDOW_LINE, cutoff: float = 16.0, tile_cull: bool = False):
+              window: int = G.WINDOW_LINE, cutoff: float = 16.0, tile_cull: bool = False,
+              absorption=None, flow_resistivity=None):
     """Differentiable complex pressure p[f, r] (complex64); ``tile_cull`` runs forward and
     backward with the exact tile pre-cull."""
     if not torch.is_tensor(beam_b):
         beam_b = torch.tensor(list(beam_b), dtype=torch.float64, device=recv.device)
+    ab = None if absorption is None else tuple(float(v) for v in absorption)
     return GBTSum.apply(gamma, ray_weight, beam_b, trace, recv, tuple(freqs), order, window,
-                        float(cutoff), bool(tile_cull))
+                        float(cutoff), bool(tile_cull), ab, flow_resistivity)

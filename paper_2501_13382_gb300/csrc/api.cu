@@ -305,6 +305,8 @@ static void validate_sum(const gbt_trace_t *trace, const gbt_sum_args *a, bool n
     for (int f = 0; f < a->n_freq; ++f) {
         GBT_REQUIRE(a->freq_hz[f] > 0 && isfinite(a->freq_hz[f]), "frequencies must be > 0");
         GBT_REQUIRE(a->beam_b[f] > 0 && isfinite(a->beam_b[f]), "beam_b must be > 0");
+        GBT_REQUIRE(a->absorption[f] >= 0 && isfinite(a->absorption[f]),
+                    "absorption must be finite and >= 0 (Np/m)");
     }
     GBT_REQUIRE(a->gamma, "gamma is NULL");
     if (a->n_recv > 0) {
@@ -648,6 +650,47 @@ gbt_status gbt_synthesize(const float *p, int32_t n_freq, int64_t n_recv, const 
     });
 }
 
+// ISO 9613-1: attenuation coefficient of air for pure tones, written from the
+// standard's equations: the saturation vapour pressure over the triple-point
+// isotherm gives the molar concentration h of water vapour; h and the pressure set
+// the relaxation frequencies of oxygen and nitrogen; alpha (dB/m) is 8.686 f^2 times
+// the classical-plus-rotational term plus the two vibrational relaxation terms.
+// Returned as the amplitude decay rate, alpha / (20 log10 e) Np/m.
+gbt_status gbt_air_absorption(int32_t n, const double *freq_hz, double temperature_c,
+                              double humidity_pct, double pressure_kpa, double *np_per_m)
+{
+    return guarded([&] {
+        GBT_REQUIRE(n >= 0, "n must be >= 0");
+        if (n == 0) return;
+        GBT_REQUIRE(freq_hz && np_per_m, "freq_hz and np_per_m must be non-NULL");
+        GBT_REQUIRE(isfinite(temperature_c) && temperature_c >= -50.0 && temperature_c <= 60.0,
+                    "temperature must be in [-50, 60] C");
+        GBT_REQUIRE(isfinite(humidity_pct) && humidity_pct >= 0.0 && humidity_pct <= 100.0,
+                    "relative humidity must be in [0, 100] %");
+        GBT_REQUIRE(isfinite(pressure_kpa) && pressure_kpa > 0.0, "pressure must be > 0 kPa");
+        for (int32_t i = 0; i < n; ++i)
+            GBT_REQUIRE(isfinite(freq_hz[i]) && freq_hz[i] > 0.0, "frequencies must be > 0");
+        const double t_kelvin = temperature_c + 273.15;
+        const double tau = t_kelvin / 293.15;             // over the reference temperature
+        const double pa = pressure_kpa / 101.325;         // over the reference pressure
+        const double vapour_exp = 4.6151 - 6.8346 * pow(273.16 / t_kelvin, 1.261);
+        const double h = humidity_pct * pow(10.0, vapour_exp) / pa;    // percent
+        const double f_o = pa * (24.0 + 40400.0 * h * (0.02 + h) / (0.391 + h));
+        const double f_n = pa / sqrt(tau) *
+                           (9.0 + 280.0 * h * exp(-4.170 * (1.0 / cbrt(tau) - 1.0)));
+        const double relax_o = 0.01275 * exp(-2239.1 / t_kelvin);
+        const double relax_n = 0.1068 * exp(-3352.0 / t_kelvin);
+        const double db_per_np = 20.0 / log(10.0);
+        for (int32_t i = 0; i < n; ++i) {
+            const double f2 = freq_hz[i] * freq_hz[i];
+            const double bracket = 1.84e-11 * sqrt(tau) / pa +
+                                   pow(tau, -2.5) * (relax_o / (f_o + f2 / f_o) +
+                                                     relax_n / (f_n + f2 / f_n));
+            np_per_m[i] = 8.686 * f2 * bracket / db_per_np;
+        }
+    });
+}
+
 gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out, void *stream)
 {
     NvtxRange nvtx_range("gbt_recv_order");
@@ -710,8 +753,9 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
         GBT_REQUIRE(args->max_device_bytes >= 0, "max_device_bytes must be >= 0");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const int64_t N = src->n_rays;
+        const int64_t loss = has_losses(*args) ? 16 * (int64_t)args->n_freq : 0;
         const int64_t per_ray = (int64_t)(src->max_reflections + 1) *
-                                (80 /*compact*/ + 80 /*padded*/ + 4 * kRecFloats + 8 + 8);
+                                (80 /*compact*/ + 80 /*padded*/ + 4 * kRecFloats + 8 + 8 + loss);
         int64_t chunk = N;
         if (args->max_device_bytes > 0) {
             chunk = std::max<int64_t>(1, args->max_device_bytes / std::max<int64_t>(per_ray, 1));

@@ -70,7 +70,8 @@ struct alignas(16) FreqConst {
     float scale;          // k b / (8 pi^2)
     float b;              // b
     float kh, invb;       // k / 2, 1 / b  (adjoint)
-    float pad0, pad1;
+    float al2e;           // amplitude decay rate of air a (Np/m) * log2(e), 0 when lossless
+    float pad1;
 };
 static_assert(sizeof(FreqConst) == 48, "three 16-byte words");
 
@@ -103,6 +104,10 @@ struct alignas(16) FwdParams {
     float *seg_H;              // per (sorted frequency, segment): sum over r of Re(conj(g) dc~/db)
     int64_t seg_stride;        // stride of seg_H rows
     int fperm[GBT_MAX_FREQ];   // sorted frequency slot -> user frequency index
+    // losses of porous surfaces (lossy instantiation): per user frequency f and segment j,
+    // seg_rf[f * rf_stride + j] = (log2 |R|, arg R / 2 pi) of the path's reflection factor
+    const float2 *seg_rf;
+    int64_t rf_stride;
     // batched launch: per-instance parameters and the first global item of each
     const struct FwdParams *inst;
     const int64_t *inst_off;   // n_inst + 1 entries
@@ -273,6 +278,13 @@ struct StageSmem {
     int32_t seg[kBatch];            // global segment index of each staged record
 };
 
+// Losses of the staged batch (lossy instantiation): per frequency slot and staged
+// segment, log2 |R| and arg R / 2 pi of its porous reflections' factor.
+template <int NF>
+struct LossSmem {
+    float2 rf[NF][kBatch];
+};
+
 // Exact geometry of one (receiver, segment) pair in float-float; returns false
 // when the pair falls outside the window.
 template <int WINDOW>
@@ -320,17 +332,24 @@ __device__ __forceinline__ bool exact_geometry(float x, float y, float z, const 
 
 // Adjoint terms of one beam: with c~ the contribution without W Gamma_path,
 // G += Re(conj(g) c~) and H += Re(conj(g) dc~/db), where
-// d log c / db = 1/b + i/E - k n^2 / (2 E^2), E = s - i b.
+// d log c / db = 1/b + i/E - k n^2 / (2 E^2), E = s - i b.  With losses c~ carries
+// the porous reflections' factor (rf: log2 |R|, arg R in turns) and exp(-a s); neither
+// depends on b, so the logarithmic derivative is the same.
+template <bool LOSSY>
 __device__ __forceinline__ void beam_adjoint(const FreqConst &q, float sh, float sl, float n2,
-                                             float invD, float2 g, float &G, float &H)
+                                             float invD, float2 g, float &G, float &H,
+                                             float2 rf = make_float2(0.f, 0.f))
 {
     const float n2invD = n2 * invD;
-    const float ga = ex2_approx(-q.kb2l2e * n2invD);
+    float ex = -q.kb2l2e * n2invD;
+    if (LOSSY) ex = fmaf(-q.al2e, sh, ex + rf.x);
+    const float ga = ex2_approx(ex);
     const float ph = __fmul_rn(q.K_hi, sh);       // rounded: pe below is its exact error
     const float pe = fmaf(q.K_hi, sh, -ph);
     const float corr = fmaf(q.K_hi, sl, fmaf(q.K_lo, sh, pe));
     float tau = __fsub_rn(ph, rintf(ph)) + corr;
     tau = fmaf(q.halfK * n2invD, sh, tau);
+    if (LOSSY) tau += rf.y;
     tau = tau - rintf(tau);
     float sn, cs;
     __sincosf(6.283185307179586f * tau, &sn, &cs);
@@ -379,9 +398,10 @@ __device__ __forceinline__ void survivor_count(const FwdParams &p, float x, floa
 // the phase reduced in turns and the 1/E factor), so each half rounds as that
 // evaluation would; only the MUFU operations run per half.  accx / accy
 // hold the two receivers' real / imaginary sums per sorted frequency.
-template <int NF, int WINDOW>
+template <int NF, int WINDOW, bool LOSSY>
 __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, f2x Z,
-                                              const StageSmem &w, int j0, int j1, bool h0, bool h1,
+                                              const StageSmem &w, const LossSmem<NF> *loss,
+                                              int j0, int j1, bool h0, bool h1,
                                               f2x (&accx)[NF], f2x (&accy)[NF])
 {
     const float4 A0 = w.A[j0], A1 = w.A[j1];
@@ -438,11 +458,19 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, 
     float n20, n21;
     upk(n2, n20, n21);
 
-    // one beam term on both halves, each half kept where its flag is set
-    auto beam = [&](const FreqConst &q, f2x invD, bool kf0, bool kf1, f2x &bx, f2x &by) {
+    // one beam term on both halves, each half kept where its flag is set; with losses
+    // the Gaussian exponent takes log2 |R| - a s log2(e) and the phase arg R / 2 pi
+    auto beam = [&](const FreqConst &q, int f, f2x invD, bool kf0, bool kf1, f2x &bx, f2x &by) {
         const f2x n2invD = mul2(n2, invD);
         float e0, e1;
-        upk(mul2(splat(-q.kb2l2e), n2invD), e0, e1);
+        f2x ex = mul2(splat(-q.kb2l2e), n2invD);
+        f2x RPH = 0ull;
+        if (LOSSY) {
+            const float2 r0 = loss->rf[f][j0], r1 = loss->rf[f][j1];
+            ex = fma2(splat(-q.al2e), sh, add2(ex, pk(r0.x, r1.x)));
+            RPH = pk(r0.y, r1.y);
+        }
+        upk(ex, e0, e1);
         const f2x ga = pk(ex2_approx(e0), ex2_approx(e1));
         const f2x KH = splat(q.K_hi);
         const f2x ph = mul2(KH, sh);
@@ -450,6 +478,7 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, 
         const f2x corr = fma2(KH, sl, fma2(splat(q.K_lo), sh, pe));
         f2x tau = add2(sub2(ph, rint2(ph)), corr);
         tau = fma2(mul2(splat(q.halfK), n2invD), sh, tau);
+        if (LOSSY) tau = add2(tau, RPH);
         tau = sub2(tau, rint2(tau));
         float t0, t1, s0, c0, s1, c1;
         upk(mul2(splat(6.283185307179586f), tau), t0, t1);
@@ -476,7 +505,7 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, 
             k0 = k0 && !(q.kb2 * r0_ > p.cutoff);
             k1 = k1 && !(q.kb2 * r1_ > p.cutoff);
             if (!(k0 || k1)) break;
-            beam(q, invD, k0, k1, accx[f], accy[f]);
+            beam(q, f, invD, k0, k1, accx[f], accy[f]);
         }
     } else {
 #pragma unroll
@@ -488,17 +517,17 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, 
             const bool kf0 = k0 && !(q.kb2 * n20 > p.cutoff * d0);
             const bool kf1 = k1 && !(q.kb2 * n21 > p.cutoff * d1);
             if (!(kf0 || kf1)) continue;
-            beam(q, pk(rcp_approx(d0), rcp_approx(d1)), kf0, kf1, accx[f], accy[f]);
+            beam(q, f, pk(rcp_approx(d0), rcp_approx(d1)), kf0, kf1, accx[f], accy[f]);
         }
     }
 }
 
 // Adjoint terms of one surviving pair added into G and H[f] (gk: this receiver's
 // g per sorted frequency, stride kR * 32 float2).
-template <int NF, int WINDOW>
+template <int NF, int WINDOW, bool LOSSY>
 __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, float y, float z,
-                                                 const StageSmem &w, int j, const float2 *gk,
-                                                 float &G, float (&H)[NF])
+                                                 const StageSmem &w, const LossSmem<NF> *loss,
+                                                 int j, const float2 *gk, float &G, float (&H)[NF])
 {
     float sh, sl, n2;
     if (!exact_geometry<WINDOW>(x, y, z, w, j, sh, sl, n2)) return;
@@ -511,7 +540,8 @@ __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, fl
             if (p.uniform_b) break;
             continue;
         }
-        beam_adjoint(q, sh, sl, n2, rcp_approx(D), gk[f * (kR * 32)], G, H[f]);
+        beam_adjoint<LOSSY>(q, sh, sl, n2, rcp_approx(D), gk[f * (kR * 32)], G, H[f],
+                            LOSSY ? loss->rf[f][j] : make_float2(0.f, 0.f));
     }
 }
 
@@ -625,11 +655,12 @@ struct WarpBuf {
     int abort_flag, pad[3];
 };
 
-template <int NF, int MODE, bool BATCHED>
+template <int NF, int MODE, bool BATCHED, bool LOSSY = false>
 struct PairCfg {
     static constexpr size_t kAdj = MODE == kBwd ? sizeof(AdjSmem<NF>) : 0;
     static constexpr size_t kInst = BATCHED ? sizeof(FwdParams) : 0;
-    static constexpr size_t kPerWarp = (sizeof(WarpBuf) + kAdj + kInst + 127) / 128 * 128;
+    static constexpr size_t kLoss = LOSSY ? sizeof(LossSmem<NF>) : 0;
+    static constexpr size_t kPerWarp = (sizeof(WarpBuf) + kAdj + kInst + kLoss + 127) / 128 * 128;
     // as many warps as fit in the shared memory budget, at most kWarpsFwd
     static constexpr int kFit = (int)(kSmemBudget / kPerWarp);
     static constexpr int kWarps = kFit < kWarpsFwd ? kFit : kWarpsFwd;
@@ -645,10 +676,11 @@ struct PairCfg {
 // warp ever waits for another, so warps whose receivers meet more surviving
 // pairs cost only themselves.  The FP32 sums fold into the item's float-float
 // partials (global, resident in L2) every kFoldEvery batches.
-template <int NF, int WINDOW, int MODE, bool BATCHED>
+template <int NF, int WINDOW, int MODE, bool BATCHED, bool LOSSY = false>
 __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParams prm)
 {
-    using Cfg = PairCfg<NF, MODE, BATCHED>;
+    using Cfg = PairCfg<NF, MODE, BATCHED, LOSSY>;
+    static_assert(!(LOSSY && BATCHED), "batches with losses run the single-sum kernel");
     constexpr bool STATS = MODE == kStats;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -656,6 +688,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
     WarpBuf &B = *reinterpret_cast<WarpBuf *>(mine);
     AdjSmem<NF> &adj = *reinterpret_cast<AdjSmem<NF> *>(mine + sizeof(WarpBuf));
     FwdParams &inst = *reinterpret_cast<FwdParams *>(mine + sizeof(WarpBuf) + Cfg::kAdj);
+    LossSmem<NF> *const loss =
+        reinterpret_cast<LossSmem<NF> *>(mine + sizeof(WarpBuf) + Cfg::kAdj + Cfg::kInst);
 
     if (lane == 0) {
         for (int i = 0; i < kWRaw; ++i) mbar_init(smem_addr(&B.bar[i]), 1);
@@ -878,6 +912,13 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             const bool seg_ok = lane < nrec;
             StageSmem &w = B.stg;
             stage_batch(w, B.raw[buf][lane], lane, seg_ok, my_seg, cx, cy, cz, alpha, beta);
+            if (LOSSY && MODE != kStats) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    loss->rf[f][lane] = (seg_ok && f < p.nf)
+                                            ? p.seg_rf[(int64_t)p.fperm[f] * p.rf_stride + my_seg]
+                                            : make_float2(0.f, 0.f);
+            }
             uint32_t tmask = 0u;
             if (p.tile_cull) {
                 // this lane's segment against the warp tile's ball (own lane's staging only)
@@ -958,7 +999,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     if (h1) mm1 ^= 0x80000000u >> j1;
                     if (!h0) j0 = j1;
                     if (!h1) j1 = j0;
-                    survivor_pair<NF, WINDOW>(p, XA, YA, ZA, w, j0, j1, h0, h1, accx, accy);
+                    survivor_pair<NF, WINDOW, LOSSY>(p, XA, YA, ZA, w, loss, j0, j1, h0, h1, accx, accy);
                 }
             } else if (MODE == kBwd) {
                 // segment by segment: the lanes holding a survivor of segment jj add their
@@ -973,9 +1014,11 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
 #pragma unroll
                     for (int f = 0; f < NF; ++f) H[f] = 0.f;
                     if ((mm0 << jj) >> 31)
-                        survivor_adjoint<NF, WINDOW>(p, xa[0], ya[0], za[0], w, jj, &adj.g[0][0][lane], G, H);
+                        survivor_adjoint<NF, WINDOW, LOSSY>(p, xa[0], ya[0], za[0], w, loss, jj,
+                                                            &adj.g[0][0][lane], G, H);
                     if ((mm1 << jj) >> 31)
-                        survivor_adjoint<NF, WINDOW>(p, xa[1], ya[1], za[1], w, jj, &adj.g[0][1][lane], G, H);
+                        survivor_adjoint<NF, WINDOW, LOSSY>(p, xa[1], ya[1], za[1], w, loss, jj,
+                                                            &adj.g[0][1][lane], G, H);
                     G = warp_sum(G);
 #pragma unroll
                     for (int f = 0; f < NF; ++f)
@@ -1045,12 +1088,52 @@ struct PrepParams {
     // F64 path records (nullptr when not needed)
     double *amp64;
     unsigned int *status;
+    // losses: per-material flow resistivity (kPa s m^-2, <= 0 hard) or nullptr, the
+    // primitives that end the segments, the scene's triangles (unit normal at 9..11)
+    const float *sigma;
+    const int32_t *hit;
+    const double *tri;
+    int64_t n_tri;
+    int nf;
+    double freq[GBT_MAX_FREQ];
+    float2 *seg_rf;            // [f][rf_stride] (log2 |R|, arg R / 2 pi), or nullptr
+    double2 *seg_r64;          // [f][rf_stride] R for the F64 path, or nullptr
+    int64_t rf_stride;
 };
 
 __device__ __forceinline__ void split_ff(double v, float &hi, float &lo)
 {
     hi = (float)v;
     lo = (float)(v - (double)hi);
+}
+
+// Cosine of the angle of incidence at the reflection that starts segment j (depth >= 1):
+// |t_j . n| with n the unit normal of the primitive that ended segment j - 1 (ground:
+// +z); a mirror reflection keeps |d . n|.  An unknown primitive is flagged.
+__device__ __forceinline__ double incidence_cos(const PrepParams &p, int64_t j)
+{
+    const int prim = p.hit[j - 1];
+    double nx = 0.0, ny = 0.0, nz = 1.0;
+    if (prim >= 1 && prim <= p.n_tri) {
+        const double *n = p.tri + 12 * (int64_t)(prim - 1) + 9;
+        nx = n[0]; ny = n[1]; nz = n[2];
+    } else if (prim != 0) {
+        atomicOr(p.status, STATUS_BAD_INPUT);
+    }
+    return fabs(p.t[3 * j] * nx + p.t[3 * j + 1] * ny + p.t[3 * j + 2] * nz);
+}
+
+// Plane-wave reflection factor of a porous, locally reacting surface of flow resistivity
+// sigma (kPa s m^-2) at frequency f for incidence cos(theta) = c: the Delany-Bazley
+// normalised impedance Z = 1 + 9.08 (f/sigma)^-0.75 + i 11.9 (f/sigma)^-0.73
+// (exp(-i omega t)) in R = (Z c - 1) / (Z c + 1).
+__device__ __forceinline__ double2 porous_reflection(double f, double sigma, double c)
+{
+    const double x = f / sigma;
+    const double zr = 1.0 + 9.08 * pow(x, -0.75), zi = 11.9 * pow(x, -0.73);
+    const double ar = zr * c - 1.0, ai = zi * c, br = zr * c + 1.0, bi = zi * c;
+    const double inv = 1.0 / (br * br + bi * bi);
+    return make_double2((ar * br + ai * bi) * inv, (ai * br - ar * bi) * inv);
 }
 
 __global__ void prepass_kernel(PrepParams p)
@@ -1085,6 +1168,30 @@ __global__ void prepass_kernel(PrepParams p)
     R[3] = make_float4(tl[0], tl[1], tl[2], Ll);      // R_TXL .. R_LL
     R[4] = make_float4((float)amp, 0.f, 0.f, 0.f);    // R_AMP
     if (p.amp64) p.amp64[j] = amp;
+    if (p.seg_rf || p.seg_r64) {
+        // per frequency: the product of the porous reflections' factors before segment j
+        for (int f = 0; f < p.nf; ++f) {
+            double rr = 1.0, ri = 0.0;
+            if (p.sigma) {
+                for (int q = 1; q <= dep; ++q) {
+                    const int64_t jq = j - dep + q;
+                    const int m = p.bmat[jq];
+                    if (m < 0 || m >= p.n_materials) continue;     // flagged above
+                    const double sg = (double)p.sigma[m];
+                    if (!(sg > 0.0)) continue;                      // hard surface
+                    const double2 r = porous_reflection(p.freq[f], sg, incidence_cos(p, jq));
+                    const double nr = rr * r.x - ri * r.y;
+                    ri = rr * r.y + ri * r.x;
+                    rr = nr;
+                }
+            }
+            const int64_t k = (int64_t)f * p.rf_stride + j;
+            if (p.seg_rf)
+                p.seg_rf[k] = make_float2((float)(0.5 * log2(rr * rr + ri * ri)),
+                                          (float)(atan2(ri, rr) * (0.5 / kPi)));
+            if (p.seg_r64) p.seg_r64[k] = make_double2(rr, ri);
+        }
+    }
 }
 
 // ------------------------------------------------------ FP64 variant --
@@ -1103,6 +1210,9 @@ struct F64Params {
     double k[GBT_MAX_FREQ], b[GBT_MAX_FREQ];
     int splits;
     double2 *partial;          // [splits][nf][n_recv]
+    double absorb[GBT_MAX_FREQ];   // amplitude decay rate of air per frequency (Np/m)
+    const double2 *r64;        // [f][r64_stride] porous reflections' factor, or nullptr
+    int64_t r64_stride;
 };
 
 template <int WINDOW>
@@ -1151,12 +1261,18 @@ __global__ void __launch_bounds__(kThreads64) gbs_fwd_f64_kernel(const F64Params
                 const double D = s * s + b * b;
                 if (k * n2 * b / (2.0 * D) > p.cutoff) continue;
                 // c = amp * (k b / 8 pi^2) / E * exp(i k s + i k n^2 / (2E)), E = s - i b
-                const double re_exp = -k * n2 * b / (2.0 * D);
+                const double re_exp = -k * n2 * b / (2.0 * D) - p.absorb[f] * s;
                 const double ph = k * s + k * n2 * s / (2.0 * D);
                 const double a = sa[q] * (k * b / (8.0 * kPi * kPi)) * exp(re_exp) / D;
                 double sn, cs;
                 sincos(ph, &sn, &cs);
-                const double vr = a * (s * cs - b * sn), vi = a * (s * sn + b * cs);
+                double vr = a * (s * cs - b * sn), vi = a * (s * sn + b * cs);
+                if (p.r64) {
+                    const double2 R = p.r64[(int64_t)f * p.r64_stride + t0 + q];
+                    const double ur = vr * R.x - vi * R.y;
+                    vi = vr * R.y + vi * R.x;
+                    vr = ur;
+                }
                 // Neumaier accumulation
                 double t1 = sr[f] + vr;
                 cr[f] += fabs(sr[f]) >= fabs(vr) ? (sr[f] - t1) + vr : (vr - t1) + sr[f];
@@ -1847,25 +1963,25 @@ __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <int NF, int WINDOW, int MODE, bool BATCHED = false>
+template <int NF, int WINDOW, int MODE, bool BATCHED = false, bool LOSSY = false>
 void launch_fwd_t(const FwdParams &p, cudaStream_t s, bool timed)
 {
     constexpr bool STATS = MODE != kFwd;
-    using Cfg = PairCfg<NF, MODE, BATCHED>;
+    using Cfg = PairCfg<NF, MODE, BATCHED, LOSSY>;
     const size_t smem = Cfg::kSmem;
     const int threads = 32 * Cfg::kWarps;
-    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED>,
+    GBT_CUDA(cudaFuncSetAttribute(gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED, LOSSY>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GBT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED>, threads, smem));
+        &per_sm, gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED, LOSSY>, threads, smem));
     if (per_sm < 1) fail(GBT_ERR_UNSUPPORTED, "GBS kernel does not fit on one SM");
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>((p.n_items + Cfg::kWarps - 1) / Cfg::kWarps,
                              (int64_t)std::max(per_sm, 1) * num_sms()));
     GBT_CUDA(cudaMemsetAsync(p.work_counter, 0, sizeof(int), s));
     if (MODE != kStats && timed) timing_begin(s);
-    gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED><<<grid, threads, smem, s>>>(p);
+    gbs_fwd_kernel<NF, WINDOW, MODE, BATCHED, LOSSY><<<grid, threads, smem, s>>>(p);
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
     if (MODE != kStats && timed) timing_end(s);
@@ -1880,9 +1996,26 @@ void launch_fwd(const FwdParams &p, cudaStream_t s, bool timed)
     else launch_fwd_t<NF, WINDOW, kFwd>(p, s, timed);
 }
 
+// With losses (seg_rf set) the forward and adjoint launches take the lossy kernel,
+// instantiated for 1, 2, 4 and 8 frequency slots; counting needs no losses.
+template <int NF, int WINDOW>
+void launch_fwd_lossy(const FwdParams &p, cudaStream_t s, bool timed)
+{
+    if (p.grad_out) launch_fwd_t<NF, WINDOW, kBwd, false, true>(p, s, timed);
+    else launch_fwd_t<NF, WINDOW, kFwd, false, true>(p, s, timed);
+}
+
 template <int WINDOW>
 void launch_fwd_nf(const FwdParams &p, cudaStream_t s, bool timed = true)
 {
+    if (p.seg_rf && !p.stats) {
+        if (p.nf <= 1) launch_fwd_lossy<1, WINDOW>(p, s, timed);
+        else if (p.nf <= 2) launch_fwd_lossy<2, WINDOW>(p, s, timed);
+        else if (p.nf <= 4) launch_fwd_lossy<4, WINDOW>(p, s, timed);
+        else if (p.nf <= 8) launch_fwd_lossy<8, WINDOW>(p, s, timed);
+        else fail(GBT_ERR_UNSUPPORTED, "pair kernel launched with more than 8 frequencies");
+        return;
+    }
     if (p.nf <= 1) launch_fwd<1, WINDOW>(p, s, timed);
     else if (p.nf <= 2) launch_fwd<2, WINDOW>(p, s, timed);
     else if (p.nf <= 4) launch_fwd<4, WINDOW>(p, s, timed);
@@ -1943,6 +2076,7 @@ FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum
         c.scale = (float)(k * b / (8.0 * kPi * kPi));
         c.kh = (float)(0.5 * k);
         c.invb = (float)(1.0 / b);
+        c.al2e = (float)(a.absorption[g] * 1.4426950408889634);
         amin = std::min(amin, 0.5 * k * b);
         bmax = std::max(bmax, b * b);
     }
@@ -1953,6 +2087,23 @@ FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum
 }
 
 }  // namespace
+
+bool has_losses(const gbt_sum_args &a)
+{
+    if (a.flow_resistivity) return true;
+    for (int f = 0; f < a.n_freq; ++f)
+        if (a.absorption[f] != 0.0) return true;
+    return false;
+}
+
+// Per (frequency, segment) loss factors of a sum: (log2 |R|, arg R / 2 pi) floats for the
+// F32 path, complex doubles for the F64 path; none without losses.
+static size_t loss_bytes(const TraceDev &td, const gbt_sum_args &a)
+{
+    if (!has_losses(a)) return 0;
+    const size_t per = a.precision == GBT_PRECISION_F64 ? sizeof(double2) : sizeof(float2);
+    return align_up((size_t)a.n_freq * (size_t)td.capacity * per, 256);
+}
 
 int choose_splits(const TraceDev &td, const gbt_sum_args &a)
 {
@@ -2125,7 +2276,7 @@ static size_t records_bytes(const TraceDev &td)
 // Prepass of a trace's segments into kernel records (and FP64 amplitudes when amp64 is
 // set), with the sum's reflection coefficients and ray weights.
 static void prepass_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
-                           float *rec, double *amp64, cudaStream_t s)
+                           float *rec, double *amp64, cudaStream_t s, void *loss = nullptr)
 {
     if (td.capacity == 0) return;
     PrepParams pp{};
@@ -2140,6 +2291,17 @@ static void prepass_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum
     pp.rec = rec;
     pp.amp64 = amp64;
     pp.status = status_word();
+    if (loss) {
+        pp.sigma = a.flow_resistivity;
+        pp.hit = td.hit;
+        pp.tri = sd.tri;
+        pp.n_tri = sd.n_tri;
+        pp.nf = a.n_freq;
+        for (int f = 0; f < a.n_freq; ++f) pp.freq[f] = a.freq_hz[f];
+        pp.rf_stride = td.capacity;
+        if (a.precision == GBT_PRECISION_F64) pp.seg_r64 = static_cast<double2 *>(loss);
+        else pp.seg_rf = static_cast<float2 *>(loss);
+    }
     prepass_kernel<<<(unsigned)((td.capacity + 255) / 256), 256, 0, s>>>(pp);
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
@@ -2154,6 +2316,7 @@ size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits
     b += align_up(part * (a.precision == GBT_PRECISION_F64 ? sizeof(double2) : sizeof(float4)),
                   256);
     if (a.precision != GBT_PRECISION_F64) b += tile_ws_bytes(a.n_recv, td.capacity, a.tile_cull != 0);
+    b += loss_bytes(td, a);
     return b;
 }
 
@@ -2172,9 +2335,11 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
                       (a.precision == GBT_PRECISION_F64 ? sizeof(double2) : sizeof(float4)),
                   256);
     void *order_ws = w;
+    if (a.precision != GBT_PRECISION_F64) w += tile_ws_bytes(a.n_recv, td.capacity, a.tile_cull != 0);
+    void *loss = loss_bytes(td, a) ? static_cast<void *>(w) : nullptr;
     const int32_t *n_seg_ptr = td.ray_off + td.n_rays;
 
-    prepass_launch(td, sd, a, rec, amp64, s);
+    prepass_launch(td, sd, a, rec, amp64, s, loss);
 
     if (a.n_recv <= 0) return;
     ReduceParams rp{};
@@ -2200,6 +2365,9 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         }
         q.splits = splits;
         q.partial = reinterpret_cast<double2 *>(partial);
+        for (int f = 0; f < a.n_freq; ++f) q.absorb[f] = a.absorption[f];
+        q.r64 = static_cast<const double2 *>(loss);
+        q.r64_stride = td.capacity;
         dim3 grid((unsigned)((a.n_recv + kThreads64 - 1) / kThreads64), (unsigned)splits);
         if (a.window == GBT_WINDOW_LINE)
             gbs_fwd_f64_kernel<GBT_WINDOW_LINE><<<grid, kThreads64, 0, s>>>(q);
@@ -2220,6 +2388,8 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         q.splits = splits;
         q.partial = reinterpret_cast<float4 *>(partial) + (int64_t)splits * g0 * a.n_recv;
         q.stats = stats;
+        q.seg_rf = static_cast<const float2 *>(loss);
+        q.rf_stride = td.capacity;
         q.n_items = cta_tiles(a.n_recv) * kTileWarps * splits;
         q.work_counter = counter;
         tile_prep_launch(q, a.window, tile_ws_layout(order_ws, a.n_recv, td.capacity, a.tile_cull != 0), s);
@@ -2288,7 +2458,7 @@ void recv_order_launch(const float *recv, int64_t n, int32_t *order, void *scrat
 static size_t bwd_layout(const TraceDev &td, const gbt_sum_args &a, const SceneDev *sd,
                          size_t *off)
 {
-    // records | amp64 | counter | seg_G | seg_H | acc | tile order
+    // records | amp64 | counter | seg_G | seg_H | acc | tile order | losses
     size_t b = 0;
     off[0] = b; b += records_bytes(td);
     off[1] = b; b += align_up((size_t)td.capacity * sizeof(double), 256);
@@ -2297,12 +2467,13 @@ static size_t bwd_layout(const TraceDev &td, const gbt_sum_args &a, const SceneD
     off[4] = b; b += align_up((size_t)a.n_freq * td.capacity * sizeof(float), 256);
     off[5] = b; b += align_up((size_t)((sd ? sd->n_materials : 1024) + GBT_MAX_FREQ) * sizeof(double), 256);
     off[6] = b; b += tile_ws_bytes(a.n_recv, td.capacity, a.tile_cull != 0);
+    off[7] = b; b += loss_bytes(td, a);
     return b;
 }
 
 size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a)
 {
-    size_t off[7];
+    size_t off[8];
     return bwd_layout(td, a, &td.scene->d, off);
 }
 
@@ -2310,7 +2481,7 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
                 const float *grad_out, float *grad_gamma, float *grad_w, double *grad_b,
                 void *work, cudaStream_t s)
 {
-    size_t off[7];
+    size_t off[8];
     bwd_layout(td, a, &sd, off);
     char *w = static_cast<char *>(work);
     float *rec = reinterpret_cast<float *>(w + off[0]);
@@ -2325,7 +2496,8 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
     GBT_CUDA(cudaMemsetAsync(acc, 0, (size_t)(sd.n_materials + GBT_MAX_FREQ) * sizeof(double), s));
     if (grad_w) GBT_CUDA(cudaMemsetAsync(grad_w, 0, (size_t)td.n_fan * sizeof(float), s));
 
-    prepass_launch(td, sd, a, rec, amp64, s);
+    void *loss = loss_bytes(td, a) ? static_cast<void *>(w + off[7]) : nullptr;
+    prepass_launch(td, sd, a, rec, amp64, s, loss);
     // per frequency group: seg_G gathers every frequency's terms, seg_H the group's rows
     // (processing slots g0 .. g0 + nf - 1)
     if (a.n_recv > 0) {
@@ -2339,6 +2511,8 @@ void bwd_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a,
             q.seg_G = seg_G;
             q.seg_H = seg_H + (int64_t)g0 * td.capacity;
             q.seg_stride = td.capacity;
+            q.seg_rf = static_cast<const float2 *>(loss);
+            q.rf_stride = td.capacity;
             tile_prep_launch(q, a.window, tile_ws_layout(w + off[6], a.n_recv, td.capacity, a.tile_cull != 0), s);
             if (a.window == GBT_WINDOW_LINE) launch_fwd_nf<GBT_WINDOW_LINE>(q, s);
             else launch_fwd_nf<GBT_WINDOW_SEGMENT>(q, s);
@@ -2420,7 +2594,7 @@ struct BatchImpl {
     std::vector<int> order;            // instance processing order (cost, descending)
     std::vector<int64_t> n_seg, cost;
     std::vector<int> splits;
-    std::vector<size_t> rec_off, part_off, ord_off;
+    std::vector<size_t> rec_off, part_off, ord_off, loss_off;
     std::vector<FwdParams> table;      // in processing order
     std::vector<int64_t> inst_off;
     void *work = nullptr;
@@ -2480,6 +2654,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
     B.rec_off.assign(n, 0);
     B.part_off.assign(n, 0);
     B.ord_off.assign(n, 0);
+    B.loss_off.assign(n, 0);
     size_t b = 0;
     for (int i = 0; i < n; ++i) {
         B.rec_off[i] = b;
@@ -2489,6 +2664,8 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
                           sizeof(float4), 256);
         B.ord_off[i] = b;
         b += tile_ws_bytes(B.args[i].n_recv, B.traces[i]->d.capacity, B.args[i].tile_cull != 0);
+        B.loss_off[i] = b;
+        b += loss_bytes(B.traces[i]->d, B.args[i]);
     }
     const size_t cnt = align_up((size_t)n * sizeof(int), 256);    // one work counter per instance
     const size_t tab = align_up((size_t)n * sizeof(FwdParams), 256);
@@ -2516,6 +2693,10 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
         q.n_items = cta_tiles(a.n_recv) * kTileWarps * q.splits;
         q.partial = reinterpret_cast<float4 *>(w + B.part_off[i]);
         q.work_counter = B.mode == kConcurrent ? B.counter + k : B.counter;
+        if (has_losses(a)) {
+            q.seg_rf = reinterpret_cast<const float2 *>(w + B.loss_off[i]);
+            q.rf_stride = td.capacity;
+        }
         {
             const TileWs t = tile_ws_layout(w + B.ord_off[i], a.n_recv, td.capacity, a.tile_cull != 0);
             q.tile_perm = t.order ? t.perm : nullptr;
@@ -2537,8 +2718,9 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
 static void batch_prepass(BatchImpl &B, int i, cudaStream_t s)
 {
     const TraceDev &td = B.traces[i]->d;
-    prepass_launch(td, td.scene->d, B.args[i],
-                   reinterpret_cast<float *>(static_cast<char *>(B.work) + B.rec_off[i]), nullptr, s);
+    char *w = static_cast<char *>(B.work);
+    prepass_launch(td, td.scene->d, B.args[i], reinterpret_cast<float *>(w + B.rec_off[i]), nullptr,
+                   s, has_losses(B.args[i]) ? static_cast<void *>(w + B.loss_off[i]) : nullptr);
 }
 
 // Merge of instance i (processing index k) into its output.
@@ -2651,11 +2833,15 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
         const int n = (int)B->args.size();
         B->use_graph = d.use_graph != 0;
         B->window = B->args[0].window;
+        bool lossy = false;
         for (int i = 0; i < n; ++i) {
             GBT_REQUIRE(B->args[i].window == B->window, "batch instances must share one window");
             GBT_REQUIRE(B->args[i].precision == GBT_PRECISION_F32, "batches are F32 only");
             B->nf_max = std::max(B->nf_max, (int)B->args[i].n_freq);
+            lossy = lossy || has_losses(B->args[i]);
         }
+        if (lossy && d.form == GBT_BATCH_FUSED)
+            fail(GBT_ERR_UNSUPPORTED, "the fused batch form has no losses: use GBT_BATCH_CONCURRENT");
         status_word();   // allocate before any capture
         // one synchronisation: segment counts of every trace
         GBT_CUDA(cudaStreamSynchronize(s));
@@ -2698,7 +2884,8 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
         double best_ips = d.form == GBT_BATCH_FUSED ? 32.0 : 0.0;
         std::vector<double> cands;
         if (d.form != GBT_BATCH_FUSED) cands.push_back(0.0);
-        if (d.form != GBT_BATCH_CONCURRENT) for (double v : {4.0, 8.0, 16.0, 32.0}) cands.push_back(v);
+        if (d.form != GBT_BATCH_CONCURRENT && !lossy)
+            for (double v : {4.0, 8.0, 16.0, 32.0}) cands.push_back(v);
         if (d.autotune && cands.size() > 1) {
             float best = 1e30f;
             cudaEvent_t e0, e1;

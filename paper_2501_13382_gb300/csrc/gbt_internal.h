@@ -146,6 +146,8 @@ size_t trace_scratch_bytes(int64_t n_rays, int max_refl);
 void csr_ray_depth_launch(TraceDev &td, cudaStream_t s);
 
 // ---- GBS launchers (gbs.cu) ----
+// Whether a sum carries propagation losses (air absorption or porous surfaces).
+bool has_losses(const gbt_sum_args &a);
 size_t sum_workspace_bytes(const TraceDev &td, const gbt_sum_args &a, int splits);
 int choose_splits(const TraceDev &td, const gbt_sum_args &a);
 void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, int splits,

@@ -76,7 +76,8 @@ class gbt_sum_args(C.Structure):
                 ("gamma", C.c_void_p), ("ray_weight", C.c_void_p), ("out", C.c_void_p),
                 ("cutoff", C.c_double), ("precision", C.c_int32), ("accumulate", C.c_int32),
                 ("seg_split", C.c_int32), ("tile_cull", C.c_int32),
-                ("max_device_bytes", C.c_int64)]
+                ("max_device_bytes", C.c_int64), ("absorption", C.c_double * MAX_FREQ),
+                ("flow_resistivity", C.c_void_p)]
 
 
 class gbt_sum_stats(C.Structure):
@@ -109,6 +110,8 @@ _SIGS = {
                                  C.c_double, C.c_double, C.c_int64, C.c_void_p, C.c_int32,
                                  C.c_void_p]),
     "gbt_recv_order": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "gbt_air_absorption": (C.c_int, [C.c_int32, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                     C.c_void_p]),
     "gbt_recv_order_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "gbt_sum_backward": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -213,6 +216,20 @@ def gbt_trace_destroy(trace: int):
 
 def gbt_sum(trace: int, args: gbt_sum_args, stream: int = 0):
     _check(load().gbt_sum(C.c_void_p(trace), C.byref(args), C.c_void_p(stream)), "gbt_sum")
+
+
+def gbt_air_absorption(freqs, temperature_c: float = 20.0, humidity_pct: float = 70.0,
+                       pressure_kpa: float = 101.325) -> np.ndarray:
+    """Amplitude decay rate of air (Np/m) per frequency, ISO 9613-1 (host computation)."""
+    fr = np.ascontiguousarray(np.atleast_1d(np.asarray(freqs, np.float64)))
+    out = np.zeros_like(fr)
+    _check(load().gbt_air_absorption(int(fr.shape[0]), fr.ctypes.data, float(temperature_c),
+                                     float(humidity_pct), float(pressure_kpa), out.ctypes.data),
+           "gbt_air_absorption")
+    return out
+
+
+air_absorption = gbt_air_absorption
 
 
 def gbt_recv_order(recv_ptr: int, n: int, order_ptr: int, stream: int = 0):
@@ -471,7 +488,8 @@ def recv_order(recv) -> "torch.Tensor":
 def sum_args(recv, freqs: Sequence[float], beam_b: Sequence[float], gamma, out,
              ray_weight=None, order=None, window: int = WINDOW_LINE, cutoff: float = 16.0,
              precision: int = PRECISION_F32, accumulate: bool = False, seg_split: int = 0,
-             max_device_bytes: int = 0, tile_cull: bool = False) -> gbt_sum_args:
+             max_device_bytes: int = 0, tile_cull: bool = False, absorption=None,
+             flow_resistivity=None) -> gbt_sum_args:
     a = gbt_sum_args()
     a.recv = _ptr(recv)
     a.n_recv = int(recv.shape[0]) if recv is not None else 0
@@ -490,12 +508,27 @@ def sum_args(recv, freqs: Sequence[float], beam_b: Sequence[float], gamma, out,
     a.seg_split = int(seg_split)
     a.tile_cull = 1 if tile_cull else 0
     a.max_device_bytes = int(max_device_bytes)
+    if absorption is not None:
+        ab = [float(v) for v in np.atleast_1d(absorption)]
+        _require(len(ab) == len(freqs), "one absorption rate per frequency")
+        for f, v in enumerate(ab):
+            a.absorption[f] = v
+    a.flow_resistivity = _ptr(flow_resistivity)
     return a
 
 
 def _require(cond: bool, msg: str):
     if not cond:
         raise ValueError(msg)
+
+
+def _check_sigma(flow_resistivity, n_materials: int):
+    import torch
+    if flow_resistivity is None:
+        return
+    _require(flow_resistivity.is_cuda and flow_resistivity.dtype == torch.float32
+             and flow_resistivity.is_contiguous() and flow_resistivity.numel() == n_materials,
+             f"flow_resistivity must be a contiguous float32 CUDA tensor of {n_materials} values")
 
 
 def _check_tensors(recv, gamma, ray_weight, order, n_materials: int | None = None,
@@ -530,16 +563,22 @@ def _check_out(out, nf: int, nr: int):
 
 def gbs_sum(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
             window: int = WINDOW_LINE, cutoff: float = 16.0, precision: int = PRECISION_F32,
-            out=None, accumulate: bool = False, seg_split: int = 0, tile_cull: bool = False):
-    """Complex pressure p[f, r] (torch complex64 on the device)."""
+            out=None, accumulate: bool = False, seg_split: int = 0, tile_cull: bool = False,
+            absorption=None, flow_resistivity=None):
+    """Complex pressure p[f, r] (torch complex64 on the device).  absorption: per-frequency
+    amplitude decay rate of air (Np/m, see air_absorption); flow_resistivity: float32 CUDA
+    tensor of per-material flow resistivities (kPa s m^-2, <= 0 hard).  Asynchronous:
+    problems a kernel detects (a bounded wait that ran out) surface at gbt_sync."""
     import torch
     _check_tensors(recv, gamma, ray_weight, order, trace.scene.n_materials, trace.n_fan)
+    _check_sigma(flow_resistivity, trace.scene.n_materials)
     nr = int(recv.shape[0])
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
     _check_out(out, len(freqs), nr)
     a = sum_args(recv, freqs, beam_b, gamma, out, ray_weight, order, window, cutoff, precision,
-                 accumulate, seg_split, tile_cull=tile_cull)
+                 accumulate, seg_split, tile_cull=tile_cull, absorption=absorption,
+                 flow_resistivity=flow_resistivity)
     gbt_sum(trace.handle, a, _stream_ptr())
     return out
 
@@ -557,16 +596,19 @@ def sum_stats(trace: Trace, recv, freqs, beam_b, gamma, ray_weight=None, order=N
 
 def gbs_solve(scene: Scene, source, recv, freqs, beam_b, gamma, ray_weight=None, order=None,
               window: int = WINDOW_LINE, cutoff: float = 16.0, max_device_bytes: int = 0,
-              out=None, accumulate: bool = False, tile_cull: bool = False):
+              out=None, accumulate: bool = False, tile_cull: bool = False, absorption=None,
+              flow_resistivity=None):
     """Trace + sum of one source, chunked over rays under a device-byte budget."""
     import torch
     _check_tensors(recv, gamma, ray_weight, order, scene.n_materials, int(source.n_rays))
+    _check_sigma(flow_resistivity, scene.n_materials)
     nr = int(recv.shape[0])
     if out is None:
         out = torch.empty((len(freqs), nr), dtype=torch.complex64, device=recv.device)
     _check_out(out, len(freqs), nr)
     a = sum_args(recv, freqs, beam_b, gamma, out, ray_weight, order, window, cutoff,
-                 PRECISION_F32, accumulate, 0, max_device_bytes, tile_cull=tile_cull)
+                 PRECISION_F32, accumulate, 0, max_device_bytes, tile_cull=tile_cull,
+                 absorption=absorption, flow_resistivity=flow_resistivity)
     gbt_solve(scene.handle, source_desc(source), a, _stream_ptr())
     return out
 
@@ -595,9 +637,11 @@ class Batch:
                                   device=recv.device)
             d = dict(inst, out=out)
             self.instances.append(d)
+            _check_sigma(inst.get("flow_resistivity"), inst["trace"].scene.n_materials)
             args.append(sum_args(recv, inst["freqs"], inst["beam_b"], inst["gamma"], out,
                                  inst.get("ray_weight"), inst.get("order"), window, cutoff,
-                                 tile_cull=tile_cull))
+                                 tile_cull=tile_cull, absorption=inst.get("absorption"),
+                                 flow_resistivity=inst.get("flow_resistivity")))
         n = len(args)
         self._args = (gbt_sum_args * n)(*args)
         self._traces = (C.c_void_p * n)(*[d["trace"].handle for d in self.instances])
@@ -649,10 +693,12 @@ def synthesize(p, freqs, amp, t0: float, dt: float, n_t: int, out=None, accumula
 
 def gbs_sum_backward(trace: Trace, recv, freqs, beam_b, gamma, grad_out, ray_weight=None,
                      order=None, window: int = WINDOW_LINE, cutoff: float = 16.0,
-                     need_weight: bool = True, need_b: bool = True, tile_cull: bool = False):
+                     need_weight: bool = True, need_b: bool = True, tile_cull: bool = False,
+                     absorption=None, flow_resistivity=None):
     """(d gamma, d ray_weight, d b) of a real loss with dL/dp = grad_out (complex64 [F, Nr])."""
     import torch
     _check_tensors(recv, gamma, ray_weight, order, trace.scene.n_materials, trace.n_fan)
+    _check_sigma(flow_resistivity, trace.scene.n_materials)
     go = grad_out.contiguous()
     _require(go.dtype == torch.complex64 and go.is_cuda
              and tuple(go.shape) == (len(freqs), int(recv.shape[0])),
@@ -661,7 +707,7 @@ def gbs_sum_backward(trace: Trace, recv, freqs, beam_b, gamma, grad_out, ray_wei
     dw = torch.empty(trace.n_fan, dtype=torch.float32, device=recv.device) if need_weight else None
     db = torch.empty(len(freqs), dtype=torch.float64, device=recv.device) if need_b else None
     a = sum_args(recv, freqs, beam_b, gamma, None, ray_weight, order, window, cutoff,
-                 tile_cull=tile_cull)
+                 tile_cull=tile_cull, absorption=absorption, flow_resistivity=flow_resistivity)
     a.out = 0
     gbt_sum_backward(trace.handle, a, _ptr(go), _ptr(dg), _ptr(dw), _ptr(db), _stream_ptr())
     return dg, dw, db

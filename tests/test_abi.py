@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version_and_error_string_without_gpu(lib):
-    assert gbt.gbt_version() == 1
+    assert gbt.gbt_version() == 2
     assert isinstance(lib.gbt_last_error(), bytes)
 
 
@@ -56,6 +56,7 @@ int main(void){
         sizeof(gbt_trace_info), sizeof(gbt_sum_args), sizeof(gbt_batch_desc));
  printf("%zu %zu %zu\n", offsetof(gbt_sum_args, gamma), offsetof(gbt_sum_args, cutoff),
         offsetof(gbt_sum_args, max_device_bytes));
+ printf("%zu %zu\n", offsetof(gbt_sum_args, absorption), offsetof(gbt_sum_args, flow_resistivity));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -68,4 +69,23 @@ int main(void){
                          ctypes.sizeof(gbt.gbt_trace_info), ctypes.sizeof(gbt.gbt_sum_args),
                          ctypes.sizeof(gbt.gbt_batch_desc)]
     assert sizes[5:] == [gbt.gbt_sum_args.gamma.offset, gbt.gbt_sum_args.cutoff.offset,
-                         gbt.gbt_sum_args.max_device_bytes.offset]
+                         gbt.gbt_sum_args.max_device_bytes.offset,
+                         gbt.gbt_sum_args.absorption.offset,
+                         gbt.gbt_sum_args.flow_resistivity.offset]
+
+
+def test_library_air_absorption_equals_the_oracles(lib):
+    """gbt_air_absorption (host code of the library, ISO 9613-1) against the oracle's
+    independent implementation, itself pinned to the standard's table; no GPU involved."""
+    import numpy as np
+    from oracle import oracle as O
+    f = np.geomspace(20.0, 20000.0, 31)
+    for T, rh, p in ((20.0, 70.0, 101.325), (-10.0, 20.0, 90.0), (35.0, 95.0, 105.0),
+                     (15.0, 0.0, 101.325)):
+        mine = gbt.gbt_air_absorption(f, T, rh, p)
+        ref = O.air_absorption(f, T, rh, p)
+        assert np.allclose(mine, ref, rtol=1e-12, atol=0), (T, rh, p)
+    with pytest.raises(gbt.GBTError):
+        gbt.gbt_air_absorption([1000.0], 20.0, 120.0, 101.325)
+    with pytest.raises(gbt.GBTError):
+        gbt.gbt_air_absorption([-5.0], 20.0, 50.0, 101.325)
