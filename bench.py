@@ -19,7 +19,8 @@ line also carries `forms` (rank 0, outside the timed steps): the city testing ev
 the large open plane (65,536 rays, 256^2 receivers, 6 bands) with and without the
 pre-cull and on the all-FP64 GPU path; the small open plane; the 32-source batched city
 at 512^2 receivers against one launch per source and per (source, frequency); the
-differentiable city's forward, forward + backward and autograd training step; the tracer
+differentiable city's forward, forward + backward and autograd training step; the city with
+propagation losses; the tracer
 alone; the time synthesis of a field into 2,048 samples.  The reference arm
 (`--impl reference`) times the FP64 CPU oracle on the same workload.
 """
@@ -53,7 +54,7 @@ LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
 # Revision of the pair kernel's source.  DRAM bytes (read + write) per launch of the
 # dominant kernel come from an ncu capture of one revision, instantiation and workload;
 # a changed kernel gets a new revision and no entry until it is captured again.
-KERNEL_REV = "r2.0"
+KERNEL_REV = "r2.1"
 KERNEL_TRAFFIC = {}
 WORKLOADS = ("city", "open_plane_large", "open_plane_small", "diff_city", "big_city")
 
@@ -334,6 +335,47 @@ def bench_solve_form(G, torch, stream, w, cull, steps, flush, mhz, st=None):
             "roofline": roofline_of(torch, st, kms, steps, tag, w.name, mhz)}
 
 
+def bench_losses(G, torch, stream, w, steps, flush, mhz):
+    """The city step with propagation losses: the paper's atmosphere (20 C, 70 %, 1 atm;
+    ISO 9613-1 absorption) and a porous ground (200 kPa s m^-2, Delany-Bazley) under hard
+    buildings, with the pre-cull; against the lossless step and the oracle on a sample."""
+    from oracle import oracle as O
+    from paper_2501_13382_gb300 import inputs as I
+    pb = Problem(G, torch, w)
+    absorb = list(G.air_absorption(pb.freqs, 20.0, 70.0, 101.325))
+    sigma = np.full(w.scene.n_materials, -10.0, np.float32)
+    sigma[0] = 200.0
+    sg = torch.as_tensor(sigma, device="cuda")
+
+    def step():
+        G.gbs_solve(pb.sc, pb.src, pb.recv, pb.freqs, pb.bb, pb.gam, order=pb.order,
+                    window=w.window, cutoff=w.cutoff, out=pb.out, tile_cull=True,
+                    absorption=absorb, flow_resistivity=sg)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    G.gbt_timing_enable(True)
+    G.gbt_timing_read(reset=True)
+    ms = _timed(torch, stream, step, steps, flush) / steps
+    G.gbt_timing_enable(False)
+    n_k, k_ms = G.gbt_timing_read(reset=True)
+    st = pb.stats(G, True)
+    evals = float(pb.recv.shape[0]) * st["n_segments"] * len(pb.freqs)
+    idx = I.receiver_subset(w.receivers, 256, 31)
+    otr = O.trace(w.scene, pb.src)
+    po = O.gbs_sum(otr, w.receivers[idx], w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma,
+                   window=w.window, cutoff=w.cutoff, absorption=absorb,
+                   sigma=sigma.astype(np.float64), scene=w.scene)
+    pg = pb.out.cpu().numpy().astype(np.complex128)[:, idx]
+    tag = kernel_tag(len(pb.freqs), w.window, True).replace(",fwd,", ",fwd+losses,")
+    return {"workload": w.name, "atmosphere": "20 C, 70 %, 101.325 kPa",
+            "absorption_np_per_m": absorb, "ground_flow_resistivity_kPa_s_m2": 200.0,
+            "value": evals / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "rel_l2_vs_oracle": float(np.linalg.norm(pg - po) / np.linalg.norm(po)),
+            "receivers_checked": int(len(idx)),
+            "roofline": roofline_of(torch, st, k_ms / max(n_k, 1), n_k, tag, w.name, mhz)}
+
+
 def bench_f64(G, torch, stream, w, steps=2):
     """The all-FP64 GPU path (every step of the sum in FP64) against the FP32 path with
     float-float phase on the same trace, and both against the FP64 oracle on a sample."""
@@ -550,7 +592,8 @@ def bench_synthesis(G, torch, stream, steps=5):
     gbs = bytes_out / (ms * 1e-3) / 1e9
     return {"samples": n_t, "receivers": int(field.shape[1]), "freqs": len(freqs), "ms": ms,
             "output_GB_per_s": gbs, "hbm_peak_GB_per_s": peak,
-            "frac": (gbs / peak) if peak else None}
+            "frac": (gbs / peak) if peak else None,
+            "note": "gbt_synthesize call (device phasor table + sum), CUDA events on its stream"}
 
 
 def main():
@@ -689,6 +732,8 @@ def main():
         forms = {}
         if want("dense"):
             forms["dense"] = bench_solve_form(G, torch, stream, w, False, 3, flush, mhz)
+        if want("losses"):
+            forms["losses"] = bench_losses(G, torch, stream, w, 10, flush, mhz)
         if want("open_plane_large"):
             op = _workload("open_plane_large")
             forms["open_plane_large"] = {

@@ -280,8 +280,11 @@ gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *str
 
 /* Spatially coherent processing order of receivers (Morton order of their
  * positions quantised to their bounding box), written to order_out (device,
- * n_recv int32).  Results do not depend on the order; neighbouring receivers
- * in one warp see similar beams, which keeps the warp's lanes busy. */
+ * n_recv int32).  The order changes results only by rounding: each warp of 64
+ * receivers forms its exact geometry relative to its first receiver, so
+ * compact warps (neighbouring receivers) are both faster (they see similar
+ * beams, which keeps the warp's lanes busy) and the most accurate; a given
+ * order always gives the same result. */
 gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out, void *stream);
 
 /* Same result as gbt_recv_order (the identical permutation), for callers that
@@ -293,7 +296,10 @@ gbt_status gbt_recv_order(const float *recv, int64_t n_recv, int32_t *order_out,
  * the library, held by every GPU that loads it until the process exits.
  * n_recv must be <= 1,048,576 (GBT_ERR_INVALID_ARG otherwise, before any
  * work).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, which
+ * assumes the device's primary context is not reset (after cudaDeviceReset the
+ * address is stale: do not call this entry point again in that process); make
+ * that first call before any stream capture.
  * All calls share the array and every call clears what it needs, but calls
  * that overlap on the GPU race on it: order them on one stream (or wait
  * between them).  recv and order_out are device pointers owned by the caller. */
@@ -388,8 +394,11 @@ gbt_status gbt_batch_destroy(gbt_batch_t *batch);
  * complex amplitudes as (re, im) doubles; out: device, n_t * n_recv float32,
  * time-major, overwritten, or added to when accumulate is 1 (more than
  * GBT_MAX_FREQ frequencies: several accumulating calls).  The phasors
- * A_f exp(-i 2 pi freq_f t_n) are formed in FP64 on the host, the sums in FP32.
- * n_freq 1 .. GBT_MAX_FREQ, n_t 1 .. 2^20, n_recv >= 0; asynchronous. */
+ * A_f exp(-i 2 pi freq_f t_n) are formed on the device (the phase in turns
+ * reduced in FP64, FP64 sine and cosine, rounded to FP32), the sums in FP32.
+ * n_freq 1 .. GBT_MAX_FREQ, n_t 1 .. 2^20, n_recv >= 0.  Asynchronous: the host
+ * arrays are read before the call returns, the phasor table lives in
+ * stream-ordered scratch, and nothing waits for the GPU. */
 gbt_status gbt_synthesize(const float *p, int32_t n_freq, int64_t n_recv, const double *freq_hz,
                           const double *amp, double t0, double dt, int64_t n_t, float *out,
                           int32_t accumulate, void *stream);
@@ -429,7 +438,13 @@ gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,
 /* ---------------------------------------------------------------- misc -- */
 
 /* Waits for `stream`, then reads and clears the device status word: returns
- * GBT_ERR_TIMEOUT or GBT_ERR_DEVICE_STATUS if a kernel flagged a problem. */
+ * GBT_ERR_TIMEOUT or GBT_ERR_DEVICE_STATUS if a kernel flagged a problem.  The
+ * status word is one per device, shared by every stream: it reports flags raised
+ * by any of the library's kernels on the current device that finished before the
+ * read, including those of the library's private streams (a chunked solve's trace
+ * stream, a batch's branch streams), and clearing it clears them for every caller.
+ * To cover work still running on other streams, synchronise those streams (or the
+ * device) first. */
 gbt_status gbt_sync(void *stream);
 
 /* Self test of the failure path for device waits (no counterpart in the paper):

@@ -120,6 +120,56 @@ void dfree(void *p, cudaStream_t s)
     else cudaFreeAsync(p, s);
 }
 
+cudaStream_t service_stream()
+{
+    static cudaStream_t streams[64] = {};
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!streams[d]) GBT_CUDA(cudaStreamCreateWithFlags(&streams[d], cudaStreamNonBlocking));
+    return streams[d];
+}
+
+void mark_used(cudaEvent_t &ev, cudaStream_t s)
+{
+    if (!ev) GBT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    GBT_CUDA(cudaEventRecord(ev, s));
+}
+
+void mark_trace_used(const gbt_trace_t *tr, cudaStream_t s)
+{
+    gbt_trace_t *t = const_cast<gbt_trace_t *>(tr);
+    mark_used(t->d.used, s);
+    if (t->d.scene) mark_used(t->d.scene->d.used, s);
+}
+
+int32_t read_device_i32(const int32_t *p, cudaEvent_t after)
+{
+    cudaStream_t q = service_stream();
+    if (after) GBT_CUDA(cudaStreamWaitEvent(q, after, 0));
+    int32_t v = 0;
+    GBT_CUDA(cudaMemcpyAsync(&v, p, sizeof(v), cudaMemcpyDeviceToHost, q));
+    GBT_CUDA(cudaStreamSynchronize(q));
+    return v;
+}
+
+// Stream on which a destroyed handle's memory is freed once its last recorded use
+// (`used`) has finished.  With the library's stream-ordered pool the frees are queued
+// behind that use and the host does not wait; an installed allocator frees at once,
+// so the host first waits for the use to end.  Neither waits for unrelated streams.
+cudaStream_t after_last_use(cudaEvent_t used)
+{
+    cudaStream_t q = service_stream();
+    if (!used) return q;
+    bool custom;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        custom = g_has_alloc;
+    }
+    if (custom) GBT_CUDA(cudaEventSynchronize(used));
+    else GBT_CUDA(cudaStreamWaitEvent(q, used, 0));
+    return q;
+}
+
 unsigned int *status_word()
 {
     const int d = current_device();
@@ -282,9 +332,11 @@ static gbt_trace_t *make_trace(const gbt_scene_t *scene, const gbt_source_desc &
         scratch = dalloc(sb, s);
         trace_launch(scene->d, td, src, scratch, sb, s);
         dfree(scratch, s);
+        mark_trace_used(tr, s);
     } catch (...) {
         if (scratch) dfree(scratch, s);
         if (td.block) dfree(td.block, s);
+        if (td.used) cudaEventDestroy(td.used);
         delete tr;
         throw;
     }
@@ -476,15 +528,16 @@ gbt_status gbt_scene_destroy(gbt_scene_t *scene)
 {
     return guarded([&] {
         if (!scene) return;
-        GBT_CUDA(cudaDeviceSynchronize());
-        dfree(scene->d.tri, nullptr);
-        dfree(scene->d.trif, nullptr);
-        dfree(scene->d.face, nullptr);
-        dfree(scene->d.mat, nullptr);
-        dfree(scene->d.cbox, nullptr);
-        dfree(scene->d.tbox, nullptr);
-        if (scene->d.bvh) dfree(scene->d.bvh, nullptr);
-        if (scene->d.bvh_perm) dfree(scene->d.bvh_perm, nullptr);
+        cudaStream_t q = after_last_use(scene->d.used);
+        dfree(scene->d.tri, q);
+        dfree(scene->d.trif, q);
+        dfree(scene->d.face, q);
+        dfree(scene->d.mat, q);
+        dfree(scene->d.cbox, q);
+        dfree(scene->d.tbox, q);
+        if (scene->d.bvh) dfree(scene->d.bvh, q);
+        if (scene->d.bvh_perm) dfree(scene->d.bvh_perm, q);
+        if (scene->d.used) cudaEventDestroy(scene->d.used);
         delete scene;
     });
 }
@@ -546,8 +599,10 @@ gbt_status gbt_trace_import(const gbt_scene_t *scene, const gbt_source_desc *src
             else if (n) GBT_CUDA(cudaMemsetAsync(td.hit, 0xff, (size_t)n * sizeof(int32_t), s));
             csr_ray_depth_launch(td, s);
             td.n_seg_host = n;
+            mark_trace_used(tr, s);
         } catch (...) {
             if (td.block) dfree(td.block, s);
+            if (td.used) cudaEventDestroy(td.used);
             delete tr;
             throw;
         }
@@ -561,12 +616,7 @@ gbt_status gbt_trace_info_get(const gbt_trace_t *trace, gbt_trace_info *info)
         GBT_REQUIRE(trace && info, "trace and info must be non-NULL");
         gbt_trace_t *tr = const_cast<gbt_trace_t *>(trace);
         TraceDev &td = tr->d;
-        if (td.n_seg_host < 0) {
-            int32_t n = 0;
-            GBT_CUDA(cudaDeviceSynchronize());
-            GBT_CUDA(cudaMemcpy(&n, td.ray_off + td.n_rays, sizeof(int32_t), cudaMemcpyDeviceToHost));
-            td.n_seg_host = n;
-        }
+        if (td.n_seg_host < 0) td.n_seg_host = read_device_i32(td.ray_off + td.n_rays, td.used);
         memset(info, 0, sizeof(*info));
         info->n_fan = td.n_fan;
         info->ray_begin = td.ray_begin;
@@ -584,9 +634,10 @@ gbt_status gbt_trace_destroy(gbt_trace_t *trace)
 {
     return guarded([&] {
         if (!trace) return;
-        GBT_CUDA(cudaDeviceSynchronize());
-        trace->d.work.release(nullptr);
-        dfree(trace->d.block, nullptr);
+        cudaStream_t q = after_last_use(trace->d.used);
+        trace->d.work.release(q);
+        dfree(trace->d.block, q);
+        if (trace->d.used) cudaEventDestroy(trace->d.used);
         delete trace;
     });
 }
@@ -602,6 +653,7 @@ gbt_status gbt_sum(const gbt_trace_t *trace, const gbt_sum_args *args, void *str
         const int splits = choose_splits(tr->d, *args);
         void *w = tr->d.work.ensure(sum_workspace_bytes(tr->d, *args, splits), s);
         sum_launch(tr->d, sd, *args, splits, w, s);
+        mark_trace_used(tr, s);
     });
 }
 
@@ -622,31 +674,8 @@ gbt_status gbt_synthesize(const float *p, int32_t n_freq, int64_t n_recv, const 
         GBT_REQUIRE(accumulate == 0 || accumulate == 1, "accumulate must be 0 or 1");
         if (n_recv == 0) return;
         GBT_REQUIRE(p && out, "p and out must be non-NULL");
-        // phasors A_f exp(-i 2 pi f t_n) in FP64: the phase in turns, reduced before the trig
-        std::vector<float2> ph((size_t)n_t * n_freq);
-        for (int64_t n = 0; n < n_t; ++n) {
-            const double t = t0 + (double)n * dt;
-            for (int f = 0; f < n_freq; ++f) {
-                double turns = freq_hz[f] * t;
-                turns -= floor(turns);
-                const double c = cos(2.0 * kPi * turns), sn = -sin(2.0 * kPi * turns);
-                const double re = amp[2 * f] * c - amp[2 * f + 1] * sn;
-                const double im = amp[2 * f] * sn + amp[2 * f + 1] * c;
-                ph[(size_t)n * n_freq + f] = make_float2((float)re, (float)im);
-            }
-        }
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        void *dev = dalloc(ph.size() * sizeof(float2), s);
-        try {
-            // from pageable memory: the copy is staged before the call returns
-            GBT_CUDA(cudaMemcpyAsync(dev, ph.data(), ph.size() * sizeof(float2),
-                                     cudaMemcpyHostToDevice, s));
-            synth_launch(p, n_freq, n_recv, static_cast<const float2 *>(dev), n_t, out, accumulate, s);
-        } catch (...) {
-            dfree(dev, s);
-            throw;
-        }
-        dfree(dev, s);
+        synth_launch(p, n_freq, n_recv, freq_hz, amp, t0, dt, n_t, out, accumulate,
+                     static_cast<cudaStream_t>(stream));
     });
 }
 
@@ -737,6 +766,7 @@ gbt_status gbt_sum_backward(const gbt_trace_t *trace, const gbt_sum_args *args,
         const SceneDev &sd = tr->d.scene->d;
         void *w = tr->d.work.ensure(bwd_workspace_bytes(tr->d, *args), s);
         bwd_launch(tr->d, sd, *args, grad_out, grad_gamma, grad_ray_weight, grad_b, w, s);
+        mark_trace_used(tr, s);
     });
 }
 
@@ -773,12 +803,15 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
             } catch (...) {
                 tr->d.work.release(s);
                 dfree(tr->d.block, s);
+                if (tr->d.used) cudaEventDestroy(tr->d.used);
                 delete tr;
                 throw;
             }
             tr->d.work.release(s);
             dfree(tr->d.block, s);
+            if (tr->d.used) cudaEventDestroy(tr->d.used);
             delete tr;
+            mark_used(scene->d.used, s);
             return;
         }
         // Chunks of rays, double-buffered: chunk i is traced on a private stream into slot
@@ -840,6 +873,7 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
                 GBT_CUDA(cudaEventRecord(summed[k], s));
             }
             // the caller's stream is last: every trace was waited for by a sum on it
+            mark_used(scene->d.used, s);
         } catch (...) {
             cleanup(true);
             throw;
@@ -915,6 +949,7 @@ gbt_status gbt_sum_stats_get(const gbt_trace_t *trace, const gbt_sum_args *args,
                                  cudaMemcpyDeviceToHost, s));
         GBT_CUDA(cudaStreamSynchronize(s));
         dfree(cnt, s);
+        mark_trace_used(tr, s);
         stats->n_segments = nseg;
         stats->pairs = (int64_t)nseg * a.n_recv;
         stats->pairs_prefiltered = (int64_t)h[1];
@@ -977,9 +1012,12 @@ gbt_status gbt_sync(void *stream)
         GBT_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
         unsigned int *sw = status_word();
         unsigned int v = 0;
-        GBT_CUDA(cudaMemcpy(&v, sw, sizeof(v), cudaMemcpyDeviceToHost));
+        cudaStream_t q = service_stream();
+        GBT_CUDA(cudaMemcpyAsync(&v, sw, sizeof(v), cudaMemcpyDeviceToHost, q));
+        GBT_CUDA(cudaStreamSynchronize(q));
         if (v) {
-            GBT_CUDA(cudaMemset(sw, 0, sizeof(unsigned int)));
+            GBT_CUDA(cudaMemsetAsync(sw, 0, sizeof(unsigned int), q));
+            GBT_CUDA(cudaStreamSynchronize(q));
             if (v & STATUS_TIMEOUT) fail(GBT_ERR_TIMEOUT, "a bounded device wait ran out");
             fail(GBT_ERR_DEVICE_STATUS, "device status flags 0x" + std::to_string(v));
         }

@@ -23,9 +23,12 @@
 //    pre-cull, per-tile segment lists with per-entry warp-tile masks and a
 //    per-warp ball test skip segments that can reach none of its receivers.
 //  * Survivors (typically a few percent of pairs) are evaluated exactly, the two
-//    receivers of a lane side by side in paired FP32: float-float s and phase
-//    (reduced in turns before the MUFU sin/cos), compensated cross product for
-//    n^2.  FP32 sums per lane fold into the item's float-float partials every 16
+//    receivers of a lane side by side in paired FP32, in the warp's frame: the
+//    staging forms per segment, relative to the warp tile's first receiver c,
+//    A = (c - o).t and S = s0 + A in float-float and the compensated
+//    N = (c - o) x t, so a receiver at c + x' needs only x'.t (float-float) and
+//    N + x' x t; then float-float s and phase (reduced in turns before the MUFU
+//    sin/cos).  FP32 sums per lane fold into the item's float-float partials every 16
 //    batches, and the per-split partials are merged in float-float (error-free
 //    FP32 sums) in a fixed order by a second kernel, so results do not depend on
 //    scheduling.
@@ -264,17 +267,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 }
 
 // One staged batch of a warp: the prefilter (hot) view relative to the warp
-// tile's first receiver and the exact-path (cold) view.
-enum { C_OXH = 0, C_OYH, C_OZH, C_OXL, C_OYL, C_OZL, C_TXL, C_TYL, C_TZL, C_S0H, C_S0L,
-       C_LH, C_LL, C_AMP, C_COUNT };
+// tile's first receiver c and the exact-path view in the same frame.  With
+// d = c - o (float-float) the exact view holds, per segment, A = d.t and
+// S = s0 + A as float-float pairs, AL = A - L (the segment window), the
+// compensated N = d x t and the direction as (hi, lo), so that for a receiver
+// at x = c + x' the pair needs only x'.t and x' x t:
+//   s_loc = A + x'.t,  s = S + x'.t,  n = N + x' x t.
 struct StageSmem {
-    float4 A[kBatch];               // tx, ty, tz, -o'.t   (exact path reads t_hi here)
-    float4 O[kBatch];               // o' = o - tile centre, s0_hi (per-warp ball test)
+    float4 A[kBatch];               // t_hi.x, t_hi.y, t_hi.z, S_hi
+    float4 O[kBatch];               // o' = o - c, s0_hi (per-warp ball test)
     // prefilter constants, each duplicated into both halves of a float pair:
     // P[0..3] = t_x, t_y, t_z, -o'.t;  P[4..7] = 2a o'_x, 2a o'_y, 2a o'_z, beta - a |o'|^2;
     // P[8] = s0 + margin, P[9] = L + margin
     float4 P[kBatch][5];
-    float cold[C_COUNT][kBatch];
+    float4 T[kBatch];               // t_lo.x, t_lo.y, t_lo.z, S_lo
+    float4 N[kBatch];               // N.x, N.y, N.z, W Gamma_path
+    float4 W[kBatch];               // A_hi, A_lo, AL_hi, AL_lo
     int32_t seg[kBatch];            // global segment index of each staged record
 };
 
@@ -285,48 +293,43 @@ struct LossSmem {
     float2 rf[NF][kBatch];
 };
 
-// Exact geometry of one (receiver, segment) pair in float-float; returns false
-// when the pair falls outside the window.
+// Exact geometry of one (receiver, segment) pair in the warp tile's frame, in
+// float-float: x' = (xh + xl) exactly; returns false when the pair falls outside
+// the window.  The paired twin in survivor_pair rounds each half identically.
 template <int WINDOW>
-__device__ __forceinline__ bool exact_geometry(float x, float y, float z, const StageSmem &w,
-                                               int j, float &sh, float &sl, float &n2)
+__device__ __forceinline__ bool frame_geometry(float xh, float yh, float zh, float xl, float yl,
+                                               float zl, const StageSmem &w, int j, float &sh,
+                                               float &sl, float &n2)
 {
-    const float oxh = w.cold[C_OXH][j], oyh = w.cold[C_OYH][j], ozh = w.cold[C_OZH][j];
-    const float4 A = w.A[j];
-    const float thx = A.x, thy = A.y, thz = A.z;
-    const float tlx = w.cold[C_TXL][j], tly = w.cold[C_TYL][j], tlz = w.cold[C_TZL][j];
-    // delta = x - o as (a + e)
-    float ax, ex, ay, ey, az, ez;
-    two_sum(x, -oxh, ax, ex);
-    two_sum(y, -oyh, ay, ey);
-    two_sum(z, -ozh, az, ez);
-    ex -= w.cold[C_OXL][j];
-    ey -= w.cold[C_OYL][j];
-    ez -= w.cold[C_OZL][j];
-    // s_loc = delta . t
-    const float p0 = __fmul_rn(ax, thx), p1 = __fmul_rn(ay, thy), p2 = __fmul_rn(az, thz);
-    float r0 = fmaf(ax, tlx, fmaf(ex, thx, fmaf(ax, thx, -p0)));
-    float r1 = fmaf(ay, tly, fmaf(ey, thy, fmaf(ay, thy, -p1)));
-    float r2 = fmaf(az, tlz, fmaf(ez, thz, fmaf(az, thz, -p2)));
-    float S1, E1, S, E2;
+    const float4 T = w.A[j], TL = w.T[j], NN = w.N[j];
+    // u = x'.t as (U + ul)
+    const float p0 = __fmul_rn(xh, T.x), p1 = __fmul_rn(yh, T.y), p2 = __fmul_rn(zh, T.z);
+    const float r0 = fmaf(xh, TL.x, fmaf(xl, T.x, fmaf(xh, T.x, -p0)));
+    const float r1 = fmaf(yh, TL.y, fmaf(yl, T.y, fmaf(yh, T.y, -p1)));
+    const float r2 = fmaf(zh, TL.z, fmaf(zl, T.z, fmaf(zh, T.z, -p2)));
+    float S1, E1, U, E2;
     two_sum(p0, p1, S1, E1);
-    two_sum(S1, p2, S, E2);
-    const float lo = (E1 + E2) + (r0 + r1 + r2);
+    two_sum(S1, p2, U, E2);
+    const float ul = __fadd_rn(__fadd_rn(E1, E2), __fadd_rn(__fadd_rn(r0, r1), r2));
     if (WINDOW == GBT_WINDOW_SEGMENT) {
-        if (!(S + lo >= 0.0f)) return false;
-        if (!((S - w.cold[C_LH][j]) + (lo - w.cold[C_LL][j]) < 0.0f)) return false;
+        const float4 AW = w.W[j];
+        if (!(__fadd_rn(__fadd_rn(AW.x, U), __fadd_rn(AW.y, ul)) >= 0.0f)) return false;
+        if (!(__fadd_rn(__fadd_rn(AW.z, U), __fadd_rn(AW.w, ul)) < 0.0f)) return false;
     }
     float e3;
-    two_sum(w.cold[C_S0H][j], S, sh, e3);
-    sl = e3 + (lo + w.cold[C_S0L][j]);
+    two_sum(T.w, U, sh, e3);
+    sl = __fadd_rn(e3, __fadd_rn(ul, TL.w));
     if (WINDOW == GBT_WINDOW_LINE) {
-        if (!(sh + sl >= 0.0f)) return false;
+        if (!(__fadd_rn(sh, sl) >= 0.0f)) return false;
     }
-    // n = delta x t, compensated
-    float nx = dop(ay, thz, az, thy) + fmaf(ay, tlz, fmaf(-az, tly, fmaf(ey, thz, -ez * thy)));
-    float ny = dop(az, thx, ax, thz) + fmaf(az, tlx, fmaf(-ax, tlz, fmaf(ez, thx, -ex * thz)));
-    float nz = dop(ax, thy, ay, thx) + fmaf(ax, tly, fmaf(-ay, tlx, fmaf(ex, thy, -ey * thx)));
-    n2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+    // n = N + x' x t: the small terms first, then the main products
+    const float cx = fmaf(yl, T.z, fmaf(-zl, T.y, fmaf(yh, TL.z, __fmul_rn(-zh, TL.y))));
+    const float cy = fmaf(zl, T.x, fmaf(-xl, T.z, fmaf(zh, TL.x, __fmul_rn(-xh, TL.z))));
+    const float cz = fmaf(xl, T.y, fmaf(-yl, T.x, fmaf(xh, TL.y, __fmul_rn(-yh, TL.x))));
+    const float nx = fmaf(yh, T.z, fmaf(-zh, T.y, __fadd_rn(NN.x, cx)));
+    const float ny = fmaf(zh, T.x, fmaf(-xh, T.z, __fadd_rn(NN.y, cy)));
+    const float nz = fmaf(xh, T.y, fmaf(-yh, T.x, __fadd_rn(NN.z, cz)));
+    n2 = fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz)));
     return true;
 }
 
@@ -366,11 +369,12 @@ __device__ __forceinline__ void beam_adjoint(const FreqConst &q, float sh, float
 // Counting pass: the kept (pair, frequency) triples of one surviving pair, with
 // the same geometry and cutoff arithmetic as the forward path.
 template <int NF, int WINDOW>
-__device__ __forceinline__ void survivor_count(const FwdParams &p, float x, float y, float z,
-                                               const StageSmem &w, int j, uint32_t &kept)
+__device__ __forceinline__ void survivor_count(const FwdParams &p, float xh, float yh, float zh,
+                                               float xl, float yl, float zl, const StageSmem &w,
+                                               int j, uint32_t &kept)
 {
     float sh, sl, n2;
-    if (!exact_geometry<WINDOW>(x, y, z, w, j, sh, sl, n2)) return;
+    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, sh, sl, n2)) return;
     if (p.uniform_b) {
         const float D = fmaf(sh, sh, p.fc[0].b2);
         const float r = n2 * rcp_approx(D);
@@ -394,67 +398,58 @@ __device__ __forceinline__ void survivor_count(const FwdParams &p, float x, floa
 // Two surviving pairs at once in paired FP32: receiver 0 of the lane with
 // segment j0 and receiver 1 with segment j1 (a side without a survivor repeats
 // the other side's segment and is masked out).  Every operation is the paired
-// twin of one pair's evaluation (exact_geometry, then per frequency the Gaussian,
+// twin of one pair's evaluation (frame_geometry, then per frequency the Gaussian,
 // the phase reduced in turns and the 1/E factor), so each half rounds as that
 // evaluation would; only the MUFU operations run per half.  accx / accy
 // hold the two receivers' real / imaginary sums per sorted frequency.
 template <int NF, int WINDOW, bool LOSSY>
-__device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, f2x Z,
-                                              const StageSmem &w, const LossSmem<NF> *loss,
-                                              int j0, int j1, bool h0, bool h1,
-                                              f2x (&accx)[NF], f2x (&accy)[NF])
+__device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH, f2x ZH,
+                                              f2x XL, f2x YL, f2x ZL, const StageSmem &w,
+                                              const LossSmem<NF> *loss, int j0, int j1, bool h0,
+                                              bool h1, f2x (&accx)[NF], f2x (&accy)[NF])
 {
-    const float4 A0 = w.A[j0], A1 = w.A[j1];
+    const float4 A0 = w.A[j0], A1 = w.A[j1], T0 = w.T[j0], T1 = w.T[j1];
+    const float4 N0 = w.N[j0], N1 = w.N[j1];
     const f2x THX = pk(A0.x, A1.x), THY = pk(A0.y, A1.y), THZ = pk(A0.z, A1.z);
-    const f2x TLX = pk(w.cold[C_TXL][j0], w.cold[C_TXL][j1]);
-    const f2x TLY = pk(w.cold[C_TYL][j0], w.cold[C_TYL][j1]);
-    const f2x TLZ = pk(w.cold[C_TZL][j0], w.cold[C_TZL][j1]);
-    // delta = x - o as (a + e)
-    f2x ax, ex, ay, ey, az, ez;
-    two_sum2(X, neg2(pk(w.cold[C_OXH][j0], w.cold[C_OXH][j1])), ax, ex);
-    two_sum2(Y, neg2(pk(w.cold[C_OYH][j0], w.cold[C_OYH][j1])), ay, ey);
-    two_sum2(Z, neg2(pk(w.cold[C_OZH][j0], w.cold[C_OZH][j1])), az, ez);
-    ex = sub2(ex, pk(w.cold[C_OXL][j0], w.cold[C_OXL][j1]));
-    ey = sub2(ey, pk(w.cold[C_OYL][j0], w.cold[C_OYL][j1]));
-    ez = sub2(ez, pk(w.cold[C_OZL][j0], w.cold[C_OZL][j1]));
-    // s_loc = delta . t
-    const f2x p0 = mul2(ax, THX), p1 = mul2(ay, THY), p2 = mul2(az, THZ);
-    const f2x r0 = fma2(ax, TLX, fma2(ex, THX, fma2(ax, THX, neg2(p0))));
-    const f2x r1 = fma2(ay, TLY, fma2(ey, THY, fma2(ay, THY, neg2(p1))));
-    const f2x r2 = fma2(az, TLZ, fma2(ez, THZ, fma2(az, THZ, neg2(p2))));
-    f2x S1, E1, S, E2;
+    const f2x TLX = pk(T0.x, T1.x), TLY = pk(T0.y, T1.y), TLZ = pk(T0.z, T1.z);
+    // u = x'.t as (U + ul)
+    const f2x p0 = mul2(XH, THX), p1 = mul2(YH, THY), p2 = mul2(ZH, THZ);
+    const f2x r0 = fma2(XH, TLX, fma2(XL, THX, fma2(XH, THX, neg2(p0))));
+    const f2x r1 = fma2(YH, TLY, fma2(YL, THY, fma2(YH, THY, neg2(p1))));
+    const f2x r2 = fma2(ZH, TLZ, fma2(ZL, THZ, fma2(ZH, THZ, neg2(p2))));
+    f2x S1, E1, U, E2;
     two_sum2(p0, p1, S1, E1);
-    two_sum2(S1, p2, S, E2);
-    const f2x lo = add2(add2(E1, E2), add2(add2(r0, r1), r2));
+    two_sum2(S1, p2, U, E2);
+    const f2x ul = add2(add2(E1, E2), add2(add2(r0, r1), r2));
     bool k0 = h0, k1 = h1;
     float u0, u1;
     if (WINDOW == GBT_WINDOW_SEGMENT) {
-        upk(add2(S, lo), u0, u1);
+        const float4 W0 = w.W[j0], W1 = w.W[j1];
+        upk(add2(add2(pk(W0.x, W1.x), U), add2(pk(W0.y, W1.y), ul)), u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
-        upk(add2(sub2(S, pk(w.cold[C_LH][j0], w.cold[C_LH][j1])),
-                 sub2(lo, pk(w.cold[C_LL][j0], w.cold[C_LL][j1]))), u0, u1);
+        upk(add2(add2(pk(W0.z, W1.z), U), add2(pk(W0.w, W1.w), ul)), u0, u1);
         k0 = k0 && u0 < 0.0f;
         k1 = k1 && u1 < 0.0f;
     }
     f2x sh, e3;
-    two_sum2(pk(w.cold[C_S0H][j0], w.cold[C_S0H][j1]), S, sh, e3);
-    const f2x sl = add2(e3, add2(lo, pk(w.cold[C_S0L][j0], w.cold[C_S0L][j1])));
+    two_sum2(pk(A0.w, A1.w), U, sh, e3);
+    const f2x sl = add2(e3, add2(ul, pk(T0.w, T1.w)));
     if (WINDOW == GBT_WINDOW_LINE) {
         upk(add2(sh, sl), u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
     }
     if (!(k0 || k1)) return;
-    // n = delta x t, compensated
-    const f2x nx = add2(dop2(ay, THZ, az, THY),
-                        fma2(ay, TLZ, fma2(neg2(az), TLY, fma2(ey, THZ, neg2(mul2(ez, THY))))));
-    const f2x ny = add2(dop2(az, THX, ax, THZ),
-                        fma2(az, TLX, fma2(neg2(ax), TLZ, fma2(ez, THX, neg2(mul2(ex, THZ))))));
-    const f2x nz = add2(dop2(ax, THY, ay, THX),
-                        fma2(ax, TLY, fma2(neg2(ay), TLX, fma2(ex, THY, neg2(mul2(ey, THX))))));
+    // n = N + x' x t
+    const f2x cx = fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, TLZ, mul2(neg2(ZH), TLY))));
+    const f2x cy = fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, TLX, mul2(neg2(XH), TLZ))));
+    const f2x cz = fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, TLY, mul2(neg2(YH), TLX))));
+    const f2x nx = fma2(YH, THZ, fma2(neg2(ZH), THY, add2(pk(N0.x, N1.x), cx)));
+    const f2x ny = fma2(ZH, THX, fma2(neg2(XH), THZ, add2(pk(N0.y, N1.y), cy)));
+    const f2x nz = fma2(XH, THY, fma2(neg2(YH), THX, add2(pk(N0.z, N1.z), cz)));
     const f2x n2 = fma2(nx, nx, fma2(ny, ny, mul2(nz, nz)));
-    const f2x amp = pk(w.cold[C_AMP][j0], w.cold[C_AMP][j1]);
+    const f2x amp = pk(N0.w, N1.w);
     float n20, n21;
     upk(n2, n20, n21);
 
@@ -525,12 +520,13 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x X, f2x Y, 
 // Adjoint terms of one surviving pair added into G and H[f] (gk: this receiver's
 // g per sorted frequency, stride kR * 32 float2).
 template <int NF, int WINDOW, bool LOSSY>
-__device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float x, float y, float z,
-                                                 const StageSmem &w, const LossSmem<NF> *loss,
-                                                 int j, const float2 *gk, float &G, float (&H)[NF])
+__device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float xh, float yh, float zh,
+                                                 float xl, float yl, float zl, const StageSmem &w,
+                                                 const LossSmem<NF> *loss, int j, const float2 *gk,
+                                                 float &G, float (&H)[NF])
 {
     float sh, sl, n2;
-    if (!exact_geometry<WINDOW>(x, y, z, w, j, sh, sl, n2)) return;
+    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, sh, sl, n2)) return;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
@@ -593,13 +589,14 @@ __device__ __forceinline__ bool ball_may_keep(const float4 &r0, const float4 &r1
     return win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
 }
 
-// Stage lane's raw record for the whole CTA: the prefilter view relative to the
-// tile centre (cx, cy, cz), the origin in that frame for the per-warp ball test,
-// and the exact-path view.  A record past the segment count becomes one no
-// receiver can keep.
-__device__ __forceinline__ void stage_batch(StageSmem &w, const float4 (&raw)[kRecFloats / 4],
-                                            int lane, bool valid, int32_t seg, float cx, float cy,
-                                            float cz, float alpha, float beta)
+// Stage lane's raw record for the warp: the prefilter view relative to the frame
+// c = (cx, cy, cz) (the warp tile's first receiver), the origin in that frame for the
+// per-warp ball test, and the exact-path view in the same frame (float-float
+// d = c - o, A = d.t, S = s0 + A, AL = A - L, compensated N = d x t).  A record past
+// the segment count becomes one no receiver can keep.  Returns L_hi.
+__device__ __forceinline__ float stage_batch(StageSmem &w, const float4 (&raw)[kRecFloats / 4],
+                                             int lane, bool valid, int32_t seg, float cx,
+                                             float cy, float cz, float alpha, float beta)
 {
     const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2], r3 = raw[3], r4 = raw[4];
     float4 *P = w.P[lane];
@@ -610,7 +607,6 @@ __device__ __forceinline__ void stage_batch(StageSmem &w, const float4 (&raw)[kR
         const float ot = fmaf(ox, r1.x, fmaf(oy, r1.y, oz * r1.z));
         const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
         const float a2 = 2.f * alpha;
-        w.A[lane] = make_float4(r1.x, r1.y, r1.z, -ot);
         P[0] = make_float4(r1.x, r1.x, r1.y, r1.y);
         P[1] = make_float4(r1.z, r1.z, -ot, -ot);
         P[2] = make_float4(a2 * ox, a2 * ox, a2 * oy, a2 * oy);
@@ -618,26 +614,52 @@ __device__ __forceinline__ void stage_batch(StageSmem &w, const float4 (&raw)[kR
         P[3] = make_float4(a2 * oz, a2 * oz, c7, c7);
         const float s0m = r0.w + kWinMargin, Lm = r1.w + kWinMargin;
         P[4] = make_float4(s0m, s0m, Lm, Lm);
-        w.cold[C_OXH][lane] = r0.x; w.cold[C_OYH][lane] = r0.y; w.cold[C_OZH][lane] = r0.z;
-        w.cold[C_S0H][lane] = r0.w;
-        w.cold[C_LH][lane] = r1.w;
-        w.cold[C_OXL][lane] = r2.x; w.cold[C_OYL][lane] = r2.y; w.cold[C_OZL][lane] = r2.z;
-        w.cold[C_S0L][lane] = r2.w;
-        w.cold[C_TXL][lane] = r3.x; w.cold[C_TYL][lane] = r3.y; w.cold[C_TZL][lane] = r3.z;
-        w.cold[C_LL][lane] = r3.w;
-        w.cold[C_AMP][lane] = r4.x;
+        // d = c - o as (dh + dl)
+        float dxh, dxe, dyh, dye, dzh, dze;
+        two_sum(cx, -r0.x, dxh, dxe);
+        two_sum(cy, -r0.y, dyh, dye);
+        two_sum(cz, -r0.z, dzh, dze);
+        const float dxl = __fsub_rn(dxe, r2.x), dyl = __fsub_rn(dye, r2.y), dzl = __fsub_rn(dze, r2.z);
+        // A = d.t, float-float
+        const float q0 = __fmul_rn(dxh, r1.x), q1 = __fmul_rn(dyh, r1.y), q2 = __fmul_rn(dzh, r1.z);
+        const float e0 = fmaf(dxh, r3.x, fmaf(dxl, r1.x, fmaf(dxh, r1.x, -q0)));
+        const float e1 = fmaf(dyh, r3.y, fmaf(dyl, r1.y, fmaf(dyh, r1.y, -q1)));
+        const float e2 = fmaf(dzh, r3.z, fmaf(dzl, r1.z, fmaf(dzh, r1.z, -q2)));
+        float S1, E1, Ah, E2;
+        two_sum(q0, q1, S1, E1);
+        two_sum(S1, q2, Ah, E2);
+        const float Al = __fadd_rn(__fadd_rn(E1, E2), __fadd_rn(__fadd_rn(e0, e1), e2));
+        // S = s0 + A, AL = A - L
+        float Sh, es, ALh, ea;
+        two_sum(r0.w, Ah, Sh, es);
+        const float Sl = __fadd_rn(es, __fadd_rn(Al, r2.w));
+        two_sum(Ah, -r1.w, ALh, ea);
+        const float ALl = __fadd_rn(ea, __fsub_rn(Al, r3.w));
+        // N = d x t, compensated
+        const float nx = dop(dyh, r1.z, dzh, r1.y) +
+                         fmaf(dyh, r3.z, fmaf(-dzh, r3.y, fmaf(dyl, r1.z, -dzl * r1.y)));
+        const float ny = dop(dzh, r1.x, dxh, r1.z) +
+                         fmaf(dzh, r3.x, fmaf(-dxh, r3.z, fmaf(dzl, r1.x, -dxl * r1.z)));
+        const float nz = dop(dxh, r1.y, dyh, r1.x) +
+                         fmaf(dxh, r3.y, fmaf(-dyh, r3.x, fmaf(dxl, r1.y, -dyl * r1.x)));
+        w.A[lane] = make_float4(r1.x, r1.y, r1.z, Sh);
+        w.T[lane] = make_float4(r3.x, r3.y, r3.z, Sl);
+        w.N[lane] = make_float4(nx, ny, nz, r4.x);
+        w.W[lane] = make_float4(Ah, Al, ALh, ALl);
     } else {
         // far behind its own start, and with finite exact-path values
         w.O[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        w.A[lane] = make_float4(0.f, 0.f, 0.f, -1e15f);
         P[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         P[1] = make_float4(0.f, 0.f, -1e15f, -1e15f);
         P[2] = make_float4(0.f, 0.f, 0.f, 0.f);
         P[3] = make_float4(0.f, 0.f, 0.f, 0.f);
         P[4] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < C_COUNT; ++c) w.cold[c][lane] = 0.f;
+        w.A[lane] = make_float4(0.f, 0.f, 0.f, -1e15f);
+        w.T[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        w.N[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        w.W[lane] = make_float4(-1e15f, 0.f, -1e15f, 0.f);
     }
+    return valid ? r1.w : 0.f;
 }
 
 template <int NF>
@@ -752,7 +774,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
         const int64_t c_idx = p.order ? p.order[wbase] : wbase;
         const float cx = p.recv[3 * c_idx], cy = p.recv[3 * c_idx + 1], cz = p.recv[3 * c_idx + 2];
 
-        float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xx[kR];
+        // receiver k of the lane at x = c + x', x' = (xp + xl) exactly
+        float xa[kR], ya[kR], za[kR], xp[kR], yp[kR], zp[kR], xl[kR], yl[kR], zl[kR], xx[kR];
         int32_t ridx[kR];
         uint32_t valid = 0;
         float4 *const part_base = p.partial + (int64_t)split * p.nf * p.n_recv;
@@ -761,12 +784,14 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             // lane holds receivers lane and lane + 32 of the warp tile: the two halves
             // of its Morton patch, so a beam edge splits work evenly over lanes
             const int64_t r = wbase + (int64_t)k * 32 + lane;
-            xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xx[k] = 0.0f;
+            xa[k] = ya[k] = za[k] = xp[k] = yp[k] = zp[k] = xl[k] = yl[k] = zl[k] = xx[k] = 0.0f;
             ridx[k] = -1;
             if (r < p.n_recv) {
                 const int64_t o = p.order ? p.order[r] : r;
                 xa[k] = p.recv[3 * o]; ya[k] = p.recv[3 * o + 1]; za[k] = p.recv[3 * o + 2];
-                xp[k] = xa[k] - cx; yp[k] = ya[k] - cy; zp[k] = za[k] - cz;
+                two_sum(xa[k], -cx, xp[k], xl[k]);
+                two_sum(ya[k], -cy, yp[k], yl[k]);
+                two_sum(za[k], -cz, zp[k], zl[k]);
                 xx[k] = fmaf(xp[k], xp[k], fmaf(yp[k], yp[k], zp[k] * zp[k]));
                 valid |= 1u << k;
                 ridx[k] = (int32_t)o;
@@ -819,7 +844,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
         f2x accx[NF], accy[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) accx[f] = accy[f] = 0ull;
-        const f2x XA = pk(xa[0], xa[1]), YA = pk(ya[0], ya[1]), ZA = pk(za[0], za[1]);
+        const f2x XL2 = pk(xl[0], xl[1]), YL2 = pk(yl[0], yl[1]), ZL2 = pk(zl[0], zl[1]);
         auto fold_all = [&]() {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -911,7 +936,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             }
             const bool seg_ok = lane < nrec;
             StageSmem &w = B.stg;
-            stage_batch(w, B.raw[buf][lane], lane, seg_ok, my_seg, cx, cy, cz, alpha, beta);
+            const float my_len = stage_batch(w, B.raw[buf][lane], lane, seg_ok, my_seg, cx, cy, cz,
+                                             alpha, beta);
             if (LOSSY && MODE != kStats) {
 #pragma unroll
                 for (int f = 0; f < NF; ++f)
@@ -924,7 +950,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 // this lane's segment against the warp tile's ball (own lane's staging only)
                 const float4 O = w.O[lane], A = w.A[lane];
                 const bool pass = seg_ok &&
-                                  ball_may_keep<WINDOW>(O, make_float4(A.x, A.y, A.z, w.cold[C_LH][lane]),
+                                  ball_may_keep<WINDOW>(O, make_float4(A.x, A.y, A.z, my_len),
                                                         O.x, O.y, O.z, sphere, alpha, beta);
                 tmask = __ballot_sync(0xffffffffu, pass);
             }
@@ -999,7 +1025,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     if (h1) mm1 ^= 0x80000000u >> j1;
                     if (!h0) j0 = j1;
                     if (!h1) j1 = j0;
-                    survivor_pair<NF, WINDOW, LOSSY>(p, XA, YA, ZA, w, loss, j0, j1, h0, h1, accx, accy);
+                    survivor_pair<NF, WINDOW, LOSSY>(p, X2, Y2, Z2, XL2, YL2, ZL2, w, loss, j0, j1, h0,
+                                                     h1, accx, accy);
                 }
             } else if (MODE == kBwd) {
                 // segment by segment: the lanes holding a survivor of segment jj add their
@@ -1014,11 +1041,13 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
 #pragma unroll
                     for (int f = 0; f < NF; ++f) H[f] = 0.f;
                     if ((mm0 << jj) >> 31)
-                        survivor_adjoint<NF, WINDOW, LOSSY>(p, xa[0], ya[0], za[0], w, loss, jj,
-                                                            &adj.g[0][0][lane], G, H);
+                        survivor_adjoint<NF, WINDOW, LOSSY>(p, xp[0], yp[0], zp[0], xl[0], yl[0],
+                                                            zl[0], w, loss, jj, &adj.g[0][0][lane],
+                                                            G, H);
                     if ((mm1 << jj) >> 31)
-                        survivor_adjoint<NF, WINDOW, LOSSY>(p, xa[1], ya[1], za[1], w, loss, jj,
-                                                            &adj.g[0][1][lane], G, H);
+                        survivor_adjoint<NF, WINDOW, LOSSY>(p, xp[1], yp[1], zp[1], xl[1], yl[1],
+                                                            zl[1], w, loss, jj, &adj.g[0][1][lane],
+                                                            G, H);
                     G = warp_sum(G);
 #pragma unroll
                     for (int f = 0; f < NF; ++f)
@@ -1039,7 +1068,8 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     while (mm) {
                         const int jj = __clz(mm);
                         mm ^= 0x80000000u >> jj;
-                        survivor_count<NF, WINDOW>(p, xa[k], ya[k], za[k], w, jj, n_kept);
+                        survivor_count<NF, WINDOW>(p, xp[k], yp[k], zp[k], xl[k], yl[k], zl[k], w, jj,
+                                                   n_kept);
                     }
                 }
             }
@@ -1711,37 +1741,78 @@ __global__ void __launch_bounds__(kListChunk) list_write_bits_kernel(
 }
 
 // Time synthesis: out[n, r] (+)= Re sum_f ph[n, f] p[f, r], ph[n, f] = A_f exp(-i omega_f t_n).
-// Threads run over receivers (coalesced), a block row over kSynthTile time samples whose
-// phasors sit in shared memory; each thread holds its receiver's field in registers.
-// Memory-bound: it writes n_t * n_recv floats and reads the field once per time tile.
-constexpr int kSynthTile = 32;
+// The phasors are formed on the device (synth_phasor_kernel: the phase in turns, f t0 +
+// n (f dt), reduced in FP64 before an FP64 sincospi, then rounded to float2).  The sum:
+// threads over receiver pairs (coalesced), a block row over kSynthTile time samples whose
+// phasors sit in shared memory, each thread holding its receivers' fields in registers.
+// Bound by writing n_t * n_recv floats (streaming stores: the output is not re-read).
+constexpr int kSynthTile = 64;
 
-__global__ void __launch_bounds__(256) synth_kernel(const float2 *__restrict__ p, int nf,
-                                                    int64_t n_recv, const float2 *__restrict__ ph,
-                                                    int64_t n_t, float *__restrict__ out,
-                                                    int accumulate)
+struct SynthPhasorParams {
+    double freq[GBT_MAX_FREQ], amp_re[GBT_MAX_FREQ], amp_im[GBT_MAX_FREQ];
+    double t0, dt;
+    int nf;
+    int64_t n_t;
+    float2 *ph;                // [n_t][nf]
+};
+
+__global__ void synth_phasor_kernel(const SynthPhasorParams p)
 {
-    __shared__ float2 sph[kSynthTile][GBT_MAX_FREQ];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= p.n_t * p.nf) return;
+    const int64_t n = i / p.nf;
+    const int f = (int)(i - n * p.nf);
+    double turns = fma((double)n, p.freq[f] * p.dt, p.freq[f] * p.t0);
+    turns -= floor(turns);
+    double sn, cs;
+    sincospi(2.0 * turns, &sn, &cs);
+    // A (cos - i sin)
+    p.ph[i] = make_float2((float)(p.amp_re[f] * cs + p.amp_im[f] * sn),
+                          (float)(p.amp_im[f] * cs - p.amp_re[f] * sn));
+}
+
+// Each thread owns two adjacent receivers (one 8-byte streaming store per sample) and
+// kSynthTile samples; NF is the exact frequency count, so no padded term costs an FMA.
+template <int NF>
+__global__ void __launch_bounds__(256) synth_kernel(const float2 *__restrict__ p, int64_t n_recv,
+                                                    const float2 *__restrict__ ph, int64_t n_t,
+                                                    float *__restrict__ out, int accumulate)
+{
+    __shared__ float2 sph[kSynthTile][NF];
     const int64_t n0 = (int64_t)blockIdx.y * kSynthTile;
-    for (int i = threadIdx.x; i < kSynthTile * GBT_MAX_FREQ; i += blockDim.x) {
-        const int a = i / GBT_MAX_FREQ, f = i - a * GBT_MAX_FREQ;
-        sph[a][f] = (f < nf && n0 + a < n_t) ? ph[(n0 + a) * nf + f] : make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < kSynthTile * NF; i += blockDim.x) {
+        const int a = i / NF, f = i - a * NF;
+        sph[a][f] = n0 + a < n_t ? ph[(n0 + a) * NF + f] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
     if (r >= n_recv) return;
-    float2 pr[GBT_MAX_FREQ];
+    const bool pair = r + 1 < n_recv;
+    float2 p0[NF], p1[NF];
 #pragma unroll
-    for (int f = 0; f < GBT_MAX_FREQ; ++f)
-        pr[f] = f < nf ? p[(int64_t)f * n_recv + r] : make_float2(0.f, 0.f);
+    for (int f = 0; f < NF; ++f) {
+        p0[f] = p[(int64_t)f * n_recv + r];
+        p1[f] = pair ? p[(int64_t)f * n_recv + r + 1] : make_float2(0.f, 0.f);
+    }
     const int na = (int)min((int64_t)kSynthTile, n_t - n0);
+    float *o = out + n0 * n_recv + r;
+    // 8-byte stores need an even row length (every row then starts 8-byte aligned)
+    const bool vec = pair && !accumulate && (n_recv & 1) == 0 && ((uintptr_t)out & 7u) == 0;
     for (int a = 0; a < na; ++a) {
-        float acc = 0.f;
+        float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
-        for (int f = 0; f < GBT_MAX_FREQ; ++f)
-            acc = fmaf(sph[a][f].x, pr[f].x, fmaf(-sph[a][f].y, pr[f].y, acc));
-        float *o = out + (n0 + a) * n_recv + r;
-        *o = accumulate ? *o + acc : acc;
+        for (int f = 0; f < NF; ++f) {
+            const float2 q = sph[a][f];
+            acc0 = fmaf(q.x, p0[f].x, fmaf(-q.y, p0[f].y, acc0));
+            acc1 = fmaf(q.x, p1[f].x, fmaf(-q.y, p1[f].y, acc1));
+        }
+        float *row = o + a * n_recv;
+        if (vec) {
+            __stcs(reinterpret_cast<float2 *>(row), make_float2(acc0, acc1));
+        } else {
+            row[0] = accumulate ? row[0] + acc0 : acc0;
+            if (pair) row[1] = accumulate ? row[1] + acc1 : acc1;
+        }
     }
 }
 
@@ -2403,15 +2474,46 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
     }
 }
 
-void synth_launch(const float *p, int nf, int64_t n_recv, const float2 *ph, int64_t n_t,
-                  float *out, int accumulate, cudaStream_t s)
+void synth_launch(const float *p, int nf, int64_t n_recv, const double *freq_hz,
+                  const double *amp, double t0, double dt, int64_t n_t, float *out,
+                  int accumulate, cudaStream_t s)
 {
     if (n_recv <= 0 || n_t <= 0) return;
-    const dim3 grid((unsigned)((n_recv + 255) / 256), (unsigned)((n_t + kSynthTile - 1) / kSynthTile));
-    synth_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(p), nf, n_recv, ph, n_t,
-                                      out, accumulate);
-    note_launches(1);
-    GBT_CUDA(cudaGetLastError());
+    SynthPhasorParams pp{};
+    for (int f = 0; f < nf; ++f) {
+        pp.freq[f] = freq_hz[f];
+        pp.amp_re[f] = amp[2 * f];
+        pp.amp_im[f] = amp[2 * f + 1];
+    }
+    pp.t0 = t0;
+    pp.dt = dt;
+    pp.nf = nf;
+    pp.n_t = n_t;
+    // stream-ordered scratch for the phasor table: no host synchronisation
+    const size_t bytes = (size_t)n_t * nf * sizeof(float2);
+    pp.ph = static_cast<float2 *>(dalloc(bytes, s));
+    try {
+        const int64_t m = n_t * nf;
+        synth_phasor_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pp);
+        const dim3 grid((unsigned)((n_recv + 511) / 512),
+                        (unsigned)((n_t + kSynthTile - 1) / kSynthTile));
+        const float2 *fp = reinterpret_cast<const float2 *>(p);
+        switch (nf) {
+#define GBT_SYNTH(NFV) \
+        case NFV: synth_kernel<NFV><<<grid, 256, 0, s>>>(fp, n_recv, pp.ph, n_t, out, accumulate); break;
+            GBT_SYNTH(1) GBT_SYNTH(2) GBT_SYNTH(3) GBT_SYNTH(4) GBT_SYNTH(5) GBT_SYNTH(6)
+            GBT_SYNTH(7) GBT_SYNTH(8) GBT_SYNTH(9) GBT_SYNTH(10) GBT_SYNTH(11) GBT_SYNTH(12)
+            GBT_SYNTH(13) GBT_SYNTH(14) GBT_SYNTH(15) GBT_SYNTH(16)
+#undef GBT_SYNTH
+        default: fail(GBT_ERR_INVALID_ARG, "synthesis takes 1 .. 16 frequencies");
+        }
+        note_launches(2);
+        GBT_CUDA(cudaGetLastError());
+    } catch (...) {
+        dfree(pp.ph, s);
+        throw;
+    }
+    dfree(pp.ph, s);
 }
 
 size_t recv_order_scratch_bytes(int64_t n)
@@ -2610,6 +2712,7 @@ struct BatchImpl {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t graph_kernels = 0;               // kernel nodes of the recorded graph
+    cudaEvent_t used = nullptr;              // after the latest submit
     // kConcurrent: each instance runs the single-instance pair kernel (parameters
     // in constant space) on one of a few branch streams forked from the submit
     // stream, so one instance's draining tail overlaps the next one's start
@@ -2843,14 +2946,12 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
         if (lossy && d.form == GBT_BATCH_FUSED)
             fail(GBT_ERR_UNSUPPORTED, "the fused batch form has no losses: use GBT_BATCH_CONCURRENT");
         status_word();   // allocate before any capture
-        // one synchronisation: segment counts of every trace
-        GBT_CUDA(cudaStreamSynchronize(s));
+        // segment counts of every trace (each read once its trace is complete)
         B->n_seg.resize(n);
         B->cost.resize(n);
         for (int i = 0; i < n; ++i) {
-            int32_t ns = 0;
             const TraceDev &td = B->traces[i]->d;
-            GBT_CUDA(cudaMemcpy(&ns, td.ray_off + td.n_rays, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            const int32_t ns = read_device_i32(td.ray_off + td.n_rays, td.used);
             B->n_seg[i] = ns;
             B->cost[i] = (int64_t)ns * B->args[i].n_recv * B->args[i].n_freq;
         }
@@ -2919,10 +3020,17 @@ BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s)
     return B;
 }
 
+static void batch_mark_used(BatchImpl *B, cudaStream_t s)
+{
+    mark_used(B->used, s);
+    for (const gbt_trace_t *t : B->traces) mark_trace_used(t, s);
+}
+
 void batch_submit(BatchImpl *B, cudaStream_t s)
 {
     if (!B->use_graph) {
         batch_record(*B, s);
+        batch_mark_used(B, s);
         return;
     }
     if (!B->exec) {
@@ -2956,19 +3064,28 @@ void batch_submit(BatchImpl *B, cudaStream_t s)
         note_launches(B->graph_kernels);
     }
     GBT_CUDA(cudaGraphLaunch(B->exec, s));
+    batch_mark_used(B, s);
 }
 
 void batch_destroy(BatchImpl *B)
 {
     if (!B) return;
-    cudaDeviceSynchronize();
+    // the batch's workspace is freed behind its latest submit; graphs, streams and
+    // events may be destroyed while work they launched is still pending
+    cudaStream_t q = nullptr;
+    try {
+        q = after_last_use(B->used);
+    } catch (...) {
+        cudaDeviceSynchronize();
+    }
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
     for (cudaStream_t b : B->branch) if (b) cudaStreamDestroy(b);
     for (cudaEvent_t e : B->join) if (e) cudaEventDestroy(e);
     if (B->fork) cudaEventDestroy(B->fork);
-    if (B->work) dfree(B->work, nullptr);
+    if (B->work) dfree(B->work, q);
+    if (B->used) cudaEventDestroy(B->used);
     delete B;
 }
 

@@ -35,6 +35,17 @@ enum : unsigned int { STATUS_BOUNDS = 1u, STATUS_TIMEOUT = 2u, STATUS_BAD_INPUT 
 
 int num_sms();
 
+// Per-device non-blocking stream of the library's own bookkeeping (small readbacks,
+// frees of destroyed handles), so that none of them waits for unrelated streams.
+cudaStream_t service_stream();
+// Records `ev` (created on first use) on s: the latest launch that read a handle.
+void mark_used(cudaEvent_t &ev, cudaStream_t s);
+// Reads one int32 from device memory once `after` (if any) has completed.
+int32_t read_device_i32(const int32_t *p, cudaEvent_t after);
+// Stream on which a destroyed handle's memory may be freed: ordered after `used` (the
+// host waits for it only when a caller-installed allocator frees immediately).
+cudaStream_t after_last_use(cudaEvent_t used);
+
 // Count of kernels the library has put on a stream (gbt_launches_read).
 void note_launches(int64_t n);
 
@@ -90,6 +101,7 @@ struct SceneDev {
     int32_t *bvh_perm = nullptr;   // triangle index of each leaf entry
     int64_t n_bvh_nodes = 0;
     int bvh_depth = 0;
+    mutable cudaEvent_t used = nullptr;   // after the latest launch that read the scene
 };
 constexpr int kTriCluster = 8;
 
@@ -135,6 +147,7 @@ struct TraceDev {
     void *block = nullptr;       // single allocation holding everything above
     DeviceBuffer work;           // scratch for sums (records, partials)
     int64_t n_seg_host = -1;     // cached once read back
+    cudaEvent_t used = nullptr;  // after the latest launch that read or wrote the trace
 };
 
 // ---- kernels' host-side launchers (trace.cu) ----
@@ -161,12 +174,15 @@ void recv_order_noalloc_launch(const float *recv, int64_t n, int32_t *order, cud
 // ---- batched persistent launch (gbs.cu) ----
 struct BatchImpl;
 BatchImpl *batch_create(const gbt_batch_desc &d, cudaStream_t s);
+// Records the trace's and its scene's last use on s (after a launch that reads them).
+void mark_trace_used(const gbt_trace_t *tr, cudaStream_t s);
 void batch_submit(BatchImpl *b, cudaStream_t s);
 void batch_destroy(BatchImpl *b);
 
-// ---- time synthesis (gbs.cu): ph holds n_t * nf phasors A_f exp(-i omega_f t_n) ----
-void synth_launch(const float *p, int nf, int64_t n_recv, const float2 *ph, int64_t n_t,
-                  float *out, int accumulate, cudaStream_t s);
+// ---- time synthesis (gbs.cu): phasors A_f exp(-i 2 pi f t_n) formed on the device ----
+void synth_launch(const float *p, int nf, int64_t n_recv, const double *freq_hz,
+                  const double *amp, double t0, double dt, int64_t n_t, float *out,
+                  int accumulate, cudaStream_t s);
 
 // ---- backward (gbs.cu) ----
 size_t bwd_workspace_bytes(const TraceDev &td, const gbt_sum_args &a);

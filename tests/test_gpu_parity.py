@@ -148,13 +148,21 @@ def test_sum_city_segment_window(G):
 
 
 def test_split_and_order_do_not_change_results(G):
+    """Splits regroup FP32 partial sums; the processing order changes each warp's frame
+    (its first receiver, relative to which the exact geometry is formed), so both change
+    results only by rounding.  Without an order a warp's 64 receivers here span 1.6 grid
+    rows (up to 500 m), the frame's worst case; every result stays on the oracle."""
     w = I.city(n_rays=8192, n_recv_side=40)
     base, _, _ = _gpu_sum(G, w, seg_split=1, order=False)
     ordered, _, _ = _gpu_sum(G, w, seg_split=1, order=True)
-    assert np.array_equal(base, ordered)          # every receiver's sum is independent
+    _, po = O.solve(w)
+    assert rel_l2(base, po) <= TOL_L2 and rel_l2(ordered, po) <= TOL_L2
+    assert rel_l2(base, ordered) < 3e-5, rel_l2(base, ordered)
+    again, _, _ = _gpu_sum(G, w, seg_split=1, order=True)
+    assert np.array_equal(again, ordered)         # deterministic for one order
     for s in (3, 17, 64):
         q, _, _ = _gpu_sum(G, w, seg_split=s)
-        assert rel_l2(q, base) < 1e-6
+        assert rel_l2(q, ordered) < 1e-6
 
 
 def test_many_tiles_every_receiver_against_oracle(G):

@@ -31,6 +31,7 @@ def test_oracle_matches_its_stored_outputs():
     for k in ("re", "im"):
         assert _close(now["open_plane"][k], ref["open_plane"][k], 1e-12), k
         assert _close(now["city_sum"][k], ref["city_sum"][k], 1e-12), k
+        assert _close(now["city_lossy"][k], ref["city_lossy"][k], 1e-12), k
     assert now["city_trace"] == ref["city_trace"]
     for k in ("grad_gamma", "grad_b", "grad_weight_sum", "grad_weight_norm"):
         assert _close(now["city_adjoint"][k], ref["city_adjoint"][k], 1e-10), k
