@@ -558,6 +558,7 @@ def bench_trace(G, torch, stream, steps=5):
                 t = G.Trace(sc, src)
                 ev[i][1].record(stream)
                 t.close()
+            torch.cuda.synchronize()
             ms = float(np.median([a0.elapsed_time(b0) for a0, b0 in ev]))
             r[an] = {"ms": ms, "rays_per_s": src.n_rays / (ms * 1e-3), "segments": n_seg}
             sc.close()

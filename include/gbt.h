@@ -395,10 +395,10 @@ gbt_status gbt_batch_destroy(gbt_batch_t *batch);
  * time-major, overwritten, or added to when accumulate is 1 (more than
  * GBT_MAX_FREQ frequencies: several accumulating calls).  The phasors
  * A_f exp(-i 2 pi freq_f t_n) are formed on the device (the phase in turns
- * reduced in FP64, FP64 sine and cosine, rounded to FP32), the sums in FP32.
- * n_freq 1 .. GBT_MAX_FREQ, n_t 1 .. 2^20, n_recv >= 0.  Asynchronous: the host
- * arrays are read before the call returns, the phasor table lives in
- * stream-ordered scratch, and nothing waits for the GPU. */
+ * reduced to [0, 1) in FP64, then FP32 sine and cosine of the reduced turn),
+ * the sums in FP32.  n_freq 1 .. GBT_MAX_FREQ, n_t 1 .. 2^20, n_recv >= 0.
+ * Asynchronous: one kernel launch, no scratch, nothing waits for the GPU (the
+ * host arrays are read before the call returns). */
 gbt_status gbt_synthesize(const float *p, int32_t n_freq, int64_t n_recv, const double *freq_hz,
                           const double *amp, double t0, double dt, int64_t n_t, float *out,
                           int32_t accumulate, void *stream);

@@ -785,7 +785,8 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
         const int64_t N = src->n_rays;
         const int64_t loss = has_losses(*args) ? 16 * (int64_t)args->n_freq : 0;
         const int64_t per_ray = (int64_t)(src->max_reflections + 1) *
-                                (80 /*compact*/ + 80 /*padded*/ + 4 * kRecFloats + 8 + 8 + loss);
+                                (80 /*compact*/ + 80 /*padded*/ + 4 * kRecFloats + 32 /*cull*/ + 8 + 8 +
+                                 loss);
         int64_t chunk = N;
         if (args->max_device_bytes > 0) {
             chunk = std::max<int64_t>(1, args->max_device_bytes / std::max<int64_t>(per_ray, 1));

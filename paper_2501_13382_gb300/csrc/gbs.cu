@@ -84,6 +84,7 @@ struct alignas(16) FwdParams {
     int64_t n_recv;
     const int32_t *n_seg_ptr;
     const float *rec;          // AoS records, kRecFloats per segment
+    const float4 *crec;        // cull records: (o_hi, s0_hi), (t_hi, L_hi) per segment
     int nf;
     int uniform_b;             // all b equal: frequencies sorted by k, loop stops at first cull
     int tile_cull;             // skip segments that reach none of a warp's receivers
@@ -591,14 +592,13 @@ __device__ __forceinline__ bool ball_may_keep(const float4 &r0, const float4 &r1
 
 // Stage lane's raw record for the warp: the prefilter view relative to the frame
 // c = (cx, cy, cz) (the warp tile's first receiver), the origin in that frame for the
-// per-warp ball test, and the exact-path view in the same frame (float-float
-// d = c - o, A = d.t, S = s0 + A, AL = A - L, compensated N = d x t).  A record past
-// the segment count becomes one no receiver can keep.  Returns L_hi.
+// per-warp ball test and the direction.  A record past the segment count becomes one no
+// receiver can keep.  Returns L_hi.
 __device__ __forceinline__ float stage_batch(StageSmem &w, const float4 (&raw)[kRecFloats / 4],
                                              int lane, bool valid, int32_t seg, float cx,
                                              float cy, float cz, float alpha, float beta)
 {
-    const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2], r3 = raw[3], r4 = raw[4];
+    const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2];
     float4 *P = w.P[lane];
     w.seg[lane] = valid ? seg : -1;
     if (valid) {
@@ -614,6 +614,26 @@ __device__ __forceinline__ float stage_batch(StageSmem &w, const float4 (&raw)[k
         P[3] = make_float4(a2 * oz, a2 * oz, c7, c7);
         const float s0m = r0.w + kWinMargin, Lm = r1.w + kWinMargin;
         P[4] = make_float4(s0m, s0m, Lm, Lm);
+    } else {
+        // far behind its own start
+        w.O[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[1] = make_float4(0.f, 0.f, -1e15f, -1e15f);
+        P[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        P[4] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return valid ? r1.w : 0.f;
+}
+
+// Stage lane's raw record's exact-path view in the warp's frame: float-float
+// d = c - o, A = d.t, S = s0 + A, AL = A - L and the compensated N = d x t, with the
+// direction as (hi, lo) and the amplitude; finite values past the segment count.
+__device__ __forceinline__ void stage_exact(StageSmem &w, const float4 (&raw)[kRecFloats / 4],
+                                            int lane, bool valid, float cx, float cy, float cz)
+{
+    const float4 r0 = raw[0], r1 = raw[1], r2 = raw[2], r3 = raw[3], r4 = raw[4];
+    if (valid) {
         // d = c - o as (dh + dl)
         float dxh, dxe, dyh, dye, dzh, dze;
         two_sum(cx, -r0.x, dxh, dxe);
@@ -647,19 +667,11 @@ __device__ __forceinline__ float stage_batch(StageSmem &w, const float4 (&raw)[k
         w.N[lane] = make_float4(nx, ny, nz, r4.x);
         w.W[lane] = make_float4(Ah, Al, ALh, ALl);
     } else {
-        // far behind its own start, and with finite exact-path values
-        w.O[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[1] = make_float4(0.f, 0.f, -1e15f, -1e15f);
-        P[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[4] = make_float4(0.f, 0.f, 0.f, 0.f);
         w.A[lane] = make_float4(0.f, 0.f, 0.f, -1e15f);
         w.T[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
         w.N[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
         w.W[lane] = make_float4(-1e15f, 0.f, -1e15f, 0.f);
     }
-    return valid ? r1.w : 0.f;
 }
 
 template <int NF>
@@ -873,14 +885,30 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
         const int64_t n_chunks = (n_seg + kBatch - 1) / kBatch;
         int64_t chunk = split;   // list: next chunk to scan
         int qlen = 0;            // list: entries queued for this warp tile (warp-uniform)
+        // The mask and entry words of the next two chunks of the item are loaded ahead of
+        // their use, so the scan below does not wait on global loads.
+        auto load_chunk = [&](int64_t ch, uint32_t &mbits, int32_t &ent) {
+            const int64_t e = ch * kBatch + lane;
+            const bool in = ch < n_chunks && e < n_seg;
+            mbits = in ? (uint32_t)p.list_mask[lst - p.list + e] : 0u;
+            ent = in ? lst[e] : -1;
+        };
+        uint32_t pm0 = 0u, pm1 = 0u;
+        int32_t pe0 = -1, pe1 = -1;
+        if (lst) {
+            load_chunk(chunk, pm0, pe0);
+            load_chunk(chunk + p.splits, pm1, pe1);
+        }
         auto next_list_batch = [&](int32_t &idx) -> int {
             while (qlen < kBatch && chunk < n_chunks) {
-                const int64_t e = chunk * kBatch + lane;
-                const bool sel = e < n_seg && (p.list_mask[lst - p.list + e] & wbit) != 0u;
+                const bool sel = (pm0 & wbit) != 0u;
                 const uint32_t m = __ballot_sync(0xffffffffu, sel);
-                if (sel) B.queue[qlen + __popc(m & ((1u << lane) - 1u))] = lst[e];
+                if (sel) B.queue[qlen + __popc(m & ((1u << lane) - 1u))] = pe0;
                 qlen += __popc(m);
                 chunk += p.splits;
+                pm0 = pm1;
+                pe0 = pe1;
+                load_chunk(chunk + p.splits, pm1, pe1);
             }
             __syncwarp();
             const int n = min(qlen, kBatch);
@@ -938,6 +966,10 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             StageSmem &w = B.stg;
             const float my_len = stage_batch(w, B.raw[buf][lane], lane, seg_ok, my_seg, cx, cy, cz,
                                              alpha, beta);
+            // The exact view: with the pre-cull at once (nearly every batch has survivors);
+            // testing every pair only after the prefilter, and only for a batch in which the
+            // warp has a survivor (most such batches have none), before raw[buf] is reused.
+            if (lst) stage_exact(w, B.raw[buf][lane], lane, seg_ok, cx, cy, cz);
             if (LOSSY && MODE != kStats) {
 #pragma unroll
                 for (int f = 0; f < NF; ++f)
@@ -948,14 +980,17 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             uint32_t tmask = 0u;
             if (p.tile_cull) {
                 // this lane's segment against the warp tile's ball (own lane's staging only)
-                const float4 O = w.O[lane], A = w.A[lane];
+                const float4 O = w.O[lane];
+                const float4 *R1 = &B.raw[buf][lane][1];   // t_hi, L_hi of the raw record
                 const bool pass = seg_ok &&
-                                  ball_may_keep<WINDOW>(O, make_float4(A.x, A.y, A.z, my_len),
+                                  ball_may_keep<WINDOW>(O, make_float4(R1->x, R1->y, R1->z, my_len),
                                                         O.x, O.y, O.z, sphere, alpha, beta);
                 tmask = __ballot_sync(0xffffffffu, pass);
             }
-            __syncwarp();        // the batch is staged and raw[buf] is free again
-            issue(kb_ + 2);
+            if (lst) {
+                __syncwarp();    // the batch is staged and raw[buf] is free again
+                issue(kb_ + 2);
+            }
 
             // ---- prefilter: one keep bit per (receiver, segment); segment jj at bit 31 - jj.
             // Both receivers of the lane go through paired FP32 instructions:
@@ -1013,6 +1048,12 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     m[0] = __funnelshift_l(kb0, m[0], 1);
                     m[1] = __funnelshift_l(kb1, m[1], 1);
                 }
+            }
+            if (!lst) {
+                if (__any_sync(0xffffffffu, (((valid & 1u) ? m[0] : 0u) | ((valid & 2u) ? m[1] : 0u)) != 0u))
+                    stage_exact(w, B.raw[buf][lane], lane, seg_ok, cx, cy, cz);
+                __syncwarp();    // the batch is staged and raw[buf] is free again
+                issue(kb_ + 2);
             }
             // ---- survivors, in segment order per receiver
             if (MODE == kFwd) {
@@ -1115,6 +1156,7 @@ struct PrepParams {
     int64_t n_fan;
     int n_materials;
     float *rec;
+    float4 *crec;              // cull records (origin, s0, direction, length), 32 B each
     // F64 path records (nullptr when not needed)
     double *amp64;
     unsigned int *status;
@@ -1197,6 +1239,8 @@ __global__ void prepass_kernel(PrepParams p)
     R[2] = make_float4(ol[0], ol[1], ol[2], s0l);     // R_OXL .. R_S0L
     R[3] = make_float4(tl[0], tl[1], tl[2], Ll);      // R_TXL .. R_LL
     R[4] = make_float4((float)amp, 0.f, 0.f, 0.f);    // R_AMP
+    p.crec[2 * j] = R[0];
+    p.crec[2 * j + 1] = R[1];
     if (p.amp64) p.amp64[j] = amp;
     if (p.seg_rf || p.seg_r64) {
         // per frequency: the product of the porous reflections' factors before segment j
@@ -1494,25 +1538,24 @@ __global__ void warp_ball_kernel(const float *recv, const int32_t *order, int64_
 }
 
 template <int WINDOW>
-__global__ void tile_weight_kernel(const float *rec, const int32_t *n_seg_ptr, const float4 *ball,
+__global__ void tile_weight_kernel(const float4 *crec, const int32_t *n_seg_ptr, const float4 *ball,
                                    int64_t n_tiles, float alpha, float beta, unsigned int *weight)
 {
     const int64_t ns = *n_seg_ptr;
     const int64_t stride = ns > kWeightSamples ? (ns + kWeightSamples - 1) / kWeightSamples : 1;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * stride;
     const bool ok = j < ns;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
     if (ok) {
-        const float4 *R = reinterpret_cast<const float4 *>(rec + j * kRecFloats);
-        r0 = R[0]; r1 = R[1]; r2 = R[2];
+        r0 = crec[2 * j];
+        r1 = crec[2 * j + 1];
     }
     for (int64_t t = 0; t < n_tiles; ++t) {
         const float4 b = ball[t];
         bool pass = false;
         if (ok)
-            pass = ball_may_keep<WINDOW>(r0, r1, (r0.x - b.x) + r2.x, (r0.y - b.y) + r2.y,
-                                         (r0.z - b.z) + r2.z, make_float4(0.f, 0.f, 0.f, b.w),
-                                         alpha, beta);
+            pass = ball_may_keep<WINDOW>(r0, r1, r0.x - b.x, r0.y - b.y, r0.z - b.z,
+                                         make_float4(0.f, 0.f, 0.f, b.w), alpha, beta);
         const unsigned int m = __ballot_sync(0xffffffffu, pass);
         if ((threadIdx.x & 31) == 0 && m) atomicAdd(&weight[t], (unsigned int)__popc(m));
     }
@@ -1541,19 +1584,23 @@ __global__ void tile_rank_kernel(const unsigned int *weight, int64_t n_tiles, in
 constexpr int kListChunk = 1024;
 
 template <int WINDOW>
-__device__ __forceinline__ bool seg_reaches_ball(const float4 &r0, const float4 &r1, const float4 &r2,
+// From a segment's cull record (its origin rounded to FP32, which the test's slack of
+// 5 cm far exceeds).
+__device__ __forceinline__ bool seg_reaches_ball(const float4 &r0, const float4 &r1,
                                                  const float4 &b, float alpha, float beta)
 {
-    return ball_may_keep<WINDOW>(r0, r1, (r0.x - b.x) + r2.x, (r0.y - b.y) + r2.y,
-                                 (r0.z - b.z) + r2.z, make_float4(0.f, 0.f, 0.f, b.w), alpha, beta);
+    return ball_may_keep<WINDOW>(r0, r1, r0.x - b.x, r0.y - b.y, r0.z - b.z,
+                                 make_float4(0.f, 0.f, 0.f, b.w), alpha, beta);
 }
 
 template <int WINDOW>
 __global__ void __launch_bounds__(kListChunk) list_count_kernel(
-    const float *rec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
+    const float4 *crec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
     int64_t n_chunks, float alpha, float beta, int32_t *counts, uint32_t *bits)
 {
+    // block (c, g): chunk c against tiles g, g + G, ... (G = gridDim.y tile groups)
     extern __shared__ int32_t cnt_s[];
+    const int64_t G = gridDim.y, g = blockIdx.y;
     for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) cnt_s[t] = 0;
     __syncthreads();
     const int64_t ns = *n_seg_ptr;
@@ -1561,13 +1608,13 @@ __global__ void __launch_bounds__(kListChunk) list_count_kernel(
     if (c * kListChunk < ns) {
         const int64_t j = c * kListChunk + threadIdx.x;
         const bool ok = j < ns;
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
         if (ok) {
-            const float4 *R = reinterpret_cast<const float4 *>(rec + j * kRecFloats);
-            r0 = R[0]; r1 = R[1]; r2 = R[2];
+            r0 = crec[2 * j];
+            r1 = crec[2 * j + 1];
         }
-        for (int64_t t = 0; t < n_tiles; ++t) {
-            const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, r2, ball[t], alpha, beta);
+        for (int64_t t = g; t < n_tiles; t += G) {
+            const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, ball[t], alpha, beta);
             const unsigned int m = __ballot_sync(0xffffffffu, pass);
             if ((threadIdx.x & 31) == 0) {
                 if (m) atomicAdd(&cnt_s[t], (int32_t)__popc(m));
@@ -1576,7 +1623,8 @@ __global__ void __launch_bounds__(kListChunk) list_count_kernel(
         }
     }
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) counts[t * n_chunks + c] = cnt_s[t];
+    for (int64_t t = g + (int64_t)threadIdx.x * G; t < n_tiles; t += (int64_t)blockDim.x * G)
+        counts[t * n_chunks + c] = cnt_s[t];
 }
 
 // Exclusive scan of 1024 values held one per thread; returns the block total.
@@ -1630,7 +1678,7 @@ __global__ void __launch_bounds__(1024) list_scan_chunks_kernel(int32_t *counts,
 // Per list entry, the warp tiles of its CTA tile whose balls the segment can reach.
 // Blocks (g, t) stride over tile t's entries.
 template <int WINDOW>
-__global__ void list_mask_kernel(const float *rec, const float4 *wball, int64_t n_wtiles,
+__global__ void list_mask_kernel(const float4 *crec, const float4 *wball, int64_t n_wtiles,
                                  float alpha, float beta, const int64_t *list_off,
                                  const int32_t *list_n, const int32_t *list, uint16_t *list_mask)
 {
@@ -1645,11 +1693,11 @@ __global__ void list_mask_kernel(const float *rec, const float4 *wball, int64_t 
 #pragma unroll 2
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 *R = reinterpret_cast<const float4 *>(rec + (int64_t)list[off + i] * kRecFloats);
-        const float4 r0 = R[0], r1 = R[1], r2 = R[2];
+        const int64_t jseg = list[off + i];
+        const float4 r0 = crec[2 * jseg], r1 = crec[2 * jseg + 1];
         uint32_t wm = 0u;
         for (int w = 0; w < nw; ++w)
-            if (seg_reaches_ball<WINDOW>(r0, r1, r2, sball[w], alpha, beta)) wm |= 1u << w;
+            if (seg_reaches_ball<WINDOW>(r0, r1, sball[w], alpha, beta)) wm |= 1u << w;
         list_mask[off + i] = (uint16_t)wm;
     }
 }
@@ -1682,7 +1730,7 @@ __global__ void __launch_bounds__(1024) list_layout_kernel(const unsigned int *t
 
 template <int WINDOW>
 __global__ void __launch_bounds__(kListChunk) list_write_kernel(
-    const float *rec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
+    const float4 *crec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
     int64_t n_chunks, float alpha, float beta, const int32_t *chunk_off, const int64_t *list_off,
     const int32_t *list_n, int32_t *list)
 {
@@ -1693,14 +1741,14 @@ __global__ void __launch_bounds__(kListChunk) list_write_kernel(
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t j = c * kListChunk + threadIdx.x;
     const bool ok = j < ns;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
     if (ok) {
-        const float4 *R = reinterpret_cast<const float4 *>(rec + j * kRecFloats);
-        r0 = R[0]; r1 = R[1]; r2 = R[2];
+        r0 = crec[2 * j];
+        r1 = crec[2 * j + 1];
     }
     for (int64_t t = 0; t < n_tiles; ++t) {
         if (list_n[t] < 0) continue;
-        const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, r2, ball[t], alpha, beta);
+        const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, ball[t], alpha, beta);
         const unsigned int m = __ballot_sync(0xffffffffu, pass);
         if (lane == 0) wsum[wid] = __popc(m);
         __syncthreads();
@@ -1726,7 +1774,7 @@ __global__ void __launch_bounds__(kListChunk) list_write_bits_kernel(
     if (c * kListChunk >= ns) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t j = c * kListChunk + threadIdx.x;
-    for (int64_t t = 0; t < n_tiles; ++t) {
+    for (int64_t t = blockIdx.y; t < n_tiles; t += gridDim.y) {     // tile group blockIdx.y
         if (list_n[t] < 0) continue;
         const uint32_t *row = bits + t * n_chunks * 32 + c * 32;
         const uint32_t m = row[wid];
@@ -1741,77 +1789,70 @@ __global__ void __launch_bounds__(kListChunk) list_write_bits_kernel(
 }
 
 // Time synthesis: out[n, r] (+)= Re sum_f ph[n, f] p[f, r], ph[n, f] = A_f exp(-i omega_f t_n).
-// The phasors are formed on the device (synth_phasor_kernel: the phase in turns, f t0 +
-// n (f dt), reduced in FP64 before an FP64 sincospi, then rounded to float2).  The sum:
-// threads over receiver pairs (coalesced), a block row over kSynthTile time samples whose
-// phasors sit in shared memory, each thread holding its receivers' fields in registers.
-// Bound by writing n_t * n_recv floats (streaming stores: the output is not re-read).
-constexpr int kSynthTile = 64;
+// Each block forms the phasors of its kSynthTile samples in shared memory: the phase in
+// turns, f t0 + n (f dt), reduced to [0, 1) in FP64, then sine and cosine of the reduced
+// turn in FP32 (sincospif, about one ulp: the phasors are FP32 numbers either way).
+// Threads run over groups of four adjacent receivers (one 16-byte streaming store per
+// sample), each holding its receivers' fields in registers; NF is the exact frequency
+// count.  Bound by writing n_t * n_recv floats.
+constexpr int kSynthTile = 32;
+constexpr int kSynthRecv = 4;                   // receivers per thread
 
-struct SynthPhasorParams {
+struct SynthParams {
+    const float2 *p;           // [nf][n_recv] fields
+    int64_t n_recv, n_t;
     double freq[GBT_MAX_FREQ], amp_re[GBT_MAX_FREQ], amp_im[GBT_MAX_FREQ];
     double t0, dt;
-    int nf;
-    int64_t n_t;
-    float2 *ph;                // [n_t][nf]
+    float *out;                // [n_t][n_recv]
+    int accumulate;
 };
 
-__global__ void synth_phasor_kernel(const SynthPhasorParams p)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= p.n_t * p.nf) return;
-    const int64_t n = i / p.nf;
-    const int f = (int)(i - n * p.nf);
-    double turns = fma((double)n, p.freq[f] * p.dt, p.freq[f] * p.t0);
-    turns -= floor(turns);
-    double sn, cs;
-    sincospi(2.0 * turns, &sn, &cs);
-    // A (cos - i sin)
-    p.ph[i] = make_float2((float)(p.amp_re[f] * cs + p.amp_im[f] * sn),
-                          (float)(p.amp_im[f] * cs - p.amp_re[f] * sn));
-}
-
-// Each thread owns two adjacent receivers (one 8-byte streaming store per sample) and
-// kSynthTile samples; NF is the exact frequency count, so no padded term costs an FMA.
 template <int NF>
-__global__ void __launch_bounds__(256) synth_kernel(const float2 *__restrict__ p, int64_t n_recv,
-                                                    const float2 *__restrict__ ph, int64_t n_t,
-                                                    float *__restrict__ out, int accumulate)
+__global__ void __launch_bounds__(256) synth_kernel(const SynthParams p)
 {
     __shared__ float2 sph[kSynthTile][NF];
     const int64_t n0 = (int64_t)blockIdx.y * kSynthTile;
     for (int i = threadIdx.x; i < kSynthTile * NF; i += blockDim.x) {
         const int a = i / NF, f = i - a * NF;
-        sph[a][f] = n0 + a < n_t ? ph[(n0 + a) * NF + f] : make_float2(0.f, 0.f);
+        double turns = fma((double)(n0 + a), p.freq[f] * p.dt, p.freq[f] * p.t0);
+        turns -= floor(turns);
+        float sn, cs;
+        sincospif(2.0f * (float)turns, &sn, &cs);
+        // A (cos - i sin)
+        sph[a][f] = make_float2((float)(p.amp_re[f] * cs + p.amp_im[f] * sn),
+                                (float)(p.amp_im[f] * cs - p.amp_re[f] * sn));
     }
     __syncthreads();
-    const int64_t r = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-    if (r >= n_recv) return;
-    const bool pair = r + 1 < n_recv;
-    float2 p0[NF], p1[NF];
+    const int64_t r = kSynthRecv * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if (r >= p.n_recv) return;
+    const int nr = (int)min((int64_t)kSynthRecv, p.n_recv - r);
+    float2 pr[kSynthRecv][NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        p0[f] = p[(int64_t)f * n_recv + r];
-        p1[f] = pair ? p[(int64_t)f * n_recv + r + 1] : make_float2(0.f, 0.f);
-    }
-    const int na = (int)min((int64_t)kSynthTile, n_t - n0);
-    float *o = out + n0 * n_recv + r;
-    // 8-byte stores need an even row length (every row then starts 8-byte aligned)
-    const bool vec = pair && !accumulate && (n_recv & 1) == 0 && ((uintptr_t)out & 7u) == 0;
+    for (int k = 0; k < kSynthRecv; ++k)
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+            pr[k][f] = k < nr ? p.p[(int64_t)f * p.n_recv + r + k] : make_float2(0.f, 0.f);
+    const int na = (int)min((int64_t)kSynthTile, p.n_t - n0);
+    float *o = p.out + n0 * p.n_recv + r;
+    // 16-byte stores need a row length divisible by four (every row then starts aligned)
+    const bool vec = nr == kSynthRecv && !p.accumulate && (p.n_recv & 3) == 0 &&
+                     ((uintptr_t)p.out & 15u) == 0;
     for (int a = 0; a < na; ++a) {
-        float acc0 = 0.f, acc1 = 0.f;
+        float acc[kSynthRecv];
+#pragma unroll
+        for (int k = 0; k < kSynthRecv; ++k) acc[k] = 0.f;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const float2 q = sph[a][f];
-            acc0 = fmaf(q.x, p0[f].x, fmaf(-q.y, p0[f].y, acc0));
-            acc1 = fmaf(q.x, p1[f].x, fmaf(-q.y, p1[f].y, acc1));
+#pragma unroll
+            for (int k = 0; k < kSynthRecv; ++k)
+                acc[k] = fmaf(q.x, pr[k][f].x, fmaf(-q.y, pr[k][f].y, acc[k]));
         }
-        float *row = o + a * n_recv;
+        float *row = o + a * p.n_recv;
         if (vec) {
-            __stcs(reinterpret_cast<float2 *>(row), make_float2(acc0, acc1));
+            __stcs(reinterpret_cast<float4 *>(row), make_float4(acc[0], acc[1], acc[2], acc[3]));
         } else {
-            row[0] = accumulate ? row[0] + acc0 : acc0;
-            if (pair) row[1] = accumulate ? row[1] + acc1 : acc1;
+            for (int k = 0; k < nr; ++k) row[k] = p.accumulate ? row[k] + acc[k] : acc[k];
         }
     }
 }
@@ -2034,6 +2075,14 @@ __global__ void extract_order(const unsigned long long *keys, int64_t n, int32_t
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The 32-byte cull records follow the 80-byte records in a sum's record region.
+float4 *cull_records(const float *rec, int64_t capacity)
+{
+    return reinterpret_cast<float4 *>(
+        reinterpret_cast<char *>(const_cast<float *>(rec)) +
+        align_up((size_t)kRecFloats * (size_t)capacity * sizeof(float), 256));
+}
+
 template <int NF, int WINDOW, int MODE, bool BATCHED = false, bool LOSSY = false>
 void launch_fwd_t(const FwdParams &p, cudaStream_t s, bool timed)
 {
@@ -2123,6 +2172,7 @@ FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum
     q.recv = a.recv; q.order = a.recv_order; q.n_recv = a.n_recv;
     q.n_seg_ptr = td.ray_off + td.n_rays;
     q.rec = rec;
+    q.crec = cull_records(rec, td.capacity);
     q.nf = std::min(kGroupFreq, a.n_freq - g0);
     q.cutoff = (float)a.cutoff;
     q.tile_cull = a.tile_cull ? 1 : 0;
@@ -2273,28 +2323,32 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
     int64_t n = 0;
     tile_ball_kernel<<<(unsigned)T, 256, 0, s>>>(q.recv, q.order, q.n_recv, t.ball, t.weight);
     ++n;
+    // tile groups of the chunk-major list passes (each block walks 1 / tg of the tiles):
+    // one, since more re-read the chunk's records for every group (measured on the city:
+    // 8 groups took list_count 1.77 -> 2.19 ms and list_write_bits 1.58 -> 1.75 ms)
+    const unsigned tg = 1;
     if (t.lists) {
         const size_t sm = (size_t)T * sizeof(int32_t);
         if (window == GBT_WINDOW_LINE) {
             GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_LINE>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            list_count_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, sm, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
+            list_count_kernel<GBT_WINDOW_LINE><<<dim3((unsigned)t.chunks, tg), kListChunk, sm, s>>>(
+                q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
         } else {
             GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_SEGMENT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            list_count_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, sm, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
+            list_count_kernel<GBT_WINDOW_SEGMENT><<<dim3((unsigned)t.chunks, tg), kListChunk, sm, s>>>(
+                q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
         }
         list_scan_chunks_kernel<<<(unsigned)T, 1024, 0, s>>>(t.counts, t.chunks, t.weight);
         n += 2;
     } else {
         if (window == GBT_WINDOW_LINE)
             tile_weight_kernel<GBT_WINDOW_LINE><<<kWeightSamples / 256, 256, 0, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, q.pre_alpha, q.pre_beta, t.weight);
+                q.crec, q.n_seg_ptr, t.ball, T, q.pre_alpha, q.pre_beta, t.weight);
         else
             tile_weight_kernel<GBT_WINDOW_SEGMENT><<<kWeightSamples / 256, 256, 0, s>>>(
-                q.rec, q.n_seg_ptr, t.ball, T, q.pre_alpha, q.pre_beta, t.weight);
+                q.crec, q.n_seg_ptr, t.ball, T, q.pre_alpha, q.pre_beta, t.weight);
         ++n;
     }
     if (t.order) {
@@ -2307,27 +2361,27 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
                                               t.list_off, t.list_n);
         warp_ball_kernel<<<(unsigned)((t.wtiles + 7) / 8), 256, 0, s>>>(q.recv, q.order, q.n_recv,
                                                                          t.wtiles, t.wball);
-        const dim3 mgrid(32, (unsigned)T);
+        const dim3 mgrid(128, (unsigned)T);     // many blocks per tile: the gathers overlap
         if (window == GBT_WINDOW_LINE) {
             if (t.bits)
-                list_write_bits_kernel<<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                list_write_bits_kernel<<<dim3((unsigned)t.chunks, tg), kListChunk, 0, s>>>(
                     q.n_seg_ptr, T, t.chunks, t.bits, t.counts, t.list_off, t.list_n, t.list);
             else
                 list_write_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
-                    q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                    q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                     t.list_off, t.list_n, t.list);
             list_mask_kernel<GBT_WINDOW_LINE><<<mgrid, 256, 0, s>>>(
-                q.rec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
+                q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
         } else {
             if (t.bits)
-                list_write_bits_kernel<<<(unsigned)t.chunks, kListChunk, 0, s>>>(
+                list_write_bits_kernel<<<dim3((unsigned)t.chunks, tg), kListChunk, 0, s>>>(
                     q.n_seg_ptr, T, t.chunks, t.bits, t.counts, t.list_off, t.list_n, t.list);
             else
                 list_write_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
-                    q.rec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                    q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                     t.list_off, t.list_n, t.list);
             list_mask_kernel<GBT_WINDOW_SEGMENT><<<mgrid, 256, 0, s>>>(
-                q.rec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
+                q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
         }
         n += 4;
         q.list = t.list;
@@ -2339,10 +2393,14 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
     note_launches(n);
 }
 
+// Kernel records: the 80-byte records, then the 32-byte cull records of the list and
+// dispatch-order kernels (sector aligned, a fraction of the size, so they stay in L2).
 static size_t records_bytes(const TraceDev &td)
 {
-    return align_up((size_t)kRecFloats * (size_t)td.capacity * sizeof(float), 256);
+    return align_up((size_t)kRecFloats * (size_t)td.capacity * sizeof(float), 256) +
+           align_up((size_t)td.capacity * 2 * sizeof(float4), 256);
 }
+
 
 // Prepass of a trace's segments into kernel records (and FP64 amplitudes when amp64 is
 // set), with the sum's reflection coefficients and ray weights.
@@ -2360,6 +2418,7 @@ static void prepass_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum
     pp.n_fan = td.n_fan;
     pp.n_materials = sd.n_materials;
     pp.rec = rec;
+    pp.crec = cull_records(rec, td.capacity);
     pp.amp64 = amp64;
     pp.status = status_word();
     if (loss) {
@@ -2479,41 +2538,33 @@ void synth_launch(const float *p, int nf, int64_t n_recv, const double *freq_hz,
                   int accumulate, cudaStream_t s)
 {
     if (n_recv <= 0 || n_t <= 0) return;
-    SynthPhasorParams pp{};
+    SynthParams sp{};
+    sp.p = reinterpret_cast<const float2 *>(p);
+    sp.n_recv = n_recv;
+    sp.n_t = n_t;
     for (int f = 0; f < nf; ++f) {
-        pp.freq[f] = freq_hz[f];
-        pp.amp_re[f] = amp[2 * f];
-        pp.amp_im[f] = amp[2 * f + 1];
+        sp.freq[f] = freq_hz[f];
+        sp.amp_re[f] = amp[2 * f];
+        sp.amp_im[f] = amp[2 * f + 1];
     }
-    pp.t0 = t0;
-    pp.dt = dt;
-    pp.nf = nf;
-    pp.n_t = n_t;
-    // stream-ordered scratch for the phasor table: no host synchronisation
-    const size_t bytes = (size_t)n_t * nf * sizeof(float2);
-    pp.ph = static_cast<float2 *>(dalloc(bytes, s));
-    try {
-        const int64_t m = n_t * nf;
-        synth_phasor_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pp);
-        const dim3 grid((unsigned)((n_recv + 511) / 512),
-                        (unsigned)((n_t + kSynthTile - 1) / kSynthTile));
-        const float2 *fp = reinterpret_cast<const float2 *>(p);
-        switch (nf) {
+    sp.t0 = t0;
+    sp.dt = dt;
+    sp.out = out;
+    sp.accumulate = accumulate;
+    const int64_t per_block = 256 * kSynthRecv;
+    const dim3 grid((unsigned)((n_recv + per_block - 1) / per_block),
+                    (unsigned)((n_t + kSynthTile - 1) / kSynthTile));
+    switch (nf) {
 #define GBT_SYNTH(NFV) \
-        case NFV: synth_kernel<NFV><<<grid, 256, 0, s>>>(fp, n_recv, pp.ph, n_t, out, accumulate); break;
-            GBT_SYNTH(1) GBT_SYNTH(2) GBT_SYNTH(3) GBT_SYNTH(4) GBT_SYNTH(5) GBT_SYNTH(6)
-            GBT_SYNTH(7) GBT_SYNTH(8) GBT_SYNTH(9) GBT_SYNTH(10) GBT_SYNTH(11) GBT_SYNTH(12)
-            GBT_SYNTH(13) GBT_SYNTH(14) GBT_SYNTH(15) GBT_SYNTH(16)
+    case NFV: synth_kernel<NFV><<<grid, 256, 0, s>>>(sp); break;
+        GBT_SYNTH(1) GBT_SYNTH(2) GBT_SYNTH(3) GBT_SYNTH(4) GBT_SYNTH(5) GBT_SYNTH(6)
+        GBT_SYNTH(7) GBT_SYNTH(8) GBT_SYNTH(9) GBT_SYNTH(10) GBT_SYNTH(11) GBT_SYNTH(12)
+        GBT_SYNTH(13) GBT_SYNTH(14) GBT_SYNTH(15) GBT_SYNTH(16)
 #undef GBT_SYNTH
-        default: fail(GBT_ERR_INVALID_ARG, "synthesis takes 1 .. 16 frequencies");
-        }
-        note_launches(2);
-        GBT_CUDA(cudaGetLastError());
-    } catch (...) {
-        dfree(pp.ph, s);
-        throw;
+    default: fail(GBT_ERR_INVALID_ARG, "synthesis takes 1 .. 16 frequencies");
     }
-    dfree(pp.ph, s);
+    note_launches(1);
+    GBT_CUDA(cudaGetLastError());
 }
 
 size_t recv_order_scratch_bytes(int64_t n)
