@@ -1289,7 +1289,11 @@ struct F64Params {
     int64_t r64_stride;
 };
 
-template <int WINDOW>
+// Every step in FP64.  The cull k n^2 b / (2 D) <= C is tested as k b n^2 <= 2 C D
+// (no division), first for the union over the frequencies (the smallest k b against the
+// largest b^2) so that a pair every frequency culls costs no per-frequency work; the
+// accumulators of NF frequency slots stay in registers.
+template <int WINDOW, int NF>
 __global__ void __launch_bounds__(kThreads64) gbs_fwd_f64_kernel(const F64Params p)
 {
     __shared__ double so[kTS64][3], stt[kTS64][3], sL[kTS64], s0s[kTS64], sa[kTS64];
@@ -1303,8 +1307,19 @@ __global__ void __launch_bounds__(kThreads64) gbs_fwd_f64_kernel(const F64Params
     const double x = valid ? (double)p.recv[3 * ri] : 0.0;
     const double y = valid ? (double)p.recv[3 * ri + 1] : 0.0;
     const double z = valid ? (double)p.recv[3 * ri + 2] : 0.0;
-    double sr[GBT_MAX_FREQ], cr[GBT_MAX_FREQ], si[GBT_MAX_FREQ], ci[GBT_MAX_FREQ];
-    for (int f = 0; f < GBT_MAX_FREQ; ++f) sr[f] = cr[f] = si[f] = ci[f] = 0.0;
+    double kb[NF], b2[NF];
+    double kbmin = 1e300, b2max = 0.0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        kb[f] = f < p.nf ? p.k[f] * p.b[f] : 1e300;
+        b2[f] = f < p.nf ? p.b[f] * p.b[f] : 0.0;
+        kbmin = fmin(kbmin, kb[f]);
+        b2max = fmax(b2max, b2[f]);
+    }
+    const double c2 = 2.0 * p.cutoff;
+    double sr[NF], cr[NF], si[NF], ci[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sr[f] = cr[f] = si[f] = ci[f] = 0.0;
     for (int64_t t0 = seg_begin; t0 < seg_end; t0 += kTS64) {
         __syncthreads();
         for (int q = threadIdx.x; q < kTS64; q += kThreads64) {
@@ -1330,14 +1345,21 @@ __global__ void __launch_bounds__(kThreads64) gbs_fwd_f64_kernel(const F64Params
             }
             const double cx = dy * tz - dz * ty, cy = dz * tx - dx * tz, cz = dx * ty - dy * tx;
             const double n2 = cx * cx + cy * cy + cz * cz;
-            for (int f = 0; f < p.nf; ++f) {
+            const double ss = s * s;
+            // union over the frequencies: culled for every f (with a relative margin far
+            // above FP64 rounding, so no pair a frequency keeps is skipped)
+            if (kbmin * n2 > c2 * (ss + b2max) * (1.0 + 1e-12)) continue;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (f >= p.nf) break;
                 const double k = p.k[f], b = p.b[f];
-                const double D = s * s + b * b;
-                if (k * n2 * b / (2.0 * D) > p.cutoff) continue;
+                const double D = ss + b2[f];
+                if (kb[f] * n2 > c2 * D) continue;
                 // c = amp * (k b / 8 pi^2) / E * exp(i k s + i k n^2 / (2E)), E = s - i b
-                const double re_exp = -k * n2 * b / (2.0 * D) - p.absorb[f] * s;
-                const double ph = k * s + k * n2 * s / (2.0 * D);
-                const double a = sa[q] * (k * b / (8.0 * kPi * kPi)) * exp(re_exp) / D;
+                const double invD = 1.0 / D;
+                const double re_exp = -0.5 * kb[f] * n2 * invD - p.absorb[f] * s;
+                const double ph = k * s + 0.5 * k * n2 * s * invD;
+                const double a = sa[q] * (kb[f] / (8.0 * kPi * kPi)) * exp(re_exp) * invD;
                 double sn, cs;
                 sincos(ph, &sn, &cs);
                 double vr = a * (s * cs - b * sn), vi = a * (s * sn + b * cs);
@@ -1358,9 +1380,21 @@ __global__ void __launch_bounds__(kThreads64) gbs_fwd_f64_kernel(const F64Params
         }
     }
     if (!valid) return;
-    for (int f = 0; f < p.nf; ++f)
-        p.partial[((int64_t)split * p.nf + f) * p.n_recv + ri] =
-            make_double2(sr[f] + cr[f], si[f] + ci[f]);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (f < p.nf)
+            p.partial[((int64_t)split * p.nf + f) * p.n_recv + ri] =
+                make_double2(sr[f] + cr[f], si[f] + ci[f]);
+}
+
+template <int WINDOW>
+void launch_f64(const F64Params &q, dim3 grid, cudaStream_t s)
+{
+    if (q.nf <= 1) gbs_fwd_f64_kernel<WINDOW, 1><<<grid, kThreads64, 0, s>>>(q);
+    else if (q.nf <= 2) gbs_fwd_f64_kernel<WINDOW, 2><<<grid, kThreads64, 0, s>>>(q);
+    else if (q.nf <= 4) gbs_fwd_f64_kernel<WINDOW, 4><<<grid, kThreads64, 0, s>>>(q);
+    else if (q.nf <= 8) gbs_fwd_f64_kernel<WINDOW, 8><<<grid, kThreads64, 0, s>>>(q);
+    else gbs_fwd_f64_kernel<WINDOW, GBT_MAX_FREQ><<<grid, kThreads64, 0, s>>>(q);
 }
 
 // ------------------------------------------------------------ adjoint --
@@ -2499,10 +2533,8 @@ void sum_launch(const TraceDev &td, const SceneDev &sd, const gbt_sum_args &a, i
         q.r64 = static_cast<const double2 *>(loss);
         q.r64_stride = td.capacity;
         dim3 grid((unsigned)((a.n_recv + kThreads64 - 1) / kThreads64), (unsigned)splits);
-        if (a.window == GBT_WINDOW_LINE)
-            gbs_fwd_f64_kernel<GBT_WINDOW_LINE><<<grid, kThreads64, 0, s>>>(q);
-        else
-            gbs_fwd_f64_kernel<GBT_WINDOW_SEGMENT><<<grid, kThreads64, 0, s>>>(q);
+        if (a.window == GBT_WINDOW_LINE) launch_f64<GBT_WINDOW_LINE>(q, grid, s);
+        else launch_f64<GBT_WINDOW_SEGMENT>(q, grid, s);
         note_launches(1);
         GBT_CUDA(cudaGetLastError());
         rp.n = (int64_t)a.n_freq * a.n_recv;
