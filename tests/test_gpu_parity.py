@@ -722,18 +722,21 @@ def test_chunked_accumulating_solve_with_twelve_frequencies(G):
         assert rel_l2(got[f].astype(np.complex128), one[f].astype(np.complex128)) < 1e-5, f
 
 
-@pytest.mark.parametrize("nf,n_t", [(1, 1), (12, 777), (16, 64)])
-def test_synthesis_against_oracle(G, nf, n_t):
-    """Time synthesis on the GPU (FP64 phasors, FP32 sums) against the oracle's FP64
-    definition, sample by sample: |error| <= 2e-6 of the summed magnitudes of the terms
-    (a ragged last time tile, one and sixteen frequencies), and added into `out`."""
+@pytest.mark.parametrize("nf,n_t,nr,t0", [(1, 1, 1000, 0.0123), (12, 777, 1003, 0.0123),
+                                          (16, 64, 2, 0.0123), (5, 100, 4097, 1234.5),
+                                          (6, 33, 4096, 0.0123)])
+def test_synthesis_against_oracle(G, nf, n_t, nr, t0):
+    """Time synthesis on the GPU (phasors from FP64-reduced turns, FP32 sums) against the
+    oracle's FP64 definition, sample by sample: |error| <= 2e-6 of the summed magnitudes of
+    the terms (ragged time tiles, one to sixteen frequencies, receiver counts that are not
+    multiples of the four a thread writes, a start time of 1234.5 s whose phases reach
+    5e6 turns), and added into `out`."""
     import torch
     rng = np.random.default_rng(nf)
-    nr = 1000
     p = (rng.normal(size=(nf, nr)) + 1j * rng.normal(size=(nf, nr))).astype(np.complex64)
     freqs = rng.uniform(100.0, 4000.0, nf)
     amp = rng.normal(size=nf) + 1j * rng.normal(size=nf)
-    t0, dt = 0.0123, 2.3e-5
+    dt = 2.3e-5
     h = G.synthesize(_dev(p), list(freqs), list(amp), t0, dt, n_t)
     torch.cuda.synchronize()
     ho = O.synthesize(p.astype(np.complex128), freqs, amp, t0, dt, n_t)
