@@ -60,6 +60,12 @@ constexpr long long kSpinLimit = 1LL << 22; // bounded mbarrier waits
 enum { kFwd = 0, kStats = 1, kBwd = 2 };    // what the pair kernel does with survivors
 constexpr int kFoldEvery = 16;              // batches between float-float folds
 constexpr float kWinMargin = 0.01f;         // prefilter window slack (m)
+// A warp item takes the FP32 local projection x'.t (instead of float-float) when
+// K_max max|x'| <= kFastTurns.  Its rounding, at most about 3 ulp of |x'|, moves a term's
+// phase by at most 3 x 2^-24 x 90 turns = 1.0e-4 rad; the roundings of different terms are
+// independent, so the field moves far less (2e-7 relative on the city, 3.5e-5 with the
+// projection in FP32 everywhere at 4 kHz).  Past the limit the float-float product stays.
+constexpr float kFastTurns = 90.0f;
 
 // Per-frequency constants, grouped in 16-byte words in the order the survivor
 // path needs them (cutoff test, then the beam), so a kernel that reads them from
@@ -90,6 +96,7 @@ struct alignas(16) FwdParams {
     int tile_cull;             // skip segments that reach none of a warp's receivers
     float cutoff;
     float pre_alpha, pre_beta; // prefilter: keep iff alpha n^2 <= s^2 + beta
+    float kmax_turns;          // largest f / c of the launch's frequencies, turns per metre
     int splits;
     int64_t n_items;           // CTA tiles x splits
     int *work_counter;         // zeroed before launch; CTAs take items from it
@@ -407,21 +414,28 @@ template <int NF, int WINDOW, bool LOSSY>
 __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH, f2x ZH,
                                               f2x XL, f2x YL, f2x ZL, const StageSmem &w,
                                               const LossSmem<NF> *loss, int j0, int j1, bool h0,
-                                              bool h1, f2x (&accx)[NF], f2x (&accy)[NF])
+                                              bool h1, bool fast, f2x (&accx)[NF], f2x (&accy)[NF])
 {
     const float4 A0 = w.A[j0], A1 = w.A[j1], T0 = w.T[j0], T1 = w.T[j1];
     const float4 N0 = w.N[j0], N1 = w.N[j1];
     const f2x THX = pk(A0.x, A1.x), THY = pk(A0.y, A1.y), THZ = pk(A0.z, A1.z);
     const f2x TLX = pk(T0.x, T1.x), TLY = pk(T0.y, T1.y), TLZ = pk(T0.z, T1.z);
-    // u = x'.t as (U + ul)
-    const f2x p0 = mul2(XH, THX), p1 = mul2(YH, THY), p2 = mul2(ZH, THZ);
-    const f2x r0 = fma2(XH, TLX, fma2(XL, THX, fma2(XH, THX, neg2(p0))));
-    const f2x r1 = fma2(YH, TLY, fma2(YL, THY, fma2(YH, THY, neg2(p1))));
-    const f2x r2 = fma2(ZH, TLZ, fma2(ZL, THZ, fma2(ZH, THZ, neg2(p2))));
-    f2x S1, E1, U, E2;
-    two_sum2(p0, p1, S1, E1);
-    two_sum2(S1, p2, U, E2);
-    const f2x ul = add2(add2(E1, E2), add2(add2(r0, r1), r2));
+    // u = x'.t as (U + ul): float-float, or (warp-uniform `fast`, compact warps at low
+    // enough frequencies) the FP32 products with the lo parts' first-order terms
+    f2x U, ul;
+    if (fast) {
+        U = fma2(XH, THX, fma2(YH, THY, mul2(ZH, THZ)));
+        ul = fma2(XL, THX, fma2(YL, THY, fma2(ZL, THZ, fma2(XH, TLX, fma2(YH, TLY, mul2(ZH, TLZ))))));
+    } else {
+        const f2x p0 = mul2(XH, THX), p1 = mul2(YH, THY), p2 = mul2(ZH, THZ);
+        const f2x r0 = fma2(XH, TLX, fma2(XL, THX, fma2(XH, THX, neg2(p0))));
+        const f2x r1 = fma2(YH, TLY, fma2(YL, THY, fma2(YH, THY, neg2(p1))));
+        const f2x r2 = fma2(ZH, TLZ, fma2(ZL, THZ, fma2(ZH, THZ, neg2(p2))));
+        f2x S1, E1, E2;
+        two_sum2(p0, p1, S1, E1);
+        two_sum2(S1, p2, U, E2);
+        ul = add2(add2(E1, E2), add2(add2(r0, r1), r2));
+    }
     bool k0 = h0, k1 = h1;
     float u0, u1;
     if (WINDOW == GBT_WINDOW_SEGMENT) {
@@ -847,6 +861,11 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
             sphere = make_float4(sx, sy, sz, sqrtf(r2));
         }
+        // the FP32 local projection when the warp is compact enough for its frequencies
+        float xmax2 = fmaxf((valid & 1u) ? xx[0] : 0.f, (valid & 2u) ? xx[1] : 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) xmax2 = fmaxf(xmax2, __shfl_xor_sync(0xffffffffu, xmax2, o));
+        const bool fast_u = sqrtf(xmax2) * p.kmax_turns <= kFastTurns;
         static_assert(kR == 2, "the paired prefilter handles two receivers per lane");
         const f2x X2 = pk(xp[0], xp[1]), Y2 = pk(yp[0], yp[1]), Z2 = pk(zp[0], zp[1]);
         const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
@@ -1067,7 +1086,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     if (!h0) j0 = j1;
                     if (!h1) j1 = j0;
                     survivor_pair<NF, WINDOW, LOSSY>(p, X2, Y2, Z2, XL2, YL2, ZL2, w, loss, j0, j1, h0,
-                                                     h1, accx, accy);
+                                                     h1, fast_u, accx, accy);
                 }
             } else if (MODE == kBwd) {
                 // segment by segment: the lanes holding a survivor of segment jj add their
@@ -2212,7 +2231,7 @@ FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum
     q.tile_cull = a.tile_cull ? 1 : 0;
     int perm[GBT_MAX_FREQ];
     q.uniform_b = freq_order(a, perm) ? 1 : 0;
-    double amin = 1e300, bmax = 0.0;
+    double amin = 1e300, bmax = 0.0, kmax = 0.0;
     for (int f = 0; f < GBT_MAX_FREQ; ++f) q.fperm[f] = f;
     for (int f = 0; f < q.nf; ++f) {
         const int g = perm[g0 + f];
@@ -2234,7 +2253,9 @@ FwdParams make_pair_params(const TraceDev &td, const SceneDev &sd, const gbt_sum
         c.al2e = (float)(a.absorption[g] * 1.4426950408889634);
         amin = std::min(amin, 0.5 * k * b);
         bmax = std::max(bmax, b * b);
+        kmax = std::max(kmax, K);
     }
+    q.kmax_turns = (float)kmax;
     q.pre_alpha = (float)(amin / (a.cutoff + 1.0));
     q.pre_beta = (float)bmax;
     q.status = status_word();

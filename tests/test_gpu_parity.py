@@ -508,10 +508,13 @@ def test_more_than_eight_frequencies_against_oracle(G, nf, uniform_b, tile_cull)
     assert st["triples_kept"] == per_f
     kept_o = O.count_kept(otr, w.receivers, freqs, b, w.scene.c, window=w.window, cutoff=w.cutoff)
     assert abs(st["triples_kept"] - kept_o) <= 1e-5 * kept_o
+    # alone, a frequency may take the other local-projection path (FP32 or float-float is
+    # chosen per warp from the launch's highest frequency), so the two agree to the FP32
+    # path's error budget rather than to rounding
     for f in (0, nf // 2, nf - 1):
         one = G.gbs_sum(tr, r, [freqs[f]], [b[f]], gam, order=o, window=w.window,
                         cutoff=w.cutoff, tile_cull=tile_cull).cpu().numpy()
-        assert rel_l2(p[f], one[0].astype(np.complex128)) < 1e-6, f
+        assert rel_l2(p[f], one[0].astype(np.complex128)) < 1e-5, f
 
 
 def _latlong_city_source(nt=64, nph=128, th=(0.0, 180.0), ph=(0.0, 360.0)):
