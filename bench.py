@@ -56,14 +56,14 @@ LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
 # a changed kernel gets a new revision and no entry until it is captured again.
 KERNEL_REV = "r2.3"
 KERNEL_TRAFFIC = {
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.2]",
-     "city_1M_rays_512x512_1kHz"): 6009001984,
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [r2.2]",
-     "city_1M_rays_512x512_1kHz"): 205102972416,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [r2.2]",
-     "open_plane_64k_rays_256x256_6f"): 467837696,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [r2.2]",
-     "open_plane_64k_rays_256x256_6f"): 193765632,
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.3]",
+     "city_1M_rays_512x512_1kHz"): 5774792448,
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [r2.3]",
+     "city_1M_rays_512x512_1kHz"): 225006282752,
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [r2.3]",
+     "open_plane_64k_rays_256x256_6f"): 468365312,
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [r2.3]",
+     "open_plane_64k_rays_256x256_6f"): 195000576,
 }
 WORKLOADS = ("city", "open_plane_large", "open_plane_small", "diff_city", "big_city")
 
