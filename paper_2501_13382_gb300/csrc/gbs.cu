@@ -49,7 +49,7 @@ namespace gbt {
 namespace {
 
 constexpr int kWarpsFwd = 16;               // warps per CTA of the pair kernel (one CTA per SM)
-constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory of one pair-kernel CTA
+constexpr size_t kSmemBudget = 227 * 1024;  // dynamic shared memory of one pair-kernel CTA (the maximum)
 constexpr int kWRaw = 2;                    // raw record buffers per warp (double buffering)
 constexpr int kR = 2;                       // receivers per lane
 constexpr int kWarpRecv = 32 * kR;          // receivers per warp tile
@@ -282,15 +282,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // at x = c + x' the pair needs only x'.t and x' x t:
 //   s_loc = A + x'.t,  s = S + x'.t,  n = N + x' x t.
 struct StageSmem {
-    float4 A[kBatch];               // t_hi.x, t_hi.y, t_hi.z, S_hi
     float4 O[kBatch];               // o' = o - c, s0_hi (per-warp ball test)
-    // prefilter constants, each duplicated into both halves of a float pair:
-    // P[0..3] = t_x, t_y, t_z, -o'.t;  P[4..7] = 2a o'_x, 2a o'_y, 2a o'_z, beta - a |o'|^2;
-    // P[8] = s0 + margin, P[9] = L + margin
-    float4 P[kBatch][5];
-    float4 T[kBatch];               // t_lo.x, t_lo.y, t_lo.z, S_lo
-    float4 N[kBatch];               // N.x, N.y, N.z, W Gamma_path
-    float4 W[kBatch];               // A_hi, A_lo, AL_hi, AL_lo
+    // prefilter constants, each duplicated into both halves of a float pair (t_x and t_y
+    // are D[0] below): P[0] = t_z, -o'.t;  P[1..2] = 2a o'_x, 2a o'_y, 2a o'_z,
+    // beta - a |o'|^2;  P[3] = s0 + margin, L + margin
+    float4 P[kBatch][4];
+    // exact-path view, two values per word, each duplicated into both halves of a float
+    // pair (a lane evaluating one segment for its two receivers loads its operands as
+    // pairs); component-major, so lanes loading different segments hit different banks:
+    // D[0] t_hi.x, t_hi.y | D[1] t_hi.z, S_hi | D[2] t_lo.x, t_lo.y | D[3] t_lo.z, S_lo
+    // D[4] N.x, N.y | D[5] N.z, W Gamma_path | D[6] A_hi, A_lo | D[7] AL_hi, AL_lo
+    float4 D[8][kBatch];
     int32_t seg[kBatch];            // global segment index of each staged record
 };
 
@@ -303,26 +305,36 @@ struct LossSmem {
 
 // Exact geometry of one (receiver, segment) pair in the warp tile's frame, in
 // float-float: x' = (xh + xl) exactly; returns false when the pair falls outside
-// the window.  The paired twin in survivor_pair rounds each half identically.
+// the window.  `fast`: the warp item's choice of the FP32 local projection.  The
+// paired twin in survivor_pair rounds each half identically.
 template <int WINDOW>
 __device__ __forceinline__ bool frame_geometry(float xh, float yh, float zh, float xl, float yl,
-                                               float zl, const StageSmem &w, int j, float &sh,
-                                               float &sl, float &n2)
+                                               float zl, const StageSmem &w, int j, bool fast,
+                                               float &sh, float &sl, float &n2)
 {
-    const float4 T = w.A[j], TL = w.T[j], NN = w.N[j];
+    const float4 d0 = w.D[0][j], d1 = w.D[1][j], d2 = w.D[2][j], d3 = w.D[3][j];
+    const float4 d4 = w.D[4][j], d5 = w.D[5][j];
+    const float4 T = make_float4(d0.x, d0.z, d1.x, d1.z), TL = make_float4(d2.x, d2.z, d3.x, d3.z);
+    const float4 NN = make_float4(d4.x, d4.z, d5.x, d5.z);
     // u = x'.t as (U + ul)
-    const float p0 = __fmul_rn(xh, T.x), p1 = __fmul_rn(yh, T.y), p2 = __fmul_rn(zh, T.z);
-    const float r0 = fmaf(xh, TL.x, fmaf(xl, T.x, fmaf(xh, T.x, -p0)));
-    const float r1 = fmaf(yh, TL.y, fmaf(yl, T.y, fmaf(yh, T.y, -p1)));
-    const float r2 = fmaf(zh, TL.z, fmaf(zl, T.z, fmaf(zh, T.z, -p2)));
-    float S1, E1, U, E2;
-    two_sum(p0, p1, S1, E1);
-    two_sum(S1, p2, U, E2);
-    const float ul = __fadd_rn(__fadd_rn(E1, E2), __fadd_rn(__fadd_rn(r0, r1), r2));
+    float U, ul;
+    if (fast) {
+        U = fmaf(xh, T.x, fmaf(yh, T.y, __fmul_rn(zh, T.z)));
+        ul = fmaf(xl, T.x, fmaf(yl, T.y, fmaf(zl, T.z, fmaf(xh, TL.x, fmaf(yh, TL.y, __fmul_rn(zh, TL.z))))));
+    } else {
+        const float p0 = __fmul_rn(xh, T.x), p1 = __fmul_rn(yh, T.y), p2 = __fmul_rn(zh, T.z);
+        const float r0 = fmaf(xh, TL.x, fmaf(xl, T.x, fmaf(xh, T.x, -p0)));
+        const float r1 = fmaf(yh, TL.y, fmaf(yl, T.y, fmaf(yh, T.y, -p1)));
+        const float r2 = fmaf(zh, TL.z, fmaf(zl, T.z, fmaf(zh, T.z, -p2)));
+        float S1, E1, E2;
+        two_sum(p0, p1, S1, E1);
+        two_sum(S1, p2, U, E2);
+        ul = __fadd_rn(__fadd_rn(E1, E2), __fadd_rn(__fadd_rn(r0, r1), r2));
+    }
     if (WINDOW == GBT_WINDOW_SEGMENT) {
-        const float4 AW = w.W[j];
-        if (!(__fadd_rn(__fadd_rn(AW.x, U), __fadd_rn(AW.y, ul)) >= 0.0f)) return false;
-        if (!(__fadd_rn(__fadd_rn(AW.z, U), __fadd_rn(AW.w, ul)) < 0.0f)) return false;
+        const float4 d6 = w.D[6][j], d7 = w.D[7][j];
+        if (!(__fadd_rn(__fadd_rn(d6.x, U), __fadd_rn(d6.z, ul)) >= 0.0f)) return false;
+        if (!(__fadd_rn(__fadd_rn(d7.x, U), __fadd_rn(d7.z, ul)) < 0.0f)) return false;
     }
     float e3;
     two_sum(T.w, U, sh, e3);
@@ -379,10 +391,10 @@ __device__ __forceinline__ void beam_adjoint(const FreqConst &q, float sh, float
 template <int NF, int WINDOW>
 __device__ __forceinline__ void survivor_count(const FwdParams &p, float xh, float yh, float zh,
                                                float xl, float yl, float zl, const StageSmem &w,
-                                               int j, uint32_t &kept)
+                                               int j, bool fast, uint32_t &kept)
 {
     float sh, sl, n2;
-    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, sh, sl, n2)) return;
+    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, fast, sh, sl, n2)) return;
     if (p.uniform_b) {
         const float D = fmaf(sh, sh, p.fc[0].b2);
         const float r = n2 * rcp_approx(D);
@@ -410,16 +422,33 @@ __device__ __forceinline__ void survivor_count(const FwdParams &p, float xh, flo
 // the phase reduced in turns and the 1/E factor), so each half rounds as that
 // evaluation would; only the MUFU operations run per half.  accx / accy
 // hold the two receivers' real / imaginary sums per sorted frequency.
-template <int NF, int WINDOW, bool LOSSY>
+// Two staged words of segments j0 (lo half) and j1 (hi half) as float pairs; with one
+// segment for both halves (SAME) the duplicated word is the pair itself.
+template <bool SAME>
+__device__ __forceinline__ void ld_pairs(const float4 &a, const float4 &b, f2x &u, f2x &v)
+{
+    if (SAME) {
+        const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(&a);
+        u = q.x;
+        v = q.y;
+    } else {
+        const float4 qa = a, qb = b;
+        u = pk(qa.x, qb.x);
+        v = pk(qa.z, qb.z);
+    }
+}
+
+template <int NF, int WINDOW, bool LOSSY, bool SAME = false>
 __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH, f2x ZH,
                                               f2x XL, f2x YL, f2x ZL, const StageSmem &w,
                                               const LossSmem<NF> *loss, int j0, int j1, bool h0,
                                               bool h1, bool fast, f2x (&accx)[NF], f2x (&accy)[NF])
 {
-    const float4 A0 = w.A[j0], A1 = w.A[j1], T0 = w.T[j0], T1 = w.T[j1];
-    const float4 N0 = w.N[j0], N1 = w.N[j1];
-    const f2x THX = pk(A0.x, A1.x), THY = pk(A0.y, A1.y), THZ = pk(A0.z, A1.z);
-    const f2x TLX = pk(T0.x, T1.x), TLY = pk(T0.y, T1.y), TLZ = pk(T0.z, T1.z);
+    f2x THX, THY, THZ, SH, TLX, TLY, TLZ, SL, NX0, NY0, NZ0, AMP;
+    ld_pairs<SAME>(w.D[0][j0], w.D[0][j1], THX, THY);
+    ld_pairs<SAME>(w.D[1][j0], w.D[1][j1], THZ, SH);
+    ld_pairs<SAME>(w.D[2][j0], w.D[2][j1], TLX, TLY);
+    ld_pairs<SAME>(w.D[3][j0], w.D[3][j1], TLZ, SL);
     // u = x'.t as (U + ul): float-float, or (warp-uniform `fast`, compact warps at low
     // enough frequencies) the FP32 products with the lo parts' first-order terms
     f2x U, ul;
@@ -439,32 +468,36 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
     bool k0 = h0, k1 = h1;
     float u0, u1;
     if (WINDOW == GBT_WINDOW_SEGMENT) {
-        const float4 W0 = w.W[j0], W1 = w.W[j1];
-        upk(add2(add2(pk(W0.x, W1.x), U), add2(pk(W0.y, W1.y), ul)), u0, u1);
+        f2x AH, AL, BH, BL;
+        ld_pairs<SAME>(w.D[6][j0], w.D[6][j1], AH, AL);
+        ld_pairs<SAME>(w.D[7][j0], w.D[7][j1], BH, BL);
+        upk(add2(add2(AH, U), add2(AL, ul)), u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
-        upk(add2(add2(pk(W0.z, W1.z), U), add2(pk(W0.w, W1.w), ul)), u0, u1);
+        upk(add2(add2(BH, U), add2(BL, ul)), u0, u1);
         k0 = k0 && u0 < 0.0f;
         k1 = k1 && u1 < 0.0f;
     }
     f2x sh, e3;
-    two_sum2(pk(A0.w, A1.w), U, sh, e3);
-    const f2x sl = add2(e3, add2(ul, pk(T0.w, T1.w)));
+    two_sum2(SH, U, sh, e3);
+    const f2x sl = add2(e3, add2(ul, SL));
     if (WINDOW == GBT_WINDOW_LINE) {
         upk(add2(sh, sl), u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
     }
     if (!(k0 || k1)) return;
+    ld_pairs<SAME>(w.D[4][j0], w.D[4][j1], NX0, NY0);
+    ld_pairs<SAME>(w.D[5][j0], w.D[5][j1], NZ0, AMP);
     // n = N + x' x t
     const f2x cx = fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, TLZ, mul2(neg2(ZH), TLY))));
     const f2x cy = fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, TLX, mul2(neg2(XH), TLZ))));
     const f2x cz = fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, TLY, mul2(neg2(YH), TLX))));
-    const f2x nx = fma2(YH, THZ, fma2(neg2(ZH), THY, add2(pk(N0.x, N1.x), cx)));
-    const f2x ny = fma2(ZH, THX, fma2(neg2(XH), THZ, add2(pk(N0.y, N1.y), cy)));
-    const f2x nz = fma2(XH, THY, fma2(neg2(YH), THX, add2(pk(N0.z, N1.z), cz)));
+    const f2x nx = fma2(YH, THZ, fma2(neg2(ZH), THY, add2(NX0, cx)));
+    const f2x ny = fma2(ZH, THX, fma2(neg2(XH), THZ, add2(NY0, cy)));
+    const f2x nz = fma2(XH, THY, fma2(neg2(YH), THX, add2(NZ0, cz)));
     const f2x n2 = fma2(nx, nx, fma2(ny, ny, mul2(nz, nz)));
-    const f2x amp = pk(N0.w, N1.w);
+    const f2x amp = AMP;
     float n20, n21;
     upk(n2, n20, n21);
 
@@ -537,11 +570,11 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
 template <int NF, int WINDOW, bool LOSSY>
 __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float xh, float yh, float zh,
                                                  float xl, float yl, float zl, const StageSmem &w,
-                                                 const LossSmem<NF> *loss, int j, const float2 *gk,
-                                                 float &G, float (&H)[NF])
+                                                 const LossSmem<NF> *loss, int j, bool fast,
+                                                 const float2 *gk, float &G, float (&H)[NF])
 {
     float sh, sl, n2;
-    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, sh, sl, n2)) return;
+    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, fast, sh, sl, n2)) return;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
@@ -604,6 +637,9 @@ __device__ __forceinline__ bool ball_may_keep(const float4 &r0, const float4 &r1
     return win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
 }
 
+// Two values, each duplicated into both halves of a float pair.
+__device__ __forceinline__ float4 dup2(float a, float b) { return make_float4(a, a, b, b); }
+
 // Stage lane's raw record for the warp: the prefilter view relative to the frame
 // c = (cx, cy, cz) (the warp tile's first receiver), the origin in that frame for the
 // per-warp ball test and the direction.  A record past the segment count becomes one no
@@ -621,21 +657,19 @@ __device__ __forceinline__ float stage_batch(StageSmem &w, const float4 (&raw)[k
         const float ot = fmaf(ox, r1.x, fmaf(oy, r1.y, oz * r1.z));
         const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
         const float a2 = 2.f * alpha;
-        P[0] = make_float4(r1.x, r1.x, r1.y, r1.y);
-        P[1] = make_float4(r1.z, r1.z, -ot, -ot);
-        P[2] = make_float4(a2 * ox, a2 * ox, a2 * oy, a2 * oy);
-        const float c7 = fmaf(-alpha, oo, beta);
-        P[3] = make_float4(a2 * oz, a2 * oz, c7, c7);
-        const float s0m = r0.w + kWinMargin, Lm = r1.w + kWinMargin;
-        P[4] = make_float4(s0m, s0m, Lm, Lm);
+        w.D[0][lane] = dup2(r1.x, r1.y);
+        P[0] = dup2(r1.z, -ot);
+        P[1] = dup2(a2 * ox, a2 * oy);
+        P[2] = dup2(a2 * oz, fmaf(-alpha, oo, beta));
+        P[3] = dup2(r0.w + kWinMargin, r1.w + kWinMargin);
     } else {
         // far behind its own start
         w.O[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[1] = make_float4(0.f, 0.f, -1e15f, -1e15f);
-        P[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-        P[4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        w.D[0][lane] = dup2(0.f, 0.f);
+        P[0] = dup2(0.f, -1e15f);
+        P[1] = dup2(0.f, 0.f);
+        P[2] = dup2(0.f, 0.f);
+        P[3] = dup2(0.f, 0.f);
     }
     return valid ? r1.w : 0.f;
 }
@@ -676,15 +710,21 @@ __device__ __forceinline__ void stage_exact(StageSmem &w, const float4 (&raw)[kR
                          fmaf(dzh, r3.x, fmaf(-dxh, r3.z, fmaf(dzl, r1.x, -dxl * r1.z)));
         const float nz = dop(dxh, r1.y, dyh, r1.x) +
                          fmaf(dxh, r3.y, fmaf(-dyh, r3.x, fmaf(dxl, r1.y, -dyl * r1.x)));
-        w.A[lane] = make_float4(r1.x, r1.y, r1.z, Sh);
-        w.T[lane] = make_float4(r3.x, r3.y, r3.z, Sl);
-        w.N[lane] = make_float4(nx, ny, nz, r4.x);
-        w.W[lane] = make_float4(Ah, Al, ALh, ALl);
+        w.D[1][lane] = dup2(r1.z, Sh);
+        w.D[2][lane] = dup2(r3.x, r3.y);
+        w.D[3][lane] = dup2(r3.z, Sl);
+        w.D[4][lane] = dup2(nx, ny);
+        w.D[5][lane] = dup2(nz, r4.x);
+        w.D[6][lane] = dup2(Ah, Al);
+        w.D[7][lane] = dup2(ALh, ALl);
     } else {
-        w.A[lane] = make_float4(0.f, 0.f, 0.f, -1e15f);
-        w.T[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        w.N[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        w.W[lane] = make_float4(-1e15f, 0.f, -1e15f, 0.f);
+        w.D[1][lane] = dup2(0.f, -1e15f);
+        w.D[2][lane] = dup2(0.f, 0.f);
+        w.D[3][lane] = dup2(0.f, 0.f);
+        w.D[4][lane] = dup2(0.f, 0.f);
+        w.D[5][lane] = dup2(0.f, 0.f);
+        w.D[6][lane] = dup2(-1e15f, 0.f);
+        w.D[7][lane] = dup2(-1e15f, 0.f);
     }
 }
 
@@ -1021,7 +1061,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             for (int k = 0; k < kR; ++k) m[k] = 0u;
             auto pair_bits = [&](int jj, uint32_t &kb0, uint32_t &kb1) {
                 const float4 *P = w.P[jj];
-                const float4 p0 = P[0], p1 = P[1], p2 = P[2], p3 = P[3], p4 = P[4];
+                const float4 p0 = w.D[0][jj], p1 = P[0], p2 = P[1], p3 = P[2], p4 = P[3];
                 const f2x TX = pk(p0.x, p0.y), TY = pk(p0.z, p0.w), TZ = pk(p1.x, p1.y);
                 const f2x OT = pk(p1.z, p1.w);
                 const f2x OX = pk(p2.x, p2.y), OY = pk(p2.z, p2.w), OZ = pk(p3.x, p3.y);
@@ -1046,7 +1086,22 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     kb1 = ~(__float_as_uint(g1) | __float_as_uint(a1)) & __float_as_uint(b1_);
                 }
             };
-            if (p.tile_cull) {
+            if (MODE == kFwd && lst) {
+                // With the pre-cull most tested pairs survive the exact test, so the
+                // prefilter is skipped: every lane takes each segment that reaches the
+                // warp tile's ball, in segment order, for both of its receivers.  The
+                // exact path rejects whatever the prefilter would have, so the kept terms,
+                // their arithmetic and their order per receiver are unchanged.
+                uint32_t T = tmask;
+                dirty |= T != 0u;
+                while (T) {
+                    const int jj = __ffs(T) - 1;
+                    T &= T - 1;
+                    survivor_pair<NF, WINDOW, LOSSY, true>(p, X2, Y2, Z2, XL2, YL2, ZL2, w, loss, jj,
+                                                           jj, (valid & 1u) != 0u, (valid & 2u) != 0u,
+                                                           fast_u, accx, accy);
+                }
+            } else if (p.tile_cull) {
                 // only the segments that can reach this warp tile's receivers
                 uint32_t T = tmask;
                 if (STATS) n_test += __popc(T) * __popc(valid);
@@ -1075,7 +1130,9 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 issue(kb_ + 2);
             }
             // ---- survivors, in segment order per receiver
-            if (MODE == kFwd) {
+            if (MODE == kFwd && lst) {
+                // evaluated above
+            } else if (MODE == kFwd) {
                 // the two receivers' survivors side by side, each in segment order
                 uint32_t mm0 = (valid & 1u) ? m[0] : 0u, mm1 = (valid & 2u) ? m[1] : 0u;
                 while (mm0 | mm1) {
@@ -1102,11 +1159,11 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     for (int f = 0; f < NF; ++f) H[f] = 0.f;
                     if ((mm0 << jj) >> 31)
                         survivor_adjoint<NF, WINDOW, LOSSY>(p, xp[0], yp[0], zp[0], xl[0], yl[0],
-                                                            zl[0], w, loss, jj, &adj.g[0][0][lane],
+                                                            zl[0], w, loss, jj, fast_u, &adj.g[0][0][lane],
                                                             G, H);
                     if ((mm1 << jj) >> 31)
                         survivor_adjoint<NF, WINDOW, LOSSY>(p, xp[1], yp[1], zp[1], xl[1], yl[1],
-                                                            zl[1], w, loss, jj, &adj.g[0][1][lane],
+                                                            zl[1], w, loss, jj, fast_u, &adj.g[0][1][lane],
                                                             G, H);
                     G = warp_sum(G);
 #pragma unroll
@@ -1129,7 +1186,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                         const int jj = __clz(mm);
                         mm ^= 0x80000000u >> jj;
                         survivor_count<NF, WINDOW>(p, xp[k], yp[k], zp[k], xl[k], yl[k], zl[k], w, jj,
-                                                   n_kept);
+                                                   fast_u, n_kept);
                     }
                 }
             }
