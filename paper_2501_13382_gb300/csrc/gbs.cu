@@ -64,7 +64,9 @@ constexpr float kWinMargin = 0.01f;         // prefilter window slack (m)
 // K_max max|x'| <= kFastTurns.  Its rounding, at most about 3 ulp of |x'|, moves a term's
 // phase by at most 3 x 2^-24 x 90 turns = 1.0e-4 rad; the roundings of different terms are
 // independent, so the field moves far less (2e-7 relative on the city, 3.5e-5 with the
-// projection in FP32 everywhere at 4 kHz).  Past the limit the float-float product stays.
+// projection in FP32 everywhere at 4 kHz).  On that path n = N + x' x t also leaves out
+// the products of the lo parts (about 1.3 ulp of |x'|; with |n| <= s the phase moves by
+// at most K x 1.3 ulp(|x'|) <= 9e-5 rad).  Past the limit the float-float products stay.
 constexpr float kFastTurns = 90.0f;
 
 // Per-frequency constants, grouped in 16-byte words in the order the survivor
@@ -197,7 +199,7 @@ __device__ __forceinline__ f2x mul2(f2x a, f2x b)
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
-__device__ __forceinline__ f2x neg2(f2x a) { return a ^ 0x8000000080000000ull; }
+__device__ __forceinline__ f2x neg2(f2x a) { return mul2(a, 0xbf800000bf800000ull); }
 __device__ __forceinline__ f2x splat(float a) { return pk(a, a); }
 // two_sum on both halves; the paired operations round each half exactly like the
 // scalar ones, so both paths give identical results
@@ -342,13 +344,17 @@ __device__ __forceinline__ bool frame_geometry(float xh, float yh, float zh, flo
     if (WINDOW == GBT_WINDOW_LINE) {
         if (!(__fadd_rn(sh, sl) >= 0.0f)) return false;
     }
-    // n = N + x' x t: the small terms first, then the main products
-    const float cx = fmaf(yl, T.z, fmaf(-zl, T.y, fmaf(yh, TL.z, __fmul_rn(-zh, TL.y))));
-    const float cy = fmaf(zl, T.x, fmaf(-xl, T.z, fmaf(zh, TL.x, __fmul_rn(-xh, TL.z))));
-    const float cz = fmaf(xl, T.y, fmaf(-yl, T.x, fmaf(xh, TL.y, __fmul_rn(-yh, TL.x))));
-    const float nx = fmaf(yh, T.z, fmaf(-zh, T.y, __fadd_rn(NN.x, cx)));
-    const float ny = fmaf(zh, T.x, fmaf(-xh, T.z, __fadd_rn(NN.y, cy)));
-    const float nz = fmaf(xh, T.y, fmaf(-yh, T.x, __fadd_rn(NN.z, cz)));
+    // n = N + x' x t: the small terms first (float-float projection only), then the
+    // main products
+    float n0x = NN.x, n0y = NN.y, n0z = NN.z;
+    if (!fast) {
+        n0x = __fadd_rn(n0x, fmaf(yl, T.z, fmaf(-zl, T.y, fmaf(yh, TL.z, __fmul_rn(-zh, TL.y)))));
+        n0y = __fadd_rn(n0y, fmaf(zl, T.x, fmaf(-xl, T.z, fmaf(zh, TL.x, __fmul_rn(-xh, TL.z)))));
+        n0z = __fadd_rn(n0z, fmaf(xl, T.y, fmaf(-yl, T.x, fmaf(xh, TL.y, __fmul_rn(-yh, TL.x)))));
+    }
+    const float nx = fmaf(yh, T.z, fmaf(-zh, T.y, n0x));
+    const float ny = fmaf(zh, T.x, fmaf(-xh, T.z, n0y));
+    const float nz = fmaf(xh, T.y, fmaf(-yh, T.x, n0z));
     n2 = fmaf(nx, nx, fmaf(ny, ny, __fmul_rn(nz, nz)));
     return true;
 }
@@ -440,7 +446,8 @@ __device__ __forceinline__ void ld_pairs(const float4 &a, const float4 &b, f2x &
 
 template <int NF, int WINDOW, bool LOSSY, bool SAME = false>
 __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH, f2x ZH,
-                                              f2x XL, f2x YL, f2x ZL, const StageSmem &w,
+                                              f2x XL, f2x YL, f2x ZL, f2x NXH, f2x NYH, f2x NZH,
+                                              const StageSmem &w,
                                               const LossSmem<NF> *loss, int j0, int j1, bool h0,
                                               bool h1, bool fast, f2x (&accx)[NF], f2x (&accy)[NF])
 {
@@ -489,13 +496,17 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
     if (!(k0 || k1)) return;
     ld_pairs<SAME>(w.D[4][j0], w.D[4][j1], NX0, NY0);
     ld_pairs<SAME>(w.D[5][j0], w.D[5][j1], NZ0, AMP);
-    // n = N + x' x t
-    const f2x cx = fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, TLZ, mul2(neg2(ZH), TLY))));
-    const f2x cy = fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, TLX, mul2(neg2(XH), TLZ))));
-    const f2x cz = fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, TLY, mul2(neg2(YH), TLX))));
-    const f2x nx = fma2(YH, THZ, fma2(neg2(ZH), THY, add2(NX0, cx)));
-    const f2x ny = fma2(ZH, THX, fma2(neg2(XH), THZ, add2(NY0, cy)));
-    const f2x nz = fma2(XH, THY, fma2(neg2(YH), THX, add2(NZ0, cz)));
+    // n = N + x' x t; the lo parts' products (about 1.3 ulp of |x'|) only where the
+    // projection is float-float: on the FP32 path they are below its own rounding
+    f2x n0x = NX0, n0y = NY0, n0z = NZ0;
+    if (!fast) {
+        n0x = add2(n0x, fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, TLZ, mul2(neg2(ZH), TLY)))));
+        n0y = add2(n0y, fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, TLX, mul2(neg2(XH), TLZ)))));
+        n0z = add2(n0z, fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, TLY, mul2(neg2(YH), TLX)))));
+    }
+    const f2x nx = fma2(YH, THZ, fma2(NZH, THY, n0x));
+    const f2x ny = fma2(ZH, THX, fma2(NXH, THZ, n0y));
+    const f2x nz = fma2(XH, THY, fma2(NYH, THX, n0z));
     const f2x n2 = fma2(nx, nx, fma2(ny, ny, mul2(nz, nz)));
     const f2x amp = AMP;
     float n20, n21;
@@ -516,13 +527,14 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
         upk(ex, e0, e1);
         const f2x ga = pk(ex2_approx(e0), ex2_approx(e1));
         const f2x KH = splat(q.K_hi);
-        const f2x ph = mul2(KH, sh);
-        const f2x pe = fma2(KH, sh, neg2(ph));
+        const f2x nph = mul2(splat(-q.K_hi), sh);    // -K_hi sh, exactly
+        const f2x pe = fma2(KH, sh, nph);
         const f2x corr = fma2(KH, sl, fma2(splat(q.K_lo), sh, pe));
-        f2x tau = add2(sub2(ph, rint2(ph)), corr);
+        f2x tau = add2(sub2(rint2(nph), nph), corr);   // = ph - rint(ph)
         tau = fma2(mul2(splat(q.halfK), n2invD), sh, tau);
         if (LOSSY) tau = add2(tau, RPH);
-        tau = sub2(tau, rint2(tau));
+        // |tau| < 2^22 turns (beyond it FP32 holds no phase): round by 1.5 x 2^23
+        tau = sub2(tau, sub2(add2(tau, splat(12582912.0f)), splat(12582912.0f)));
         float t0, t1, s0, c0, s1, c1;
         upk(mul2(splat(6.283185307179586f), tau), t0, t1);
         __sincosf(t0, &s0, &c0);
@@ -531,7 +543,7 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
         const f2x gg = mul2(mul2(mul2(mul2(splat(q.scale), amp), ga), invD),
                             pk(kf0 ? 1.0f : 0.0f, kf1 ? 1.0f : 0.0f));
         const f2x B = splat(q.b);
-        bx = fma2(gg, fma2(sh, CS, neg2(mul2(B, SN))), bx);
+        bx = fma2(gg, fma2(sh, CS, mul2(splat(-q.b), SN)), bx);
         by = fma2(gg, fma2(sh, SN, mul2(B, CS)), by);
     };
     if (p.uniform_b) {
@@ -916,6 +928,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
 #pragma unroll
         for (int f = 0; f < NF; ++f) accx[f] = accy[f] = 0ull;
         const f2x XL2 = pk(xl[0], xl[1]), YL2 = pk(yl[0], yl[1]), ZL2 = pk(zl[0], zl[1]);
+        const f2x NX2 = neg2(X2), NY2 = neg2(Y2), NZ2 = neg2(Z2);
         auto fold_all = [&]() {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -1097,7 +1110,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 while (T) {
                     const int jj = __ffs(T) - 1;
                     T &= T - 1;
-                    survivor_pair<NF, WINDOW, LOSSY, true>(p, X2, Y2, Z2, XL2, YL2, ZL2, w, loss, jj,
+                    survivor_pair<NF, WINDOW, LOSSY, true>(p, X2, Y2, Z2, XL2, YL2, ZL2, NX2, NY2, NZ2, w, loss, jj,
                                                            jj, (valid & 1u) != 0u, (valid & 2u) != 0u,
                                                            fast_u, accx, accy);
                 }
@@ -1142,7 +1155,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     if (h1) mm1 ^= 0x80000000u >> j1;
                     if (!h0) j0 = j1;
                     if (!h1) j1 = j0;
-                    survivor_pair<NF, WINDOW, LOSSY>(p, X2, Y2, Z2, XL2, YL2, ZL2, w, loss, j0, j1, h0,
+                    survivor_pair<NF, WINDOW, LOSSY>(p, X2, Y2, Z2, XL2, YL2, ZL2, NX2, NY2, NZ2, w, loss, j0, j1, h0,
                                                      h1, fast_u, accx, accy);
                 }
             } else if (MODE == kBwd) {
