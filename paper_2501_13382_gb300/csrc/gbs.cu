@@ -54,6 +54,7 @@ constexpr int kWRaw = 2;                    // raw record buffers per warp (doub
 constexpr int kR = 2;                       // receivers per lane
 constexpr int kWarpRecv = 32 * kR;          // receivers per warp tile
 constexpr int kTileWarps = 15;              // warp tiles per CTA tile (dispatch order, lists)
+constexpr int kChunkWords = 16;             // warp-tile words per 32-entry chunk of a tile list
 constexpr int kCtaRecv = kTileWarps * kWarpRecv;
 constexpr int kBatch = 32;                  // segments per staged batch
 constexpr long long kSpinLimit = 1LL << 22; // bounded mbarrier waits
@@ -107,7 +108,9 @@ struct alignas(16) FwdParams {
     const int32_t *list;       // segment indices, each tile's in segment order, or null
     const int64_t *list_off;   // per tile: first entry in list
     const int32_t *list_n;     // per tile: entries, or -1 (no list: stream every segment)
-    const uint16_t *list_mask; // per entry: bit w set if the segment can reach warp tile w
+    // per 32-entry chunk of a tile's list (every list starts on a chunk boundary), one
+    // word per warp tile w: bit b set if entry b of the chunk can reach warp tile w
+    const uint32_t *list_words;
     float4 *partial;           // [splits][nf][n_recv]: re_hi, im_hi, re_lo, im_lo
     unsigned long long *stats; // counting mode when non-null: [1] prefiltered, [2] kept
     unsigned int *status;      // device status word (timeouts)
@@ -751,7 +754,7 @@ struct WarpBuf {
     float4 raw[kWRaw][kBatch][kRecFloats / 4];
     StageSmem stg;
     unsigned long long bar[kWRaw];
-    int32_t queue[2 * kBatch];       // list entries selected for this warp tile, not yet batched
+    int32_t queue[kBatch];           // list positions of the next batch for this warp tile
     int abort_flag, pad[3];
 };
 
@@ -946,48 +949,49 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
 
         // Batches of the item, double-buffered: raw buffer k % 2 receives batch k.  Consecutive
         // segments: batch k is split + k * splits, one bulk copy (lane 0) on the buffer's
-        // mbarrier.  A tile list: the item scans the list's 32-entry chunks split, split +
-        // splits, ..., keeps the entries whose mask has this warp tile's bit, and every
-        // lane gathers its own record of each full batch of kept entries with 16-byte
-        // async copies (one commit group per batch, empty past the end).
+        // mbarrier.  A tile list: the item takes the list's 32-entry chunks split, split +
+        // splits, ..., reads this warp tile's word of 32 such chunks at once (one per lane),
+        // queues the set bits' list positions in order, gathers the entries of each full
+        // batch, and every lane copies its own record with 16-byte async copies (one commit
+        // group per batch, empty past the end).
         // Per buffer: records in the batch, and this lane's segment index (or -1).
         int nrec0 = 0, nrec1 = 0;
         int32_t seg0 = -1, seg1 = -1;
-        const uint32_t wbit = 1u << wl;
         const int64_t n_chunks = (n_seg + kBatch - 1) / kBatch;
-        int64_t chunk = split;   // list: next chunk to scan
-        int qlen = 0;            // list: entries queued for this warp tile (warp-uniform)
-        // The mask and entry words of the next two chunks of the item are loaded ahead of
-        // their use, so the scan below does not wait on global loads.
-        auto load_chunk = [&](int64_t ch, uint32_t &mbits, int32_t &ent) {
-            const int64_t e = ch * kBatch + lane;
-            const bool in = ch < n_chunks && e < n_seg;
-            mbits = in ? (uint32_t)p.list_mask[lst - p.list + e] : 0u;
-            ent = in ? lst[e] : -1;
-        };
-        uint32_t pm0 = 0u, pm1 = 0u;
-        int32_t pe0 = -1, pe1 = -1;
-        if (lst) {
-            load_chunk(chunk, pm0, pe0);
-            load_chunk(chunk + p.splits, pm1, pe1);
-        }
-        auto next_list_batch = [&](int32_t &idx) -> int {
-            while (qlen < kBatch && chunk < n_chunks) {
-                const bool sel = (pm0 & wbit) != 0u;
-                const uint32_t m = __ballot_sync(0xffffffffu, sel);
-                if (sel) B.queue[qlen + __popc(m & ((1u << lane) - 1u))] = pe0;
-                qlen += __popc(m);
-                chunk += p.splits;
-                pm0 = pm1;
-                pe0 = pe1;
-                load_chunk(chunk + p.splits, pm1, pe1);
+        const uint32_t *lw =
+            lst ? p.list_words + (p.list_off[tile] / kBatch) * kChunkWords + wl : nullptr;
+        int64_t wnext = split;   // list: lane 0's chunk of the next window
+        int64_t wchunk = 0;      // list: this lane's chunk in the current window
+        uint32_t word = 0u;      // list: its entries for this warp tile not yet queued
+        auto next_list_batch = [&](int32_t &pos) -> int {
+            int n = 0;
+            for (;;) {
+                if (!__any_sync(0xffffffffu, word != 0u)) {
+                    if (wnext >= n_chunks) break;
+                    wchunk = wnext + (int64_t)lane * p.splits;
+                    word = wchunk < n_chunks ? lw[wchunk * kChunkWords] : 0u;
+                    wnext += (int64_t)kBatch * p.splits;
+                    continue;
+                }
+                // lanes in chunk order, bits in entry order
+                const int cnt = __popc(word);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                int slot = n + incl - cnt;
+                while (word != 0u && slot < kBatch) {
+                    B.queue[slot++] = (int32_t)(wchunk * kBatch + __ffs(word) - 1);
+                    word &= word - 1u;
+                }
+                n = min(n + total, kBatch);
+                if (n == kBatch) break;
             }
             __syncwarp();
-            const int n = min(qlen, kBatch);
-            idx = lane < n ? B.queue[lane] : -1;
-            __syncwarp();
-            if (lane + kBatch < qlen) B.queue[lane] = B.queue[lane + kBatch];
-            qlen -= n;
+            pos = lane < n ? B.queue[lane] : -1;
             __syncwarp();
             return n;
         };
@@ -996,7 +1000,9 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             int n = 0;
             int32_t idx = -1;
             if (lst) {
-                n = next_list_batch(idx);
+                int32_t pos;
+                n = next_list_batch(pos);
+                idx = pos >= 0 ? lst[pos] : -1;
                 if (idx >= 0) {
                     const float4 *src =
                         reinterpret_cast<const float4 *>(p.rec + (int64_t)idx * kRecFloats);
@@ -1054,9 +1060,11 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                 // this lane's segment against the warp tile's ball (own lane's staging only)
                 const float4 O = w.O[lane];
                 const float4 *R1 = &B.raw[buf][lane][1];   // t_hi, L_hi of the raw record
-                const bool pass = seg_ok &&
+                // a list entry carrying this warp tile's bit already passed the same test
+                // against the warp tile's ball when the lists were built
+                const bool pass = seg_ok && (lst != nullptr ||
                                   ball_may_keep<WINDOW>(O, make_float4(R1->x, R1->y, R1->z, my_len),
-                                                        O.x, O.y, O.z, sphere, alpha, beta);
+                                                        O.x, O.y, O.z, sphere, alpha, beta));
                 tmask = __ballot_sync(0xffffffffu, pass);
             }
             if (lst) {
@@ -1798,13 +1806,15 @@ __global__ void __launch_bounds__(1024) list_scan_chunks_kernel(int32_t *counts,
     if (threadIdx.x == 0) total[blockIdx.x] = (unsigned int)carry;
 }
 
-// Per list entry, the warp tiles of its CTA tile whose balls the segment can reach.
-// Blocks (g, t) stride over tile t's entries.
+// Per 32-entry chunk of a tile list, one word per warp tile of the CTA tile: bit b set
+// if entry b can reach the warp tile's ball.  Each warp takes whole chunks (blocks
+// (g, t) stride over tile t's chunks) and writes the chunk's 16 words in one store.
 template <int WINDOW>
-__global__ void list_mask_kernel(const float4 *crec, const float4 *wball, int64_t n_wtiles,
-                                 float alpha, float beta, const int64_t *list_off,
-                                 const int32_t *list_n, const int32_t *list, uint16_t *list_mask)
+__global__ void list_words_kernel(const float4 *crec, const float4 *wball, int64_t n_wtiles,
+                                  float alpha, float beta, const int64_t *list_off,
+                                  const int32_t *list_n, const int32_t *list, uint32_t *list_words)
 {
+    static_assert(kTileWarps <= kChunkWords, "one word per warp tile");
     __shared__ float4 sball[kTileWarps];
     const int64_t t = blockIdx.y;
     const int32_t n = list_n[t];
@@ -1812,20 +1822,33 @@ __global__ void list_mask_kernel(const float4 *crec, const float4 *wball, int64_
     const int nw = (int)min((int64_t)kTileWarps, n_wtiles - t * kTileWarps);
     if (threadIdx.x < nw) sball[threadIdx.x] = wball[t * kTileWarps + threadIdx.x];
     __syncthreads();
-    const int64_t off = list_off[t];
-#pragma unroll 2
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t jseg = list[off + i];
-        const float4 r0 = crec[2 * jseg], r1 = crec[2 * jseg + 1];
-        uint32_t wm = 0u;
-        for (int w = 0; w < nw; ++w)
-            if (seg_reaches_ball<WINDOW>(r0, r1, sball[w], alpha, beta)) wm |= 1u << w;
-        list_mask[off + i] = (uint16_t)wm;
+    const int lane = threadIdx.x & 31;
+    const int64_t off = list_off[t];       // a multiple of 32
+    uint32_t *words = list_words + (off / 32) * kChunkWords;
+    const int64_t n_ch = ((int64_t)n + 31) / 32;
+    const int64_t wpb = blockDim.x / 32;
+    for (int64_t ch = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); ch < n_ch;
+         ch += (int64_t)gridDim.x * wpb) {
+        const int64_t i = ch * 32 + lane;
+        const bool in = i < n;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        if (in) {
+            const int64_t jseg = list[off + i];
+            r0 = crec[2 * jseg];
+            r1 = crec[2 * jseg + 1];
+        }
+        uint32_t mine = 0u;
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t m =
+                __ballot_sync(0xffffffffu, in && seg_reaches_ball<WINDOW>(r0, r1, sball[w], alpha, beta));
+            if (lane == w) mine = m;
+        }
+        if (lane < kChunkWords) words[ch * kChunkWords + lane] = mine;
     }
 }
 
-// One block: list ranges, tiles lightest first (perm lists them heaviest first).
+// One block: list ranges, tiles lightest first (perm lists them heaviest first), each
+// starting on a 32-entry chunk boundary.
 __global__ void __launch_bounds__(1024) list_layout_kernel(const unsigned int *total,
                                                            const int32_t *perm, int64_t n_tiles,
                                                            int64_t cap, int64_t *list_off,
@@ -1838,16 +1861,17 @@ __global__ void __launch_bounds__(1024) list_layout_kernel(const unsigned int *t
         const int64_t r = n_tiles - 1 - i;
         return perm ? (int64_t)perm[r] : r;
     };
+    auto padded = [](int64_t n) { return (n + 31) / 32 * 32; };   // whole 32-entry chunks
     int64_t sum = 0;
-    for (int64_t i = i0; i < i0 + per && i < n_tiles; ++i) sum += total[tile_at(i)];
+    for (int64_t i = i0; i < i0 + per && i < n_tiles; ++i) sum += padded(total[tile_at(i)]);
     int64_t off;
     block_scan_1024(sum, off, ws);
     for (int64_t i = i0; i < i0 + per && i < n_tiles; ++i) {
         const int64_t t = tile_at(i);
         const int64_t n = total[t];
         list_off[t] = off;
-        list_n[t] = off + n <= cap ? (int32_t)n : -1;
-        off += n;
+        list_n[t] = off + padded(n) <= cap ? (int32_t)n : -1;
+        off += padded(n);
     }
 }
 
@@ -2386,7 +2410,7 @@ struct TileWs {
     int64_t *list_off = nullptr;
     int32_t *list_n = nullptr;
     int32_t *list = nullptr;
-    uint16_t *mask = nullptr;      // per list entry: warp tiles it can reach
+    uint32_t *words = nullptr;     // per 32-entry list chunk: one word per warp tile
     float4 *wball = nullptr;       // per warp tile: bounding ball
     uint32_t *bits = nullptr;      // [tiles][chunks * 32]: the counting pass's ballots, or null
     int64_t tiles = 0, chunks = 0, cap = 0, wtiles = 0;
@@ -2404,7 +2428,9 @@ static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, boo
     t.chunks = t.lists ? (seg_capacity + kListChunk - 1) / kListChunk : 0;
     // room for an eighth of all (tile, segment) pairs, at least 16M entries
     const int64_t all = t.tiles * seg_capacity;
+    // (a multiple of 32: every tile's list starts on a 32-entry chunk boundary)
     t.cap = t.lists ? std::min<int64_t>(all, std::max<int64_t>(int64_t(1) << 24, all / 8)) : 0;
+    t.cap = (t.cap + 31) / 32 * 32;
     t.wtiles = (n_recv + kWarpRecv - 1) / kWarpRecv;
     char *w = static_cast<char *>(ws);
     size_t off = 0;
@@ -2421,7 +2447,7 @@ static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, boo
         t.list_off = reinterpret_cast<int64_t *>(take((size_t)t.tiles * sizeof(int64_t)));
         t.list_n = reinterpret_cast<int32_t *>(take((size_t)t.tiles * sizeof(int32_t)));
         t.list = reinterpret_cast<int32_t *>(take((size_t)t.cap * sizeof(int32_t)));
-        t.mask = reinterpret_cast<uint16_t *>(take((size_t)t.cap * sizeof(uint16_t)));
+        t.words = reinterpret_cast<uint32_t *>(take((size_t)(t.cap / 32) * kChunkWords * sizeof(uint32_t)));
         t.wball = reinterpret_cast<float4 *>(take((size_t)t.wtiles * sizeof(float4)));
         // the ballots, unless they would take more than 4 GiB (then the write pass repeats
         // the ball tests)
@@ -2495,8 +2521,8 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
                 list_write_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
                     q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                     t.list_off, t.list_n, t.list);
-            list_mask_kernel<GBT_WINDOW_LINE><<<mgrid, 256, 0, s>>>(
-                q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
+            list_words_kernel<GBT_WINDOW_LINE><<<mgrid, 256, 0, s>>>(
+                q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.words);
         } else {
             if (t.bits)
                 list_write_bits_kernel<<<dim3((unsigned)t.chunks, tg), kListChunk, 0, s>>>(
@@ -2505,14 +2531,14 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
                 list_write_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
                     q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                     t.list_off, t.list_n, t.list);
-            list_mask_kernel<GBT_WINDOW_SEGMENT><<<mgrid, 256, 0, s>>>(
-                q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.mask);
+            list_words_kernel<GBT_WINDOW_SEGMENT><<<mgrid, 256, 0, s>>>(
+                q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.words);
         }
         n += 4;
         q.list = t.list;
         q.list_off = t.list_off;
         q.list_n = t.list_n;
-        q.list_mask = t.mask;
+        q.list_words = t.words;
     }
     GBT_CUDA(cudaGetLastError());
     note_launches(n);
@@ -2980,7 +3006,7 @@ static void batch_layout(BatchImpl &B, cudaStream_t s)
             q.list = t.lists ? t.list : nullptr;
             q.list_off = t.lists ? t.list_off : nullptr;
             q.list_n = t.lists ? t.list_n : nullptr;
-            q.list_mask = t.lists ? t.mask : nullptr;
+            q.list_words = t.lists ? t.words : nullptr;
         }
         B.table.push_back(q);
         B.inst_off.push_back(B.inst_off.back() + q.n_items);
