@@ -642,7 +642,11 @@ __device__ __forceinline__ bool ball_may_keep(const float4 &r0, const float4 &r1
     const float dx = sphere.x - ox, dy = sphere.y - oy, dz = sphere.z - oz;
     const float sc = fmaf(dx, r1.x, fmaf(dy, r1.y, dz * r1.z));
     const float cxr = dy * r1.z - dz * r1.y, cyr = dz * r1.x - dx * r1.z, czr = dx * r1.y - dy * r1.x;
-    const float nc = sqrtf(fmaf(cxr, cxr, fmaf(cyr, cyr, czr * czr)));
+    // |d x t| from below: the approximate square root is within a few ulp, and the
+    // factor takes it under the exact root
+    float nc;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(nc) : "f"(fmaf(cxr, cxr, fmaf(cyr, cyr, czr * czr))));
+    nc *= 0.999999f;
     const float R = sphere.w * 1.0001f + 0.05f + 1e-5f * (fabsf(ox) + fabsf(oy) + fabsf(oz));
     bool win;
     if (WINDOW == GBT_WINDOW_LINE) win = r0.w + sc + R >= -kWinMargin;
@@ -1909,7 +1913,8 @@ __global__ void __launch_bounds__(kListChunk) list_write_kernel(
 }
 
 // The same lists from the ballots the counting pass stored (one 32-bit word per tile and
-// warp of 32 segments): no ball test is repeated, and each warp finds its place within
+// warp of 32 segments): no ball test is repeated.  Each warp reads its word of 32 tiles at
+// once (one per lane; most are zero), and for each non-zero one finds its place within
 // the chunk from the earlier warps' words, so there is no block barrier per tile.  Entry
 // order is the same (chunk, then warp, then lane).
 __global__ void __launch_bounds__(kListChunk) list_write_bits_kernel(
@@ -1921,17 +1926,25 @@ __global__ void __launch_bounds__(kListChunk) list_write_bits_kernel(
     if (c * kListChunk >= ns) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t j = c * kListChunk + threadIdx.x;
-    for (int64_t t = blockIdx.y; t < n_tiles; t += gridDim.y) {     // tile group blockIdx.y
-        if (list_n[t] < 0) continue;
-        const uint32_t *row = bits + t * n_chunks * 32 + c * 32;
-        const uint32_t m = row[wid];
-        if (m == 0u) continue;
-        int before = lane < wid ? __popc(row[lane]) : 0;
+    const int64_t row_stride = n_chunks * 32;
+    for (int64_t t0 = (int64_t)blockIdx.y * 32; t0 < n_tiles; t0 += (int64_t)gridDim.y * 32) {
+        const int64_t tl = t0 + lane;
+        uint32_t mw = 0u;
+        if (tl < n_tiles && list_n[tl] >= 0) mw = bits[tl * row_stride + c * 32 + wid];
+        uint32_t nz = __ballot_sync(0xffffffffu, mw != 0u);
+        while (nz) {
+            const int k = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            const int64_t t = t0 + k;
+            const uint32_t m = __shfl_sync(0xffffffffu, mw, k);
+            const uint32_t *row = bits + t * row_stride + c * 32;
+            int before = lane < wid ? __popc(row[lane]) : 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-        if ((m >> lane) & 1u)
-            list[list_off[t] + chunk_off[t * n_chunks + c] + before +
-                 __popc(m & ((1u << lane) - 1u))] = (int32_t)j;
+            for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+            if ((m >> lane) & 1u)
+                list[list_off[t] + chunk_off[t * n_chunks + c] + before +
+                     __popc(m & ((1u << lane) - 1u))] = (int32_t)j;
+        }
     }
 }
 
