@@ -212,13 +212,6 @@ __device__ __forceinline__ void two_sum2(f2x a, f2x b, f2x &s, f2x &e)
     const f2x bv = sub2(s, a);
     e = add2(sub2(a, sub2(s, bv)), sub2(b, bv));
 }
-__device__ __forceinline__ f2x dop2(f2x a, f2x b, f2x c, f2x d)
-{
-    const f2x w = mul2(c, d);
-    const f2x e = fma2(neg2(c), d, w);
-    const f2x f = fma2(a, b, neg2(w));
-    return add2(f, e);
-}
 __device__ __forceinline__ f2x rint2(f2x a)
 {
     float x, y;
@@ -1597,8 +1590,20 @@ __global__ void grad_out_kernel(GradOutParams p)
 constexpr int kWeightSamples = 1 << 15;        // sampled segments per estimate
 constexpr int64_t kMaxOrderedTiles = 1 << 14;  // beyond this the rank pass is skipped
 
+// A ball with its share of the list test's slack, and a segment's share (seg_reaches_ball).
+__device__ __forceinline__ float4 reach_ball(const float4 &b)
+{
+    return make_float4(b.x, b.y, b.z,
+                       fmaf(b.w, 1.0001f, 0.05f) + 1e-5f * (fabsf(b.x) + fabsf(b.y) + fabsf(b.z)));
+}
+__device__ __forceinline__ float segment_slack(const float4 &r0)
+{
+    return 1e-5f * (fabsf(r0.x) + fabsf(r0.y) + fabsf(r0.z));
+}
+
+// Also each tile's reach ball (the list passes' form, with the ball's share of the slack).
 __global__ void tile_ball_kernel(const float *recv, const int32_t *order, int64_t n_recv,
-                                 float4 *ball, unsigned int *weight)
+                                 float4 *ball, unsigned int *weight, float4 *rball)
 {
     __shared__ float red[4][8];
     const int64_t base = (int64_t)blockIdx.x * kCtaRecv;
@@ -1632,6 +1637,7 @@ __global__ void tile_ball_kernel(const float *recv, const int32_t *order, int64_
     if (threadIdx.x == 0) {
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r2 = fmaxf(r2, red[3][k]);
         ball[blockIdx.x] = make_float4(cx, cy, cz, sqrtf(r2));
+        rball[blockIdx.x] = reach_ball(ball[blockIdx.x]);
         weight[blockIdx.x] = 0u;
     }
 }
@@ -1718,22 +1724,40 @@ __global__ void tile_rank_kernel(const unsigned int *weight, int64_t n_tiles, in
 // segment, which gives the same field.
 constexpr int kListChunk = 1024;
 
+// The list passes' form of ball_may_keep, with its slack split between the ball and the
+// segment: a reach ball (centre, W) with W = r 1.0001 + 0.05 + 1e-5 (|cx| + |cy| + |cz|),
+// and the segment's 1e-5 (|ox| + |oy| + |oz|).  Their sum bounds the slack of
+// ball_may_keep (|o - c| <= |o| + |c|), so the test is at least as conservative and
+// costs each (segment, ball) pair a single add for it.  From a segment's cull record
+// (its origin rounded to FP32, which the slack of 5 cm far exceeds).
 template <int WINDOW>
-// From a segment's cull record (its origin rounded to FP32, which the test's slack of
-// 5 cm far exceeds).
 __device__ __forceinline__ bool seg_reaches_ball(const float4 &r0, const float4 &r1,
-                                                 const float4 &b, float alpha, float beta)
+                                                 const float4 &rb, float slack, float alpha,
+                                                 float beta)
 {
-    return ball_may_keep<WINDOW>(r0, r1, r0.x - b.x, r0.y - b.y, r0.z - b.z,
-                                 make_float4(0.f, 0.f, 0.f, b.w), alpha, beta);
+    const float dx = rb.x - r0.x, dy = rb.y - r0.y, dz = rb.z - r0.z;
+    const float sc = fmaf(dx, r1.x, fmaf(dy, r1.y, dz * r1.z));
+    const float cxr = dy * r1.z - dz * r1.y, cyr = dz * r1.x - dx * r1.z, czr = dx * r1.y - dy * r1.x;
+    float nc;   // |d x t| from below (see ball_may_keep)
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(nc) : "f"(fmaf(cxr, cxr, fmaf(cyr, cyr, czr * czr))));
+    nc *= 0.999999f;
+    const float R = rb.w + slack;
+    bool win;
+    if (WINDOW == GBT_WINDOW_LINE) win = r0.w + sc + R >= -kWinMargin;
+    else win = (sc + R >= -kWinMargin) && (sc - R <= r1.w + kWinMargin);
+    const float sabs = fabsf(r0.w + sc) + R;
+    const float nn = nc - R;
+    return win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
 }
 
 template <int WINDOW>
 __global__ void __launch_bounds__(kListChunk) list_count_kernel(
-    const float4 *crec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
+    const float4 *crec, const int32_t *n_seg_ptr, const float4 *rball, int64_t n_tiles,
     int64_t n_chunks, float alpha, float beta, int32_t *counts, uint32_t *bits)
 {
-    // block (c, g): chunk c against tiles g, g + G, ... (G = gridDim.y tile groups)
+    // block (c, g): chunk c against the 32-tile groups g, g + G, ... (G = gridDim.y); lane
+    // k of each warp keeps tile k's ballot of the group, so the group ends with one count
+    // and one ballot store per lane
     extern __shared__ int32_t cnt_s[];
     const int64_t G = gridDim.y, g = blockIdx.y;
     for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x) cnt_s[t] = 0;
@@ -1748,18 +1772,25 @@ __global__ void __launch_bounds__(kListChunk) list_count_kernel(
             r0 = crec[2 * j];
             r1 = crec[2 * j + 1];
         }
-        for (int64_t t = g; t < n_tiles; t += G) {
-            const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, ball[t], alpha, beta);
-            const unsigned int m = __ballot_sync(0xffffffffu, pass);
-            if ((threadIdx.x & 31) == 0) {
-                if (m) atomicAdd(&cnt_s[t], (int32_t)__popc(m));
-                if (bits) bits[t * n_chunks * 32 + c * 32 + (threadIdx.x >> 5)] = m;
+        const float slack = segment_slack(r0);
+        const int lane = threadIdx.x & 31;
+        for (int64_t t0 = g * 32; t0 < n_tiles; t0 += G * 32) {
+            const int nt = (int)min((int64_t)32, n_tiles - t0);
+            uint32_t mine = 0u;
+            for (int k = 0; k < nt; ++k) {
+                const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, rball[t0 + k], slack, alpha, beta);
+                const uint32_t m = __ballot_sync(0xffffffffu, pass);
+                if (lane == k) mine = m;
+            }
+            if (lane < nt) {
+                if (mine) atomicAdd(&cnt_s[t0 + lane], (int32_t)__popc(mine));
+                if (bits) bits[(t0 + lane) * n_chunks * 32 + c * 32 + (threadIdx.x >> 5)] = mine;
             }
         }
     }
     __syncthreads();
-    for (int64_t t = g + (int64_t)threadIdx.x * G; t < n_tiles; t += (int64_t)blockDim.x * G)
-        counts[t * n_chunks + c] = cnt_s[t];
+    for (int64_t t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        if ((t / 32) % G == g) counts[t * n_chunks + c] = cnt_s[t];
 }
 
 // Exclusive scan of 1024 values held one per thread; returns the block total.
@@ -1824,7 +1855,7 @@ __global__ void list_words_kernel(const float4 *crec, const float4 *wball, int64
     const int32_t n = list_n[t];
     if (n <= 0) return;                    // uniform over the block
     const int nw = (int)min((int64_t)kTileWarps, n_wtiles - t * kTileWarps);
-    if (threadIdx.x < nw) sball[threadIdx.x] = wball[t * kTileWarps + threadIdx.x];
+    if (threadIdx.x < nw) sball[threadIdx.x] = reach_ball(wball[t * kTileWarps + threadIdx.x]);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t off = list_off[t];       // a multiple of 32
@@ -1841,10 +1872,11 @@ __global__ void list_words_kernel(const float4 *crec, const float4 *wball, int64
             r0 = crec[2 * jseg];
             r1 = crec[2 * jseg + 1];
         }
+        const float slack = segment_slack(r0);
         uint32_t mine = 0u;
         for (int w = 0; w < nw; ++w) {
-            const uint32_t m =
-                __ballot_sync(0xffffffffu, in && seg_reaches_ball<WINDOW>(r0, r1, sball[w], alpha, beta));
+            const uint32_t m = __ballot_sync(
+                0xffffffffu, in && seg_reaches_ball<WINDOW>(r0, r1, sball[w], slack, alpha, beta));
             if (lane == w) mine = m;
         }
         if (lane < kChunkWords) words[ch * kChunkWords + lane] = mine;
@@ -1881,7 +1913,7 @@ __global__ void __launch_bounds__(1024) list_layout_kernel(const unsigned int *t
 
 template <int WINDOW>
 __global__ void __launch_bounds__(kListChunk) list_write_kernel(
-    const float4 *crec, const int32_t *n_seg_ptr, const float4 *ball, int64_t n_tiles,
+    const float4 *crec, const int32_t *n_seg_ptr, const float4 *rball, int64_t n_tiles,
     int64_t n_chunks, float alpha, float beta, const int32_t *chunk_off, const int64_t *list_off,
     const int32_t *list_n, int32_t *list)
 {
@@ -1897,9 +1929,10 @@ __global__ void __launch_bounds__(kListChunk) list_write_kernel(
         r0 = crec[2 * j];
         r1 = crec[2 * j + 1];
     }
+    const float slack = segment_slack(r0);
     for (int64_t t = 0; t < n_tiles; ++t) {
         if (list_n[t] < 0) continue;
-        const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, ball[t], alpha, beta);
+        const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, rball[t], slack, alpha, beta);
         const unsigned int m = __ballot_sync(0xffffffffu, pass);
         if (lane == 0) wsum[wid] = __popc(m);
         __syncthreads();
@@ -2417,6 +2450,7 @@ static int64_t cta_tiles(int64_t n_recv) { return (n_recv + kCtaRecv - 1) / kCta
 // first), plus, with the tile pre-cull, the per-tile segment lists.
 struct TileWs {
     float4 *ball = nullptr;
+    float4 *rball = nullptr;       // the balls with their share of the list test's slack
     unsigned int *weight = nullptr;
     int32_t *perm = nullptr;
     int32_t *counts = nullptr;     // [tiles][chunks]: counts, then offsets within the tile
@@ -2453,6 +2487,7 @@ static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, boo
         return r;
     };
     t.ball = reinterpret_cast<float4 *>(take((size_t)t.tiles * sizeof(float4)));
+    t.rball = reinterpret_cast<float4 *>(take((size_t)t.tiles * sizeof(float4)));
     t.weight = reinterpret_cast<unsigned int *>(take((size_t)t.tiles * sizeof(unsigned int)));
     t.perm = reinterpret_cast<int32_t *>(take((size_t)t.tiles * sizeof(int32_t)));
     if (t.lists) {
@@ -2485,7 +2520,7 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
     if (!t.order && !t.lists) return;
     const int64_t T = t.tiles;
     int64_t n = 0;
-    tile_ball_kernel<<<(unsigned)T, 256, 0, s>>>(q.recv, q.order, q.n_recv, t.ball, t.weight);
+    tile_ball_kernel<<<(unsigned)T, 256, 0, s>>>(q.recv, q.order, q.n_recv, t.ball, t.weight, t.rball);
     ++n;
     // tile groups of the chunk-major list passes (each block walks 1 / tg of the tiles):
     // one, since more re-read the chunk's records for every group (measured on the city:
@@ -2497,12 +2532,12 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
             GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_LINE>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             list_count_kernel<GBT_WINDOW_LINE><<<dim3((unsigned)t.chunks, tg), kListChunk, sm, s>>>(
-                q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
+                q.crec, q.n_seg_ptr, t.rball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
         } else {
             GBT_CUDA(cudaFuncSetAttribute(list_count_kernel<GBT_WINDOW_SEGMENT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             list_count_kernel<GBT_WINDOW_SEGMENT><<<dim3((unsigned)t.chunks, tg), kListChunk, sm, s>>>(
-                q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
+                q.crec, q.n_seg_ptr, t.rball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts, t.bits);
         }
         list_scan_chunks_kernel<<<(unsigned)T, 1024, 0, s>>>(t.counts, t.chunks, t.weight);
         n += 2;
@@ -2532,7 +2567,7 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
                     q.n_seg_ptr, T, t.chunks, t.bits, t.counts, t.list_off, t.list_n, t.list);
             else
                 list_write_kernel<GBT_WINDOW_LINE><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
-                    q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                    q.crec, q.n_seg_ptr, t.rball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                     t.list_off, t.list_n, t.list);
             list_words_kernel<GBT_WINDOW_LINE><<<mgrid, 256, 0, s>>>(
                 q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.words);
@@ -2542,7 +2577,7 @@ static void tile_prep_launch(FwdParams &q, int window, const TileWs &t, cudaStre
                     q.n_seg_ptr, T, t.chunks, t.bits, t.counts, t.list_off, t.list_n, t.list);
             else
                 list_write_kernel<GBT_WINDOW_SEGMENT><<<(unsigned)t.chunks, kListChunk, 0, s>>>(
-                    q.crec, q.n_seg_ptr, t.ball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
+                    q.crec, q.n_seg_ptr, t.rball, T, t.chunks, q.pre_alpha, q.pre_beta, t.counts,
                     t.list_off, t.list_n, t.list);
             list_words_kernel<GBT_WINDOW_SEGMENT><<<mgrid, 256, 0, s>>>(
                 q.crec, t.wball, t.wtiles, q.pre_alpha, q.pre_beta, t.list_off, t.list_n, t.list, t.words);
