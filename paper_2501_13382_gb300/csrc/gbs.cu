@@ -1730,22 +1730,41 @@ constexpr int kListChunk = 1024;
 // ball_may_keep (|o - c| <= |o| + |c|), so the test is at least as conservative and
 // costs each (segment, ball) pair a single add for it.  From a segment's cull record
 // (its origin rounded to FP32, which the slack of 5 cm far exceeds).
+// A segment's terms of the test, formed once for all the balls it meets: with d = c - o,
+// d.t = c.t - o.t and d x t = c x t - o x t, whose extra rounding (a few ulp of |c| and
+// |o|) the slack's 1e-5 (|o| + |c|) far exceeds.
+struct SegCull {
+    float tx, ty, tz, len, s0;   // direction, length, start
+    float ot, ox, oy, oz;        // o.t and o x t
+    float slack;                 // the segment's share of the slack
+};
+__device__ __forceinline__ SegCull seg_cull(const float4 &r0, const float4 &r1)
+{
+    SegCull g;
+    g.tx = r1.x; g.ty = r1.y; g.tz = r1.z; g.len = r1.w; g.s0 = r0.w;
+    g.ot = fmaf(r0.x, r1.x, fmaf(r0.y, r1.y, r0.z * r1.z));
+    g.ox = fmaf(r0.y, r1.z, -r0.z * r1.y);
+    g.oy = fmaf(r0.z, r1.x, -r0.x * r1.z);
+    g.oz = fmaf(r0.x, r1.y, -r0.y * r1.x);
+    g.slack = segment_slack(r0);
+    return g;
+}
 template <int WINDOW>
-__device__ __forceinline__ bool seg_reaches_ball(const float4 &r0, const float4 &r1,
-                                                 const float4 &rb, float slack, float alpha,
+__device__ __forceinline__ bool seg_reaches_ball(const SegCull &g, const float4 &rb, float alpha,
                                                  float beta)
 {
-    const float dx = rb.x - r0.x, dy = rb.y - r0.y, dz = rb.z - r0.z;
-    const float sc = fmaf(dx, r1.x, fmaf(dy, r1.y, dz * r1.z));
-    const float cxr = dy * r1.z - dz * r1.y, cyr = dz * r1.x - dx * r1.z, czr = dx * r1.y - dy * r1.x;
+    const float sc = fmaf(rb.x, g.tx, fmaf(rb.y, g.ty, fmaf(rb.z, g.tz, -g.ot)));
+    const float cxr = fmaf(rb.y, g.tz, fmaf(-rb.z, g.ty, -g.ox));
+    const float cyr = fmaf(rb.z, g.tx, fmaf(-rb.x, g.tz, -g.oy));
+    const float czr = fmaf(rb.x, g.ty, fmaf(-rb.y, g.tx, -g.oz));
     float nc;   // |d x t| from below (see ball_may_keep)
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(nc) : "f"(fmaf(cxr, cxr, fmaf(cyr, cyr, czr * czr))));
     nc *= 0.999999f;
-    const float R = rb.w + slack;
+    const float R = rb.w + g.slack;
     bool win;
-    if (WINDOW == GBT_WINDOW_LINE) win = r0.w + sc + R >= -kWinMargin;
-    else win = (sc + R >= -kWinMargin) && (sc - R <= r1.w + kWinMargin);
-    const float sabs = fabsf(r0.w + sc) + R;
+    if (WINDOW == GBT_WINDOW_LINE) win = g.s0 + sc + R >= -kWinMargin;
+    else win = (sc + R >= -kWinMargin) && (sc - R <= g.len + kWinMargin);
+    const float sabs = fabsf(g.s0 + sc) + R;
     const float nn = nc - R;
     return win && (nn <= 0.f || alpha * nn * nn <= fmaf(sabs, sabs, beta));
 }
@@ -1772,13 +1791,13 @@ __global__ void __launch_bounds__(kListChunk) list_count_kernel(
             r0 = crec[2 * j];
             r1 = crec[2 * j + 1];
         }
-        const float slack = segment_slack(r0);
+        const SegCull sg = seg_cull(r0, r1);
         const int lane = threadIdx.x & 31;
         for (int64_t t0 = g * 32; t0 < n_tiles; t0 += G * 32) {
             const int nt = (int)min((int64_t)32, n_tiles - t0);
             uint32_t mine = 0u;
             for (int k = 0; k < nt; ++k) {
-                const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, rball[t0 + k], slack, alpha, beta);
+                const bool pass = ok && seg_reaches_ball<WINDOW>(sg, rball[t0 + k], alpha, beta);
                 const uint32_t m = __ballot_sync(0xffffffffu, pass);
                 if (lane == k) mine = m;
             }
@@ -1872,11 +1891,11 @@ __global__ void list_words_kernel(const float4 *crec, const float4 *wball, int64
             r0 = crec[2 * jseg];
             r1 = crec[2 * jseg + 1];
         }
-        const float slack = segment_slack(r0);
+        const SegCull sg = seg_cull(r0, r1);
         uint32_t mine = 0u;
         for (int w = 0; w < nw; ++w) {
             const uint32_t m = __ballot_sync(
-                0xffffffffu, in && seg_reaches_ball<WINDOW>(r0, r1, sball[w], slack, alpha, beta));
+                0xffffffffu, in && seg_reaches_ball<WINDOW>(sg, sball[w], alpha, beta));
             if (lane == w) mine = m;
         }
         if (lane < kChunkWords) words[ch * kChunkWords + lane] = mine;
@@ -1929,10 +1948,10 @@ __global__ void __launch_bounds__(kListChunk) list_write_kernel(
         r0 = crec[2 * j];
         r1 = crec[2 * j + 1];
     }
-    const float slack = segment_slack(r0);
+    const SegCull sg = seg_cull(r0, r1);
     for (int64_t t = 0; t < n_tiles; ++t) {
         if (list_n[t] < 0) continue;
-        const bool pass = ok && seg_reaches_ball<WINDOW>(r0, r1, rball[t], slack, alpha, beta);
+        const bool pass = ok && seg_reaches_ball<WINDOW>(sg, rball[t], alpha, beta);
         const unsigned int m = __ballot_sync(0xffffffffu, pass);
         if (lane == 0) wsum[wid] = __popc(m);
         __syncthreads();
