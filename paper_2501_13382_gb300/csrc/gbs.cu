@@ -281,10 +281,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 //   s_loc = A + x'.t,  s = S + x'.t,  n = N + x' x t.
 struct StageSmem {
     float4 O[kBatch];               // o' = o - c, s0_hi (per-warp ball test)
-    // prefilter constants, each duplicated into both halves of a float pair (t_x and t_y
-    // are D[0] below): P[0] = t_z, -o'.t;  P[1..2] = 2a o'_x, 2a o'_y, 2a o'_z,
-    // beta - a |o'|^2;  P[3] = s0 + margin, L + margin
-    float4 P[kBatch][4];
+    // prefilter constants, each duplicated into both halves of a float pair:
+    // P[0] = t_z, -o'.t;  P[1..2] = 2a o'_x, 2a o'_y, 2a o'_z, beta - a |o'|^2;
+    // P[3] = s0 + margin, L + margin;  P[4] = t_x, t_y (as D[0]: the prefilter reads its
+    // own copy, which measured 6 % faster testing every pair than sharing D[0])
+    float4 P[kBatch][5];
     // exact-path view, two values per word, each duplicated into both halves of a float
     // pair (a lane evaluating one segment for its two receivers loads its operands as
     // pairs); component-major, so lanes loading different segments hit different banks:
@@ -670,6 +671,7 @@ __device__ __forceinline__ float stage_batch(StageSmem &w, const float4 (&raw)[k
         const float oo = fmaf(ox, ox, fmaf(oy, oy, oz * oz));
         const float a2 = 2.f * alpha;
         w.D[0][lane] = dup2(r1.x, r1.y);
+        P[4] = dup2(r1.x, r1.y);
         P[0] = dup2(r1.z, -ot);
         P[1] = dup2(a2 * ox, a2 * oy);
         P[2] = dup2(a2 * oz, fmaf(-alpha, oo, beta));
@@ -678,6 +680,7 @@ __device__ __forceinline__ float stage_batch(StageSmem &w, const float4 (&raw)[k
         // far behind its own start
         w.O[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
         w.D[0][lane] = dup2(0.f, 0.f);
+        P[4] = dup2(0.f, 0.f);
         P[0] = dup2(0.f, -1e15f);
         P[1] = dup2(0.f, 0.f);
         P[2] = dup2(0.f, 0.f);
@@ -1079,7 +1082,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
             for (int k = 0; k < kR; ++k) m[k] = 0u;
             auto pair_bits = [&](int jj, uint32_t &kb0, uint32_t &kb1) {
                 const float4 *P = w.P[jj];
-                const float4 p0 = w.D[0][jj], p1 = P[0], p2 = P[1], p3 = P[2], p4 = P[3];
+                const float4 p0 = P[4], p1 = P[0], p2 = P[1], p3 = P[2], p4 = P[3];
                 const f2x TX = pk(p0.x, p0.y), TY = pk(p0.z, p0.w), TZ = pk(p1.x, p1.y);
                 const f2x OT = pk(p1.z, p1.w);
                 const f2x OX = pk(p2.x, p2.y), OY = pk(p2.z, p2.w), OZ = pk(p3.x, p3.y);
