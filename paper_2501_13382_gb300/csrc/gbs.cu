@@ -65,7 +65,9 @@ constexpr float kWinMargin = 0.01f;         // prefilter window slack (m)
 // K_max max|x'| <= kFastTurns.  Its rounding, at most about 3 ulp of |x'|, moves a term's
 // phase by at most 3 x 2^-24 x 90 turns = 1.0e-4 rad; the roundings of different terms are
 // independent, so the field moves far less (2e-7 relative on the city, 3.5e-5 with the
-// projection in FP32 everywhere at 4 kHz).  On that path n = N + x' x t also leaves out
+// projection in FP32 everywhere at 4 kHz).  The window test is a hard cutoff, so a pair
+// within the FP32 projection's error bound of an end of its window is decided and
+// evaluated with the float-float projection.  On that path n = N + x' x t also leaves out
 // the products of the lo parts (about 1.3 ulp of |x'|; with |n| <= s the phase moves by
 // at most K x 1.3 ulp(|x'|) <= 9e-5 rad).  Past the limit the float-float products stay.
 constexpr float kFastTurns = 90.0f;
@@ -304,12 +306,14 @@ struct LossSmem {
 
 // Exact geometry of one (receiver, segment) pair in the warp tile's frame, in
 // float-float: x' = (xh + xl) exactly; returns false when the pair falls outside
-// the window.  `fast`: the warp item's choice of the FP32 local projection.  The
+// the window.  `fast`: the warp item's choice of the FP32 local projection, within eps
+// of x'.t; a pair within eps of an end of its window is decided and evaluated with the
+// float-float projection instead, so the window test is as exact as on that path.  The
 // paired twin in survivor_pair rounds each half identically.
 template <int WINDOW>
 __device__ __forceinline__ bool frame_geometry(float xh, float yh, float zh, float xl, float yl,
                                                float zl, const StageSmem &w, int j, bool fast,
-                                               float &sh, float &sl, float &n2)
+                                               float eps, float &sh, float &sl, float &n2)
 {
     const float4 d0 = w.D[0][j], d1 = w.D[1][j], d2 = w.D[2][j], d3 = w.D[3][j];
     const float4 d4 = w.D[4][j], d5 = w.D[5][j];
@@ -317,10 +321,7 @@ __device__ __forceinline__ bool frame_geometry(float xh, float yh, float zh, flo
     const float4 NN = make_float4(d4.x, d4.z, d5.x, d5.z);
     // u = x'.t as (U + ul)
     float U, ul;
-    if (fast) {
-        U = fmaf(xh, T.x, fmaf(yh, T.y, __fmul_rn(zh, T.z)));
-        ul = fmaf(xl, T.x, fmaf(yl, T.y, fmaf(zl, T.z, fmaf(xh, TL.x, fmaf(yh, TL.y, __fmul_rn(zh, TL.z))))));
-    } else {
+    auto exact_u = [&]() {
         const float p0 = __fmul_rn(xh, T.x), p1 = __fmul_rn(yh, T.y), p2 = __fmul_rn(zh, T.z);
         const float r0 = fmaf(xh, TL.x, fmaf(xl, T.x, fmaf(xh, T.x, -p0)));
         const float r1 = fmaf(yh, TL.y, fmaf(yl, T.y, fmaf(yh, T.y, -p1)));
@@ -329,17 +330,39 @@ __device__ __forceinline__ bool frame_geometry(float xh, float yh, float zh, flo
         two_sum(p0, p1, S1, E1);
         two_sum(S1, p2, U, E2);
         ul = __fadd_rn(__fadd_rn(E1, E2), __fadd_rn(__fadd_rn(r0, r1), r2));
+    };
+    if (fast) {
+        U = fmaf(xh, T.x, fmaf(yh, T.y, __fmul_rn(zh, T.z)));
+        ul = fmaf(xl, T.x, fmaf(yl, T.y, fmaf(zl, T.z, fmaf(xh, TL.x, fmaf(yh, TL.y, __fmul_rn(zh, TL.z))))));
+    } else {
+        exact_u();
     }
     if (WINDOW == GBT_WINDOW_SEGMENT) {
         const float4 d6 = w.D[6][j], d7 = w.D[7][j];
-        if (!(__fadd_rn(__fadd_rn(d6.x, U), __fadd_rn(d6.z, ul)) >= 0.0f)) return false;
-        if (!(__fadd_rn(__fadd_rn(d7.x, U), __fadd_rn(d7.z, ul)) < 0.0f)) return false;
+        float wa = __fadd_rn(__fadd_rn(d6.x, U), __fadd_rn(d6.z, ul));
+        float wb = __fadd_rn(__fadd_rn(d7.x, U), __fadd_rn(d7.z, ul));
+        if (fast && fminf(fabsf(wa), fabsf(wb)) <= eps) {
+            fast = false;
+            exact_u();
+            wa = __fadd_rn(__fadd_rn(d6.x, U), __fadd_rn(d6.z, ul));
+            wb = __fadd_rn(__fadd_rn(d7.x, U), __fadd_rn(d7.z, ul));
+        }
+        if (!(wa >= 0.0f)) return false;
+        if (!(wb < 0.0f)) return false;
     }
     float e3;
     two_sum(T.w, U, sh, e3);
     sl = __fadd_rn(e3, __fadd_rn(ul, TL.w));
     if (WINDOW == GBT_WINDOW_LINE) {
-        if (!(__fadd_rn(sh, sl) >= 0.0f)) return false;
+        float ss = __fadd_rn(sh, sl);
+        if (fast && fabsf(ss) <= eps) {
+            fast = false;
+            exact_u();
+            two_sum(T.w, U, sh, e3);
+            sl = __fadd_rn(e3, __fadd_rn(ul, TL.w));
+            ss = __fadd_rn(sh, sl);
+        }
+        if (!(ss >= 0.0f)) return false;
     }
     // n = N + x' x t: the small terms first (float-float projection only), then the
     // main products
@@ -394,10 +417,10 @@ __device__ __forceinline__ void beam_adjoint(const FreqConst &q, float sh, float
 template <int NF, int WINDOW>
 __device__ __forceinline__ void survivor_count(const FwdParams &p, float xh, float yh, float zh,
                                                float xl, float yl, float zl, const StageSmem &w,
-                                               int j, bool fast, uint32_t &kept)
+                                               int j, bool fast, float eps, uint32_t &kept)
 {
     float sh, sl, n2;
-    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, fast, sh, sl, n2)) return;
+    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, fast, eps, sh, sl, n2)) return;
     if (p.uniform_b) {
         const float D = fmaf(sh, sh, p.fc[0].b2);
         const float r = n2 * rcp_approx(D);
@@ -441,12 +464,31 @@ __device__ __forceinline__ void ld_pairs(const float4 &a, const float4 &b, f2x &
     }
 }
 
+// ld_pairs from shared memory again, as an opaque load the compiler cannot merge with the
+// first one, so the values need not stay in registers until a rare later use.
+template <bool SAME>
+__device__ __forceinline__ void ld_pairs_again(const float4 &a, const float4 &b, f2x &u, f2x &v)
+{
+    if (SAME) {
+        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(u), "=l"(v) : "r"(smem_addr(&a)));
+    } else {
+        float a0, a1, a2, a3, b0, b1, b2, b3;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(a0), "=f"(a1), "=f"(a2), "=f"(a3) : "r"(smem_addr(&a)));
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(b3) : "r"(smem_addr(&b)));
+        u = pk(a0, b0);
+        v = pk(a2, b2);
+    }
+}
+
 template <int NF, int WINDOW, bool LOSSY, bool SAME = false>
 __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH, f2x ZH,
                                               f2x XL, f2x YL, f2x ZL, f2x NXH, f2x NYH, f2x NZH,
                                               const StageSmem &w,
                                               const LossSmem<NF> *loss, int j0, int j1, bool h0,
-                                              bool h1, bool fast, f2x (&accx)[NF], f2x (&accy)[NF])
+                                              bool h1, bool fast, float eps, f2x (&accx)[NF],
+                                              f2x (&accy)[NF])
 {
     f2x THX, THY, THZ, SH, TLX, TLY, TLZ, SL, NX0, NY0, NZ0, AMP;
     ld_pairs<SAME>(w.D[0][j0], w.D[0][j1], THX, THY);
@@ -454,39 +496,88 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
     ld_pairs<SAME>(w.D[2][j0], w.D[2][j1], TLX, TLY);
     ld_pairs<SAME>(w.D[3][j0], w.D[3][j1], TLZ, SL);
     // u = x'.t as (U + ul): float-float, or (warp-uniform `fast`, compact warps at low
-    // enough frequencies) the FP32 products with the lo parts' first-order terms
+    // enough frequencies) the FP32 products with the lo parts' first-order terms, within
+    // eps of x'.t.  A half within eps of an end of its window takes the float-float
+    // projection instead (ex0 / ex1), as frame_geometry does for one pair.
     f2x U, ul;
-    if (fast) {
-        U = fma2(XH, THX, fma2(YH, THY, mul2(ZH, THZ)));
-        ul = fma2(XL, THX, fma2(YL, THY, fma2(ZL, THZ, fma2(XH, TLX, fma2(YH, TLY, mul2(ZH, TLZ))))));
-    } else {
+    auto exact_u = [&](f2x TLX, f2x TLY, f2x TLZ, f2x &Ue, f2x &ule) {
         const f2x p0 = mul2(XH, THX), p1 = mul2(YH, THY), p2 = mul2(ZH, THZ);
         const f2x r0 = fma2(XH, TLX, fma2(XL, THX, fma2(XH, THX, neg2(p0))));
         const f2x r1 = fma2(YH, TLY, fma2(YL, THY, fma2(YH, THY, neg2(p1))));
         const f2x r2 = fma2(ZH, TLZ, fma2(ZL, THZ, fma2(ZH, THZ, neg2(p2))));
         f2x S1, E1, E2;
         two_sum2(p0, p1, S1, E1);
-        two_sum2(S1, p2, U, E2);
-        ul = add2(add2(E1, E2), add2(add2(r0, r1), r2));
+        two_sum2(S1, p2, Ue, E2);
+        ule = add2(add2(E1, E2), add2(add2(r0, r1), r2));
+    };
+    bool ex0 = !fast, ex1 = !fast;
+    if (fast) {
+        U = fma2(XH, THX, fma2(YH, THY, mul2(ZH, THZ)));
+        ul = fma2(XL, THX, fma2(YL, THY, fma2(ZL, THZ, fma2(XH, TLX, fma2(YH, TLY, mul2(ZH, TLZ))))));
+    } else {
+        exact_u(TLX, TLY, TLZ, U, ul);
     }
+    // the lo direction again from shared memory where it is needed after the projection
+    auto lo_dir = [&](f2x &lx, f2x &ly, f2x &lz) {
+        f2x s_;
+        ld_pairs_again<SAME>(w.D[2][j0], w.D[2][j1], lx, ly);
+        ld_pairs_again<SAME>(w.D[3][j0], w.D[3][j1], lz, s_);
+    };
+    auto refine = [&](bool n0, bool n1) {   // the near halves to the float-float projection
+        f2x Ue, ule, lx, ly, lz;
+        lo_dir(lx, ly, lz);
+        exact_u(lx, ly, lz, Ue, ule);
+        float a0, a1, b0, b1;
+        upk(U, a0, a1);
+        upk(Ue, b0, b1);
+        U = pk(n0 ? b0 : a0, n1 ? b1 : a1);
+        upk(ul, a0, a1);
+        upk(ule, b0, b1);
+        ul = pk(n0 ? b0 : a0, n1 ? b1 : a1);
+        ex0 = ex0 || n0;
+        ex1 = ex1 || n1;
+    };
     bool k0 = h0, k1 = h1;
     float u0, u1;
     if (WINDOW == GBT_WINDOW_SEGMENT) {
         f2x AH, AL, BH, BL;
         ld_pairs<SAME>(w.D[6][j0], w.D[6][j1], AH, AL);
         ld_pairs<SAME>(w.D[7][j0], w.D[7][j1], BH, BL);
-        upk(add2(add2(AH, U), add2(AL, ul)), u0, u1);
+        f2x WA = add2(add2(AH, U), add2(AL, ul)), WB = add2(add2(BH, U), add2(BL, ul));
+        if (fast) {
+            float a0, a1, b0, b1;
+            upk(WA, a0, a1);
+            upk(WB, b0, b1);
+            const bool n0 = fminf(fabsf(a0), fabsf(b0)) <= eps, n1 = fminf(fabsf(a1), fabsf(b1)) <= eps;
+            if (n0 || n1) {
+                refine(n0, n1);
+                WA = add2(add2(AH, U), add2(AL, ul));
+                WB = add2(add2(BH, U), add2(BL, ul));
+            }
+        }
+        upk(WA, u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
-        upk(add2(add2(BH, U), add2(BL, ul)), u0, u1);
+        upk(WB, u0, u1);
         k0 = k0 && u0 < 0.0f;
         k1 = k1 && u1 < 0.0f;
     }
     f2x sh, e3;
     two_sum2(SH, U, sh, e3);
-    const f2x sl = add2(e3, add2(ul, SL));
+    f2x sl = add2(e3, add2(ul, SL));
     if (WINDOW == GBT_WINDOW_LINE) {
-        upk(add2(sh, sl), u0, u1);
+        f2x SS = add2(sh, sl);
+        if (fast) {
+            upk(SS, u0, u1);
+            const bool n0 = !ex0 && fabsf(u0) <= eps, n1 = !ex1 && fabsf(u1) <= eps;
+            if (n0 || n1) {
+                refine(n0, n1);
+                two_sum2(SH, U, sh, e3);
+                sl = add2(e3, add2(ul, SL));
+                SS = add2(sh, sl);
+            }
+        }
+        upk(SS, u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
     }
@@ -496,10 +587,21 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
     // n = N + x' x t; the lo parts' products (about 1.3 ulp of |x'|) only where the
     // projection is float-float: on the FP32 path they are below its own rounding
     f2x n0x = NX0, n0y = NY0, n0z = NZ0;
-    if (!fast) {
-        n0x = add2(n0x, fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, TLZ, mul2(neg2(ZH), TLY)))));
-        n0y = add2(n0y, fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, TLX, mul2(neg2(XH), TLZ)))));
-        n0z = add2(n0z, fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, TLY, mul2(neg2(YH), TLX)))));
+    if (ex0 || ex1) {
+        f2x lx, ly, lz;
+        lo_dir(lx, ly, lz);
+        f2x cx = fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, lz, mul2(neg2(ZH), ly))));
+        f2x cy = fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, lx, mul2(neg2(XH), lz))));
+        f2x cz = fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, ly, mul2(neg2(YH), lx))));
+        if (!(ex0 && ex1)) {   // only the halves on the float-float projection (x 1 is exact)
+            const f2x m = pk(ex0 ? 1.0f : 0.0f, ex1 ? 1.0f : 0.0f);
+            cx = mul2(cx, m);
+            cy = mul2(cy, m);
+            cz = mul2(cz, m);
+        }
+        n0x = add2(n0x, cx);
+        n0y = add2(n0y, cy);
+        n0z = add2(n0z, cz);
     }
     const f2x nx = fma2(YH, THZ, fma2(NZH, THY, n0x));
     const f2x ny = fma2(ZH, THX, fma2(NXH, THZ, n0y));
@@ -580,10 +682,11 @@ template <int NF, int WINDOW, bool LOSSY>
 __device__ __forceinline__ void survivor_adjoint(const FwdParams &p, float xh, float yh, float zh,
                                                  float xl, float yl, float zl, const StageSmem &w,
                                                  const LossSmem<NF> *loss, int j, bool fast,
-                                                 const float2 *gk, float &G, float (&H)[NF])
+                                                 float eps, const float2 *gk, float &G,
+                                                 float (&H)[NF])
 {
     float sh, sl, n2;
-    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, fast, sh, sl, n2)) return;
+    if (!frame_geometry<WINDOW>(xh, yh, zh, xl, yl, zl, w, j, fast, eps, sh, sl, n2)) return;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
@@ -921,6 +1024,9 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) xmax2 = fmaxf(xmax2, __shfl_xor_sync(0xffffffffu, xmax2, o));
         const bool fast_u = sqrtf(xmax2) * p.kmax_turns <= kFastTurns;
+        // its error bound: the three-term FP32 dot product with |t| = 1 is within about
+        // 3 x 2^-24 max|x'| of x'.t; eps is over five times that
+        const float eps_u = 1e-6f * sqrtf(xmax2);
         static_assert(kR == 2, "the paired prefilter handles two receivers per lane");
         const f2x X2 = pk(xp[0], xp[1]), Y2 = pk(yp[0], yp[1]), Z2 = pk(zp[0], zp[1]);
         const f2x NAXX = pk(-alpha * xx[0], -alpha * xx[1]);
@@ -1120,7 +1226,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     T &= T - 1;
                     survivor_pair<NF, WINDOW, LOSSY, true>(p, X2, Y2, Z2, XL2, YL2, ZL2, NX2, NY2, NZ2, w, loss, jj,
                                                            jj, (valid & 1u) != 0u, (valid & 2u) != 0u,
-                                                           fast_u, accx, accy);
+                                                           fast_u, eps_u, accx, accy);
                 }
             } else if (p.tile_cull) {
                 // only the segments that can reach this warp tile's receivers
@@ -1164,7 +1270,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     if (!h0) j0 = j1;
                     if (!h1) j1 = j0;
                     survivor_pair<NF, WINDOW, LOSSY>(p, X2, Y2, Z2, XL2, YL2, ZL2, NX2, NY2, NZ2, w, loss, j0, j1, h0,
-                                                     h1, fast_u, accx, accy);
+                                                     h1, fast_u, eps_u, accx, accy);
                 }
             } else if (MODE == kBwd) {
                 // segment by segment: the lanes holding a survivor of segment jj add their
@@ -1180,11 +1286,13 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                     for (int f = 0; f < NF; ++f) H[f] = 0.f;
                     if ((mm0 << jj) >> 31)
                         survivor_adjoint<NF, WINDOW, LOSSY>(p, xp[0], yp[0], zp[0], xl[0], yl[0],
-                                                            zl[0], w, loss, jj, fast_u, &adj.g[0][0][lane],
+                                                            zl[0], w, loss, jj, fast_u, eps_u,
+                                                            &adj.g[0][0][lane],
                                                             G, H);
                     if ((mm1 << jj) >> 31)
                         survivor_adjoint<NF, WINDOW, LOSSY>(p, xp[1], yp[1], zp[1], xl[1], yl[1],
-                                                            zl[1], w, loss, jj, fast_u, &adj.g[0][1][lane],
+                                                            zl[1], w, loss, jj, fast_u, eps_u,
+                                                            &adj.g[0][1][lane],
                                                             G, H);
                     G = warp_sum(G);
 #pragma unroll
@@ -1207,7 +1315,7 @@ __global__ void __maxnreg__(128) gbs_fwd_kernel(const __grid_constant__ FwdParam
                         const int jj = __clz(mm);
                         mm ^= 0x80000000u >> jj;
                         survivor_count<NF, WINDOW>(p, xp[k], yp[k], zp[k], xl[k], yl[k], zl[k], w, jj,
-                                                   fast_u, n_kept);
+                                                   fast_u, eps_u, n_kept);
                     }
                 }
             }
