@@ -752,3 +752,63 @@ def test_synthesis_against_oracle(G, nf, n_t, nr, t0):
     assert np.all(np.abs(out.cpu().numpy() - b - ho) <= 2e-6 * scale + 1e-6 * np.abs(b))
     G.gbt_sync()
 
+
+
+def _window_start_receivers(w, n_side=16, half=3.0):
+    """Receivers straddling the start plane of an oblique ground-reflected segment near the
+    origin (FP32 coordinates there resolve about 1e-6 m), in a patch 2 `half` wide: offsets
+    of 1e-7 to 1e-5 m on both sides, then rounded to FP32.  The direction is oblique, so the
+    products of x'.t are metres that cancel: their FP32 rounding is comparable to the
+    offsets.  Returns the oracle trace, the segment and the receivers."""
+    ot = O.trace(w.scene, w.sources[0])
+    prev_ground = np.zeros(ot.n_seg, bool)
+    prev_ground[1:] = (ot.hit[:-1] == 0) & (ot.ray[:-1] == ot.ray[1:])
+    r0 = np.linalg.norm(ot.o, axis=1)
+    tz = np.abs(ot.t[:, 2])
+    cand = np.where(prev_ground & (ot.depth == 1) & (ot.L > 10.0) & (r0 < 12.0) &
+                    (tz > 0.5) & (tz < 0.85))[0]
+    assert len(cand) > 0
+    j = int(cand[np.argmin(r0[cand])])
+    o, t = ot.o[j], ot.t[j]
+    e1 = np.cross(t, [0.0, 0.0, 1.0] if abs(t[2]) < 0.9 else [1.0, 0.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(t, e1)
+    g = np.linspace(-half, half, n_side)
+    offs = np.array([1e-7, 3e-7, 1e-6, 3e-6, 1e-5])
+    pts = []
+    for ia, a in enumerate(g):
+        for ib, b in enumerate(g):
+            k = ia * n_side + ib
+            u = offs[k % len(offs)] * (1.0 if (k // len(offs)) % 2 else -1.0)
+            pts.append(o + u * t + a * e1 + b * e2)
+    return ot, j, np.asarray(pts, np.float32)
+
+
+@pytest.mark.parametrize("tile_cull", [False, True])
+def test_window_ends_decided_as_the_oracle_does(G, tile_cull):
+    """The segment window is a hard cutoff.  Receivers within 1e-7..1e-5 m of a segment's
+    window start, in one compact patch (so the warps take the FP32 local projection), must
+    have each term counted or left out as the FP64 oracle decides: one misplaced term of
+    this strong, nearby beam is a large share of the receiver's field."""
+    import torch
+    w = I.city(n_rays=16384, n_recv_side=48)
+    ot, j, recv = _window_start_receivers(w)
+    x = recv.astype(np.float64)
+    u = (x - ot.o[j]) @ ot.t[j]
+    assert np.sum(np.abs(u) < 1e-6) >= 32          # many receivers at the window's start
+    po = O.gbs_sum(ot, recv, w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma, window=w.window,
+                   cutoff=w.cutoff)
+    # the segment's own term just inside its window is a large share of the field there
+    one = O.gbs_sum(ot.subset_rays(int(ot.ray[j]), int(ot.ray[j]) + 1), recv, w.freqs,
+                    w.beam_b[0], w.scene.c, w.scene.gamma, window=w.window, cutoff=w.cutoff)
+    inside = u > 1e-6
+    assert np.median(np.abs(one[0, inside]) / np.abs(po[0, inside])) > 1e-2
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, w.sources[0])
+    r = _dev(recv, torch.float32)
+    p = G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[0]), _dev(w.scene.gamma, torch.float32),
+                  order=G.recv_order(r), window=w.window, cutoff=w.cutoff, tile_cull=tile_cull)
+    torch.cuda.synchronize()
+    p = p.cpu().numpy().astype(np.complex128)
+    err = np.abs(p - po)[0] / np.abs(po)[0]
+    assert err.max() <= 1e-4, (int(np.argmax(err)), float(err.max()), float(u[np.argmax(err)]))
