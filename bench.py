@@ -56,14 +56,14 @@ LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
 # a changed kernel gets a new revision and no entry until it is captured again.
 KERNEL_REV = "r2.9"
 KERNEL_TRAFFIC = {
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.8]",
-     "city_1M_rays_512x512_1kHz"): 5288733952,
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [r2.8]",
-     "city_1M_rays_512x512_1kHz"): 210004231680,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [r2.8]",
-     "open_plane_64k_rays_256x256_6f"): 466998784,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [r2.8]",
-     "open_plane_64k_rays_256x256_6f"): 194469120,
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.9]",
+     "city_1M_rays_512x512_1kHz"): 5275472128,
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [r2.9]",
+     "city_1M_rays_512x512_1kHz"): 221307539200,
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [r2.9]",
+     "open_plane_64k_rays_256x256_6f"): 467974912,
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [r2.9]",
+     "open_plane_64k_rays_256x256_6f"): 193972992,
 }
 WORKLOADS = ("city", "open_plane_large", "open_plane_small", "diff_city", "big_city")
 
