@@ -54,7 +54,7 @@ LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
 # Revision of the pair kernel's source.  DRAM bytes (read + write) per launch of the
 # dominant kernel come from an ncu capture of one revision, instantiation and workload;
 # a changed kernel gets a new revision and no entry until it is captured again.
-KERNEL_REV = "r2.9"
+KERNEL_REV = "r2.10"
 KERNEL_TRAFFIC = {
     ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.9]",
      "city_1M_rays_512x512_1kHz"): 5275472128,

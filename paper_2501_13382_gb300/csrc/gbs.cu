@@ -309,7 +309,10 @@ struct LossSmem {
 // the window.  `fast`: the warp item's choice of the FP32 local projection, within eps
 // of x'.t; a pair within eps of an end of its window is decided and evaluated with the
 // float-float projection instead, so the window test is as exact as on that path.  The
-// paired twin in survivor_pair rounds each half identically.
+// paired twin in survivor_pair rounds each half identically, except that it switches a
+// whole pair to the float-float projection when either half is near a window end (the
+// other half's value then differs by at most the FP32 projection's error, and its window
+// decision is the same).
 template <int WINDOW>
 __device__ __forceinline__ bool frame_geometry(float xh, float yh, float zh, float xl, float yl,
                                                float zl, const StageSmem &w, int j, bool fast,
@@ -464,24 +467,6 @@ __device__ __forceinline__ void ld_pairs(const float4 &a, const float4 &b, f2x &
     }
 }
 
-// ld_pairs from shared memory again, as an opaque load the compiler cannot merge with the
-// first one, so the values need not stay in registers until a rare later use.
-template <bool SAME>
-__device__ __forceinline__ void ld_pairs_again(const float4 &a, const float4 &b, f2x &u, f2x &v)
-{
-    if (SAME) {
-        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(u), "=l"(v) : "r"(smem_addr(&a)));
-    } else {
-        float a0, a1, a2, a3, b0, b1, b2, b3;
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(a0), "=f"(a1), "=f"(a2), "=f"(a3) : "r"(smem_addr(&a)));
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(b3) : "r"(smem_addr(&b)));
-        u = pk(a0, b0);
-        v = pk(a2, b2);
-    }
-}
-
 template <int NF, int WINDOW, bool LOSSY, bool SAME = false>
 __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH, f2x ZH,
                                               f2x XL, f2x YL, f2x ZL, f2x NXH, f2x NYH, f2x NZH,
@@ -497,87 +482,55 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
     ld_pairs<SAME>(w.D[3][j0], w.D[3][j1], TLZ, SL);
     // u = x'.t as (U + ul): float-float, or (warp-uniform `fast`, compact warps at low
     // enough frequencies) the FP32 products with the lo parts' first-order terms, within
-    // eps of x'.t.  A half within eps of an end of its window takes the float-float
-    // projection instead (ex0 / ex1), as frame_geometry does for one pair.
+    // eps of x'.t.  A pair with a live half within eps of an end of its window takes the
+    // float-float projection instead (`exact`), so every window decision is as exact as
+    // on that path (frame_geometry does the same for one pair).
     f2x U, ul;
-    auto exact_u = [&](f2x TLX, f2x TLY, f2x TLZ, f2x &Ue, f2x &ule) {
+    f2x AH, AL, BH, BL;
+    if (WINDOW == GBT_WINDOW_SEGMENT) {
+        ld_pairs<SAME>(w.D[6][j0], w.D[6][j1], AH, AL);
+        ld_pairs<SAME>(w.D[7][j0], w.D[7][j1], BH, BL);
+    }
+    bool exact = !fast;
+    if (fast) {
+        U = fma2(XH, THX, fma2(YH, THY, mul2(ZH, THZ)));
+        ul = fma2(XL, THX, fma2(YL, THY, fma2(ZL, THZ, fma2(XH, TLX, fma2(YH, TLY, mul2(ZH, TLZ))))));
+        float a0, a1, b0, b1;
+        if (WINDOW == GBT_WINDOW_SEGMENT) {
+            upk(add2(add2(AH, U), add2(AL, ul)), a0, a1);
+            upk(add2(add2(BH, U), add2(BL, ul)), b0, b1);
+        } else {
+            upk(add2(add2(SH, U), add2(SL, ul)), a0, a1);   // s, near 0 exact as the sum
+            b0 = a0;
+            b1 = a1;
+        }
+        exact = (h0 && fminf(fabsf(a0), fabsf(b0)) <= eps) || (h1 && fminf(fabsf(a1), fabsf(b1)) <= eps);
+    }
+    if (exact) {
         const f2x p0 = mul2(XH, THX), p1 = mul2(YH, THY), p2 = mul2(ZH, THZ);
         const f2x r0 = fma2(XH, TLX, fma2(XL, THX, fma2(XH, THX, neg2(p0))));
         const f2x r1 = fma2(YH, TLY, fma2(YL, THY, fma2(YH, THY, neg2(p1))));
         const f2x r2 = fma2(ZH, TLZ, fma2(ZL, THZ, fma2(ZH, THZ, neg2(p2))));
         f2x S1, E1, E2;
         two_sum2(p0, p1, S1, E1);
-        two_sum2(S1, p2, Ue, E2);
-        ule = add2(add2(E1, E2), add2(add2(r0, r1), r2));
-    };
-    bool ex0 = !fast, ex1 = !fast;
-    if (fast) {
-        U = fma2(XH, THX, fma2(YH, THY, mul2(ZH, THZ)));
-        ul = fma2(XL, THX, fma2(YL, THY, fma2(ZL, THZ, fma2(XH, TLX, fma2(YH, TLY, mul2(ZH, TLZ))))));
-    } else {
-        exact_u(TLX, TLY, TLZ, U, ul);
+        two_sum2(S1, p2, U, E2);
+        ul = add2(add2(E1, E2), add2(add2(r0, r1), r2));
     }
-    // the lo direction again from shared memory where it is needed after the projection
-    auto lo_dir = [&](f2x &lx, f2x &ly, f2x &lz) {
-        f2x s_;
-        ld_pairs_again<SAME>(w.D[2][j0], w.D[2][j1], lx, ly);
-        ld_pairs_again<SAME>(w.D[3][j0], w.D[3][j1], lz, s_);
-    };
-    auto refine = [&](bool n0, bool n1) {   // the near halves to the float-float projection
-        f2x Ue, ule, lx, ly, lz;
-        lo_dir(lx, ly, lz);
-        exact_u(lx, ly, lz, Ue, ule);
-        float a0, a1, b0, b1;
-        upk(U, a0, a1);
-        upk(Ue, b0, b1);
-        U = pk(n0 ? b0 : a0, n1 ? b1 : a1);
-        upk(ul, a0, a1);
-        upk(ule, b0, b1);
-        ul = pk(n0 ? b0 : a0, n1 ? b1 : a1);
-        ex0 = ex0 || n0;
-        ex1 = ex1 || n1;
-    };
     bool k0 = h0, k1 = h1;
     float u0, u1;
     if (WINDOW == GBT_WINDOW_SEGMENT) {
-        f2x AH, AL, BH, BL;
-        ld_pairs<SAME>(w.D[6][j0], w.D[6][j1], AH, AL);
-        ld_pairs<SAME>(w.D[7][j0], w.D[7][j1], BH, BL);
-        f2x WA = add2(add2(AH, U), add2(AL, ul)), WB = add2(add2(BH, U), add2(BL, ul));
-        if (fast) {
-            float a0, a1, b0, b1;
-            upk(WA, a0, a1);
-            upk(WB, b0, b1);
-            const bool n0 = fminf(fabsf(a0), fabsf(b0)) <= eps, n1 = fminf(fabsf(a1), fabsf(b1)) <= eps;
-            if (n0 || n1) {
-                refine(n0, n1);
-                WA = add2(add2(AH, U), add2(AL, ul));
-                WB = add2(add2(BH, U), add2(BL, ul));
-            }
-        }
-        upk(WA, u0, u1);
+        upk(add2(add2(AH, U), add2(AL, ul)), u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
-        upk(WB, u0, u1);
+        upk(add2(add2(BH, U), add2(BL, ul)), u0, u1);
         k0 = k0 && u0 < 0.0f;
         k1 = k1 && u1 < 0.0f;
     }
     f2x sh, e3;
     two_sum2(SH, U, sh, e3);
-    f2x sl = add2(e3, add2(ul, SL));
+    const f2x sl = add2(e3, add2(ul, SL));
     if (WINDOW == GBT_WINDOW_LINE) {
-        f2x SS = add2(sh, sl);
-        if (fast) {
-            upk(SS, u0, u1);
-            const bool n0 = !ex0 && fabsf(u0) <= eps, n1 = !ex1 && fabsf(u1) <= eps;
-            if (n0 || n1) {
-                refine(n0, n1);
-                two_sum2(SH, U, sh, e3);
-                sl = add2(e3, add2(ul, SL));
-                SS = add2(sh, sl);
-            }
-        }
-        upk(SS, u0, u1);
+        upk(add2(sh, sl), u0, u1);
         k0 = k0 && u0 >= 0.0f;
         k1 = k1 && u1 >= 0.0f;
     }
@@ -587,21 +540,10 @@ __device__ __forceinline__ void survivor_pair(const FwdParams &p, f2x XH, f2x YH
     // n = N + x' x t; the lo parts' products (about 1.3 ulp of |x'|) only where the
     // projection is float-float: on the FP32 path they are below its own rounding
     f2x n0x = NX0, n0y = NY0, n0z = NZ0;
-    if (ex0 || ex1) {
-        f2x lx, ly, lz;
-        lo_dir(lx, ly, lz);
-        f2x cx = fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, lz, mul2(neg2(ZH), ly))));
-        f2x cy = fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, lx, mul2(neg2(XH), lz))));
-        f2x cz = fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, ly, mul2(neg2(YH), lx))));
-        if (!(ex0 && ex1)) {   // only the halves on the float-float projection (x 1 is exact)
-            const f2x m = pk(ex0 ? 1.0f : 0.0f, ex1 ? 1.0f : 0.0f);
-            cx = mul2(cx, m);
-            cy = mul2(cy, m);
-            cz = mul2(cz, m);
-        }
-        n0x = add2(n0x, cx);
-        n0y = add2(n0y, cy);
-        n0z = add2(n0z, cz);
+    if (exact) {
+        n0x = add2(n0x, fma2(YL, THZ, fma2(neg2(ZL), THY, fma2(YH, TLZ, mul2(neg2(ZH), TLY)))));
+        n0y = add2(n0y, fma2(ZL, THX, fma2(neg2(XL), THZ, fma2(ZH, TLX, mul2(neg2(XH), TLZ)))));
+        n0z = add2(n0z, fma2(XL, THY, fma2(neg2(YL), THX, fma2(XH, TLY, mul2(neg2(YH), TLX)))));
     }
     const f2x nx = fma2(YH, THZ, fma2(NZH, THY, n0x));
     const f2x ny = fma2(ZH, THX, fma2(NXH, THZ, n0y));
