@@ -56,14 +56,14 @@ LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
 # a changed kernel gets a new revision and no entry until it is captured again.
 KERNEL_REV = "r2.10"
 KERNEL_TRAFFIC = {
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.9]",
-     "city_1M_rays_512x512_1kHz"): 5275472128,
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [r2.9]",
-     "city_1M_rays_512x512_1kHz"): 221307539200,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [r2.9]",
-     "open_plane_64k_rays_256x256_6f"): 467974912,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [r2.9]",
-     "open_plane_64k_rays_256x256_6f"): 193972992,
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.10]",
+     "city_1M_rays_512x512_1kHz"): 5284817920,
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [r2.10]",
+     "city_1M_rays_512x512_1kHz"): 241523122432,
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [r2.10]",
+     "open_plane_64k_rays_256x256_6f"): 468206080,
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [r2.10]",
+     "open_plane_64k_rays_256x256_6f"): 195008000,
 }
 WORKLOADS = ("city", "open_plane_large", "open_plane_small", "diff_city", "big_city")
 
