@@ -403,6 +403,15 @@ gbt_status gbt_synthesize(const float *p, int32_t n_freq, int64_t n_recv, const 
                           const double *amp, double t0, double dt, int64_t n_t, float *out,
                           int32_t accumulate, void *stream);
 
+/* Bound on the device memory of the tile pre-cull's segment lists: at most `entries`
+ * list entries (4 bytes each, plus 2 bytes of warp-tile words) per sum, for the sums
+ * planned after this call; 0 restores the default (an eighth of all (tile, segment)
+ * pairs, at least 16M entries).  Tiles are laid out lightest first; a tile whose list
+ * does not fit tests every segment instead, which gives the same field up to FP32
+ * rounding of the regrouped partial sums (the kept terms do not depend on it).
+ * Process-wide, no GPU work; GBT_ERR_INVALID_ARG for entries < 0. */
+gbt_status gbt_list_capacity_set(int64_t entries);
+
 /* ---------------------------------------------------------- measurement --
  * Kernel timing: while enabled, each launch of the GBS pair kernel (forward
  * or backward) is bracketed by CUDA events recorded on its launch stream.

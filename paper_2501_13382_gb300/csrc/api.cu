@@ -883,6 +883,14 @@ gbt_status gbt_solve(const gbt_scene_t *scene, const gbt_source_desc *src, const
     });
 }
 
+gbt_status gbt_list_capacity_set(int64_t entries)
+{
+    return guarded([&] {
+        GBT_REQUIRE(entries >= 0, "entries must be >= 0");
+        set_list_capacity(entries);
+    });
+}
+
 gbt_status gbt_timing_enable(int32_t enable)
 {
     return guarded([&] {

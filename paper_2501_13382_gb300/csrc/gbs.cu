@@ -38,6 +38,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 #include <cmath>
@@ -2537,6 +2538,8 @@ struct TileWs {
     size_t bytes = 0;              // workspace the layout needs
 };
 
+std::atomic<int64_t> g_list_cap_limit{0};   // set_list_capacity (0: the default)
+
 static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, bool tile_cull)
 {
     TileWs t;
@@ -2549,6 +2552,8 @@ static TileWs tile_ws_layout(void *ws, int64_t n_recv, int64_t seg_capacity, boo
     const int64_t all = t.tiles * seg_capacity;
     // (a multiple of 32: every tile's list starts on a 32-entry chunk boundary)
     t.cap = t.lists ? std::min<int64_t>(all, std::max<int64_t>(int64_t(1) << 24, all / 8)) : 0;
+    const int64_t limit = g_list_cap_limit.load();
+    if (limit > 0) t.cap = std::min(t.cap, limit);
     t.cap = (t.cap + 31) / 32 * 32;
     t.wtiles = (n_recv + kWarpRecv - 1) / kWarpRecv;
     char *w = static_cast<char *>(ws);
@@ -3500,5 +3505,7 @@ void recv_order_noalloc_launch(const float *recv, int64_t n, int32_t *order, cud
     note_launches(1);
     GBT_CUDA(cudaGetLastError());
 }
+
+void set_list_capacity(int64_t entries) { g_list_cap_limit.store(entries); }
 
 }  // namespace gbt

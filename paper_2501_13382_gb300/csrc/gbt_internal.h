@@ -35,6 +35,10 @@ enum : unsigned int { STATUS_BOUNDS = 1u, STATUS_TIMEOUT = 2u, STATUS_BAD_INPUT 
 
 int num_sms();
 
+// Upper bound on a tile-list workspace, in list entries (0: the default of an eighth of all
+// (tile, segment) pairs, at least 16M); tiles whose lists do not fit stream every segment.
+void set_list_capacity(int64_t entries);
+
 // Per-device non-blocking stream of the library's own bookkeeping (small readbacks,
 // frees of destroyed handles), so that none of them waits for unrelated streams.
 cudaStream_t service_stream();

@@ -124,6 +124,7 @@ _SIGS = {
     "gbt_sync": (C.c_int, [C.c_void_p]),
     "gbt_selftest_timeout": (C.c_int, [C.c_int64, C.c_void_p]),
     "gbt_timing_enable": (C.c_int, [C.c_int32]),
+    "gbt_list_capacity_set": (C.c_int, [C.c_int64]),
     "gbt_timing_read": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int32]),
     "gbt_launches_read": (C.c_int, [C.POINTER(C.c_int64), C.c_int32]),
     "gbt_sum_stats_get": (C.c_int, [C.c_void_p, C.POINTER(gbt_sum_args), C.POINTER(gbt_sum_stats),
@@ -308,6 +309,12 @@ def use_torch_allocator():
     def free(ptr, stream):
         torch.cuda.caching_allocator_delete(ptr)
     gbt_set_allocator(alloc, free)
+
+
+def gbt_list_capacity_set(entries: int):
+    """Bound on the tile lists' entries for the sums planned afterwards (0: the default);
+    tiles whose lists do not fit test every segment, with the same field."""
+    _check(load().gbt_list_capacity_set(C.c_int64(int(entries))), "gbt_list_capacity_set")
 
 
 def gbt_timing_enable(enable: bool):

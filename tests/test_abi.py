@@ -89,3 +89,12 @@ def test_library_air_absorption_equals_the_oracles(lib):
         gbt.gbt_air_absorption([1000.0], 20.0, 120.0, 101.325)
     with pytest.raises(gbt.GBTError):
         gbt.gbt_air_absorption([-5.0], 20.0, 50.0, 101.325)
+
+
+def test_list_capacity_setter_checks_its_argument(lib):
+    """gbt_list_capacity_set is host state only: any entries >= 0 is taken (0 restores the
+    default), a negative bound is rejected."""
+    gbt.gbt_list_capacity_set(1 << 20)
+    gbt.gbt_list_capacity_set(0)
+    with pytest.raises(gbt.GBTError):
+        gbt.gbt_list_capacity_set(-1)

@@ -812,3 +812,34 @@ def test_window_ends_decided_as_the_oracle_does(G, tile_cull):
     p = p.cpu().numpy().astype(np.complex128)
     err = np.abs(p - po)[0] / np.abs(po)[0]
     assert err.max() <= 1e-4, (int(np.argmax(err)), float(err.max()), float(u[np.argmax(err)]))
+
+
+@pytest.mark.parametrize("cap", [32, 20000, 1 << 22])
+def test_lists_that_do_not_fit_stream_every_segment(G, cap):
+    """With the tile-list buffer bounded, the lightest tiles keep their lists and the others
+    test every segment, in the same launch (no list fits at 32 entries, some at 20,000,
+    all at 4M): the field is the oracle's, and the unbounded pre-cull's to rounding."""
+    import torch
+    w = I.city(n_rays=16384, n_recv_side=128)
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, w.sources[0])
+    r = _dev(w.receivers, torch.float32)
+    gam = _dev(w.scene.gamma, torch.float32)
+    order = G.recv_order(r)
+
+    def run():
+        p = G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[0]), gam, order=order,
+                      window=w.window, cutoff=w.cutoff, tile_cull=True)
+        torch.cuda.synchronize()
+        return p.cpu().numpy().astype(np.complex128)
+
+    full = run()
+    G.gbt_list_capacity_set(cap)
+    try:
+        bounded = run()
+    finally:
+        G.gbt_list_capacity_set(0)
+    G.gbt_sync()
+    _, po = O.solve(w)
+    assert rel_l2(bounded, po) <= TOL_L2
+    assert rel_l2(bounded, full) <= 1e-6
