@@ -54,15 +54,15 @@ LANES_PER_SM_CLK = 128          # FP32 lanes per SM per clock (4 SMSPs x 32)
 # Revision of the pair kernel's source.  DRAM bytes (read + write) per launch of the
 # dominant kernel come from an ncu capture of one revision, instantiation and workload;
 # a changed kernel gets a new revision and no entry until it is captured again.
-KERNEL_REV = "r2.10"
+KERNEL_REV = "rev10"
 KERNEL_TRAFFIC = {
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [r2.10]",
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> tile segment lists [rev10]",
      "city_1M_rays_512x512_1kHz"): 5284817920,
-    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [r2.10]",
+    ("gbs_fwd_kernel<1,SEGMENT,fwd,plain> every pair [rev10]",
      "city_1M_rays_512x512_1kHz"): 241523122432,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [r2.10]",
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> tile segment lists [rev10]",
      "open_plane_64k_rays_256x256_6f"): 468206080,
-    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [r2.10]",
+    ("gbs_fwd_kernel<6,LINE,fwd,plain> every pair [rev10]",
      "open_plane_64k_rays_256x256_6f"): 195008000,
 }
 WORKLOADS = ("city", "open_plane_large", "open_plane_small", "diff_city", "big_city")
