@@ -843,3 +843,41 @@ def test_lists_that_do_not_fit_stream_every_segment(G, cap):
     _, po = O.solve(w)
     assert rel_l2(bounded, po) <= TOL_L2
     assert rel_l2(bounded, full) <= 1e-6
+
+
+@pytest.mark.parametrize("tile_cull", [False, True])
+def test_line_window_start_decided_as_the_oracle_does(G, tile_cull):
+    """The LINE window keeps s >= 0, a hard cutoff too.  Receivers within 1e-7..1e-5 m of the
+    s = 0 plane of an oblique ray leaving the source (the plane through the source across
+    the ray), in a 24 m patch at 500 Hz: the warps still take the FP32 local projection,
+    whose rounding over warp tiles about 12 m wide is comparable to the offsets.  Each
+    term is counted or left out as the FP64 oracle decides."""
+    import torch
+    w = I.open_plane_small()
+    ot = O.trace(w.scene, w.sources[0])
+    tz = np.abs(ot.t[:, 2])
+    cand = np.where((ot.depth == 0) & (tz > 0.5) & (tz < 0.85))[0]
+    assert len(cand) > 0
+    j = int(cand[0])
+    o, t = ot.o[j] - ot.s0[j] * ot.t[j], ot.t[j]     # where s = 0 on the ray's line
+    e1 = np.cross(t, [0.0, 0.0, 1.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(t, e1)
+    g = np.linspace(-12.0, 12.0, 16)
+    offs = np.array([1e-7, 3e-7, 1e-6, 3e-6, 1e-5])
+    pts = [o + offs[k % 5] * (1.0 if (k // 5) % 2 else -1.0) * t + a * e1 + b * e2
+           for k, (a, b) in enumerate((a, b) for a in g for b in g)]
+    recv = np.asarray(pts, np.float32)
+    s = (recv.astype(np.float64) - ot.o[j]) @ t + ot.s0[j]
+    assert np.sum(np.abs(s) < 3e-6) >= 32
+    po = O.gbs_sum(ot, recv, w.freqs, w.beam_b[0], w.scene.c, w.scene.gamma, window=w.window,
+                   cutoff=w.cutoff)
+    sc = G.Scene(w.scene)
+    tr = G.Trace(sc, w.sources[0])
+    r = _dev(recv, torch.float32)
+    p = G.gbs_sum(tr, r, list(w.freqs), list(w.beam_b[0]), _dev(w.scene.gamma, torch.float32),
+                  order=G.recv_order(r), window=w.window, cutoff=w.cutoff, tile_cull=tile_cull)
+    torch.cuda.synchronize()
+    p = p.cpu().numpy().astype(np.complex128)
+    err = np.abs(p - po)[0] / np.abs(po)[0]
+    assert err.max() <= 1e-4, (int(np.argmax(err)), float(err.max()), float(s[np.argmax(err)]))
