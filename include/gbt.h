@@ -224,7 +224,11 @@ gbt_status gbt_trace_import(const gbt_scene_t *scene, const gbt_source_desc *src
  * reduction, FP32 MUFU exp/sin/cos, compensated per-receiver accumulation;
  * relative L2 error against an FP64 evaluation measured at 1e-7..4e-7 on the
  * synthetic open-plane and city workloads (tested to 1e-6 with 4 kHz phases
- * over 1 km paths).  F64 precision: every step in FP64 (2.6e-8, the rounding of
+ * over 1 km paths).  Where a receiver group is compact for the call's highest
+ * frequency (K max|x'| <= 90 turns), the receivers' projection on a segment is
+ * formed in FP32 (a term's phase moves by at most about 1e-4 rad); a pair within
+ * that projection's error bound of an end of its window is decided and evaluated
+ * in float-float, so the window decisions are those of the exact arithmetic.  F64 precision: every step in FP64 (2.6e-8, the rounding of
  * the complex64 output), at FP64 speed.
  * With more than 8 frequencies the F32 path runs one pair launch per group of
  * at most 8 (frequencies sorted by value when every b_f is equal, otherwise in
